@@ -1,0 +1,322 @@
+"""FP64 CPU oracle of the BDIM time step -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the bench's CPU-baseline leg
+may import this package. The product path (``paper_2407_16032_b300``) never
+imports, loads or calls it; the two share no code except the seeded input
+generators in ``synth``.
+
+The arithmetic lives in ``wl_oracle.c`` (plain C loops, FP64); this module
+compiles it with gcc and marshals numpy arrays through ctypes. Every routine
+cites the part of the paper it follows in the C source.
+
+Parity status: every function here is pinned by ``tests/test_oracle.py``
+(closed forms, invariants, brute force); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wl_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (plain gcc, no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
+               "-o", _LIB + ".tmp", _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class Grid(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("n", C.c_int * 3), ("periodic", C.c_int * 3),
+                ("exit_hi_x", C.c_int), ("U", C.c_double * 3), ("nu", C.c_double),
+                ("eps", C.c_double)]
+
+
+class BodyS(C.Structure):
+    _fields_ = [("kind", C.c_int), ("centre", C.c_double * 3), ("radius", C.c_double),
+                ("semi", C.c_double * 2), ("heave_amp", C.c_double), ("pitch_amp", C.c_double),
+                ("omega", C.c_double), ("phase", C.c_double), ("heave_axis", C.c_int)]
+
+
+class Solver(C.Structure):
+    _fields_ = [("tol", C.c_double), ("itmax", C.c_int), ("smooth_iters", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("vcycles", C.c_int), ("rel_resid", C.c_double), ("bnorm", C.c_double)]
+
+
+_lib = None
+_P = C.POINTER(C.c_double)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        L = _lib
+        for name, args, res in [
+            ("orc_quick", [C.c_double] * 3, C.c_double),
+            ("orc_mu0", [C.c_double, C.c_double], C.c_double),
+            ("orc_mu1", [C.c_double, C.c_double], C.c_double),
+            ("orc_kernel", [C.c_double, C.c_double], C.c_double),
+            ("orc_conv_diff", [C.POINTER(Grid), _P, _P, _P], None),
+            ("orc_body_eval", [C.POINTER(BodyS), C.c_int, _P, C.c_double, _P, _P, _P], None),
+            ("orc_measure", [C.POINTER(Grid), C.POINTER(BodyS), C.c_double, _P, _P, _P], None),
+            ("orc_coeffs", [C.POINTER(Grid), _P, _P], None),
+            ("orc_bdim", [C.POINTER(Grid), _P, _P, C.c_double, _P, _P, _P, _P, _P], None),
+            ("orc_exit_bc", [C.POINTER(Grid), _P, _P, _P, C.c_double, C.c_int, _P, _P, _P], None),
+            ("orc_divergence", [C.POINTER(Grid), _P, _P, _P], None),
+            ("orc_poisson_apply", [C.POINTER(Grid), _P, _P, _P], None),
+            ("orc_poisson_diag", [C.POINTER(Grid), _P, _P], None),
+            ("orc_mg_levels", [C.POINTER(Grid)], C.c_int),
+            ("orc_poisson_solve", [C.POINTER(Grid), _P, _P, _P, C.POINTER(Solver), C.POINTER(Stats)], C.c_int),
+            ("orc_grad_update", [C.POINTER(Grid), _P, _P, C.c_double, _P], None),
+            ("orc_project", [C.POINTER(Grid), _P, _P, _P, _P, C.c_double, C.c_double, C.POINTER(Solver), C.POINTER(Stats)], C.c_int),
+            ("orc_cfl", [C.POINTER(Grid), _P, _P, C.c_double, C.c_double], C.c_double),
+            ("orc_forces", [C.POINTER(Grid), C.POINTER(BodyS), C.c_double, _P, _P], None),
+            ("orc_step", [C.POINTER(Grid), C.POINTER(BodyS), C.c_double, C.c_double, _P, _P, _P, C.POINTER(Solver), C.POINTER(Stats)], C.c_int),
+            ("orc_diagnostics", [C.POINTER(Grid), _P, _P, _P, _P], None),
+        ]:
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"], (a.dtype, a.flags)
+    return a.ctypes.data_as(_P)
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_grid(ndim, n, periodic=(False, False, False), exit_hi_x=False, U=(0.0, 0.0, 0.0), nu=0.0, eps=1.0):
+    g = Grid()
+    g.ndim = ndim
+    nn = list(n) + [1] * (3 - len(n))
+    if ndim == 2:
+        nn[2] = 1
+    for a in range(3):
+        g.n[a] = int(nn[a])
+        g.periodic[a] = int(bool(periodic[a])) if a < len(periodic) else 0
+        g.U[a] = float(U[a]) if a < len(U) else 0.0
+    g.exit_hi_x = int(bool(exit_hi_x))
+    g.nu = float(nu)
+    g.eps = float(eps)
+    return g
+
+
+def grid_from_case(case):
+    return make_grid(case.ndim, case.n, case.periodic, case.exit_hi_x, case.U, case.nu, case.eps)
+
+
+def make_body(body):
+    b = BodyS()
+    b.kind = body.kind_id
+    for a in range(3):
+        b.centre[a] = float(body.centre[a])
+    b.radius = float(body.radius)
+    b.semi[0], b.semi[1] = float(body.semi[0]), float(body.semi[1])
+    b.heave_amp, b.pitch_amp = float(body.heave_amp), float(body.pitch_amp)
+    b.omega, b.phase = float(body.omega), float(body.phase)
+    b.heave_axis = int(body.heave_axis)
+    return b
+
+
+def make_solver(tol=1e-10, itmax=64, smooth_iters=4):
+    s = Solver()
+    s.tol, s.itmax, s.smooth_iters = float(tol), int(itmax), int(smooth_iters)
+    return s
+
+
+def _shape(g):
+    return (g.n[2], g.n[1], g.n[0]) if g.ndim == 3 else (g.n[1], g.n[0])
+
+
+def plane_size(g):
+    return g.n[1] * g.n[2]
+
+
+# ---------------------------------------------------------------- wrappers
+def quick(u, c, d):
+    return lib().orc_quick(float(u), float(c), float(d))
+
+
+def mu0(d, eps=1.0):
+    return lib().orc_mu0(float(d), float(eps))
+
+
+def mu1(d, eps=1.0):
+    return lib().orc_mu1(float(d), float(eps))
+
+
+def kernel(d, eps=1.0):
+    return lib().orc_kernel(float(d), float(eps))
+
+
+def conv_diff(g, u, ue):
+    u, ue = _d(u), _d(ue)
+    r = np.zeros_like(u)
+    lib().orc_conv_diff(C.byref(g), _p(u), _p(ue), _p(r))
+    return r
+
+
+def body_eval(body_s, ndim, x, t):
+    xx = _d(np.array(list(x) + [0.0] * (3 - len(x))))
+    d = np.zeros(1)
+    n = np.zeros(3)
+    V = np.zeros(3)
+    lib().orc_body_eval(C.byref(body_s), ndim, _p(xx), float(t), _p(d), _p(n), _p(V))
+    return d[0], n, V
+
+
+def measure(g, body_s, t):
+    sh = _shape(g)
+    mu0a = np.zeros((g.ndim,) + sh)
+    mu1n = np.zeros((g.ndim, 3) + sh)
+    V = np.zeros((g.ndim,) + sh)
+    lib().orc_measure(C.byref(g), C.byref(body_s), float(t), _p(mu0a), _p(mu1n), _p(V))
+    return mu0a, mu1n, V
+
+
+def coeffs(g, mu0a=None):
+    c = np.zeros((g.ndim,) + _shape(g))
+    lib().orc_coeffs(C.byref(g), _p(_d(mu0a)) if mu0a is not None else None, _p(c))
+    return c
+
+
+def bdim(g, u0, r, dt, mu0a=None, mu1n=None, V=None, ustar=None):
+    out = np.zeros_like(_d(u0))
+    keep = [_d(u0), _d(r)] + [(_d(x) if x is not None else None) for x in (mu0a, mu1n, V, ustar)]
+    lib().orc_bdim(C.byref(g), _p(keep[0]), _p(keep[1]), float(dt), _p(keep[2]), _p(keep[3]),
+                   _p(keep[4]), _p(keep[5]), _p(out))
+    return out
+
+
+def exit_bc(g, ue0, uG, ueG, dt, corrector, ustar_e, u_new, ue):
+    ue = _d(ue).copy()
+    args = [_d(ue0), _d(uG), _d(ueG), _d(ustar_e) if ustar_e is not None else None, _d(u_new)]
+    lib().orc_exit_bc(C.byref(g), _p(args[0]), _p(args[1]), _p(args[2]), float(dt), int(corrector),
+                      _p(args[3]), _p(args[4]), _p(ue))
+    return ue
+
+
+def divergence(g, u, ue):
+    b = np.zeros(_shape(g))
+    lib().orc_divergence(C.byref(g), _p(_d(u)), _p(_d(ue)), _p(b))
+    return b
+
+
+def poisson_apply(g, c, p):
+    out = np.zeros(_shape(g))
+    lib().orc_poisson_apply(C.byref(g), _p(_d(c)), _p(_d(p)), _p(out))
+    return out
+
+
+def poisson_diag(g, c):
+    out = np.zeros(_shape(g))
+    lib().orc_poisson_diag(C.byref(g), _p(_d(c)), _p(out))
+    return out
+
+
+def mg_levels(g):
+    return lib().orc_mg_levels(C.byref(g))
+
+
+def poisson_solve(g, c, b, p0=None, tol=1e-10, itmax=64, smooth_iters=4):
+    p = np.zeros(_shape(g)) if p0 is None else _d(p0).copy()
+    S = make_solver(tol, itmax, smooth_iters)
+    st = Stats()
+    rc = lib().orc_poisson_solve(C.byref(g), _p(_d(c)), _p(_d(b)), _p(p), C.byref(S), C.byref(st))
+    return p, rc, st
+
+
+def grad_update(g, c, p, wdt, u):
+    u = _d(u).copy()
+    lib().orc_grad_update(C.byref(g), _p(_d(c)), _p(_d(p)), float(wdt), _p(u))
+    return u
+
+
+def project(g, c, u, ue, P, w, dt, tol=1e-10, itmax=64, smooth_iters=4):
+    u = _d(u).copy()
+    P = _d(P).copy()
+    S = make_solver(tol, itmax, smooth_iters)
+    st = Stats()
+    rc = lib().orc_project(C.byref(g), _p(_d(c)), _p(u), _p(_d(ue)), _p(P), float(w), float(dt), C.byref(S), C.byref(st))
+    return u, P, rc, st
+
+
+def cfl(g, u, ue, cfl=1.0, dt_max=1.0):
+    return lib().orc_cfl(C.byref(g), _p(_d(u)), _p(_d(ue)), float(cfl), float(dt_max))
+
+
+def forces(g, body_s, t, p):
+    F = np.zeros(3)
+    lib().orc_forces(C.byref(g), C.byref(body_s), float(t), _p(_d(p)), _p(F))
+    return F
+
+
+def diagnostics(g, u, ue):
+    ke = np.zeros(1)
+    en = np.zeros(1)
+    lib().orc_diagnostics(C.byref(g), _p(_d(u)), _p(_d(ue)), _p(ke), _p(en))
+    return ke[0], en[0]
+
+
+@dataclass
+class State:
+    u: np.ndarray
+    ue: np.ndarray
+    P: np.ndarray
+    t: float
+    dt: float
+
+
+class Sim:
+    """Host-side stepping loop around ``orc_step`` (the same Heun step as C6)."""
+
+    def __init__(self, case, tol=1e-10, itmax=64, smooth_iters=4, u=None, ue=None):
+        from synth import initial_velocity
+        self.case = case
+        self.g = grid_from_case(case)
+        self.b = make_body(case.body)
+        self.S = make_solver(tol, itmax, smooth_iters)
+        if u is None:
+            u, ue = initial_velocity(case)
+        self.u = _d(u).copy()
+        self.ue = _d(ue).copy() if case.exit_hi_x else np.zeros(max(plane_size(self.g), 1))
+        self.P = np.zeros(_shape(self.g))
+        self.t = 0.0
+        self.dt = case.dt0
+        # boundary values of the initial field: inflow / wall faces carry U
+        for a in range(case.ndim):
+            if not case.periodic[a]:
+                idx = [slice(None)] * case.ndim
+                idx[case.ndim - 1 - a] = 0
+                self.u[(a,) + tuple(idx)] = case.U[a]
+        self.stats = []
+
+    def step(self, dt=None):
+        dt = self.dt if dt is None else float(dt)
+        st = (Stats * 2)()
+        bad = lib().orc_step(C.byref(self.g), C.byref(self.b), self.t, dt, _p(self.u), _p(self.ue),
+                             _p(self.P), C.byref(self.S), st)
+        self.stats.append((st[0].vcycles, st[0].rel_resid, st[1].vcycles, st[1].rel_resid))
+        self.t += dt
+        self.dt = cfl(self.g, self.u, self.ue, self.case.cfl, self.case.dt_max)
+        return bad, dt

@@ -1,0 +1,821 @@
+/*
+ * wl_oracle.c -- plain, slow FP64 CPU oracle of one BDIM time step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file; only the tests, the smoke check and the bench's CPU-baseline
+ * leg do.  It shares no code, header, table or constant with the CUDA path.
+ *
+ * What it computes (WaterLily, arXiv 2407.16032):
+ *   Sec. 2  -- momentum equation F-dot (u_i' = -p_,i - (u_i u_j)_,j + nu u_i,jj),
+ *              body equation B (u_i = V_i), convolved through the BDIM kernel
+ *              of half-width eps using the signed distance d and normal n.
+ *   Sec. 2  -- finite volume, uniform Cartesian staggered grid (h = 1), central
+ *              differences for pressure and diffusion, flux-limited QUICK for
+ *              convection, explicit predictor-corrector (Heun) in time, pressure
+ *              projection with a variable-coefficient Poisson equation solved by
+ *              geometric multigrid, CFL-adapted time step.
+ *   Sec. 3  -- pressure-gradient update u[I,i] -= c[I,i]*(p[I]-p[I-d(i)]),
+ *              with c the Poisson coefficients; velocity component i on the
+ *              lower i-face of cell I.
+ *   Sec. 4.2 -- multigrid uses a preconditioned-conjugate-gradient smoother.
+ *
+ * Where the paper is silent the reading taken is written next to the code
+ * (grid coordinates, the QUICK variant and limiter, boundary treatment, the
+ * kernel moments, the exit condition, multigrid details, CFL formula).
+ *
+ * Layout: every field is component-major, x fastest: u[a*nc + i + n0*(j + n1*k)].
+ * 2D uses n[2] = 1 and ndim = 2.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_PI 3.14159265358979323846
+
+typedef struct {
+    int ndim;
+    int n[3];
+    int periodic[3];
+    int exit_hi_x;       /* convective outlet on the upper x face */
+    double U[3];         /* free-stream velocity (boundary normal values) */
+    double nu;
+    double eps;          /* BDIM kernel half-width */
+} orc_grid;
+
+typedef struct {
+    int kind;            /* 0 none, 1 sphere (circle in 2D), 2 ellipse (2D) */
+    double centre[3];
+    double radius;
+    double semi[2];      /* ellipse semi-axes along chord and thickness */
+    double heave_amp, pitch_amp, omega, phase;
+    int heave_axis;
+} orc_body;
+
+typedef struct {
+    double tol;          /* relative L2 residual target */
+    int itmax;           /* max V-cycles */
+    int smooth_iters;    /* PCG iterations per level (post-smoothing) */
+} orc_solver;
+
+typedef struct {
+    int vcycles;
+    double rel_resid;
+    double bnorm;
+} orc_stats;
+
+static inline size_t ncell(const orc_grid *g) { return (size_t)g->n[0] * g->n[1] * g->n[2]; }
+static inline size_t lin(const orc_grid *g, int i, int j, int k) {
+    return (size_t)i + (size_t)g->n[0] * ((size_t)j + (size_t)g->n[1] * (size_t)k);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Velocity samples with boundary treatment.                                 */
+/* Reading: periodic axes wrap; on a non-periodic axis the tangential        */
+/* components are extended by zero gradient (index clamped to the interior), */
+/* and the normal component u_a has faces 0..N_a, where face N_a is the upper */
+/* boundary face whose value is U_a (slip/inflow) or the stored exit plane.  */
+/* Indices beyond are clamped to those end faces (zero-gradient extension).  */
+/* ------------------------------------------------------------------------ */
+static double su(const orc_grid *g, const double *u, const double *ue, int a, int i, int j, int k)
+{
+    int idx[3] = {i, j, k};
+    int upper = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+        int N = g->n[ax];
+        if (ax >= g->ndim) { idx[ax] = 0; continue; }
+        if (g->periodic[ax]) {
+            idx[ax] = ((idx[ax] % N) + N) % N;
+        } else if (ax == a) {
+            if (idx[ax] < 0) idx[ax] = 0;
+            if (idx[ax] >= N) { idx[ax] = N; upper = 1; }
+        } else {
+            if (idx[ax] < 0) idx[ax] = 0;
+            if (idx[ax] > N - 1) idx[ax] = N - 1;
+        }
+    }
+    if (upper) {
+        if (a == 0 && g->exit_hi_x) return ue[(size_t)idx[1] + (size_t)g->n[1] * idx[2]];
+        return g->U[a];
+    }
+    return u[(size_t)a * ncell(g) + lin(g, idx[0], idx[1], idx[2])];
+}
+
+/* Sample of a stored face array with every axis clamped / wrapped to the stored
+ * range (used for the BDIM gradient term and the body velocity). */
+static double sc(const orc_grid *g, const double *f, int a, int i, int j, int k)
+{
+    int idx[3] = {i, j, k};
+    for (int ax = 0; ax < 3; ++ax) {
+        int N = g->n[ax];
+        if (ax >= g->ndim) { idx[ax] = 0; continue; }
+        if (g->periodic[ax]) idx[ax] = ((idx[ax] % N) + N) % N;
+        else { if (idx[ax] < 0) idx[ax] = 0; if (idx[ax] > N - 1) idx[ax] = N - 1; }
+    }
+    return f[(size_t)a * ncell(g) + lin(g, idx[0], idx[1], idx[2])];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Flux-limited QUICK face value (Sec. 2: "flux-limited Quick scheme").      */
+/* Reading: upwind-biased third-order interpolation (5c + 2d - u)/6 limited  */
+/* by median(phi, c, median(10c - 9u, c, d)), u/c/d being the far-upstream,  */
+/* upstream and downstream samples.                                          */
+/* ------------------------------------------------------------------------ */
+static double median3(double a, double b, double c)
+{
+    return fmax(fmin(a, b), fmin(fmax(a, b), c));
+}
+
+double orc_quick(double uu, double c, double d)
+{
+    double phi = (5.0 * c + 2.0 * d - uu) / 6.0;
+    return median3(phi, c, median3(10.0 * c - 9.0 * uu, c, d));
+}
+
+/* Total (convective + diffusive) flux of u_a through the lower b-face of the
+ * u_a control volume of cell I, positive in +b. */
+static double face_flux(const orc_grid *g, const double *u, const double *ue, int a, int b, int i, int j, int k)
+{
+    int db[3] = {0, 0, 0}, da[3] = {0, 0, 0};
+    db[b] = 1; da[a] = 1;
+    /* advecting velocity: mean of the two u_b samples straddling the face along a */
+    double Uf = 0.5 * (su(g, u, ue, b, i, j, k) + su(g, u, ue, b, i - da[0], j - da[1], k - da[2]));
+    double sm2 = su(g, u, ue, a, i - 2 * db[0], j - 2 * db[1], k - 2 * db[2]);
+    double sm1 = su(g, u, ue, a, i - db[0], j - db[1], k - db[2]);
+    double s0 = su(g, u, ue, a, i, j, k);
+    double sp1 = su(g, u, ue, a, i + db[0], j + db[1], k + db[2]);
+    double phi = (Uf > 0.0) ? orc_quick(sm2, sm1, s0) : orc_quick(sp1, s0, sm1);
+    return Uf * phi - g->nu * (s0 - sm1);
+}
+
+/* Momentum RHS r = -(u_a u_b)_,b + nu u_a,bb in flux form (Sec. 2, Eq. F-dot
+ * without the pressure term). r is zero on the lower boundary face of a
+ * non-periodic axis (its value is set by the boundary condition). */
+void orc_conv_diff(const orc_grid *g, const double *u, const double *ue, double *r)
+{
+    size_t nc = ncell(g);
+    for (int a = 0; a < g->ndim; ++a)
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i) {
+                    int I[3] = {i, j, k};
+                    double acc = 0.0;
+                    if (!(g->periodic[a] == 0 && I[a] == 0)) {
+                        for (int b = 0; b < g->ndim; ++b) {
+                            int db[3] = {0, 0, 0};
+                            db[b] = 1;
+                            acc += face_flux(g, u, ue, a, b, i, j, k)
+                                 - face_flux(g, u, ue, a, b, i + db[0], j + db[1], k + db[2]);
+                        }
+                    }
+                    r[(size_t)a * nc + lin(g, i, j, k)] = acc;
+                }
+}
+
+/* ------------------------------------------------------------------------ */
+/* BDIM kernel moments (Sec. 2: thickness eps, signed distance d, normal n). */
+/* Kernel K(s) = (1 + cos(pi s/eps))/(2 eps), |s| < eps.  mu0 = integral of  */
+/* K over the fluid side, mu1 = first moment of K over the fluid side.       */
+/* d > 0 in the fluid, n = grad d points into the fluid (reading).            */
+/* ------------------------------------------------------------------------ */
+double orc_mu0(double d, double eps)
+{
+    double r = d / eps;
+    if (r <= -1.0) return 0.0;
+    if (r >= 1.0) return 1.0;
+    return 0.5 * (1.0 + r + sin(OR_PI * r) / OR_PI);
+}
+
+double orc_mu1(double d, double eps)
+{
+    double r = d / eps;
+    if (r <= -1.0 || r >= 1.0) return 0.0;
+    return eps * (0.25 - 0.25 * r * r - (r * sin(OR_PI * r) + (1.0 + cos(OR_PI * r)) / OR_PI) / (2.0 * OR_PI));
+}
+
+double orc_kernel(double d, double eps)
+{
+    double r = d / eps;
+    if (r <= -1.0 || r >= 1.0) return 0.0;
+    return (1.0 + cos(OR_PI * r)) / (2.0 * eps);
+}
+
+/* Signed distance, unit normal and rigid-body velocity of an analytic body at
+ * point x and time t (Sec. 3 AutoBody: distance function + coordinate map). */
+void orc_body_eval(const orc_body *B, int ndim, const double *x, double t, double *d, double *nrm, double *V)
+{
+    double c[3] = {B->centre[0], B->centre[1], B->centre[2]};
+    double cdot[3] = {0.0, 0.0, 0.0};
+    c[B->heave_axis] += B->heave_amp * sin(B->omega * t + B->phase);
+    cdot[B->heave_axis] = B->heave_amp * B->omega * cos(B->omega * t + B->phase);
+    nrm[0] = nrm[1] = nrm[2] = 0.0;
+    V[0] = cdot[0]; V[1] = cdot[1]; V[2] = cdot[2];
+    if (B->kind == 0) { *d = 1e30; return; }
+    if (B->kind == 1) {
+        double r2 = 0.0, rv[3] = {0, 0, 0};
+        for (int a = 0; a < ndim; ++a) { rv[a] = x[a] - c[a]; r2 += rv[a] * rv[a]; }
+        double rr = sqrt(r2);
+        *d = rr - B->radius;
+        if (rr > 0.0) for (int a = 0; a < ndim; ++a) nrm[a] = rv[a] / rr;
+        else nrm[0] = 1.0;
+        return;
+    }
+    /* ellipse (2D): body frame x' = Rot(-theta)(x - c); q = |(x'/sa, y'/sb)|;
+     * first-order distance d = (q - 1) q / |(x'/sa^2, y'/sb^2)|;
+     * normal = direction of grad q (reading); V = cdot + thetadot e_z x (x - c). */
+    double th = B->pitch_amp * sin(B->omega * t + B->phase + 0.5 * OR_PI);
+    double thd = B->pitch_amp * B->omega * cos(B->omega * t + B->phase + 0.5 * OR_PI);
+    double rx = x[0] - c[0], ry = x[1] - c[1];
+    double ct = cos(th), st = sin(th);
+    double xp = ct * rx + st * ry, yp = -st * rx + ct * ry;
+    double sa = B->semi[0], sb = B->semi[1];
+    double q = sqrt((xp / sa) * (xp / sa) + (yp / sb) * (yp / sb));
+    double gx = xp / (sa * sa), gy = yp / (sb * sb);
+    double gn = sqrt(gx * gx + gy * gy);
+    if (gn > 0.0) {
+        *d = (q - 1.0) * q / gn;
+        double nxp = gx / gn, nyp = gy / gn;
+        nrm[0] = ct * nxp - st * nyp;
+        nrm[1] = st * nxp + ct * nyp;
+    } else {
+        *d = -sb;
+        nrm[0] = 1.0;
+    }
+    V[0] += -thd * ry;
+    V[1] += thd * rx;
+}
+
+/* Measure the body onto every stored face of every component at time t:
+ * mu0 (3 x nc), mu1n (9 x nc, index (a*3+b)*nc: mu1 * n_b on face a),
+ * V (3 x nc).  Face a of cell I sits at (I + 1/2) - e_a/2. */
+void orc_measure(const orc_grid *g, const orc_body *B, double t, double *mu0, double *mu1n, double *V)
+{
+    size_t nc = ncell(g);
+    for (int a = 0; a < g->ndim; ++a)
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i) {
+                    double x[3] = {i + 0.5, j + 0.5, k + 0.5};
+                    x[a] -= 0.5;
+                    double d, nrm[3], v[3];
+                    orc_body_eval(B, g->ndim, x, t, &d, nrm, v);
+                    size_t L = lin(g, i, j, k);
+                    mu0[(size_t)a * nc + L] = orc_mu0(d, g->eps);
+                    double m1 = orc_mu1(d, g->eps);
+                    for (int b = 0; b < 3; ++b) mu1n[(size_t)(a * 3 + b) * nc + L] = (b < g->ndim) ? m1 * nrm[b] : 0.0;
+                    V[(size_t)a * nc + L] = v[a];
+                }
+}
+
+/* Poisson coefficients c_a = mu0 on face a, zero on non-periodic boundary faces
+ * (Neumann condition at the domain boundary). */
+void orc_coeffs(const orc_grid *g, const double *mu0, double *c)
+{
+    size_t nc = ncell(g);
+    for (int a = 0; a < g->ndim; ++a)
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i) {
+                    int I[3] = {i, j, k};
+                    size_t L = (size_t)a * nc + lin(g, i, j, k);
+                    c[L] = (!g->periodic[a] && I[a] == 0) ? 0.0 : (mu0 ? mu0[L] : 1.0);
+                }
+}
+
+/* ------------------------------------------------------------------------ */
+/* BDIM blend (Sec. 2: F-dot convolved with B):                              */
+/*   f = u0 + dt r;  u = V + mu0 (f - V) + mu1 n . grad(f - V)               */
+/* with a central difference for the gradient at the face (reading).          */
+/* When corrector != 0 the result is averaged with u_star: u = (u* + B(f))/2 */
+/* (the Heun corrector). Then lower boundary faces get U_a.                  */
+/* ------------------------------------------------------------------------ */
+void orc_bdim(const orc_grid *g, const double *u0, const double *r, double dt,
+              const double *mu0, const double *mu1n, const double *V,
+              const double *ustar, double *out)
+{
+    size_t nc = ncell(g);
+    double *f = (double *)malloc(sizeof(double) * g->ndim * nc);
+    for (size_t q = 0; q < (size_t)g->ndim * nc; ++q) f[q] = u0[q] + dt * r[q];
+    for (int a = 0; a < g->ndim; ++a)
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i) {
+                    int I[3] = {i, j, k};
+                    size_t L = (size_t)a * nc + lin(g, i, j, k);
+                    double val;
+                    if (mu0) {
+                        double fv = f[L] - V[L];
+                        double grad = 0.0;
+                        for (int b = 0; b < g->ndim; ++b) {
+                            int db[3] = {0, 0, 0};
+                            db[b] = 1;
+                            double up = sc(g, f, a, i + db[0], j + db[1], k + db[2]) - sc(g, V, a, i + db[0], j + db[1], k + db[2]);
+                            double dn = sc(g, f, a, i - db[0], j - db[1], k - db[2]) - sc(g, V, a, i - db[0], j - db[1], k - db[2]);
+                            grad += mu1n[(size_t)(a * 3 + b) * nc + lin(g, i, j, k)] * 0.5 * (up - dn);
+                        }
+                        val = V[L] + mu0[L] * fv + grad;
+                    } else {
+                        val = f[L];
+                    }
+                    if (ustar) val = 0.5 * (ustar[L] + val);
+                    if (!g->periodic[a] && I[a] == 0) val = g->U[a];
+                    out[L] = val;
+                }
+    free(f);
+}
+
+/* Net volume flux out of the domain through non-periodic boundary faces. */
+static double boundary_outflux(const orc_grid *g, const double *u, const double *ue)
+{
+    double q = 0.0;
+    for (int a = 0; a < g->ndim; ++a) {
+        if (g->periodic[a]) continue;
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i) {
+                    int I[3] = {i, j, k};
+                    if (I[a] != 0) continue;
+                    int J[3] = {i, j, k};
+                    J[a] = g->n[a];
+                    q += su(g, u, ue, a, J[0], J[1], J[2]) - su(g, u, ue, a, i, j, k);
+                }
+    }
+    return q;
+}
+
+/* Convective exit on the upper x face (Sec. 4: "convective outlet").
+ * Reading: the exit face value obeys du/dt + Ubar du/dx = 0 with a first-order
+ * upwind difference against the last interior u_x face, Ubar = U_x, advanced
+ * by the same Heun stages as the interior; afterwards a uniform correction
+ * makes the net boundary volume flux exactly zero.
+ *   stage 1: ue = ue0 + dt G(ue0, u0)
+ *   stage 2: ue = (ue* + ue0 + dt G(ue*, u*))/2,   G(ue, u) = -Ubar (ue - u_x[N-1]) */
+void orc_exit_bc(const orc_grid *g, const double *ue0, const double *uG, const double *ueG,
+                 double dt, int corrector, const double *ustar_e, double *u_new, double *ue)
+{
+    if (!g->exit_hi_x) return;
+    int n0 = g->n[0], np = g->n[1] * g->n[2];
+    double Ubar = g->U[0];
+    for (int p = 0; p < np; ++p) {
+        int j = p % g->n[1], k = p / g->n[1];
+        double last = uG[lin(g, n0 - 1, j, k)];
+        double G = -Ubar * (ueG[p] - last);
+        double v = ue0[p] + dt * G;
+        if (corrector) v = 0.5 * (ustar_e[p] + v);
+        ue[p] = v;
+    }
+    double q = boundary_outflux(g, u_new, ue);
+    double corr = -q / (double)np;
+    for (int p = 0; p < np; ++p) ue[p] += corr;
+}
+
+/* Discrete divergence sum_a (u_a[I+e_a] - u_a[I]). */
+void orc_divergence(const orc_grid *g, const double *u, const double *ue, double *div)
+{
+    for (int k = 0; k < g->n[2]; ++k)
+        for (int j = 0; j < g->n[1]; ++j)
+            for (int i = 0; i < g->n[0]; ++i) {
+                double s = 0.0;
+                for (int a = 0; a < g->ndim; ++a) {
+                    int da[3] = {0, 0, 0};
+                    da[a] = 1;
+                    s += su(g, u, ue, a, i + da[0], j + da[1], k + da[2]) - su(g, u, ue, a, i, j, k);
+                }
+                div[lin(g, i, j, k)] = s;
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Variable-coefficient Poisson operator (Sec. 2 / Sec. 3):                  */
+/*  (A p)[I] = sum_a c_a[I+e_a](p[I+e_a]-p[I]) - c_a[I](p[I]-p[I-e_a])         */
+/* c of the upper boundary face of a non-periodic axis is zero.               */
+/* ------------------------------------------------------------------------ */
+typedef struct { int ndim; int n[3]; int periodic[3]; double *c; } orc_level;
+
+static size_t lv_nc(const orc_level *L) { return (size_t)L->n[0] * L->n[1] * L->n[2]; }
+static size_t lv_lin(const orc_level *L, int i, int j, int k) {
+    return (size_t)i + (size_t)L->n[0] * ((size_t)j + (size_t)L->n[1] * (size_t)k);
+}
+/* coefficient of face a of cell I (I may be one past the end on axis a) */
+static double lv_c(const orc_level *L, int a, const int *I)
+{
+    int J[3] = {I[0], I[1], I[2]};
+    if (J[a] == L->n[a]) {
+        if (!L->periodic[a]) return 0.0;
+        J[a] = 0;
+    }
+    return L->c[(size_t)a * lv_nc(L) + lv_lin(L, J[0], J[1], J[2])];
+}
+static double lv_p(const orc_level *L, const double *p, const int *I)
+{
+    int J[3] = {I[0], I[1], I[2]};
+    for (int a = 0; a < L->ndim; ++a) {
+        int N = L->n[a];
+        if (J[a] < 0) J[a] = L->periodic[a] ? J[a] + N : 0;
+        if (J[a] >= N) J[a] = L->periodic[a] ? J[a] - N : N - 1;
+    }
+    return p[lv_lin(L, J[0], J[1], J[2])];
+}
+
+static double lv_apply_row(const orc_level *L, const double *p, int i, int j, int k)
+{
+    int I[3] = {i, j, k};
+    double pI = p[lv_lin(L, i, j, k)];
+    double s = 0.0;
+    for (int a = 0; a < L->ndim; ++a) {
+        int Ip[3] = {i, j, k}, Im[3] = {i, j, k};
+        Ip[a] += 1; Im[a] -= 1;
+        s += lv_c(L, a, Ip) * (lv_p(L, p, Ip) - pI) - lv_c(L, a, I) * (pI - lv_p(L, p, Im));
+    }
+    return s;
+}
+
+static double lv_diag(const orc_level *L, int i, int j, int k)
+{
+    int I[3] = {i, j, k};
+    double s = 0.0;
+    for (int a = 0; a < L->ndim; ++a) {
+        int Ip[3] = {i, j, k};
+        Ip[a] += 1;
+        s -= lv_c(L, a, Ip) + lv_c(L, a, I);
+    }
+    return s;
+}
+
+static void lv_apply(const orc_level *L, const double *p, double *Ap)
+{
+    for (int k = 0; k < L->n[2]; ++k)
+        for (int j = 0; j < L->n[1]; ++j)
+            for (int i = 0; i < L->n[0]; ++i) Ap[lv_lin(L, i, j, k)] = lv_apply_row(L, p, i, j, k);
+}
+
+static orc_level fine_level(const orc_grid *g, double *c)
+{
+    orc_level L;
+    L.ndim = g->ndim;
+    for (int a = 0; a < 3; ++a) { L.n[a] = g->n[a]; L.periodic[a] = a < g->ndim ? g->periodic[a] : 0; }
+    L.c = c;
+    return L;
+}
+
+void orc_poisson_apply(const orc_grid *g, const double *c, const double *p, double *Ap)
+{
+    orc_level L = fine_level(g, (double *)c);
+    lv_apply(&L, p, Ap);
+}
+
+void orc_poisson_diag(const orc_grid *g, const double *c, double *D)
+{
+    orc_level L = fine_level(g, (double *)c);
+    for (int k = 0; k < L.n[2]; ++k)
+        for (int j = 0; j < L.n[1]; ++j)
+            for (int i = 0; i < L.n[0]; ++i) D[lv_lin(&L, i, j, k)] = lv_diag(&L, i, j, k);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Geometric multigrid (Sec. 2, Sec. 4.2: MG with a PCG smoother).           */
+/* Readings: halve every axis while all are even and all halves are >= 4;    */
+/* restriction sums the 2^n children; the coarse face coefficient is half    */
+/* the sum of the 2^(n-1) fine faces on it; prolongation is injection; the   */
+/* cycle is V(0,k): k Jacobi-preconditioned CG iterations after the coarse   */
+/* correction on every level; the coarsest level is solved by Jacobi-PCG to  */
+/* round-off.                                                                */
+/* ------------------------------------------------------------------------ */
+#define OR_MAXLEV 24
+
+static int can_coarsen(const orc_level *L)
+{
+    for (int a = 0; a < L->ndim; ++a)
+        if ((L->n[a] % 2) != 0 || L->n[a] / 2 < 4) return 0;
+    return 1;
+}
+
+static void coarsen(const orc_level *F, orc_level *C)
+{
+    C->ndim = F->ndim;
+    for (int a = 0; a < 3; ++a) { C->n[a] = a < F->ndim ? F->n[a] / 2 : 1; C->periodic[a] = F->periodic[a]; }
+    size_t ncc = lv_nc(C), ncf = lv_nc(F);
+    C->c = (double *)calloc((size_t)C->ndim * ncc, sizeof(double));
+    int kz = F->ndim == 3 ? 2 : 1;
+    for (int a = 0; a < C->ndim; ++a)
+        for (int k = 0; k < C->n[2]; ++k)
+            for (int j = 0; j < C->n[1]; ++j)
+                for (int i = 0; i < C->n[0]; ++i) {
+                    double s = 0.0;
+                    for (int oz = 0; oz < kz; ++oz)
+                        for (int oy = 0; oy < 2; ++oy)
+                            for (int ox = 0; ox < 2; ++ox) {
+                                int o[3] = {ox, oy, oz};
+                                if (o[a] != 0) continue;  /* fine faces on the coarse lower a-face */
+                                s += F->c[(size_t)a * ncf + lv_lin(F, 2 * i + ox, 2 * j + oy, 2 * k + oz)];
+                            }
+                    C->c[(size_t)a * ncc + lv_lin(C, i, j, k)] = 0.5 * s;
+                }
+}
+
+static void restrict_sum(const orc_level *F, const orc_level *C, const double *rf, double *rc)
+{
+    int kz = F->ndim == 3 ? 2 : 1;
+    for (int k = 0; k < C->n[2]; ++k)
+        for (int j = 0; j < C->n[1]; ++j)
+            for (int i = 0; i < C->n[0]; ++i) {
+                double s = 0.0;
+                for (int oz = 0; oz < kz; ++oz)
+                    for (int oy = 0; oy < 2; ++oy)
+                        for (int ox = 0; ox < 2; ++ox) s += rf[lv_lin(F, 2 * i + ox, 2 * j + oy, 2 * k + oz)];
+                rc[lv_lin(C, i, j, k)] = s;
+            }
+}
+
+static void prolong_inject(const orc_level *F, const orc_level *C, const double *ec, double *ef)
+{
+    for (int k = 0; k < F->n[2]; ++k)
+        for (int j = 0; j < F->n[1]; ++j)
+            for (int i = 0; i < F->n[0]; ++i)
+                ef[lv_lin(F, i, j, k)] = ec[lv_lin(C, i / 2, j / 2, F->ndim == 3 ? k / 2 : 0)];
+}
+
+static double dot(const double *a, const double *b, size_t n)
+{
+    double s = 0.0;
+    for (size_t q = 0; q < n; ++q) s += a[q] * b[q];
+    return s;
+}
+
+/* Jacobi-preconditioned CG on A x = r from the given x, for `iters` iterations
+ * or until the residual norm falls to rtol * |r|. Rows with zero diagonal are
+ * held fixed (their residual is zero by construction). */
+static void pcg(const orc_level *L, const double *r, double *x, int iters, double rtol)
+{
+    size_t n = lv_nc(L);
+    double *s = malloc(n * sizeof(double)), *z = malloc(n * sizeof(double));
+    double *d = malloc(n * sizeof(double)), *q = malloc(n * sizeof(double));
+    double *iD = malloc(n * sizeof(double));
+    for (int k = 0; k < L->n[2]; ++k)
+        for (int j = 0; j < L->n[1]; ++j)
+            for (int i = 0; i < L->n[0]; ++i) {
+                double D = lv_diag(L, i, j, k);
+                iD[lv_lin(L, i, j, k)] = D != 0.0 ? 1.0 / D : 0.0;
+            }
+    lv_apply(L, x, q);
+    for (size_t e = 0; e < n; ++e) { s[e] = iD[e] != 0.0 ? r[e] - q[e] : 0.0; z[e] = iD[e] * s[e]; d[e] = z[e]; }
+    double rho = dot(s, z, n);
+    double r0 = sqrt(dot(r, r, n));
+    for (int it = 0; it < iters; ++it) {
+        if (rho == 0.0) break;
+        if (rtol > 0.0 && sqrt(dot(s, s, n)) <= rtol * r0) break;
+        lv_apply(L, d, q);
+        double dq = dot(d, q, n);
+        if (dq == 0.0) break;
+        double alpha = rho / dq;
+        for (size_t e = 0; e < n; ++e) { x[e] += alpha * d[e]; s[e] -= alpha * q[e]; z[e] = iD[e] * s[e]; }
+        double rho2 = dot(s, z, n);
+        double beta = rho2 / rho;
+        rho = rho2;
+        for (size_t e = 0; e < n; ++e) d[e] = z[e] + beta * d[e];
+    }
+    free(s); free(z); free(d); free(q); free(iD);
+}
+
+static void vcycle(orc_level *lev, int l, int nlev, const double *r, double *e, int k_smooth)
+{
+    size_t n = lv_nc(&lev[l]);
+    if (l == nlev - 1) {
+        /* The coarsest system is singular (periodic / Neumann boxes): solve for
+         * the mean-free part of r over active rows, return a mean-free e. */
+        double *rm = malloc(n * sizeof(double));
+        char *act = malloc(n);
+        double sr = 0.0, na = 0.0;
+        orc_level *L = &lev[l];
+        for (int k = 0; k < L->n[2]; ++k)
+            for (int j = 0; j < L->n[1]; ++j)
+                for (int i = 0; i < L->n[0]; ++i) {
+                    size_t q = lv_lin(L, i, j, k);
+                    act[q] = lv_diag(L, i, j, k) != 0.0;
+                    if (act[q]) { sr += r[q]; na += 1.0; }
+                }
+        for (size_t q = 0; q < n; ++q) rm[q] = act[q] ? r[q] - sr / na : 0.0;
+        memset(e, 0, n * sizeof(double));
+        pcg(L, rm, e, 2 * (int)n + 200, 1e-14);
+        double se = 0.0;
+        for (size_t q = 0; q < n; ++q) if (act[q]) se += e[q];
+        for (size_t q = 0; q < n; ++q) if (act[q]) e[q] -= se / na;
+        free(rm); free(act);
+        return;
+    }
+    size_t nc2 = lv_nc(&lev[l + 1]);
+    double *rc = malloc(nc2 * sizeof(double)), *ec = malloc(nc2 * sizeof(double));
+    restrict_sum(&lev[l], &lev[l + 1], r, rc);
+    vcycle(lev, l + 1, nlev, rc, ec, k_smooth);
+    prolong_inject(&lev[l], &lev[l + 1], ec, e);
+    pcg(&lev[l], r, e, k_smooth, 0.0);
+    free(rc); free(ec);
+}
+
+int orc_mg_levels(const orc_grid *g)
+{
+    orc_level L = fine_level(g, NULL);
+    int nl = 1;
+    while (can_coarsen(&L) && nl < OR_MAXLEV) {
+        for (int a = 0; a < L.ndim; ++a) L.n[a] /= 2;
+        ++nl;
+    }
+    return nl;
+}
+
+/* Solve A p = b - mean(b) for the pressure (warm start from p).
+ * Readings: mean of b removed over active rows (nonzero diagonal); converged
+ * when |b - A p|_2 <= tol |b|_2 over active rows; the returned p has zero mean
+ * over active rows and zero on inactive rows. Returns 0, or 1 if not converged. */
+int orc_poisson_solve(const orc_grid *g, const double *c, const double *b_in, double *p,
+                      const orc_solver *S, orc_stats *st)
+{
+    orc_level lev[OR_MAXLEV];
+    int nlev = 1;
+    lev[0] = fine_level(g, (double *)c);
+    while (can_coarsen(&lev[nlev - 1]) && nlev < OR_MAXLEV) {
+        coarsen(&lev[nlev - 1], &lev[nlev]);
+        ++nlev;
+    }
+    size_t n = lv_nc(&lev[0]);
+    double *D = malloc(n * sizeof(double)), *b = malloc(n * sizeof(double));
+    double *r = malloc(n * sizeof(double)), *e = malloc(n * sizeof(double));
+    orc_poisson_diag(g, c, D);
+    double sb = 0.0, na = 0.0;
+    for (size_t q = 0; q < n; ++q) if (D[q] != 0.0) { sb += b_in[q]; na += 1.0; }
+    double mean = na > 0 ? sb / na : 0.0;
+    for (size_t q = 0; q < n; ++q) b[q] = D[q] != 0.0 ? b_in[q] - mean : 0.0;
+    double bn = sqrt(dot(b, b, n));
+    int it = 0, rc = 0;
+    double rel = 0.0;
+    for (;;) {
+        lv_apply(&lev[0], p, r);
+        for (size_t q = 0; q < n; ++q) r[q] = D[q] != 0.0 ? b[q] - r[q] : 0.0;
+        double rn = sqrt(dot(r, r, n));
+        rel = bn > 0.0 ? rn / bn : 0.0;
+        if (rel <= S->tol) break;
+        if (it >= S->itmax) { rc = 1; break; }
+        vcycle(lev, 0, nlev, r, e, S->smooth_iters);
+        for (size_t q = 0; q < n; ++q) p[q] += e[q];
+        ++it;
+    }
+    double sp = 0.0;
+    for (size_t q = 0; q < n; ++q) if (D[q] != 0.0) sp += p[q];
+    double pm = na > 0 ? sp / na : 0.0;
+    for (size_t q = 0; q < n; ++q) p[q] = D[q] != 0.0 ? p[q] - pm : 0.0;
+    if (st) { st->vcycles = it; st->rel_resid = rel; st->bnorm = bn; }
+    for (int l = 1; l < nlev; ++l) free(lev[l].c);
+    free(D); free(b); free(r); free(e);
+    return rc;
+}
+
+/* Pressure-gradient update u_a[I] -= w dt c_a[I] (p[I] - p[I-e_a]) (Sec. 3 listing). */
+void orc_grad_update(const orc_grid *g, const double *c, const double *p, double wdt, double *u)
+{
+    size_t nc = ncell(g);
+    orc_level L = fine_level(g, (double *)c);
+    for (int a = 0; a < g->ndim; ++a)
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i) {
+                    int I[3] = {i, j, k}, Im[3] = {i, j, k};
+                    Im[a] -= 1;
+                    size_t q = (size_t)a * nc + lin(g, i, j, k);
+                    u[q] -= wdt * c[q] * (p[lin(g, i, j, k)] - lv_p(&L, p, Im));
+                    (void)I;
+                }
+}
+
+/* Projection with weight w: A P = div(u)/(w dt), u -= w dt c grad P.
+ * P is the warm start on entry and the solution on exit. */
+int orc_project(const orc_grid *g, const double *c, double *u, const double *ue, double *P,
+                double w, double dt, const orc_solver *S, orc_stats *st)
+{
+    size_t nc = ncell(g);
+    double *b = malloc(nc * sizeof(double));
+    orc_divergence(g, u, ue, b);
+    double s = 1.0 / (w * dt);
+    for (size_t q = 0; q < nc; ++q) b[q] *= s;
+    int rc = orc_poisson_solve(g, c, b, P, S, st);
+    orc_grad_update(g, c, P, w * dt, u);
+    free(b);
+    return rc;
+}
+
+/* CFL time step (Sec. 2: "time step adapted to ensure a stable CFL number").
+ * Reading: dt = min(dt_max, cfl / (max_I sum_a [max(0,u_a[I+e_a]) - min(0,u_a[I])] + 5 nu)). */
+double orc_cfl(const orc_grid *g, const double *u, const double *ue, double cfl, double dt_max)
+{
+    double m = 0.0;
+    for (int k = 0; k < g->n[2]; ++k)
+        for (int j = 0; j < g->n[1]; ++j)
+            for (int i = 0; i < g->n[0]; ++i) {
+                double s = 0.0;
+                for (int a = 0; a < g->ndim; ++a) {
+                    int da[3] = {0, 0, 0};
+                    da[a] = 1;
+                    s += fmax(0.0, su(g, u, ue, a, i + da[0], j + da[1], k + da[2])) - fmin(0.0, su(g, u, ue, a, i, j, k));
+                }
+                if (s > m) m = s;
+            }
+    double dt = cfl / (m + 5.0 * g->nu);
+    return dt < dt_max ? dt : dt_max;
+}
+
+/* Pressure force on the body (Sec. 5 uses drag / power coefficients).
+ * Reading: F = -sum_I p_I n(x_I) K_eps(d(x_I)) over cell centres (h^n = 1). */
+void orc_forces(const orc_grid *g, const orc_body *B, double t, const double *p, double *F)
+{
+    F[0] = F[1] = F[2] = 0.0;
+    if (B->kind == 0) return;
+    for (int k = 0; k < g->n[2]; ++k)
+        for (int j = 0; j < g->n[1]; ++j)
+            for (int i = 0; i < g->n[0]; ++i) {
+                double x[3] = {i + 0.5, j + 0.5, k + 0.5};
+                double d, nrm[3], v[3];
+                orc_body_eval(B, g->ndim, x, t, &d, nrm, v);
+                double K = orc_kernel(d, g->eps);
+                if (K == 0.0) continue;
+                double pk = p[lin(g, i, j, k)] * K;
+                for (int a = 0; a < g->ndim; ++a) F[a] -= pk * nrm[a];
+            }
+}
+
+/* One Heun predictor-corrector step with projections (Sec. 2).
+ * State: u (ndim x nc), ue (exit plane), P (pressure, warm start in/out).
+ * Body measured at t + dt (the end of the step) and held for both stages.
+ *   u0 = u
+ *   predictor:  u = B(u0 + dt R(u0)); BC; exit; project(w = 1)      -> u*
+ *   corrector:  u = (u* + B(u0 + dt R(u*)))/2; BC; exit; project(w = 1/2)
+ * Returns the number of projections that did not converge. */
+int orc_step(const orc_grid *g, const orc_body *B, double t, double dt,
+             double *u, double *ue, double *P, const orc_solver *S, orc_stats *st2)
+{
+    size_t nc = ncell(g);
+    size_t nu = (size_t)g->ndim * nc;
+    int np = g->n[1] * g->n[2];
+    double *u0 = malloc(nu * sizeof(double)), *r = malloc(nu * sizeof(double));
+    double *ue0 = malloc((size_t)np * sizeof(double)), *ues = malloc((size_t)np * sizeof(double));
+    double *c = malloc(nu * sizeof(double));
+    double *mu0 = NULL, *mu1n = NULL, *V = NULL;
+    if (B && B->kind != 0) {
+        mu0 = malloc(nu * sizeof(double));
+        mu1n = malloc(9 * nc * sizeof(double));
+        V = malloc(nu * sizeof(double));
+        orc_measure(g, B, t + dt, mu0, mu1n, V);
+    }
+    orc_coeffs(g, mu0, c);
+    memcpy(u0, u, nu * sizeof(double));
+    memcpy(ue0, ue, (size_t)np * sizeof(double));
+    int bad = 0;
+    /* predictor */
+    orc_conv_diff(g, u0, ue0, r);
+    orc_bdim(g, u0, r, dt, mu0, mu1n, V, NULL, u);
+    orc_exit_bc(g, ue0, u0, ue0, dt, 0, NULL, u, ue);
+    bad += orc_project(g, c, u, ue, P, 1.0, dt, S, st2 ? &st2[0] : NULL);
+    /* corrector */
+    memcpy(ues, ue, (size_t)np * sizeof(double));
+    orc_conv_diff(g, u, ue, r);
+    double *us = malloc(nu * sizeof(double));
+    memcpy(us, u, nu * sizeof(double));
+    orc_bdim(g, u0, r, dt, mu0, mu1n, V, us, u);
+    orc_exit_bc(g, ue0, us, ues, dt, 1, ues, u, ue);
+    bad += orc_project(g, c, u, ue, P, 0.5, dt, S, st2 ? &st2[1] : NULL);
+    free(us); free(u0); free(r); free(ue0); free(ues); free(c);
+    free(mu0); free(mu1n); free(V);
+    return bad;
+}
+
+/* Diagnostics: kinetic energy (mean over cells of |u|^2/2 with u interpolated
+ * to cell centres), and mean squared vorticity over cell edges (ν<|ω|²> is the
+ * enstrophy form of the dissipation). */
+void orc_diagnostics(const orc_grid *g, const double *u, const double *ue, double *ke, double *ens)
+{
+    double s = 0.0, w = 0.0;
+    size_t nc = ncell(g);
+    for (int k = 0; k < g->n[2]; ++k)
+        for (int j = 0; j < g->n[1]; ++j)
+            for (int i = 0; i < g->n[0]; ++i) {
+                int I[3] = {i, j, k};
+                for (int a = 0; a < g->ndim; ++a) {
+                    int da[3] = {0, 0, 0};
+                    da[a] = 1;
+                    double uc = 0.5 * (su(g, u, ue, a, i, j, k) + su(g, u, ue, a, i + da[0], j + da[1], k + da[2]));
+                    s += 0.5 * uc * uc;
+                }
+                /* vorticity component about axis e on the edge at the lower corner:
+                 * w_e = d_a u_b - d_b u_a, (a, b, e) cyclic */
+                for (int e = 0; e < 3; ++e) {
+                    int a = (e + 1) % 3, b = (e + 2) % 3;
+                    if (g->ndim == 2 && e != 2) continue;
+                    int ma[3] = {i, j, k}, mb[3] = {i, j, k};
+                    ma[a] -= 1; mb[b] -= 1;
+                    double om = (su(g, u, ue, b, i, j, k) - su(g, u, ue, b, ma[0], ma[1], ma[2]))
+                              - (su(g, u, ue, a, i, j, k) - su(g, u, ue, a, mb[0], mb[1], mb[2]));
+                    w += om * om;
+                    (void)I;
+                }
+            }
+    *ke = s / (double)nc;
+    *ens = w / (double)nc;
+}
