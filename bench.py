@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark of the BDIM incompressible-flow time step on B300.
+
+One step = one Heun predictor-corrector step of the solver (two convection-
+diffusion + BDIM stages, two projections each converged to a 1e-6 relative
+Poisson residual, CFL update) through the C ABI of libwl.so.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload tgv256]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Multi-GPU: the time step does not shard without a halo exchange, so N > 1 runs
+N independent replicas (one per rank, weak scaling) and reports the aggregate.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-steps/s at 1e-6 Poisson residual (learned-guess vs plain MG); HBM GB/s"
+UNIT = "cell-steps/s"
+
+
+def workload(name):
+    import synth
+    table = {
+        "tgv256": lambda: synth.config2_tgv(256),
+        "tgv128": lambda: synth.config2_tgv(128),
+        "tgv64": lambda: synth.config2_tgv(64),
+        "sphere": lambda: synth.config3_sphere(),
+        "msphere": lambda: synth.config5_moving_sphere(),
+        "circle": lambda: synth.config1_circle(),
+        "ellipse": lambda: synth.config4_ellipse(),
+    }
+    return table[name]()
+
+
+def describe(case, prec):
+    return {"workload": f"{case.name} {'x'.join(str(v) for v in case.n[:case.ndim])}",
+            "cells": case.ncell, "nu": case.nu, "body": case.body.kind,
+            "bc": "periodic" if all(case.periodic[:case.ndim]) else "inflow/slip/convective-exit",
+            "precision": prec, "poisson_tol": 1e-6, "smoother": "PCG x4 per level, V(0,4)",
+            "guess": "warm start (previous pressure)",
+            "l2": "inputs larger than L2 (velocity alone > 126 MB)" if case.ncell * 12 > 126e6 else "small"}
+
+
+# bytes per cell of each kernel's algorithmic traffic (T = element size, nd = ndim)
+def algo_bytes(name, T, nd, has_body=False):
+    m1 = nd * nd
+    return {
+        "flux_pred": 2 * nd * T, "flux_pred_f": 2 * nd * T,
+        "flux_corr": 3 * nd * T, "flux_corr_f": 3 * nd * T,
+        "blend": (nd + nd + m1 + nd + nd) * T,
+        "div": (nd + 2) * T,
+        "resid": (2 + 1 + nd + 1 + 1) * T,
+        "restrict": 9 * T if nd == 3 else 5 * T,
+        "pcg_init": (1 / 8 + 1 + nd + 1 + 3) * T if nd == 3 else (1 / 4 + 1 + nd + 1 + 3) * T,
+        "pcg_q0": (1 + nd + 1) * T,
+        "pcg_q": (3 + nd + 2) * T,
+        "pcg_u": 7 * T,
+        "pcg_u_last": 3 * T,
+        "pcg_u_last_fine": 6 * T,
+        "grad": (nd + 2 + 2 * nd) * T,
+        "cfl": nd * T,
+        "measure": ((nd + m1 + nd) if has_body else nd) * T,
+    }.get(name)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6400.0), "measured"
+    return 6400.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2407_16032_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.strip().split(",") for l in open(self.f.name) if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[3:7]):
+                if v.strip().lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(sample_n=96, steps=1):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload:
+    the Taylor-Green vortex at the same Reynolds number on a sample_n^3 grid,
+    one untimed step then `steps` timed steps; per-cell cost is size-independent
+    for the oracle, so cell-steps/s carries over."""
+    import oracle
+    import synth
+    case = synth.config2_tgv(sample_n)
+    s = oracle.Sim(case, tol=1e-6)
+    s.step(0.4)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.step()
+    dt = time.perf_counter() - t0
+    return {"value": case.ncell * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"TGV {sample_n}^3 (Re 1600 on 1/k), {steps} warm step(s) after 1 untimed step, "
+                      f"FP64 single-threaded C, MG to 1e-6; {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    case = synth.config2_tgv(64)
+    s = oracle.Sim(case, tol=1e-6)
+    for _ in range(args.warmup):
+        s.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step()
+    dt = time.perf_counter() - t0
+    v = case.ncell * args.steps / dt
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (analytic Taylor-Green initial field)",
+           "config": describe(workload(args.workload), "fp32") | {
+               "reference_sample": "each step: one oracle step of TGV 64^3 (same Re), host cores"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "TGV 64^3 per step, FP64 single-threaded C oracle"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="tgv256")
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import synth
+    from paper_2407_16032_b300 import build, sim_from_case
+    if rank == 0 and world == 1:
+        build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    case = workload(args.workload)
+    prec = args.precision or ("f64" if args.workload == "circle" else "f32")
+    sim = sim_from_case(case, prec, tol=1e-6, itmax=32)
+    u, ue = synth.initial_velocity(case)
+    tdt = torch.float32 if prec == "f32" else torch.float64
+    u_dev = torch.tensor(u, dtype=tdt, device="cuda")
+    ue_dev = torch.tensor(ue, dtype=tdt, device="cuda")
+    sim.set_velocity(u_dev, ue_dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(args.warmup, 3)):
+        sim.mom_step()
+    _, l0 = sim.info()
+    clk = Clocks(local)
+    vcyc = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st, rc = sim.mom_step()
+        vcyc.append(st.proj[0].vcycles + st.proj[1].vcycles)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    _, l1 = sim.info()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = case.ncell * args.steps * world / (ms / 1000.0)
+
+    # ---- roofline of the dominant kernel: per-kernel CUDA-event timing pass
+    roof, kernels = None, []
+    if not args.no_profile:
+        sim.profile(True)
+        for _ in range(2):
+            sim.mom_step()
+        rows = sim.profile_report()
+        sim.profile(False)
+        tot = sum(r[3] for r in rows)
+        by = {}
+        for nm, lv, n, tms, cells in rows:
+            by.setdefault(nm, [0.0, 0, 0.0])
+            by[nm][0] += tms
+            b = algo_bytes(nm, 4 if prec == "f32" else 8, case.ndim, case.body.kind != "none")
+            if b is not None:
+                by[nm][2] += b * cells * n
+            by[nm][1] += n
+        peak, src = load_peaks()
+        for nm, (tms, n, byt) in sorted(by.items(), key=lambda kv: -kv[1][0]):
+            kernels.append({"kernel": nm, "share": round(tms / tot, 4), "launches": n,
+                            "avg_us": round(1000 * tms / n, 2),
+                            "GBps": round(byt / (tms / 1000) / 1e9, 1) if byt else None})
+        fine = [(nm, lv, n, tms, cells) for nm, lv, n, tms, cells in rows if lv == 0 and
+                algo_bytes(nm, 4, case.ndim) is not None]
+        top = max(fine, key=lambda r: r[3])
+        nm, lv, n, tms, cells = top
+        bpl = algo_bytes(nm, 4 if prec == "f32" else 8, case.ndim, case.body.kind != "none") * cells
+        ach = bpl / (tms / n / 1000) / 1e9
+        roof = {"bound": "hbm", "kernel": f"{nm} (fine level)", "achieved": round(ach, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": src,
+                "algorithmic_bytes_per_launch": int(bpl), "traffic": traffic_for(nm)}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hu = torch.empty_like(u_dev, device="cpu").pin_memory()
+        hue = torch.empty_like(ue_dev, device="cpu").pin_memory()
+        sim.get_velocity(hu, hue)
+        n_e2e = max(3, args.steps // 2)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            sim.set_velocity(hu, hue)       # H2D of the step's input field
+            st, rc = sim.mom_step()
+            sim.get_velocity(hu, hue)       # D2H of the step's result field
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        nb = hu.numel() * hu.element_size() + (hue.numel() * hue.element_size() if case.exit_hi_x else 0)
+        e2e = {"value": case.ncell * n_e2e * world / el, "unit": UNIT, "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb + 96}
+
+    if rank == 0:
+        cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline()
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic (analytic fields, seeded noise)",
+               "config": describe(case, prec) | {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                                                 "vcycles_per_step_mean": statistics.mean(vcyc)},
+               "hbm_GBps_dominant_kernel": roof["achieved"] if roof else None,
+               "roofline": roof, "kernels": kernels[:10], "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": l1 - l0, "clocks": clocks,
+               "paper_context": {"ns_per_cell_step": 1.57, "cell_steps_per_s": 6.4e8,
+                                 "hw": "NVIDIA H100, FP32, TGV 134M cells (Sec. 4.1)"}}
+        print(json.dumps(out))
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

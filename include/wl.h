@@ -1,0 +1,226 @@
+/*
+ * wl.h -- C ABI of the B300 (sm_103a) BDIM incompressible-flow time step.
+ *
+ * The library advances the velocity/pressure of an incompressible viscous flow
+ * around an immersed body on a uniform staggered Cartesian grid (cell size
+ * h = 1), following WaterLily (arXiv 2407.16032):
+ *   Sec. 2  the momentum equation (F-dot) integrated with an explicit
+ *           predictor-corrector (Heun), the boundary-data-immersion (BDIM)
+ *           blend (F-dot convolved with the body equation B through the
+ *           kernel moments mu0/mu1 of the signed distance), the pressure
+ *           projection with a variable-coefficient Poisson equation solved by
+ *           geometric multigrid, and a CFL-limited time step;
+ *   Sec. 3  the problem statement Simulation(dims, U, L; nu, body) with the
+ *           body given by a distance function plus a motion map (AutoBody),
+ *           and the pressure-gradient update u[I,i] -= c[I,i](p[I]-p[I-d(i)]);
+ *   Sec. 4  the boundary conditions: slip walls, inflow, convective outlet,
+ *           periodic directions.
+ *
+ * Conventions for every entry point:
+ *   - Returns a wl_status; nothing throws or aborts across the ABI.
+ *     On error, wl_last_error(sim) describes it and the simulation state stays
+ *     defined (the last completed step's fields are kept).
+ *   - Field layout: component-major, x fastest. A velocity field of an
+ *     ndim-dimensional grid n[0] x n[1] (x n[2]) is ndim consecutive arrays of
+ *     n[0]*n[1]*n[2] values; value (a, i, j, k) sits at
+ *     a*N + i + n[0]*(j + n[1]*k), N = n[0]*n[1]*n[2].  Component a lives on
+ *     the lower a-face of cell (i,j,k), i.e. at (i+1/2, j+1/2, k+1/2) - e_a/2.
+ *     The exit plane (convective outlet, upper x face) holds n[1]*n[2] values
+ *     of u_x at x = n[0], index j + n[1]*k.
+ *   - Element type: float for WL_F32, double for WL_F64 (velocity, coefficient
+ *     and body arrays); pressure and scalars are always double on the host side.
+ *   - Pointers: any argument documented "host or device" may point to host
+ *     memory (pageable or pinned) or to device memory of the sim's device;
+ *     the library copies with cudaMemcpyAsync(cudaMemcpyDefault) on the sim's
+ *     stream and synchronises that stream before returning.  Caller keeps
+ *     ownership of every pointer it passes; the sim owns what it allocates.
+ *   - All device work is enqueued on cfg.stream.  One sim must not be used by
+ *     two host threads at once.
+ */
+#ifndef WL_H
+#define WL_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define WL_API __attribute__((visibility("default")))
+#else
+#define WL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wl_sim wl_sim;
+
+typedef enum {
+    WL_OK = 0,
+    WL_ERR_ARG = 1,            /* invalid argument or configuration */
+    WL_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    WL_ERR_ALLOC = 3,          /* device allocation failed */
+    WL_ERR_NOT_CONVERGED = 4,  /* Poisson solve hit itmax before tol */
+    WL_ERR_NONFINITE = 5,      /* NaN/Inf appeared in the solution */
+    WL_ERR_UNSTABLE = 6,       /* CFL time step fell below dt_min */
+    WL_ERR_STATE = 7           /* call not valid in the current state */
+} wl_status;
+
+typedef enum { WL_F32 = 0, WL_F64 = 1 } wl_precision;
+
+typedef enum { WL_BODY_NONE = 0, WL_BODY_SPHERE = 1, WL_BODY_ELLIPSE = 2 } wl_body_kind;
+
+/* Optional device allocator (e.g. a framework's caching allocator).
+ * alloc returns a device pointer of at least `bytes` (256-byte aligned) or
+ * NULL; free releases it. NULL alloc => cudaMalloc/cudaFree. */
+typedef struct {
+    void *ctx;
+    void *(*alloc)(void *ctx, size_t bytes);
+    void (*free)(void *ctx, void *ptr);
+} wl_allocator;
+
+/* Problem statement (Sec. 3 Simulation; Sec. 4 boundary conditions). */
+typedef struct {
+    int ndim;              /* 2 or 3 */
+    int n[3];              /* cells per axis (n[2] ignored when ndim == 2) */
+    int periodic[3];       /* nonzero: periodic axis */
+    int exit_hi_x;         /* nonzero: convective outlet on the upper x face */
+    double U[3];           /* free stream: normal velocity of non-periodic boundary faces */
+    double nu;             /* kinematic viscosity (grid units) */
+    double eps;            /* BDIM kernel half-width (1 = one cell) */
+    int precision;         /* wl_precision */
+    double cfl;            /* CFL number for the adaptive time step (1) */
+    double dt_max;         /* upper bound of the adaptive time step (1) */
+    double dt_init;        /* first time step (0.25) */
+    double dt_min;         /* below this the step reports WL_ERR_UNSTABLE (1e-6) */
+    double tol;            /* relative L2 residual of each Poisson solve (1e-6) */
+    int itmax;             /* max multigrid V-cycles per solve (32) */
+    int smooth_iters;      /* PCG smoothing iterations per level (4) */
+    void *stream;          /* cudaStream_t; NULL = legacy default stream */
+    wl_allocator allocator;
+} wl_config;
+
+/* Analytic immersed body (Sec. 3 AutoBody: signed distance + motion map).
+ * SPHERE is a circle in 2D. The centre heaves along heave_axis as
+ * centre + heave_amp sin(omega t + phase); ELLIPSE (2D) has semi-axes semi[0]
+ * (chord/2, along x at zero pitch) and semi[1] (thickness/2) and pitches about
+ * its centre by pitch_amp sin(omega t + phase + pi/2). Signed distance d > 0 in
+ * the fluid; normal = grad d (into the fluid); V = rigid-body velocity. */
+typedef struct {
+    int kind;              /* wl_body_kind */
+    double centre[3];
+    double radius;
+    double semi[2];
+    double heave_amp, pitch_amp, omega, phase;
+    int heave_axis;
+} wl_body;
+
+typedef struct {
+    int vcycles;           /* V-cycles used */
+    double rel_resid;      /* final |b - A p|_2 / |b|_2 over active rows */
+    double bnorm;          /* |b|_2 of the mean-free right-hand side */
+} wl_solve_stats;
+
+typedef struct {
+    wl_solve_stats proj[2];  /* predictor and corrector projections */
+    double dt;               /* time step taken */
+    double t;                /* time after the step */
+    double dt_next;          /* CFL time step for the next step */
+} wl_step_stats;
+
+/* Fill *cfg with defaults for an ndim grid of n cells (free stream 0, slip
+ * walls, FP32, tol 1e-6, itmax 32, 4 smoothing iterations, eps 1, cfl 1). */
+WL_API void wl_config_default(wl_config *cfg, int ndim, const int *n);
+
+/* Create a simulation (Sec. 3 Simulation(dims, U, L; nu, body)).
+ * Allocates all device state on the current device, measures the body at
+ * t = 0, sets u = 0 with U on the inflow/wall faces and the exit plane, p = 0.
+ * body may be NULL (no body). Errors: WL_ERR_ARG (bad sizes, ndim, eps <= 0,
+ * nu < 0, ellipse in 3D, exit without non-periodic x), WL_ERR_ALLOC, WL_ERR_CUDA. */
+WL_API int wl_sim_create(const wl_config *cfg, const wl_body *body, wl_sim **out);
+
+/* Free everything the sim allocated. NULL is accepted. */
+WL_API int wl_sim_destroy(wl_sim *sim);
+
+/* Copy a velocity field in (host or device; cfg.precision element type;
+ * layout above). ue may be NULL when there is no exit plane. The lower
+ * boundary faces of non-periodic axes are overwritten with U. */
+WL_API int wl_set_velocity(wl_sim *sim, const void *u, const void *ue);
+
+/* Copy the velocity field (and exit plane, if ue != NULL) out (host or device). */
+WL_API int wl_get_velocity(wl_sim *sim, void *u, void *ue);
+
+/* Pressure (doubles, one per cell, host or device). get returns the pressure of
+ * the last projection with zero mean over active cells and 0 in cells whose
+ * faces are all solid; set gives the warm start of the next solve. */
+WL_API int wl_get_pressure(wl_sim *sim, double *p);
+WL_API int wl_set_pressure(wl_sim *sim, const double *p);
+
+/* Simulation time and the time step the next wl_mom_step will use. */
+WL_API int wl_set_time(wl_sim *sim, double t, double dt_next);
+WL_API int wl_get_time(wl_sim *sim, double *t, double *dt_next);
+
+/* One Heun predictor-corrector step with two projections (Sec. 2):
+ *   u0 = u; u* = P_1[ B(u0 + dt R(u0)) ];  u = P_1/2[ (u* + B(u0 + dt R(u*)))/2 ]
+ * where R is the convection-diffusion flux, B the BDIM blend (with the body
+ * measured at t + dt), and P_w the projection with weight w. dt_fixed > 0 uses
+ * that step; otherwise the CFL step computed after the previous step.
+ * Errors: WL_ERR_NOT_CONVERGED (state advanced, residual above tol),
+ * WL_ERR_NONFINITE, WL_ERR_UNSTABLE (state kept), WL_ERR_CUDA. stats may be NULL. */
+WL_API int wl_mom_step(wl_sim *sim, double dt_fixed, wl_step_stats *stats);
+
+/* Project the current velocity: solve A P = div(u)/(w dt) and set
+ * u -= w dt c grad P (Sec. 3 listing), P warm-started from the last solve. */
+WL_API int wl_project(wl_sim *sim, double w, double dt, wl_solve_stats *stats);
+
+/* Solve A p = b - mean(b) with the sim's current coefficients.
+ * b: cfg.precision element type, host or device; p: doubles, host or device,
+ * warm start in / solution out (zero mean over active cells). */
+WL_API int wl_poisson_solve(wl_sim *sim, const void *b, double *p, wl_solve_stats *stats);
+
+/* Convection-diffusion right-hand side r = R(u) (Sec. 2 F-dot without the
+ * pressure term) of a given field u (+ exit plane ue, may be NULL), into r.
+ * All three host or device, cfg.precision element type. r is 0 on the lower
+ * boundary faces of non-periodic axes. Uses the sim's scratch buffers. */
+WL_API int wl_conv_diff(wl_sim *sim, const void *u, const void *ue, void *r);
+
+/* Pressure force on the body, F = -sum_I p_I n(x_I) K_eps(d(x_I)) over cell
+ * centres (the BDIM kernel-weighted surface integral), at the time the body
+ * was last measured. F: 3 doubles (host). */
+WL_API int wl_forces(wl_sim *sim, double *F);
+
+/* Measure the body at time t onto the faces (mu0, mu1 n, V) and rebuild the
+ * multigrid coefficients (Sec. 2 / Sec. 3 measure of AutoBody). */
+WL_API int wl_body_update(wl_sim *sim, double t);
+
+/* Copy the measured face fields out (host or device, cfg.precision type):
+ * c = Poisson coefficients (mu0 with non-periodic lower boundary faces zeroed,
+ * ndim arrays), mu1n = mu1 * n_b on face a at (a*3+b) (9 arrays, b >= ndim
+ * zero), V = body velocity (ndim arrays). Any may be NULL. */
+WL_API int wl_get_body_fields(wl_sim *sim, void *c, void *mu1n, void *V);
+
+/* Kinetic energy (mean over cells of |u|^2/2, u at cell centres), mean squared
+ * vorticity over cell edges, and max |div u| over active cells. Host doubles. */
+WL_API int wl_diagnostics(wl_sim *sim, double *ke, double *enstrophy, double *max_div);
+
+/* Number of multigrid levels and the kernel launch counter (kernels launched
+ * by this sim since creation). */
+WL_API int wl_info(wl_sim *sim, int *levels, long long *launches);
+
+/* Per-kernel timing mode. on != 0: every kernel of the following calls is
+ * bracketed by CUDA events on the sim's stream (the multigrid V-cycle then runs
+ * as direct launches instead of its CUDA graph) and times are accumulated per
+ * kernel and multigrid level; on == 0 stops it. Enabling clears the totals. */
+WL_API int wl_profile(wl_sim *sim, int on);
+
+/* Text report of the accumulated timing, one line per kernel and level:
+ * "name level launches total_ms cells_per_launch". Writes at most len bytes
+ * (NUL-terminated) into buf; *needed (may be NULL) receives the full size. */
+WL_API int wl_profile_report(wl_sim *sim, char *buf, size_t len, size_t *needed);
+
+WL_API const char *wl_last_error(const wl_sim *sim);
+WL_API const char *wl_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

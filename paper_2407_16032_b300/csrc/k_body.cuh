@@ -1,0 +1,208 @@
+// k_body.cuh -- analytic body measure, BDIM blend and pressure force.
+//
+// Sec. 2: the momentum update is convolved with the body equation u = V
+// through a kernel of half-width eps; with the signed distance d (> 0 in the
+// fluid) and the normal n = grad d, the zeroth and first kernel moments are
+//     mu0(d) = (1 + r + sin(pi r)/pi)/2,
+//     mu1(d) = eps [1/4 - r^2/4 - (r sin(pi r) + (1 + cos(pi r))/pi)/(2 pi)],
+// r = d/eps on |r| < 1 (mu0 = 0 / 1 and mu1 = 0 outside), and the blended
+// velocity on face a is  u = V + mu0 (f - V) + mu1 n . grad(f - V).
+// Sec. 3: bodies are a distance function plus a motion map (AutoBody); here the
+// map is a rigid heave (and pitch for the 2D ellipse), evaluated per face.
+#pragma once
+#include "wl_common.cuh"
+#include "k_poisson.cuh"
+
+// Body state at one instant, prepared on the host in double precision.
+// The centre is split into an integer part and a remainder so that face
+// offsets x - c stay accurate in single precision.
+struct BodyState {
+    int kind;          // 0 none, 1 sphere/circle, 2 ellipse (2D)
+    double chi[3];     // integer part of the centre
+    double clo[3];     // centre - chi
+    double radius;
+    double sa, sb;     // ellipse semi-axes
+    double cth, sth;   // cos / sin of the pitch angle
+    double vc[3];      // centre velocity
+    double thd;        // pitch rate
+    double eps;
+};
+
+__device__ __forceinline__ float sinpi_t(float x) { return sinpif(x); }
+__device__ __forceinline__ double sinpi_t(double x) { return sinpi(x); }
+__device__ __forceinline__ float cospi_t(float x) { return cospif(x); }
+__device__ __forceinline__ double cospi_t(double x) { return cospi(x); }
+
+template <typename T>
+__device__ __forceinline__ T kmu0(T d, T eps) {
+    const T r = d / eps;
+    if (r <= T(-1)) return T(0);
+    if (r >= T(1)) return T(1);
+    return T(0.5) * (T(1) + r + sinpi_t(r) * T(0.31830988618379067154));
+}
+template <typename T>
+__device__ __forceinline__ T kmu1(T d, T eps) {
+    const T r = d / eps;
+    if (r <= T(-1) || r >= T(1)) return T(0);
+    const T ip = T(0.31830988618379067154);
+    return eps * (T(0.25) - T(0.25) * r * r - (r * sinpi_t(r) + (T(1) + cospi_t(r)) * ip) * (T(0.5) * ip));
+}
+template <typename T>
+__device__ __forceinline__ T kkernel(T d, T eps) {
+    const T r = d / eps;
+    if (r <= T(-1) || r >= T(1)) return T(0);
+    return (T(1) + cospi_t(r)) / (T(2) * eps);
+}
+
+// Signed distance, normal and velocity of the body at point p = (cell index
+// + offsets) given as exact small values px (offsets from the integer centre
+// are formed before the remainder is removed).
+template <typename T>
+__device__ __forceinline__ void body_eval(const BodyState &B, int ndim, const T (&px)[3], T &d, T (&nrm)[3], T (&V)[3]) {
+    T rv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        rv[a] = a < ndim ? (px[a] - (T)B.chi[a]) - (T)B.clo[a] : T(0);
+        nrm[a] = T(0);
+        V[a] = (T)B.vc[a];
+    }
+    if (B.kind == 1) {
+        T r2 = rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+        T rr = sqrt(r2);
+        d = rr - (T)B.radius;
+        if (rr > T(0)) {
+            const T inv = T(1) / rr;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) nrm[a] = rv[a] * inv;
+        } else {
+            nrm[0] = T(1);
+        }
+    } else if (B.kind == 2) {
+        const T ct = (T)B.cth, st = (T)B.sth, sa = (T)B.sa, sb = (T)B.sb;
+        const T xp = ct * rv[0] + st * rv[1], yp = -st * rv[0] + ct * rv[1];
+        const T q = sqrt((xp / sa) * (xp / sa) + (yp / sb) * (yp / sb));
+        const T gx = xp / (sa * sa), gy = yp / (sb * sb);
+        const T gn = sqrt(gx * gx + gy * gy);
+        if (gn > T(0)) {
+            d = (q - T(1)) * q / gn;
+            const T nx = gx / gn, ny = gy / gn;
+            nrm[0] = ct * nx - st * ny;
+            nrm[1] = st * nx + ct * ny;
+        } else {
+            d = -sb;
+            nrm[0] = T(1);
+        }
+        V[0] += -(T)B.thd * rv[1];
+        V[1] += (T)B.thd * rv[0];
+    } else {
+        d = T(1e30);
+    }
+}
+
+// Measure every stored face: c_a = mu0 (0 on lower faces of non-periodic axes),
+// mu1n[a*3+b] = mu1 n_b, V[a] = body velocity component a.
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_measure(LevelD<T> L, BodyState B, Vec3P<T> c, T *mu1n0, long long mstride,
+                                                 Vec3P<T> V, bool full) {
+    const T eps = (T)B.eps;
+    const GridD &g = L.g;
+    for_cells<NDIM>(g, L.tl, nullptr, [&](int i, int j, int k, long long idx, bool) {
+        const int I[3] = {i, j, k};
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            T px[3] = {T(i) + T(0.5), T(j) + T(0.5), T(k) + T(0.5)};
+            px[a] -= T(0.5);
+            T d, nrm[3], v[3];
+            body_eval<T>(B, NDIM, px, d, nrm, v);
+            T m0 = kmu0<T>(d, eps), m1 = kmu1<T>(d, eps);
+            if (sizeof(T) < sizeof(double) && d > -eps - T(0.5) && d < eps + T(0.5)) {
+                // inside the kernel band: distance, normal and moments in double
+                // (a thin shell of faces), rounded once to T
+                double pd[3] = {i + 0.5, j + 0.5, k + 0.5}, dd, nd[3], vd[3];
+                pd[a] -= 0.5;
+                body_eval<double>(B, NDIM, pd, dd, nd, vd);
+                m0 = (T)kmu0<double>(dd, B.eps);
+                m1 = (T)kmu1<double>(dd, B.eps);
+#pragma unroll
+                for (int b = 0; b < 3; ++b) { nrm[b] = (T)nd[b]; v[b] = (T)vd[b]; }
+            }
+            c.p[a][idx] = (!g.per[a] && I[a] == 0) ? T(0) : m0;
+            if (full) {
+#pragma unroll
+                for (int b = 0; b < NDIM; ++b) mu1n0[(a * 3 + b) * mstride + idx] = m1 * nrm[b];
+                V.p[a][idx] = v[a];
+            }
+        }
+    });
+}
+
+// BDIM blend of the stage value f (Sec. 2): u = V + mu0 (f - V) + mu1 n.grad(f - V);
+// corrector stage averages with u*: u = (u* + blend)/2; lower boundary faces of
+// non-periodic axes take U_a. Tiles flagged uniform (no body face in the tile
+// or its halo) have mu0 = 1, mu1 = 0 and skip the body arrays.
+template <typename T, int NDIM, bool CORR>
+__global__ void __launch_bounds__(256) k_blend(LevelD<T> L, CVec3P<T> f, const T *mu1n0, long long mstride,
+                                               CVec3P<T> V, CVec3P<T> ustar, Vec3P<T> out) {
+    const GridD &g = L.g;
+    for_cells<NDIM>(g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
+        const int I[3] = {i, j, k};
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            const T fa = f.p[a][idx];
+            T val;
+            if (uni) {
+                val = fa;
+            } else {
+                const T Va = V.p[a][idx];
+                T grad = T(0);
+#pragma unroll
+                for (int b = 0; b < NDIM; ++b) {
+                    const T m = mu1n0[(a * 3 + b) * mstride + idx];
+                    if (m != T(0)) {
+                        int P[3] = {i, j, k}, M[3] = {i, j, k};
+                        P[b] += 1;
+                        M[b] -= 1;
+                        const T up = face_sample<T>(g, f.p[a], P[0], P[1], P[2]) - face_sample<T>(g, V.p[a], P[0], P[1], P[2]);
+                        const T dn = face_sample<T>(g, f.p[a], M[0], M[1], M[2]) - face_sample<T>(g, V.p[a], M[0], M[1], M[2]);
+                        grad += m * T(0.5) * (up - dn);
+                    }
+                }
+                val = Va + L.c[a][idx] * (fa - Va) + grad;
+            }
+            if (CORR) val = T(0.5) * (ustar.p[a][idx] + val);
+            if (!g.per[a] && I[a] == 0) val = (T)g.U[a];
+            out.p[a][idx] = val;
+        }
+    });
+}
+
+// Pressure force F = -sum_I (p_I - pmean) n(x_I) K_eps(d(x_I)) over active cells.
+template <typename T>
+__global__ void k_forces(GridD g, BodyState B, const T *ph, const T *pl, const T *invD, DevScalars *S, double *part) {
+    const T eps = (T)B.eps;
+    const T pm = (T)S->pmean;
+    T acc[3] = {T(0), T(0), T(0)};
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nc;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        decode(g, idx, i, j, k);
+        if (invD[idx] == T(0)) continue;
+        T px[3] = {T(i) + T(0.5), T(j) + T(0.5), T(k) + T(0.5)};
+        T d, nrm[3], v[3];
+        body_eval<T>(B, g.ndim, px, d, nrm, v);
+        if (!(d > -eps - T(0.5) && d < eps + T(0.5))) continue;
+        double pd[3] = {i + 0.5, j + 0.5, k + 0.5}, dd, nd[3], vd[3];
+        body_eval<double>(B, g.ndim, pd, dd, nd, vd);
+        const T K = (T)kkernel<double>(dd, B.eps);
+        if (K == T(0)) continue;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) nrm[a] = (T)nd[a];
+        const T p = (ph[idx] - pm) + pl[idx];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[a] -= p * K * nrm[a];
+    }
+    double out[3];
+    if (grid_reduce<3, false, T>(acc, part, &S->counters[RS_FORCE], out)) {
+        if (threadIdx.x == 0) { S->red[0] = out[0]; S->red[1] = out[1]; S->red[2] = out[2]; }
+    }
+}

@@ -1,0 +1,653 @@
+// k_poisson.cuh -- projection and geometric multigrid kernels.
+//
+// Sec. 2: the velocity is made divergence-free by a pressure projection whose
+// variable-coefficient Poisson equation is solved by geometric multigrid;
+// Sec. 3: the coefficients are c (face mu0) and the gradient update is
+// u[I,a] -= c[I,a] (p[I] - p[I-e_a]);  Sec. 4.2: the multigrid smoother is a
+// preconditioned conjugate gradient.
+//
+//   (A p)[I] = sum_a c_a[I+e_a](p[I+e_a]-p[I]) - c_a[I](p[I]-p[I-e_a])
+//
+// Layout and mapping: every level is swept in tiles of 32 x 8 (x TZ) cells, one
+// 32x8 thread block per tile (grid-stride over tiles), so neighbour offsets are
+// +-1, +-n0, +-n0*n1 with wrap-around only on the domain edge. A per-tile flag
+// marks tiles whose faces (and those of a one-cell halo) all carry the level's
+// fluid coefficient cu (or 0 on the domain boundary): there c and 1/D are
+// formed from the position instead of being loaded.
+//
+// Precision: stencils and smoothing in the working type T. The refinement
+// pressure is an unevaluated pair p = ph + pl of T values (double-T); its
+// residual is evaluated with exact differences (two-sum) and exact products
+// (FMA) wherever the coefficients vary, and by the second difference of exact
+// hi-part differences where they are uniform. Norms and dot products are
+// combined in double across warps and blocks; the coarsest level is solved in
+// double.
+#pragma once
+#include "wl_common.cuh"
+
+template <int NDIM> struct MT {
+    static constexpr int TX = 32, TY = 8, TZ = NDIM == 3 ? 4 : 1;
+};
+
+struct Tiles {
+    int ntx, nty, ntz, nt;
+};
+
+inline Tiles tiles_of(const GridD &g, int TZ) {
+    Tiles t;
+    t.ntx = (g.n[0] + 31) / 32;
+    t.nty = (g.n[1] + 7) / 8;
+    t.ntz = (g.n[2] + TZ - 1) / TZ;
+    t.nt = t.ntx * t.nty * t.ntz;
+    return t;
+}
+
+template <typename T> struct LevelD {
+    GridD g;
+    const T *c[3];
+    T *invD;
+    T *x, *r, *s, *q;
+    T *d[2];
+    const unsigned char *tflag;
+    T cu;    // fluid face coefficient of this level
+    Tiles tl;
+};
+
+// Sweep all cells of a level tile by tile; f(i, j, k, idx, uniform_tile).
+template <int NDIM, typename F>
+__device__ __forceinline__ void for_cells(const GridD &g, const Tiles &tl, const unsigned char *tflag, F &&f) {
+    for (int t = blockIdx.x; t < tl.nt; t += gridDim.x) {
+        const int bx = t % tl.ntx, rr = t / tl.ntx;
+        const int by = rr % tl.nty, bz = rr / tl.nty;
+        const bool uni = tflag ? tflag[t] != 0 : false;
+        const int i = bx * 32 + threadIdx.x, j = by * 8 + threadIdx.y;
+        if (i >= g.n[0] || j >= g.n[1]) continue;
+#pragma unroll
+        for (int kk = 0; kk < MT<NDIM>::TZ; ++kk) {
+            const int k = bz * MT<NDIM>::TZ + kk;
+            if (k >= g.n[2]) break;
+            const long long idx = (long long)i + (long long)g.n[0] * ((long long)j + (long long)g.n[1] * k);
+            f(i, j, k, idx, uni);
+        }
+    }
+}
+
+// Neighbour indices and face coefficients of cell (i,j,k) = idx. In uniform
+// tiles the coefficients come from the position (cu, or 0 on a non-periodic
+// domain face); elsewhere they are loaded.
+template <typename T, int NDIM>
+__device__ __forceinline__ void nb_setup(const LevelD<T> &L, bool uni, int i, int j, int k, long long idx,
+                                         long long (&ip)[3], long long (&im)[3], T (&cp)[3], T (&cm)[3]) {
+    const int I[3] = {i, j, k};
+    const long long st[3] = {1, (long long)L.g.n[0], (long long)L.g.n[0] * L.g.n[1]};
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        const int N = L.g.n[a];
+        const bool top = I[a] == N - 1, bot = I[a] == 0, per = L.g.per[a] != 0;
+        ip[a] = top ? (per ? idx - (long long)(N - 1) * st[a] : idx) : idx + st[a];
+        im[a] = bot ? (per ? idx + (long long)(N - 1) * st[a] : idx) : idx - st[a];
+        if (uni) {
+            cp[a] = (top && !per) ? T(0) : L.cu;
+            cm[a] = (bot && !per) ? T(0) : L.cu;
+        } else {
+            cp[a] = (top && !per) ? T(0) : L.c[a][ip[a]];
+            cm[a] = L.c[a][idx];
+        }
+    }
+}
+
+// 1/D of a cell of a uniform tile (all faces cu except non-periodic domain faces).
+template <typename T, int NDIM>
+__device__ __forceinline__ T invd_uniform(const LevelD<T> &L, int i, int j, int k) {
+    const int I[3] = {i, j, k};
+    int nf = 0;
+#pragma unroll
+    for (int a = 0; a < NDIM; ++a) {
+        if (!L.g.per[a]) nf += (I[a] == 0) + (I[a] == L.g.n[a] - 1);
+    }
+    const int faces = 2 * NDIM - nf;
+    return faces > 0 ? T(-1) / (T(faces) * L.cu) : T(0);
+}
+
+template <typename T, int NDIM>
+__device__ __forceinline__ T invd_at(const LevelD<T> &L, bool uni, int i, int j, int k, long long idx) {
+    return uni ? invd_uniform<T, NDIM>(L, i, j, k) : L.invD[idx];
+}
+
+// ------------------------------------------------------------------ set-up
+// Inverse Jacobi diagonal 1/D, D = -sum of the 2n face coefficients (0 -> 0);
+// counts active rows (D != 0) into S->nact when COUNT.
+template <typename T, int NDIM, bool COUNT>
+__global__ void __launch_bounds__(256) k_invd(LevelD<T> L, DevScalars *S, double *part) {
+    T cnt[1] = {T(0)};
+    for_cells<NDIM>(L.g, L.tl, nullptr, [&](int i, int j, int k, long long idx, bool) {
+        long long ip[3], im[3];
+        T cp[3], cm[3];
+        nb_setup<T, NDIM>(L, false, i, j, k, idx, ip, im, cp, cm);
+        T D = T(0);
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) D -= cp[a] + cm[a];
+        L.invD[idx] = D != T(0) ? T(1) / D : T(0);
+        if (COUNT && D != T(0)) cnt[0] += T(1);
+    });
+    if (COUNT) {
+        double out[1];
+        if (grid_reduce<1, false, T>(cnt, part, &S->counters[RS_INVD], out))
+            if (threadIdx.x == 0 && threadIdx.y == 0) S->nact = out[0];
+    }
+}
+
+// Tile flags: clear the flag of every tile whose cells or one-cell halo have a
+// face coefficient different from the uniform pattern (flags preset to 1).
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_tileflags(LevelD<T> L, unsigned char *flags) {
+    for_cells<NDIM>(L.g, L.tl, nullptr, [&](int i, int j, int k, long long idx, bool) {
+        long long ip[3], im[3];
+        T cp[3], cm[3], up[3], um[3];
+        nb_setup<T, NDIM>(L, false, i, j, k, idx, ip, im, cp, cm);
+        nb_setup<T, NDIM>(L, true, i, j, k, idx, ip, im, up, um);
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) ok = ok && cp[a] == up[a] && cm[a] == um[a];
+        if (ok) return;
+        const int I[3] = {i, j, k};
+        const int TZ = MT<NDIM>::TZ;
+        for (int dz = (NDIM == 3 ? -1 : 0); dz <= (NDIM == 3 ? 1 : 0); ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int J[3] = {I[0] + dx, I[1] + dy, I[2] + dz};
+                    bool skip = false;
+                    for (int a = 0; a < NDIM; ++a) {
+                        if (J[a] < 0 || J[a] >= L.g.n[a]) {
+                            if (L.g.per[a]) J[a] = wrapi(J[a], L.g.n[a]);
+                            else skip = true;
+                        }
+                    }
+                    if (skip) continue;
+                    const int t = (J[0] / 32) + L.tl.ntx * ((J[1] / 8) + L.tl.nty * (J[2] / TZ));
+                    flags[t] = 0;
+                }
+    });
+}
+
+// Coarse coefficients: half the sum of the 2^(n-1) fine faces on each coarse face.
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_coarsen_c(GridD gf, CVec3P<T> cf, LevelD<T> C, Vec3P<T> cc) {
+    for_cells<NDIM>(C.g, C.tl, nullptr, [&](int i, int j, int k, long long idx, bool) {
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            T s = T(0);
+            for (int oz = 0; oz < (NDIM == 3 ? 2 : 1); ++oz)
+                for (int oy = 0; oy < 2; ++oy)
+                    for (int ox = 0; ox < 2; ++ox) {
+                        const int o[3] = {ox, oy, oz};
+                        if (o[a] != 0) continue;
+                        s += cf.p[a][lin3(gf, 2 * i + ox, 2 * j + oy, 2 * k + oz)];
+                    }
+            cc.p[a][idx] = T(0.5) * s;
+        }
+    });
+}
+
+// --------------------------------------------------------- right-hand side
+// b = div(u) / (w dt) (Sec. 2 projection) and its sum / sum of squares over
+// active rows -> mean and |b - mean|.
+template <typename T>
+__device__ __forceinline__ void two_sum(T a, T b, T &s, T &e);
+
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_div(LevelD<T> L, CVec3P<T> u, const T *ue, T inv_wdt, T *b, T *bl,
+                                             DevScalars *S, double *part) {
+    const GridD &g = L.g;
+    T acc[2] = {T(0), T(0)};
+    for_cells<NDIM>(g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
+        const int I[3] = {i, j, k};
+        const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
+        // divergence of the stored velocity as an unevaluated pair (exact
+        // face differences, two-sum accumulation), then scaled by 1/(w dt)
+        T sh = T(0), sl = T(0);
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            T up;
+            if (I[a] + 1 < g.n[a]) up = u.p[a][idx + st[a]];
+            else if (g.per[a]) up = u.p[a][idx - (long long)(g.n[a] - 1) * st[a]];
+            else up = (a == 0 && g.exit_x) ? ue[j + (long long)g.n[1] * k] : (T)g.U[a];
+            T d, de, s2, e2;
+            two_sum(up, -u.p[a][idx], d, de);
+            two_sum(sh, d, s2, e2);
+            sh = s2;
+            sl += e2 + de;
+        }
+        T h = sh + sl;
+        T l = sl - (h - sh);
+        const T bh = h * inv_wdt;
+        const T blo = fma(h, inv_wdt, -bh) + l * inv_wdt;
+        const T s = bh + blo;
+        b[idx] = s;
+        bl[idx] = blo - (s - bh);
+        if (uni || L.invD[idx] != T(0)) { acc[0] += s; acc[1] += s * s; }
+    });
+    double out[2];
+    if (grid_reduce<2, false, T>(acc, part, &S->counters[RS_DIV], out)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const double n = S->nact > 0 ? S->nact : 1.0;
+            S->bsum = out[0];
+            S->bsq = out[1];
+            S->bmean = out[0] / n;
+            const double v = out[1] - out[0] * out[0] / n;
+            S->bnorm = sqrt(v > 0 ? v : 0.0);
+            if (!(out[1] == out[1]) || out[1] > 1e300) S->status |= 1;
+        }
+    }
+}
+
+// Statistics of a given right-hand side b over active rows.
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_bstats(LevelD<T> L, const T *b, DevScalars *S, double *part) {
+    T acc[2] = {T(0), T(0)};
+    for_cells<NDIM>(L.g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
+        if (uni || L.invD[idx] != T(0)) { const T v = b[idx]; acc[0] += v; acc[1] += v * v; }
+    });
+    double out[2];
+    if (grid_reduce<2, false, T>(acc, part, &S->counters[RS_DIV], out)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const double n = S->nact > 0 ? S->nact : 1.0;
+            S->bsum = out[0];
+            S->bsq = out[1];
+            S->bmean = out[0] / n;
+            const double v = out[1] - out[0] * out[0] / n;
+            S->bnorm = sqrt(v > 0 ? v : 0.0);
+            if (!(out[1] == out[1]) || out[1] > 1e300) S->status |= 1;
+        }
+    }
+}
+
+// ---------------------------------------------------- refinement residual
+// Exact pair arithmetic on T (two-sum, FMA two-product).
+template <typename T>
+__device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
+    s = a + b;
+    const T bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// c * (pN - p0) as an unevaluated pair, from the pairs (hN, lN), (h0, l0).
+template <typename T>
+__device__ __forceinline__ void face_term(T hN, T lN, T h0, T l0, T c, T &th, T &tl) {
+    T s, e;
+    two_sum(hN, -h0, s, e);
+    e += lN - l0;
+    const T dh = s + e;
+    const T dl = e - (dh - s);
+    th = c * dh;
+    tl = fma(c, dh, -th) + c * dl;
+}
+
+// r = (b - mean) - A (ph + pl) at active rows (0 elsewhere) into the fine-level
+// right-hand side; |r| / |b - mean| -> S->rel.
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_resid(LevelD<T> L, const T *b, const T *bl, const T *ph, const T *pl,
+                                               DevScalars *S, double *part) {
+    const T bm = (T)S->bmean;
+    const T bml = (T)(S->bmean - (double)bm);
+    T acc[1] = {T(0)};
+    for_cells<NDIM>(L.g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
+        long long ip[3], im[3];
+        T cp[3], cm[3];
+        nb_setup<T, NDIM>(L, uni, i, j, k, idx, ip, im, cp, cm);
+        T res = T(0);
+        if (uni || L.invD[idx] != T(0)) {
+            const T h0 = ph[idx], l0 = pl[idx];
+            T Ah = T(0), Al = T(0);
+#pragma unroll
+            for (int a = 0; a < NDIM; ++a) {
+                if (cp[a] == cm[a]) {
+                    // equal faces: c [(p+ - p) - (p - p-)], the second difference
+                    // formed exactly (two-sums) before the single rounding
+                    T hp, ehp, hm, ehm, s2, es, th, tl, s, e;
+                    two_sum(ph[ip[a]], -h0, hp, ehp);
+                    two_sum(h0, -ph[im[a]], hm, ehm);
+                    two_sum(hp, -hm, s2, es);
+                    const T lo = ((ehp - ehm) + es) + ((pl[ip[a]] - l0) - (l0 - pl[im[a]]));
+                    th = cm[a] * s2;
+                    tl = fma(cm[a], s2, -th) + cm[a] * lo;
+                    two_sum(Ah, th, s, e);
+                    Ah = s;
+                    Al += e + tl;
+                } else {
+                    T th, tl, s, e;
+                    face_term(ph[ip[a]], pl[ip[a]], h0, l0, cp[a], th, tl);
+                    two_sum(Ah, th, s, e);
+                    Ah = s;
+                    Al += e + tl;
+                    face_term(ph[im[a]], pl[im[a]], h0, l0, cm[a], th, tl);
+                    two_sum(Ah, th, s, e);
+                    Ah = s;
+                    Al += e + tl;
+                }
+            }
+            res = (((b[idx] - bm) - Ah) + (bl[idx] - bml)) - Al;
+            acc[0] += res * res;
+        }
+        L.r[idx] = res;
+    });
+    double out[1];
+    if (grid_reduce<1, false, T>(acc, part, &S->counters[RS_RESID], out)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            S->rnorm2 = out[0];
+            const double bn = S->bnorm;
+            const double rel = bn > 0 ? sqrt(out[0]) / bn : (out[0] > 0 ? 1e300 : 0.0);
+            S->rel = rel;
+            if (!(rel == rel) || !(bn == bn) || rel >= 1e300) S->status |= 1;
+        }
+    }
+}
+
+// Restriction: coarse r = sum of the 2^n fine children.
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_restrict(GridD gf, const T *rf, LevelD<T> C) {
+    for_cells<NDIM>(C.g, C.tl, nullptr, [&](int i, int j, int k, long long idx, bool) {
+        T s = T(0);
+        for (int oz = 0; oz < (NDIM == 3 ? 2 : 1); ++oz)
+            for (int oy = 0; oy < 2; ++oy) {
+                const long long base = lin3(gf, 2 * i, 2 * j + oy, 2 * k + oz);
+                s += rf[base] + rf[base + 1];
+            }
+        C.r[idx] = s;
+    });
+}
+
+// Parent (injection) index of the fine cell (i,j,k) offset by o along axis a,
+// wrapped on periodic axes, clamped otherwise (its coefficient is 0 there).
+__device__ __forceinline__ long long parent_off(const GridD &gf, const GridD &gc, int i, int j, int k, int a, int o) {
+    int I[3] = {i, j, k};
+    I[a] += o;
+    if (I[a] < 0) I[a] = gf.per[a] ? gf.n[a] - 1 : 0;
+    if (I[a] >= gf.n[a]) I[a] = gf.per[a] ? 0 : gf.n[a] - 1;
+    return lin3(gc, I[0] >> 1, I[1] >> 1, gf.ndim == 3 ? (I[2] >> 1) : 0);
+}
+
+// PCG start on a level after the coarse correction: x = P x_c (injection),
+// s = r - A x, z = D^-1 s, d = z, rho = <s, z>.
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_pcg_init(LevelD<T> L, GridD gc, const T *xc, DevScalars *S, double *part,
+                                                  int lev) {
+    T acc[1] = {T(0)};
+    for_cells<NDIM>(L.g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
+        const T x0 = xc[lin3(gc, i >> 1, j >> 1, NDIM == 3 ? (k >> 1) : 0)];
+        L.x[idx] = x0;
+        const T iD = invd_at<T, NDIM>(L, uni, i, j, k, idx);
+        T s = T(0);
+        if (iD != T(0)) {
+            long long ip[3], im[3];
+            T cp[3], cm[3];
+            nb_setup<T, NDIM>(L, uni, i, j, k, idx, ip, im, cp, cm);
+            T Ax = T(0);
+#pragma unroll
+            for (int a = 0; a < NDIM; ++a)
+                Ax += cp[a] * (xc[parent_off(L.g, gc, i, j, k, a, 1)] - x0) -
+                      cm[a] * (x0 - xc[parent_off(L.g, gc, i, j, k, a, -1)]);
+            s = L.r[idx] - Ax;
+        }
+        const T z = iD * s;
+        L.s[idx] = s;
+        L.d[0][idx] = z;
+        acc[0] += s * z;
+    });
+    double out[1];
+    if (grid_reduce<1, false, T>(acc, part, &S->counters[RS_INIT], out))
+        if (threadIdx.x == 0 && threadIdx.y == 0) S->rho[lev] = out[0];
+}
+
+// PCG step part 1: the search direction d (iteration it > 0: d = D^-1 s + beta
+// d_prev, formed at every stencil point) and q = A d; alpha = rho / <d, q>.
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_pcg_q(LevelD<T> L, DevScalars *S, double *part, int lev, int it) {
+    const T *dprev = L.d[(it + 1) & 1];
+    T *dcur = L.d[it & 1];
+    const T beta = it > 0 ? (T)S->beta[lev] : T(0);
+    T acc[1] = {T(0)};
+    for_cells<NDIM>(L.g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
+        long long ip[3], im[3];
+        T cp[3], cm[3];
+        nb_setup<T, NDIM>(L, uni, i, j, k, idx, ip, im, cp, cm);
+        T d0;
+        if (it == 0) {
+            d0 = dcur[idx];
+        } else {
+            d0 = invd_at<T, NDIM>(L, uni, i, j, k, idx) * L.s[idx] + beta * dprev[idx];
+            dcur[idx] = d0;
+        }
+        const int I[3] = {i, j, k};
+        T Ad = T(0);
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            T dp, dm;
+            if (it == 0) {
+                dp = dcur[ip[a]];
+                dm = dcur[im[a]];
+            } else {
+                T iDp, iDm;
+                if (uni) {
+                    int P[3] = {I[0], I[1], I[2]}, M[3] = {I[0], I[1], I[2]};
+                    P[a] = (P[a] + 1 == L.g.n[a]) ? (L.g.per[a] ? 0 : P[a]) : P[a] + 1;
+                    M[a] = (M[a] == 0) ? (L.g.per[a] ? L.g.n[a] - 1 : 0) : M[a] - 1;
+                    iDp = invd_uniform<T, NDIM>(L, P[0], P[1], P[2]);
+                    iDm = invd_uniform<T, NDIM>(L, M[0], M[1], M[2]);
+                } else {
+                    iDp = L.invD[ip[a]];
+                    iDm = L.invD[im[a]];
+                }
+                dp = iDp * L.s[ip[a]] + beta * dprev[ip[a]];
+                dm = iDm * L.s[im[a]] + beta * dprev[im[a]];
+            }
+            Ad += cp[a] * (dp - d0) - cm[a] * (d0 - dm);
+        }
+        L.q[idx] = Ad;
+        acc[0] += d0 * Ad;
+    });
+    double out[1];
+    if (grid_reduce<1, false, T>(acc, part, &S->counters[RS_Q], out))
+        if (threadIdx.x == 0 && threadIdx.y == 0) S->alpha[lev] = out[0] != 0.0 ? S->rho[lev] / out[0] : 0.0;
+}
+
+// PCG step part 2: x += alpha d; s -= alpha q; rho' = <s, D^-1 s>; beta = rho'/rho.
+// On the last iteration only x is updated; on the fine level the correction
+// is added straight into the refinement pressure (ph, pl) instead.
+template <typename T, int NDIM, bool LAST, bool FINE>
+__global__ void __launch_bounds__(256) k_pcg_u(LevelD<T> L, T *ph, T *pl, DevScalars *S, double *part, int lev,
+                                               int it) {
+    const T *dcur = L.d[it & 1];
+    const T alpha = (T)S->alpha[lev];
+    T acc[1] = {T(0)};
+    for_cells<NDIM>(L.g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
+        const T xn = L.x[idx] + alpha * dcur[idx];
+        if (LAST && FINE) {
+            T sh, err;
+            two_sum(ph[idx], xn, sh, err);
+            const T lo = pl[idx] + err;
+            const T hi = sh + lo;
+            ph[idx] = hi;
+            pl[idx] = lo - (hi - sh);
+        } else {
+            L.x[idx] = xn;
+        }
+        if (!LAST) {
+            const T s = L.s[idx] - alpha * L.q[idx];
+            L.s[idx] = s;
+            acc[0] += s * invd_at<T, NDIM>(L, uni, i, j, k, idx) * s;
+        }
+    });
+    if (!LAST) {
+        double out[1];
+        if (grid_reduce<1, false, T>(acc, part, &S->counters[RS_U], out))
+            if (threadIdx.x == 0 && threadIdx.y == 0) {
+                const double rho = S->rho[lev];
+                S->beta[lev] = rho != 0.0 ? out[0] / rho : 0.0;
+                S->rho[lev] = out[0];
+            }
+    }
+}
+
+// Single-level case: the coarse solve itself is the fine correction.
+template <typename T>
+__global__ void k_padd(GridD g, const T *x, T *ph, T *pl) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nc;
+         idx += (long long)gridDim.x * blockDim.x) {
+        T sh, err;
+        two_sum(ph[idx], x[idx], sh, err);
+        const T lo = pl[idx] + err;
+        const T hi = sh + lo;
+        ph[idx] = hi;
+        pl[idx] = lo - (hi - sh);
+    }
+}
+
+// Coarsest level: one block, double-precision Jacobi-PCG on the mean-free part
+// of the right-hand side over active rows, to 1e-12 relative or maxit; the
+// mean-free solution is written to L.x. w: 4*nc doubles of scratch.
+template <typename T>
+__global__ void k_coarsest(LevelD<T> L, double *w, int maxit) {
+    const GridD &g = L.g;
+    const long long n = g.nc;
+    double *xs = w, *ss = w + n, *ds = w + 2 * n, *qs = w + 3 * n;
+    __shared__ double sh[64];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
+    double v1[1], o1[1];
+    double sr = 0.0, na = 0.0;
+    for (long long e = tid; e < n; e += nt)
+        if (L.invD[e] != T(0)) { sr += (double)L.r[e]; na += 1.0; }
+    double v2[2] = {sr, na}, o2[2];
+    block_reduce<2, false, double>(v2, o2, sh);
+    if (tid == 0) { sh[40] = o2[0]; sh[41] = o2[1]; }
+    __syncthreads();
+    const double rmean = sh[41] > 0 ? sh[40] / sh[41] : 0.0, nact = sh[41];
+    __syncthreads();
+    double r0 = 0.0, rho = 0.0;
+    for (long long e = tid; e < n; e += nt) {
+        const bool act = L.invD[e] != T(0);
+        const double s = act ? (double)L.r[e] - rmean : 0.0;
+        xs[e] = 0.0;
+        ss[e] = s;
+        ds[e] = (double)L.invD[e] * s;
+        rho += s * ds[e];
+        r0 += s * s;
+    }
+    double v3[2] = {rho, r0}, o3[2];
+    block_reduce<2, false, double>(v3, o3, sh);
+    if (tid == 0) { sh[40] = o3[0]; sh[41] = o3[1]; }
+    __syncthreads();
+    rho = sh[40];
+    const double rnorm0 = sqrt(sh[41]);
+    __syncthreads();
+    for (int it = 0; it < maxit; ++it) {
+        if (rho == 0.0) break;
+        double dq = 0.0;
+        for (long long e = tid; e < n; e += nt) {
+            const long long q = e / g.n[0];
+            const int I[3] = {(int)(e - q * g.n[0]), (int)(q % g.n[1]), (int)(q / g.n[1])};
+            double Ad = 0.0;
+            const double d0 = ds[e];
+            for (int a = 0; a < g.ndim; ++a) {
+                const int N = g.n[a];
+                const bool top = I[a] == N - 1, bot = I[a] == 0, per = g.per[a] != 0;
+                const long long ip = top ? (per ? e - (long long)(N - 1) * st[a] : e) : e + st[a];
+                const long long im = bot ? (per ? e + (long long)(N - 1) * st[a] : e) : e - st[a];
+                const double cp = (top && !per) ? 0.0 : (double)L.c[a][ip];
+                const double cm = (double)L.c[a][e];
+                Ad += cp * (ds[ip] - d0) - cm * (d0 - ds[im]);
+            }
+            qs[e] = Ad;
+            dq += d0 * Ad;
+        }
+        v1[0] = dq;
+        block_reduce<1, false, double>(v1, o1, sh);
+        if (tid == 0) sh[40] = o1[0];
+        __syncthreads();
+        dq = sh[40];
+        __syncthreads();
+        if (dq == 0.0) break;
+        const double alpha = rho / dq;
+        double rn = 0.0, ss2 = 0.0;
+        for (long long e = tid; e < n; e += nt) {
+            xs[e] += alpha * ds[e];
+            const double s = ss[e] - alpha * qs[e];
+            ss[e] = s;
+            rn += s * (double)L.invD[e] * s;
+            ss2 += s * s;
+        }
+        v3[0] = rn;
+        v3[1] = ss2;
+        block_reduce<2, false, double>(v3, o3, sh);
+        if (tid == 0) { sh[40] = o3[0]; sh[41] = o3[1]; }
+        __syncthreads();
+        const double rho2 = sh[40], sn = sqrt(sh[41]);
+        __syncthreads();
+        const double beta = rho2 / rho;
+        rho = rho2;
+        for (long long e = tid; e < n; e += nt) ds[e] = (double)L.invD[e] * ss[e] + beta * ds[e];
+        __syncthreads();
+        if (sn <= 1e-12 * rnorm0) break;
+    }
+    double sx = 0.0;
+    for (long long e = tid; e < n; e += nt)
+        if (L.invD[e] != T(0)) sx += xs[e];
+    v1[0] = sx;
+    block_reduce<1, false, double>(v1, o1, sh);
+    if (tid == 0) sh[40] = o1[0];
+    __syncthreads();
+    const double xm = nact > 0 ? sh[40] / nact : 0.0;
+    for (long long e = tid; e < n; e += nt) L.x[e] = L.invD[e] != T(0) ? (T)(xs[e] - xm) : T(0);
+}
+
+// ------------------------------------------------------------- projection
+// Pressure-gradient update (Sec. 3 listing): u_a[I] -= w dt c_a[I] (p[I] - p[I-e_a]).
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_grad(LevelD<T> L, const T *ph, const T *pl, T wdt, Vec3P<T> u) {
+    for_cells<NDIM>(L.g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
+        long long ip[3], im[3];
+        T cp[3], cm[3];
+        nb_setup<T, NDIM>(L, uni, i, j, k, idx, ip, im, cp, cm);
+        const T h0 = ph[idx], l0 = pl[idx];
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            if (cm[a] == T(0)) continue;
+            const T dp = (h0 - ph[im[a]]) + (l0 - pl[im[a]]);
+            u.p[a][idx] -= wdt * cm[a] * dp;
+        }
+    });
+}
+
+// Mean of the pressure over active rows -> S->pmean.
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_pmean(LevelD<T> L, const T *ph, const T *pl, DevScalars *S, double *part) {
+    T acc[2] = {T(0), T(0)};
+    for_cells<NDIM>(L.g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
+        if (uni || L.invD[idx] != T(0)) { acc[0] += ph[idx]; acc[1] += pl[idx]; }
+    });
+    double out[2];
+    if (grid_reduce<2, false, T>(acc, part, &S->counters[RS_PMEAN], out))
+        if (threadIdx.x == 0 && threadIdx.y == 0) S->pmean = S->nact > 0 ? (out[0] + out[1]) / S->nact : 0.0;
+}
+
+// Reported pressure: p - mean on active rows, 0 elsewhere (double).
+template <typename T>
+__global__ void k_pout(GridD g, const T *ph, const T *pl, const T *invD, const DevScalars *S, double *p) {
+    const double pm = S->pmean;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nc;
+         idx += (long long)gridDim.x * blockDim.x)
+        p[idx] = invD[idx] != T(0) ? ((double)ph[idx] - pm) + (double)pl[idx] : 0.0;
+}
+
+// Warm start from doubles: split into (hi, lo).
+template <typename T>
+__global__ void k_pin(GridD g, const double *p, T *ph, T *pl) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nc;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const double v = p[idx];
+        const T h = (T)v;
+        ph[idx] = h;
+        pl[idx] = (T)(v - (double)h);
+    }
+}

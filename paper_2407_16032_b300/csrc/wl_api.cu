@@ -1,0 +1,897 @@
+// wl_api.cu -- host driver of the BDIM time step and the C ABI of include/wl.h.
+//
+// One simulation owns every device array of the step; the step enqueues its
+// kernels on the caller's stream and reads back one small block of scalars per
+// multigrid V-cycle (convergence test) and per step (time step, status).
+// The V-cycle (restrictions, coarsest solve, prolongation + PCG smoothing on
+// every level, and the next refinement residual) is one CUDA graph.
+#include "../../include/wl.h"
+#include "wl_common.cuh"
+#include "k_flux.cuh"
+#include "k_body.cuh"
+#include "k_poisson.cuh"
+#include "k_misc.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+namespace {
+
+const double PI = 3.14159265358979323846;
+
+struct Err {
+    int code;
+    std::string msg;
+};
+
+#define WL_CK(call)                                                                         \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            throw Err{WL_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};     \
+        }                                                                                   \
+    } while (0)
+
+#define WL_LAUNCH_CK()                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = cudaGetLastError();                                                \
+        if (e_ != cudaSuccess) throw Err{WL_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e_)}; \
+    } while (0)
+
+struct SimBase {
+    wl_config cfg{};
+    wl_body body{};
+    std::string err;
+    virtual ~SimBase() {}
+    virtual void set_velocity(const void *u, const void *ue) = 0;
+    virtual void get_velocity(void *u, void *ue) = 0;
+    virtual void get_pressure(double *p) = 0;
+    virtual void set_pressure(const double *p) = 0;
+    virtual int mom_step(double dt_fixed, wl_step_stats *st) = 0;
+    virtual int project(double w, double dt, wl_solve_stats *st) = 0;
+    virtual int poisson_solve(const void *b, double *p, wl_solve_stats *st) = 0;
+    virtual void conv_diff(const void *u, const void *ue, void *r) = 0;
+    virtual void forces(double *F) = 0;
+    virtual void body_update(double t) = 0;
+    virtual void get_body_fields(void *c, void *mu1n, void *V) = 0;
+    virtual void diagnostics(double *ke, double *ens, double *maxdiv) = 0;
+    virtual void info(int *levels, long long *launches) = 0;
+    virtual void profile(int on) = 0;
+    virtual std::string profile_report() = 0;
+    double t = 0.0, dt_next = 0.25;
+};
+
+// Per-kernel timing with CUDA events on the sim's stream (profiling mode only:
+// the V-cycle then runs as direct launches instead of its graph).
+struct Prof {
+    struct Rec { const char *name; int level; long long cells; cudaEvent_t a, b; };
+    bool on = false;
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    std::map<std::pair<std::string, int>, std::pair<long long, std::pair<double, long long>>> acc;
+    cudaEvent_t get() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e;
+        WL_CK(cudaEventCreate(&e));
+        return e;
+    }
+    void beg(cudaStream_t s, const char *name, int level, long long cells) {
+        if (!on) return;
+        Rec r{name, level, cells, get(), get()};
+        WL_CK(cudaEventRecord(r.a, s));
+        pending.push_back(r);
+    }
+    void end(cudaStream_t s) {
+        if (!on || pending.empty()) return;
+        WL_CK(cudaEventRecord(pending.back().b, s));
+    }
+    void flush() {
+        for (auto &r : pending) {
+            WL_CK(cudaEventSynchronize(r.b));
+            float ms = 0.f;
+            WL_CK(cudaEventElapsedTime(&ms, r.a, r.b));
+            auto &v = acc[{std::string(r.name), r.level}];
+            v.first += 1;
+            v.second.first += ms;
+            v.second.second = r.cells;
+            pool.push_back(r.a);
+            pool.push_back(r.b);
+        }
+        pending.clear();
+    }
+    ~Prof() {
+        for (auto &r : pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+template <typename T, int ND>
+struct Sim : SimBase {
+    cudaStream_t st = nullptr;
+    cudaStream_t cap = nullptr;
+    int nsm = 148, maxb = 1184;
+    GridD g{};
+    int nlev = 1;
+    GridD gl[WL_MAXLEV];
+    std::vector<void *> allocs;
+    // fields
+    T *vel[4][3] = {};
+    int cur = 0;
+    T *ueA = nullptr, *ueB = nullptr, *ueC = nullptr;
+    T *mu1n = nullptr;
+    T *Vb[3] = {};
+    T *b = nullptr, *bl = nullptr, *ph = nullptr, *pl = nullptr;
+    LevelD<T> lv[WL_MAXLEV];
+    T *lc[WL_MAXLEV][3] = {};
+    unsigned char *tfl[WL_MAXLEV] = {};
+    double *cw = nullptr;   // coarsest scratch
+    double *pout = nullptr; // reported pressure scratch
+    DevScalars *S = nullptr, *hS = nullptr;
+    double *part = nullptr;
+    cudaGraphExec_t vexec = nullptr;
+    long long vnodes = 0;
+    long long launches = 0;
+    bool has_body = false, moving = false;
+    double body_t = -1.0;
+    int np = 1;
+    Prof prof;
+    void P0(const char *name, int level, long long cells) { prof.beg(st, name, level, cells); }
+    void P1() { prof.end(st); }
+
+    void *dalloc(size_t bytes) {
+        void *p = nullptr;
+        bytes = (bytes + 255) & ~size_t(255);
+        if (cfg.allocator.alloc) {
+            p = cfg.allocator.alloc(cfg.allocator.ctx, bytes);
+            if (!p) throw Err{WL_ERR_ALLOC, "allocator callback returned NULL"};
+        } else {
+            cudaError_t e = cudaMalloc(&p, bytes);
+            if (e != cudaSuccess) throw Err{WL_ERR_ALLOC, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
+        }
+        allocs.push_back(p);
+        WL_CK(cudaMemsetAsync(p, 0, bytes, st));
+        return p;
+    }
+    template <typename Q> Q *alloc_n(size_t n) { return (Q *)dalloc(n * sizeof(Q)); }
+
+    int blocks(long long n) const {
+        long long b = (n + 255) / 256;
+        return (int)(b < maxb ? (b < 1 ? 1 : b) : maxb);
+    }
+    // tiled kernels: one 32x8 block per tile, grid-stride over tiles
+    int tgrid(int l) const { return lv[l].tl.nt < maxb ? lv[l].tl.nt : maxb; }
+    dim3 tblk() const { return dim3(32, 8, 1); }
+
+    ~Sim() override {
+        if (vexec) cudaGraphExecDestroy(vexec);
+        if (cap) cudaStreamDestroy(cap);
+        if (hS) cudaFreeHost(hS);
+        for (void *p : allocs) {
+            if (cfg.allocator.alloc) {
+                if (cfg.allocator.free) cfg.allocator.free(cfg.allocator.ctx, p);
+            } else {
+                cudaFree(p);
+            }
+        }
+    }
+
+    void init(const wl_config &c, const wl_body *bd) {
+        cfg = c;
+        st = (cudaStream_t)c.stream;
+        if (bd) body = *bd; else { std::memset(&body, 0, sizeof(body)); body.kind = WL_BODY_NONE; }
+        int dev = 0;
+        WL_CK(cudaGetDevice(&dev));
+        WL_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        maxb = nsm * 8;
+        if (maxb > WL_MAXPART) maxb = WL_MAXPART;
+        WL_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        WL_CK(cudaMallocHost(&hS, sizeof(DevScalars)));
+        g.ndim = c.ndim;
+        for (int a = 0; a < 3; ++a) {
+            g.n[a] = (a < c.ndim) ? c.n[a] : 1;
+            g.per[a] = (a < c.ndim) ? (c.periodic[a] != 0) : 0;
+            g.U[a] = (a < c.ndim) ? c.U[a] : 0.0;
+        }
+        g.exit_x = c.exit_hi_x != 0;
+        g.nu = c.nu;
+        g.nc = (long long)g.n[0] * g.n[1] * g.n[2];
+        np = g.n[1] * g.n[2];
+        has_body = body.kind != WL_BODY_NONE;
+        moving = has_body && (body.heave_amp != 0.0 || body.pitch_amp != 0.0);
+        const long long nc = g.nc;
+        for (int q = 0; q < 4; ++q)
+            for (int a = 0; a < g.ndim; ++a) vel[q][a] = alloc_n<T>(nc);
+        ueA = alloc_n<T>(np);
+        ueB = alloc_n<T>(np);
+        ueC = alloc_n<T>(np);
+        if (has_body) {
+            mu1n = alloc_n<T>((size_t)9 * nc);
+            for (int a = 0; a < g.ndim; ++a) Vb[a] = alloc_n<T>(nc);
+        }
+        b = alloc_n<T>(nc);
+        bl = alloc_n<T>(nc);
+        ph = alloc_n<T>(nc);
+        pl = alloc_n<T>(nc);
+        S = alloc_n<DevScalars>(1);
+        part = alloc_n<double>(8 * WL_MAXPART);
+        // multigrid hierarchy: halve every axis while all are even and >= 8
+        gl[0] = g;
+        nlev = 1;
+        while (nlev < WL_MAXLEV) {
+            const GridD &f = gl[nlev - 1];
+            bool ok = true;
+            for (int a = 0; a < g.ndim; ++a)
+                if ((f.n[a] % 2) != 0 || f.n[a] / 2 < 4) ok = false;
+            if (!ok) break;
+            GridD cg = f;
+            for (int a = 0; a < g.ndim; ++a) cg.n[a] = f.n[a] / 2;
+            cg.nc = (long long)cg.n[0] * cg.n[1] * cg.n[2];
+            gl[nlev++] = cg;
+        }
+        for (int l = 0; l < nlev; ++l) {
+            const long long m = gl[l].nc;
+            LevelD<T> &L = lv[l];
+            L.g = gl[l];
+            for (int a = 0; a < 3; ++a) {
+                lc[l][a] = (a < g.ndim) ? alloc_n<T>(m) : nullptr;
+                L.c[a] = lc[l][a];
+            }
+            L.invD = alloc_n<T>(m);
+            L.x = alloc_n<T>(m);
+            L.r = alloc_n<T>(m);
+            L.s = alloc_n<T>(m);
+            L.q = alloc_n<T>(m);
+            L.d[0] = alloc_n<T>(m);
+            L.d[1] = alloc_n<T>(m);
+            L.tl = tiles_of(gl[l], MT<ND>::TZ);
+            tfl[l] = alloc_n<unsigned char>(L.tl.nt);
+            L.tflag = tfl[l];
+            L.cu = (T)std::pow(2.0, (double)l * (ND - 2));
+        }
+        cw = alloc_n<double>(4 * gl[nlev - 1].nc);
+        // initial state: u = 0 with U on boundary normal faces, exit plane U_x
+        t = 0.0;
+        dt_next = c.dt_init;
+        set_velocity_fill();
+        body_update(0.0);
+        build_vcycle_graph();
+        WL_CK(cudaStreamSynchronize(st));
+    }
+
+    // ------------------------------------------------------------ helpers
+    CVec3P<T> cv(int q) const { CVec3P<T> r{}; for (int a = 0; a < 3; ++a) r.p[a] = vel[q][a]; return r; }
+    Vec3P<T> vv(int q) const { Vec3P<T> r{}; for (int a = 0; a < 3; ++a) r.p[a] = vel[q][a]; return r; }
+    CVec3P<T> cc0() const { CVec3P<T> r{}; for (int a = 0; a < 3; ++a) r.p[a] = lc[0][a]; return r; }
+
+    void fill_boundary(int q) {
+        k_bc_lower<T><<<blocks(g.nc), 256, 0, st>>>(g, vv(q));
+        WL_LAUNCH_CK();
+        ++launches;
+    }
+
+    void set_velocity_fill() {
+        for (int a = 0; a < g.ndim; ++a) WL_CK(cudaMemsetAsync(vel[cur][a], 0, g.nc * sizeof(T), st));
+        fill_boundary(cur);
+        k_fill<T><<<blocks(np), 256, 0, st>>>((long long)np, (T)g.U[0], ueA);
+        WL_LAUNCH_CK();
+        ++launches;
+    }
+
+    BodyState body_state(double tt) const {
+        BodyState B{};
+        B.kind = body.kind;
+        B.eps = cfg.eps;
+        double c[3] = {body.centre[0], body.centre[1], body.centre[2]};
+        double vc[3] = {0, 0, 0};
+        const int ax = body.heave_axis;
+        if (ax >= 0 && ax < 3) {
+            c[ax] += body.heave_amp * std::sin(body.omega * tt + body.phase);
+            vc[ax] = body.heave_amp * body.omega * std::cos(body.omega * tt + body.phase);
+        }
+        for (int a = 0; a < 3; ++a) {
+            B.chi[a] = std::floor(c[a]);
+            B.clo[a] = c[a] - B.chi[a];
+            B.vc[a] = vc[a];
+        }
+        B.radius = body.radius;
+        B.sa = body.semi[0];
+        B.sb = body.semi[1];
+        const double th = body.pitch_amp * std::sin(body.omega * tt + body.phase + 0.5 * PI);
+        B.thd = body.pitch_amp * body.omega * std::cos(body.omega * tt + body.phase + 0.5 * PI);
+        B.cth = std::cos(th);
+        B.sth = std::sin(th);
+        return B;
+    }
+
+    void read_scalars() {
+        WL_CK(cudaMemcpyAsync(hS, S, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+        WL_CK(cudaStreamSynchronize(st));
+    }
+
+    // ------------------------------------------------------------ body
+    void body_update(double tt) override {
+        BodyState B = body_state(tt);
+        Vec3P<T> c{}, V{};
+        for (int a = 0; a < 3; ++a) { c.p[a] = lc[0][a]; V.p[a] = Vb[a]; }
+        P0("measure", 0, g.nc);
+        k_measure<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], B, c, mu1n, (long long)g.nc, V, has_body);
+        P1();
+        WL_LAUNCH_CK();
+        ++launches;
+        for (int l = 1; l < nlev; ++l) {
+            CVec3P<T> cf{};
+            Vec3P<T> cc{};
+            for (int a = 0; a < 3; ++a) { cf.p[a] = lc[l - 1][a]; cc.p[a] = lc[l][a]; }
+            k_coarsen_c<T, ND><<<tgrid(l), tblk(), 0, st>>>(gl[l - 1], cf, lv[l], cc);
+            WL_LAUNCH_CK();
+            ++launches;
+        }
+        for (int l = 0; l < nlev; ++l) {
+            if (l == 0) k_invd<T, ND, true><<<tgrid(l), tblk(), 0, st>>>(lv[l], S, part);
+            else k_invd<T, ND, false><<<tgrid(l), tblk(), 0, st>>>(lv[l], S, part);
+            WL_LAUNCH_CK();
+            WL_CK(cudaMemsetAsync(tfl[l], 1, lv[l].tl.nt, st));
+            k_tileflags<T, ND><<<tgrid(l), tblk(), 0, st>>>(lv[l], tfl[l]);
+            WL_LAUNCH_CK();
+            launches += 2;
+        }
+        body_t = tt;
+    }
+
+    void get_body_fields(void *c, void *m1, void *V) override {
+        const size_t bytes = g.nc * sizeof(T);
+        for (int a = 0; a < g.ndim; ++a) {
+            if (c) WL_CK(cudaMemcpyAsync((char *)c + a * bytes, lc[0][a], bytes, cudaMemcpyDefault, st));
+            if (V && has_body) WL_CK(cudaMemcpyAsync((char *)V + a * bytes, Vb[a], bytes, cudaMemcpyDefault, st));
+        }
+        if (m1 && has_body) WL_CK(cudaMemcpyAsync(m1, mu1n, 9 * bytes, cudaMemcpyDefault, st));
+        WL_CK(cudaStreamSynchronize(st));
+    }
+
+    // ------------------------------------------------------------ multigrid
+    void enqueue_vcycle(cudaStream_t s, long long &nodes) {
+        const int k = cfg.smooth_iters;
+        const bool tm = prof.on && s == st;
+        auto B = [&](const char *nm, int l) { if (tm) P0(nm, l, gl[l].nc); };
+        auto E = [&]() { if (tm) P1(); ++nodes; };
+        for (int l = 0; l + 1 < nlev; ++l) {
+            B("restrict", l + 1);
+            k_restrict<T, ND><<<tgrid(l + 1), tblk(), 0, s>>>(gl[l], lv[l].r, lv[l + 1]);
+            E();
+        }
+        const int L = nlev - 1;
+        long long ncl = gl[L].nc;
+        int maxit = (int)(2 * ncl + 200);
+        if (maxit > 2000) maxit = 2000;
+        B("coarsest", L);
+        k_coarsest<T><<<1, ncl >= 512 ? 512 : 256, 0, s>>>(lv[L], cw, maxit);
+        E();
+        for (int l = nlev - 2; l >= 0; --l) {
+            B("pcg_init", l);
+            k_pcg_init<T, ND><<<tgrid(l), tblk(), 0, s>>>(lv[l], gl[l + 1], lv[l + 1].x, S, part, l);
+            E();
+            for (int it = 0; it < k; ++it) {
+                B(it == 0 ? "pcg_q0" : "pcg_q", l);
+                k_pcg_q<T, ND><<<tgrid(l), tblk(), 0, s>>>(lv[l], S, part, l, it);
+                E();
+                const bool last = it == k - 1;
+                B(last ? (l == 0 ? "pcg_u_last_fine" : "pcg_u_last") : "pcg_u", l);
+                if (!last) k_pcg_u<T, ND, false, false><<<tgrid(l), tblk(), 0, s>>>(lv[l], ph, pl, S, part, l, it);
+                else if (l > 0) k_pcg_u<T, ND, true, false><<<tgrid(l), tblk(), 0, s>>>(lv[l], ph, pl, S, part, l, it);
+                else k_pcg_u<T, ND, true, true><<<tgrid(l), tblk(), 0, s>>>(lv[l], ph, pl, S, part, l, it);
+                E();
+            }
+        }
+        if (nlev == 1) {
+            B("padd", 0);
+            k_padd<T><<<blocks(g.nc), 256, 0, s>>>(g, lv[0].x, ph, pl);
+            E();
+        }
+        B("resid", 0);
+        k_resid<T, ND><<<tgrid(0), tblk(), 0, s>>>(lv[0], b, bl, ph, pl, S, part);
+        E();
+    }
+
+    void build_vcycle_graph() {
+        cudaGraph_t graph;
+        long long nodes = 0;
+        WL_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        enqueue_vcycle(cap, nodes);
+        cudaError_t e = cudaStreamEndCapture(cap, &graph);
+        if (e != cudaSuccess) throw Err{WL_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e)};
+        WL_CK(cudaGraphInstantiate(&vexec, graph, 0));
+        WL_CK(cudaGraphDestroy(graph));
+        vnodes = nodes;
+    }
+
+    // b is in place; solve A (ph+pl) = b - mean with warm start; fills stats.
+    int solve(wl_solve_stats *sts) {
+        P0("resid", 0, g.nc);
+        k_resid<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], b, bl, ph, pl, S, part);
+        P1();
+        WL_LAUNCH_CK();
+        ++launches;
+        read_scalars();
+        int it = 0;
+        while (hS->rel > cfg.tol && it < cfg.itmax && !(hS->status & 1)) {
+            if (prof.on) {
+                long long nodes = 0;
+                enqueue_vcycle(st, nodes);
+                WL_LAUNCH_CK();
+                launches += nodes;
+            } else {
+                WL_CK(cudaGraphLaunch(vexec, st));
+                launches += vnodes;
+            }
+            read_scalars();
+            ++it;
+        }
+        if (sts) { sts->vcycles = it; sts->rel_resid = hS->rel; sts->bnorm = hS->bnorm; }
+        if (hS->status & 1) return WL_ERR_NONFINITE;
+        if (hS->rel > cfg.tol) return WL_ERR_NOT_CONVERGED;
+        return WL_OK;
+    }
+
+    int project_buf(int q, const T *ue, double w, double dt, wl_solve_stats *sts) {
+        P0("div", 0, g.nc);
+        k_div<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], cv(q), ue, (T)(1.0 / (w * dt)), b, bl, S, part);
+        P1();
+        WL_LAUNCH_CK();
+        ++launches;
+        int rc = solve(sts);
+        P0("grad", 0, g.nc);
+        k_grad<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], ph, pl, (T)(w * dt), vv(q));
+        P1();
+        WL_LAUNCH_CK();
+        ++launches;
+        return rc;
+    }
+
+    // ------------------------------------------------------------ stages
+    template <int NDIM, int MODE>
+    void flux_launch(const FluxArgs<T> &A) {
+        using TL = FluxTile<NDIM>;
+        const size_t smem = (size_t)NDIM * TL::SN * sizeof(T);
+        static bool attr = false;
+        if (!attr) {
+            WL_CK(cudaFuncSetAttribute(k_flux<T, NDIM, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr = true;
+        }
+        const long long ntiles = (long long)((g.n[0] + TL::TX - 1) / TL::TX) * ((g.n[1] + TL::TY - 1) / TL::TY) *
+                                 ((g.n[2] + TL::TZ - 1) / TL::TZ);
+        int occ = 0;
+        WL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_flux<T, NDIM, MODE>, TL::NT, smem));
+        if (occ < 1) occ = 1;
+        long long grid = (long long)nsm * occ;
+        if (grid > ntiles) grid = ntiles;
+        dim3 blk(TL::TX, TL::TY, TL::TZ);
+        static const char *names[5] = {"flux_raw", "flux_pred_f", "flux_pred", "flux_corr_f", "flux_corr"};
+        P0(names[MODE], 0, g.nc);
+        k_flux<T, NDIM, MODE><<<(int)grid, blk, smem, st>>>(g, A);
+        P1();
+        WL_LAUNCH_CK();
+        ++launches;
+    }
+    template <int MODE>
+    void flux(const FluxArgs<T> &A) {
+        flux_launch<ND, MODE>(A);
+    }
+
+    FluxArgs<T> fargs(int qu, const T *ue, int qu0, int qout, double dt) {
+        FluxArgs<T> A{};
+        for (int a = 0; a < 3; ++a) {
+            A.u[a] = vel[qu][a];
+            A.u0[a] = qu0 >= 0 ? vel[qu0][a] : nullptr;
+            A.out[a] = vel[qout][a];
+        }
+        A.ue = ue;
+        A.dt = (T)dt;
+        return A;
+    }
+
+    void exit_stage(bool corr, int quG, double dt) {
+        if (!g.exit_x) return;
+        // ueB: start-of-step plane; ueC: star plane (corrector); result into ueA
+        if (!corr) {
+            P0("exit", 0, np);
+            k_exit<T, false><<<1, 1024, 0, st>>>(g, ueB, vel[quG][0], ueB, nullptr, (T)dt, ueA);
+            P1();
+        } else {
+            WL_CK(cudaMemcpyAsync(ueC, ueA, np * sizeof(T), cudaMemcpyDeviceToDevice, st));
+            P0("exit", 0, np);
+            k_exit<T, true><<<1, 1024, 0, st>>>(g, ueB, vel[quG][0], ueC, ueC, (T)dt, ueA);
+            P1();
+        }
+        WL_LAUNCH_CK();
+        ++launches;
+    }
+
+    void blend(bool corr, int qf, int qstar, int qout) {
+        CVec3P<T> f = cv(qf), V{}, us{};
+        for (int a = 0; a < 3; ++a) { V.p[a] = Vb[a]; us.p[a] = qstar >= 0 ? vel[qstar][a] : nullptr; }
+        P0("blend", 0, g.nc);
+        if (corr) k_blend<T, ND, true><<<tgrid(0), tblk(), 0, st>>>(lv[0], f, mu1n, (long long)g.nc, V, us, vv(qout));
+        else k_blend<T, ND, false><<<tgrid(0), tblk(), 0, st>>>(lv[0], f, mu1n, (long long)g.nc, V, us, vv(qout));
+        P1();
+        WL_LAUNCH_CK();
+        ++launches;
+    }
+
+    int mom_step(double dt_fixed, wl_step_stats *sts) override {
+        const double dt = dt_fixed > 0 ? dt_fixed : dt_next;
+        if (!(dt > cfg.dt_min)) throw Err{WL_ERR_UNSTABLE, "time step below dt_min"};
+        if (moving) body_update(t + dt);
+        const int A0 = cur, B1 = (cur + 1) & 3, C2 = (cur + 2) & 3, D3 = (cur + 3) & 3;
+        if (g.exit_x) WL_CK(cudaMemcpyAsync(ueB, ueA, np * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        wl_solve_stats s0{}, s1{};
+        int rc0, rc1;
+        int ustar, unew;
+        if (!has_body) {
+            flux<FM_PRED_U>(fargs(A0, ueB, -1, B1, dt));
+            ustar = B1;
+        } else {
+            flux<FM_PRED_F>(fargs(A0, ueB, -1, B1, dt));
+            blend(false, B1, -1, C2);
+            ustar = C2;
+        }
+        exit_stage(false, A0, dt);
+        rc0 = project_buf(ustar, ueA, 1.0, dt, &s0);
+        if (rc0 == WL_ERR_NONFINITE) return fail_restore(rc0, "non-finite values in the predictor projection");
+        if (!has_body) {
+            flux<FM_CORR_U>(fargs(ustar, ueA, A0, C2, dt));
+            unew = C2;
+        } else {
+            flux<FM_CORR_F>(fargs(ustar, ueA, A0, B1, dt));
+            blend(true, B1, ustar, D3);
+            unew = D3;
+        }
+        exit_stage(true, ustar, dt);
+        rc1 = project_buf(unew, ueA, 0.5, dt, &s1);
+        if (rc1 == WL_ERR_NONFINITE) return fail_restore(rc1, "non-finite values in the corrector projection");
+        // CFL for the next step
+        P0("cfl", 0, g.nc);
+        k_cfl<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], cv(unew), ueA, cfg.cfl, cfg.dt_max, S, part);
+        P1();
+        WL_LAUNCH_CK();
+        ++launches;
+        read_scalars();
+        prof.flush();
+        cur = unew;
+        t += dt;
+        dt_next = hS->dt_next;
+        if (sts) {
+            sts->proj[0] = s0;
+            sts->proj[1] = s1;
+            sts->dt = dt;
+            sts->t = t;
+            sts->dt_next = dt_next;
+        }
+        if (!(dt_next == dt_next)) { err = "non-finite CFL time step"; return WL_ERR_NONFINITE; }
+        if (rc0 != WL_OK || rc1 != WL_OK) { err = "Poisson solve did not reach tol within itmax"; return WL_ERR_NOT_CONVERGED; }
+        if (dt_next < cfg.dt_min) { err = "CFL time step below dt_min"; return WL_ERR_UNSTABLE; }
+        return WL_OK;
+    }
+
+    int fail_restore(int rc, const char *msg) {
+        if (g.exit_x) WL_CK(cudaMemcpyAsync(ueA, ueB, np * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        WL_CK(cudaStreamSynchronize(st));
+        err = msg;
+        return rc;
+    }
+
+    int project(double w, double dt, wl_solve_stats *sts) override {
+        if (!(w > 0 && dt > 0)) throw Err{WL_ERR_ARG, "project: w and dt must be positive"};
+        int rc = project_buf(cur, ueA, w, dt, sts);
+        WL_CK(cudaStreamSynchronize(st));
+        return rc;
+    }
+
+    int poisson_solve(const void *bin, double *p, wl_solve_stats *sts) override {
+        WL_CK(cudaMemcpyAsync(b, bin, g.nc * sizeof(T), cudaMemcpyDefault, st));
+        WL_CK(cudaMemsetAsync(bl, 0, g.nc * sizeof(T), st));
+        if (!pout) pout = alloc_n<double>(g.nc);
+        WL_CK(cudaMemcpyAsync(pout, p, g.nc * sizeof(double), cudaMemcpyDefault, st));
+        k_pin<T><<<blocks(g.nc), 256, 0, st>>>(g, pout, ph, pl);
+        ++launches;
+        k_bstats<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], b, S, part);
+        WL_LAUNCH_CK();
+        ++launches;
+        int rc = solve(sts);
+        get_pressure(p);
+        return rc;
+    }
+
+    void conv_diff(const void *u, const void *ue, void *r) override {
+        const int qi = (cur + 1) & 3, qo = (cur + 2) & 3;
+        const size_t bytes = g.nc * sizeof(T);
+        for (int a = 0; a < g.ndim; ++a) WL_CK(cudaMemcpyAsync(vel[qi][a], (const char *)u + a * bytes, bytes, cudaMemcpyDefault, st));
+        if (ue && g.exit_x) WL_CK(cudaMemcpyAsync(ueC, ue, np * sizeof(T), cudaMemcpyDefault, st));
+        flux<FM_RAW>(fargs(qi, ueC, -1, qo, 1.0));
+        for (int a = 0; a < g.ndim; ++a) WL_CK(cudaMemcpyAsync((char *)r + a * bytes, vel[qo][a], bytes, cudaMemcpyDefault, st));
+        WL_CK(cudaStreamSynchronize(st));
+    }
+
+    void set_velocity(const void *u, const void *ue) override {
+        const size_t bytes = g.nc * sizeof(T);
+        for (int a = 0; a < g.ndim; ++a) WL_CK(cudaMemcpyAsync(vel[cur][a], (const char *)u + a * bytes, bytes, cudaMemcpyDefault, st));
+        fill_boundary(cur);
+        if (ue && g.exit_x) WL_CK(cudaMemcpyAsync(ueA, ue, np * sizeof(T), cudaMemcpyDefault, st));
+        WL_CK(cudaStreamSynchronize(st));
+    }
+
+    void get_velocity(void *u, void *ue) override {
+        const size_t bytes = g.nc * sizeof(T);
+        for (int a = 0; a < g.ndim; ++a) WL_CK(cudaMemcpyAsync((char *)u + a * bytes, vel[cur][a], bytes, cudaMemcpyDefault, st));
+        if (ue && g.exit_x) WL_CK(cudaMemcpyAsync(ue, ueA, np * sizeof(T), cudaMemcpyDefault, st));
+        WL_CK(cudaStreamSynchronize(st));
+    }
+
+    void pmean() {
+        k_pmean<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], ph, pl, S, part);
+        WL_LAUNCH_CK();
+        ++launches;
+    }
+
+    void get_pressure(double *p) override {
+        if (!pout) pout = alloc_n<double>(g.nc);
+        pmean();
+        k_pout<T><<<blocks(g.nc), 256, 0, st>>>(g, ph, pl, lv[0].invD, S, pout);
+        WL_LAUNCH_CK();
+        ++launches;
+        WL_CK(cudaMemcpyAsync(p, pout, g.nc * sizeof(double), cudaMemcpyDefault, st));
+        WL_CK(cudaStreamSynchronize(st));
+    }
+
+    void set_pressure(const double *p) override {
+        if (!pout) pout = alloc_n<double>(g.nc);
+        WL_CK(cudaMemcpyAsync(pout, p, g.nc * sizeof(double), cudaMemcpyDefault, st));
+        k_pin<T><<<blocks(g.nc), 256, 0, st>>>(g, pout, ph, pl);
+        WL_LAUNCH_CK();
+        ++launches;
+        WL_CK(cudaStreamSynchronize(st));
+    }
+
+    void forces(double *F) override {
+        F[0] = F[1] = F[2] = 0.0;
+        if (!has_body) return;
+        pmean();
+        k_forces<T><<<blocks(g.nc), 256, 0, st>>>(g, body_state(body_t), ph, pl, lv[0].invD, S, part);
+        WL_LAUNCH_CK();
+        ++launches;
+        read_scalars();
+        F[0] = hS->red[0];
+        F[1] = hS->red[1];
+        F[2] = hS->red[2];
+    }
+
+    void diagnostics(double *ke, double *ens, double *maxdiv) override {
+        k_diag<T><<<blocks(g.nc), 256, 0, st>>>(g, cv(cur), ueA, lv[0].invD, S, part);
+        WL_LAUNCH_CK();
+        ++launches;
+        read_scalars();
+        if (ke) *ke = hS->red[0];
+        if (ens) *ens = hS->red[1];
+        if (maxdiv) *maxdiv = hS->red[2];
+    }
+
+    void profile(int on) override {
+        prof.flush();
+        prof.on = on != 0;
+        if (on) prof.acc.clear();
+    }
+
+    std::string profile_report() override {
+        WL_CK(cudaStreamSynchronize(st));
+        prof.flush();
+        std::string out;
+        char line[256];
+        for (auto &kv : prof.acc) {
+            std::snprintf(line, sizeof(line), "%s %d %lld %.6f %lld\n", kv.first.first.c_str(), kv.first.second,
+                          kv.second.first, kv.second.second.first, kv.second.second.second);
+            out += line;
+        }
+        return out;
+    }
+
+    void info(int *levels, long long *nl) override {
+        if (levels) *levels = nlev;
+        if (nl) *nl = launches;
+    }
+};
+
+int validate(const wl_config *c, const wl_body *bd, std::string &msg) {
+    if (!c) { msg = "cfg is NULL"; return WL_ERR_ARG; }
+    if (c->ndim != 2 && c->ndim != 3) { msg = "ndim must be 2 or 3"; return WL_ERR_ARG; }
+    for (int a = 0; a < c->ndim; ++a)
+        if (c->n[a] < 2 || c->n[a] > (1 << 20)) { msg = "n[a] must be in [2, 2^20]"; return WL_ERR_ARG; }
+    long long nc = 1;
+    for (int a = 0; a < c->ndim; ++a) nc *= c->n[a];
+    if (nc > (1LL << 34)) { msg = "grid too large"; return WL_ERR_ARG; }
+    if (c->precision != WL_F32 && c->precision != WL_F64) { msg = "precision must be WL_F32 or WL_F64"; return WL_ERR_ARG; }
+    if (!(c->eps > 0)) { msg = "eps must be positive"; return WL_ERR_ARG; }
+    if (!(c->nu >= 0)) { msg = "nu must be >= 0"; return WL_ERR_ARG; }
+    if (c->exit_hi_x && c->periodic[0]) { msg = "exit_hi_x needs a non-periodic x axis"; return WL_ERR_ARG; }
+    if (!(c->tol > 0) || c->itmax < 0 || c->smooth_iters < 1 || c->smooth_iters > 64) { msg = "bad solver settings"; return WL_ERR_ARG; }
+    if (!(c->dt_init > 0) || !(c->dt_max > 0) || !(c->cfl > 0)) { msg = "bad time-step settings"; return WL_ERR_ARG; }
+    if (bd) {
+        if (bd->kind < 0 || bd->kind > 2) { msg = "unknown body kind"; return WL_ERR_ARG; }
+        if (bd->kind == WL_BODY_ELLIPSE && c->ndim != 2) { msg = "ellipse body is 2D only"; return WL_ERR_ARG; }
+        if (bd->kind == WL_BODY_SPHERE && !(bd->radius > 0)) { msg = "sphere radius must be positive"; return WL_ERR_ARG; }
+        if (bd->kind == WL_BODY_ELLIPSE && !(bd->semi[0] > 0 && bd->semi[1] > 0)) { msg = "ellipse semi-axes must be positive"; return WL_ERR_ARG; }
+        if (bd->heave_axis < 0 || bd->heave_axis >= c->ndim) { msg = "heave_axis out of range"; return WL_ERR_ARG; }
+    }
+    return WL_OK;
+}
+
+}  // namespace
+
+struct wl_sim {
+    SimBase *impl;
+    std::string err;
+};
+
+template <typename F>
+static int guard(wl_sim *s, F &&f) {
+    if (!s || !s->impl) return WL_ERR_ARG;
+    try {
+        int rc = f();
+        s->err = rc == WL_OK ? std::string() : s->impl->err;
+        return rc;
+    } catch (const Err &e) {
+        s->err = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        s->err = "host allocation failed";
+        return WL_ERR_ALLOC;
+    }
+}
+
+extern "C" {
+
+void wl_config_default(wl_config *c, int ndim, const int *n) {
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->ndim = ndim;
+    for (int a = 0; a < 3; ++a) c->n[a] = (n && a < ndim) ? n[a] : 1;
+    c->eps = 1.0;
+    c->precision = WL_F32;
+    c->cfl = 1.0;
+    c->dt_max = 1.0;
+    c->dt_init = 0.25;
+    c->dt_min = 1e-6;
+    c->tol = 1e-6;
+    c->itmax = 32;
+    c->smooth_iters = 4;
+}
+
+int wl_sim_create(const wl_config *cfg, const wl_body *body, wl_sim **out) {
+    if (!out) return WL_ERR_ARG;
+    *out = nullptr;
+    std::string msg;
+    int rc = validate(cfg, body, msg);
+    if (rc != WL_OK) { std::fprintf(stderr, "wl_sim_create: %s\n", msg.c_str()); return rc; }
+    wl_sim *s = new (std::nothrow) wl_sim();
+    if (!s) return WL_ERR_ALLOC;
+    try {
+        if (cfg->precision == WL_F64) {
+            if (cfg->ndim == 3) { auto *p = new Sim<double, 3>(); s->impl = p; p->init(*cfg, body); }
+            else { auto *p = new Sim<double, 2>(); s->impl = p; p->init(*cfg, body); }
+        } else {
+            if (cfg->ndim == 3) { auto *p = new Sim<float, 3>(); s->impl = p; p->init(*cfg, body); }
+            else { auto *p = new Sim<float, 2>(); s->impl = p; p->init(*cfg, body); }
+        }
+    } catch (const Err &e) {
+        std::fprintf(stderr, "wl_sim_create: %s\n", e.msg.c_str());
+        delete s->impl;
+        delete s;
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        delete s->impl;
+        delete s;
+        return WL_ERR_ALLOC;
+    }
+    *out = s;
+    return WL_OK;
+}
+
+int wl_sim_destroy(wl_sim *s) {
+    if (!s) return WL_OK;
+    delete s->impl;
+    delete s;
+    return WL_OK;
+}
+
+int wl_set_velocity(wl_sim *s, const void *u, const void *ue) {
+    if (!u) return WL_ERR_ARG;
+    return guard(s, [&] { s->impl->set_velocity(u, ue); return (int)WL_OK; });
+}
+int wl_get_velocity(wl_sim *s, void *u, void *ue) {
+    if (!u) return WL_ERR_ARG;
+    return guard(s, [&] { s->impl->get_velocity(u, ue); return (int)WL_OK; });
+}
+int wl_get_pressure(wl_sim *s, double *p) {
+    if (!p) return WL_ERR_ARG;
+    return guard(s, [&] { s->impl->get_pressure(p); return (int)WL_OK; });
+}
+int wl_set_pressure(wl_sim *s, const double *p) {
+    if (!p) return WL_ERR_ARG;
+    return guard(s, [&] { s->impl->set_pressure(p); return (int)WL_OK; });
+}
+int wl_set_time(wl_sim *s, double t, double dt_next) {
+    if (!(dt_next > 0)) return WL_ERR_ARG;
+    return guard(s, [&] { s->impl->t = t; s->impl->dt_next = dt_next; return (int)WL_OK; });
+}
+int wl_get_time(wl_sim *s, double *t, double *dt_next) {
+    return guard(s, [&] {
+        if (t) *t = s->impl->t;
+        if (dt_next) *dt_next = s->impl->dt_next;
+        return (int)WL_OK;
+    });
+}
+int wl_mom_step(wl_sim *s, double dt_fixed, wl_step_stats *st) {
+    return guard(s, [&] { return s->impl->mom_step(dt_fixed, st); });
+}
+int wl_project(wl_sim *s, double w, double dt, wl_solve_stats *st) {
+    return guard(s, [&] { return s->impl->project(w, dt, st); });
+}
+int wl_poisson_solve(wl_sim *s, const void *b, double *p, wl_solve_stats *st) {
+    if (!b || !p) return WL_ERR_ARG;
+    return guard(s, [&] { return s->impl->poisson_solve(b, p, st); });
+}
+int wl_conv_diff(wl_sim *s, const void *u, const void *ue, void *r) {
+    if (!u || !r) return WL_ERR_ARG;
+    return guard(s, [&] { s->impl->conv_diff(u, ue, r); return (int)WL_OK; });
+}
+int wl_forces(wl_sim *s, double *F) {
+    if (!F) return WL_ERR_ARG;
+    return guard(s, [&] { s->impl->forces(F); return (int)WL_OK; });
+}
+int wl_body_update(wl_sim *s, double t) {
+    return guard(s, [&] { s->impl->body_update(t); return (int)WL_OK; });
+}
+int wl_get_body_fields(wl_sim *s, void *c, void *mu1n, void *V) {
+    return guard(s, [&] { s->impl->get_body_fields(c, mu1n, V); return (int)WL_OK; });
+}
+int wl_diagnostics(wl_sim *s, double *ke, double *ens, double *maxdiv) {
+    return guard(s, [&] { s->impl->diagnostics(ke, ens, maxdiv); return (int)WL_OK; });
+}
+int wl_info(wl_sim *s, int *levels, long long *launches) {
+    return guard(s, [&] { s->impl->info(levels, launches); return (int)WL_OK; });
+}
+int wl_profile(wl_sim *s, int on) {
+    return guard(s, [&] { s->impl->profile(on); return (int)WL_OK; });
+}
+int wl_profile_report(wl_sim *s, char *buf, size_t len, size_t *needed) {
+    return guard(s, [&] {
+        std::string r = s->impl->profile_report();
+        if (needed) *needed = r.size() + 1;
+        if (buf && len > 0) {
+            size_t n = r.size() < len - 1 ? r.size() : len - 1;
+            std::memcpy(buf, r.data(), n);
+            buf[n] = 0;
+        }
+        return (int)WL_OK;
+    });
+}
+const char *wl_last_error(const wl_sim *s) { return s ? s->err.c_str() : "null sim"; }
+const char *wl_status_string(int st) {
+    switch (st) {
+    case WL_OK: return "ok";
+    case WL_ERR_ARG: return "invalid argument";
+    case WL_ERR_CUDA: return "CUDA error";
+    case WL_ERR_ALLOC: return "allocation failed";
+    case WL_ERR_NOT_CONVERGED: return "Poisson solve not converged";
+    case WL_ERR_NONFINITE: return "non-finite values";
+    case WL_ERR_UNSTABLE: return "time step below dt_min";
+    case WL_ERR_STATE: return "invalid state";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

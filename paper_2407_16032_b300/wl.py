@@ -1,0 +1,318 @@
+"""ctypes binding of libwl.so (include/wl.h): argument marshalling only.
+
+Every step of the solver runs in the CUDA kernels of libwl.so. PyTorch provides
+device memory (through the wl_allocator callback into its caching allocator)
+and the CUDA stream. There is no CPU fallback: if the library or a CUDA device
+is missing, construction raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwl.so")
+
+WL_OK, WL_ERR_ARG, WL_ERR_CUDA, WL_ERR_ALLOC, WL_ERR_NOT_CONVERGED, WL_ERR_NONFINITE, WL_ERR_UNSTABLE, WL_ERR_STATE = range(8)
+WL_F32, WL_F64 = 0, 1
+BODY_KIND = {"none": 0, "sphere": 1, "ellipse": 2}
+
+EXPORTS = (
+    "wl_config_default", "wl_sim_create", "wl_sim_destroy", "wl_set_velocity", "wl_get_velocity",
+    "wl_get_pressure", "wl_set_pressure", "wl_set_time", "wl_get_time", "wl_mom_step", "wl_project",
+    "wl_poisson_solve", "wl_conv_diff", "wl_forces", "wl_body_update", "wl_get_body_fields",
+    "wl_diagnostics", "wl_info", "wl_profile", "wl_profile_report", "wl_last_error", "wl_status_string",
+)
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("alloc", _ALLOC_FN), ("free", _FREE_FN)]
+
+
+class Config(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("n", C.c_int * 3), ("periodic", C.c_int * 3), ("exit_hi_x", C.c_int),
+                ("U", C.c_double * 3), ("nu", C.c_double), ("eps", C.c_double), ("precision", C.c_int),
+                ("cfl", C.c_double), ("dt_max", C.c_double), ("dt_init", C.c_double), ("dt_min", C.c_double),
+                ("tol", C.c_double), ("itmax", C.c_int), ("smooth_iters", C.c_int), ("stream", C.c_void_p),
+                ("allocator", Allocator)]
+
+
+class Body(C.Structure):
+    _fields_ = [("kind", C.c_int), ("centre", C.c_double * 3), ("radius", C.c_double), ("semi", C.c_double * 2),
+                ("heave_amp", C.c_double), ("pitch_amp", C.c_double), ("omega", C.c_double),
+                ("phase", C.c_double), ("heave_axis", C.c_int)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("vcycles", C.c_int), ("rel_resid", C.c_double), ("bnorm", C.c_double)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("proj", SolveStats * 2), ("dt", C.c_double), ("t", C.c_double), ("dt_next", C.c_double)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libwl.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libwl.so not built ({LIB_PATH}); run python -m paper_2407_16032_b300.build")
+        L = C.CDLL(LIB_PATH)
+        vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+        sig = {
+            "wl_config_default": ([C.POINTER(Config), ip, C.POINTER(C.c_int)], None),
+            "wl_sim_create": ([C.POINTER(Config), C.POINTER(Body), C.POINTER(vp)], ip),
+            "wl_sim_destroy": ([vp], ip),
+            "wl_set_velocity": ([vp, vp, vp], ip),
+            "wl_get_velocity": ([vp, vp, vp], ip),
+            "wl_get_pressure": ([vp, vp], ip),
+            "wl_set_pressure": ([vp, vp], ip),
+            "wl_set_time": ([vp, C.c_double, C.c_double], ip),
+            "wl_get_time": ([vp, dp, dp], ip),
+            "wl_mom_step": ([vp, C.c_double, C.POINTER(StepStats)], ip),
+            "wl_project": ([vp, C.c_double, C.c_double, C.POINTER(SolveStats)], ip),
+            "wl_poisson_solve": ([vp, vp, vp, C.POINTER(SolveStats)], ip),
+            "wl_conv_diff": ([vp, vp, vp, vp], ip),
+            "wl_forces": ([vp, dp], ip),
+            "wl_body_update": ([vp, C.c_double], ip),
+            "wl_get_body_fields": ([vp, vp, vp, vp], ip),
+            "wl_diagnostics": ([vp, dp, dp, dp], ip),
+            "wl_info": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_longlong)], ip),
+            "wl_profile": ([vp, ip], ip),
+            "wl_profile_report": ([vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)], ip),
+            "wl_last_error": ([vp], C.c_char_p),
+            "wl_status_string": ([ip], C.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+class WLError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+def _ptr(x) -> Optional[int]:
+    """Address of a torch tensor (host or device) or a numpy array (host)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    assert x.is_contiguous()
+    return x.data_ptr()
+
+
+@dataclass
+class SolveResult:
+    vcycles: int
+    rel_resid: float
+    bnorm: float
+
+
+class Sim:
+    """A simulation object of libwl (wl_sim_create ... wl_sim_destroy)."""
+
+    def __init__(self, ndim, n, periodic=(False, False, False), exit_hi_x=False, U=(0.0, 0.0, 0.0), nu=0.0,
+                 eps=1.0, precision="f32", body=None, tol=1e-6, itmax=32, smooth_iters=4, cfl=1.0, dt_max=1.0,
+                 dt_init=0.25, dt_min=1e-6, device=None, use_torch_allocator=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libwl needs a CUDA device")
+        self.torch = torch
+        L = lib()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.ndim = ndim
+        self.n = tuple(int(v) for v in (list(n) + [1, 1])[:3])
+        if ndim == 2:
+            self.n = (self.n[0], self.n[1], 1)
+        self.ncell = self.n[0] * self.n[1] * self.n[2]
+        self.dtype = torch.float32 if precision in ("f32", WL_F32) else torch.float64
+        self.exit = bool(exit_hi_x)
+        cfg = Config()
+        nn = (C.c_int * 3)(*self.n)
+        L.wl_config_default(C.byref(cfg), ndim, nn)
+        for a in range(3):
+            cfg.periodic[a] = int(bool(periodic[a])) if a < len(periodic) else 0
+            cfg.U[a] = float(U[a]) if a < len(U) else 0.0
+        cfg.exit_hi_x = int(self.exit)
+        cfg.nu, cfg.eps = float(nu), float(eps)
+        cfg.precision = WL_F32 if self.dtype == torch.float32 else WL_F64
+        cfg.tol, cfg.itmax, cfg.smooth_iters = float(tol), int(itmax), int(smooth_iters)
+        cfg.cfl, cfg.dt_max, cfg.dt_init, cfg.dt_min = float(cfl), float(dt_max), float(dt_init), float(dt_min)
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.current_stream()
+        cfg.stream = self.stream.cuda_stream
+        self._blocks = {}
+        if use_torch_allocator:
+            def _alloc(ctx, nbytes):
+                try:
+                    t = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+                except RuntimeError:
+                    return None
+                self._blocks[t.data_ptr()] = t
+                return t.data_ptr()
+
+            def _free(ctx, p):
+                self._blocks.pop(p, None)
+
+            self._alloc_cb, self._free_cb = _ALLOC_FN(_alloc), _FREE_FN(_free)
+            cfg.allocator.alloc, cfg.allocator.free = self._alloc_cb, self._free_cb
+        bd = None
+        if body is not None and getattr(body, "kind", "none") != "none":
+            bd = Body()
+            bd.kind = BODY_KIND[body.kind]
+            for a in range(3):
+                bd.centre[a] = float(body.centre[a])
+            bd.radius = float(body.radius)
+            bd.semi[0], bd.semi[1] = float(body.semi[0]), float(body.semi[1])
+            bd.heave_amp, bd.pitch_amp = float(body.heave_amp), float(body.pitch_amp)
+            bd.omega, bd.phase, bd.heave_axis = float(body.omega), float(body.phase), int(body.heave_axis)
+        self._h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = L.wl_sim_create(C.byref(cfg), C.byref(bd) if bd is not None else None, C.byref(self._h))
+        if rc != WL_OK:
+            raise WLError(rc, "wl_sim_create failed: " + L.wl_status_string(rc).decode())
+        self.cfg = cfg
+
+    # -------------------------------------------------------------- plumbing
+    def _check(self, rc, what, ok=(WL_OK,)):
+        if rc not in ok:
+            msg = lib().wl_last_error(self._h).decode()
+            raise WLError(rc, f"{what}: {msg or lib().wl_status_string(rc).decode()}")
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().wl_sim_destroy(self._h)
+            self._h = C.c_void_p()
+            self._blocks.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _shape(self):
+        return (self.n[2], self.n[1], self.n[0]) if self.ndim == 3 else (self.n[1], self.n[0])
+
+    def new_velocity(self, device=True):
+        return self.torch.zeros((self.ndim,) + self._shape(), dtype=self.dtype,
+                                device=self.device if device else "cpu")
+
+    def new_plane(self, device=True):
+        return self.torch.zeros(max(self.n[1] * self.n[2], 1), dtype=self.dtype,
+                                device=self.device if device else "cpu")
+
+    # ------------------------------------------------------------ C-ABI calls
+    def set_velocity(self, u, ue=None):
+        self._check(lib().wl_set_velocity(self._h, _ptr(u), _ptr(ue)), "wl_set_velocity")
+
+    def get_velocity(self, u=None, ue=None):
+        u = self.new_velocity() if u is None else u
+        if ue is None and self.exit:
+            ue = self.new_plane(device=u.is_cuda if hasattr(u, "is_cuda") else False)
+        self._check(lib().wl_get_velocity(self._h, _ptr(u), _ptr(ue)), "wl_get_velocity")
+        return u, ue
+
+    def get_pressure(self, p=None):
+        p = self.torch.zeros(self._shape(), dtype=self.torch.float64, device=self.device) if p is None else p
+        self._check(lib().wl_get_pressure(self._h, _ptr(p)), "wl_get_pressure")
+        return p
+
+    def set_pressure(self, p):
+        self._check(lib().wl_set_pressure(self._h, _ptr(p)), "wl_set_pressure")
+
+    def set_time(self, t, dt_next):
+        self._check(lib().wl_set_time(self._h, float(t), float(dt_next)), "wl_set_time")
+
+    def get_time(self):
+        t, dt = C.c_double(), C.c_double()
+        self._check(lib().wl_get_time(self._h, C.byref(t), C.byref(dt)), "wl_get_time")
+        return t.value, dt.value
+
+    def mom_step(self, dt_fixed=0.0, allow_unconverged=False):
+        st = StepStats()
+        ok = (WL_OK, WL_ERR_NOT_CONVERGED) if allow_unconverged else (WL_OK,)
+        rc = self._check(lib().wl_mom_step(self._h, float(dt_fixed), C.byref(st)), "wl_mom_step", ok)
+        return st, rc
+
+    def project(self, w, dt):
+        st = SolveStats()
+        self._check(lib().wl_project(self._h, float(w), float(dt), C.byref(st)), "wl_project")
+        return SolveResult(st.vcycles, st.rel_resid, st.bnorm)
+
+    def poisson_solve(self, b, p):
+        st = SolveStats()
+        rc = lib().wl_poisson_solve(self._h, _ptr(b), _ptr(p), C.byref(st))
+        self._check(rc, "wl_poisson_solve", (WL_OK, WL_ERR_NOT_CONVERGED))
+        return SolveResult(st.vcycles, st.rel_resid, st.bnorm), rc
+
+    def conv_diff(self, u, ue=None, r=None):
+        r = self.torch.empty_like(u) if r is None else r
+        self._check(lib().wl_conv_diff(self._h, _ptr(u), _ptr(ue), _ptr(r)), "wl_conv_diff")
+        return r
+
+    def forces(self):
+        F = (C.c_double * 3)()
+        self._check(lib().wl_forces(self._h, F), "wl_forces")
+        return np.array(F[:])
+
+    def body_update(self, t):
+        self._check(lib().wl_body_update(self._h, float(t)), "wl_body_update")
+
+    def get_body_fields(self):
+        T = self.torch
+        c = T.zeros((self.ndim,) + self._shape(), dtype=self.dtype, device=self.device)
+        m = T.zeros((9,) + self._shape(), dtype=self.dtype, device=self.device)
+        V = T.zeros((self.ndim,) + self._shape(), dtype=self.dtype, device=self.device)
+        self._check(lib().wl_get_body_fields(self._h, _ptr(c), _ptr(m), _ptr(V)), "wl_get_body_fields")
+        return c, m.reshape((3, 3) + self._shape())[: self.ndim], V
+
+    def diagnostics(self):
+        ke, en, md = C.c_double(), C.c_double(), C.c_double()
+        self._check(lib().wl_diagnostics(self._h, C.byref(ke), C.byref(en), C.byref(md)), "wl_diagnostics")
+        return ke.value, en.value, md.value
+
+    def profile(self, on=True):
+        self._check(lib().wl_profile(self._h, int(bool(on))), "wl_profile")
+
+    def profile_report(self):
+        """[(kernel, level, launches, total_ms, cells_per_launch)] from wl_profile_report."""
+        need = C.c_size_t()
+        self._check(lib().wl_profile_report(self._h, None, 0, C.byref(need)), "wl_profile_report")
+        buf = C.create_string_buffer(need.value + 16)
+        self._check(lib().wl_profile_report(self._h, buf, len(buf), None), "wl_profile_report")
+        rows = []
+        for line in buf.value.decode().splitlines():
+            nm, lv, n, ms, cells = line.split()
+            rows.append((nm, int(lv), int(n), float(ms), int(cells)))
+        return rows
+
+    def info(self):
+        lv, nl = C.c_int(), C.c_longlong()
+        self._check(lib().wl_info(self._h, C.byref(lv), C.byref(nl)), "wl_info")
+        return lv.value, nl.value
+
+
+def sim_from_case(case, precision="f32", **kw) -> Sim:
+    """Build a Sim from a workload description with the attributes of a case
+    (ndim, n, periodic, exit_hi_x, U, nu, eps, body, cfl, dt_max, dt0)."""
+    return Sim(case.ndim, case.n, case.periodic, case.exit_hi_x, case.U, case.nu, case.eps, precision,
+               case.body, cfl=case.cfl, dt_max=case.dt_max, dt_init=case.dt0, **kw)

@@ -1,0 +1,212 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs. Bars: FP32 fields within 1e-5 relative max-norm after 10
+steps (u and mean-free p); FP64 within 1e-9; stage kernels tighter."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import gpu_fields, gpu_sim, rel_max, run_pair
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_16032_b300 import build
+    build.build()
+
+
+def _t(x, prec="f32"):
+    import torch
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float32 if prec == "f32" else torch.float64).cuda()
+
+
+# ------------------------------------------------------------------ stages --
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("shape,per,exit", [
+    ((70, 37, 21), (False, False, False), True),      # ragged, walls + exit, several tiles
+    ((48, 20, 18), (True, True, True), False),        # periodic
+    ((33, 64, 9), (True, False, True), False),        # mixed
+    ((100, 45, 1), (False, False, False), True),      # 2D ragged
+    ((64, 64, 1), (True, True, False), False),        # 2D periodic
+])
+def test_conv_diff_matches_oracle(prec, shape, per, exit):
+    nd = 2 if shape[2] == 1 else 3
+    case = synth.Case("cd", nd, shape, per, exit, (1.0, 0.0, 0.0), 0.037)
+    u = synth.random_field(17, nd, shape, 0.8, (0.4, -0.1, 0.2))
+    ue = 1.0 + 0.1 * synth.random_scalar(5, 2, (shape[1], shape[2], 1)).ravel()
+    if prec == "f32":
+        u, ue = u.astype(np.float32).astype(np.float64), ue.astype(np.float32).astype(np.float64)
+    r_or = oracle.conv_diff(oracle.grid_from_case(case), u, ue)
+    sim = gpu_sim(case, prec)
+    r = sim.conv_diff(_t(u, prec), _t(ue, prec)).double().cpu().numpy()
+    # each r sums ~4 n face fluxes of size |u|^2, each rounded a few times in the
+    # working precision: bound the error by 32 eps max|u|^2
+    eps = np.finfo(np.float32 if prec == "f32" else np.float64).eps
+    assert np.abs(r - r_or).max() <= 32 * eps * max(np.abs(u).max(), np.abs(ue).max()) ** 2
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("body,nd,shape,t", [
+    (synth.Body("sphere", (20.3, 17.7, 15.2), 7.3, heave_amp=3.0, omega=0.1, heave_axis=1), 3, (44, 36, 30), 2.5),
+    (synth.Body("sphere", (30.6, 20.1, 0.0), 9.1), 2, (70, 40, 1), 0.0),
+    (synth.Body("ellipse", (40.2, 30.7, 0.0), 0.0, (16.0, 3.84), heave_amp=4.0, pitch_amp=0.26, omega=0.03), 2,
+     (96, 64, 1), 7.0),
+])
+def test_body_measure_matches_oracle(prec, body, nd, shape, t):
+    case = synth.Case("m", nd, shape, (False,) * 3, True, (1.0, 0, 0), 0.01, body)
+    g = oracle.grid_from_case(case)
+    mu0, mu1n, V = oracle.measure(g, oracle.make_body(body), t)
+    c_or = oracle.coeffs(g, mu0)
+    sim = gpu_sim(case, prec)
+    sim.body_update(t)
+    c, m, Vg = (x.double().cpu().numpy() for x in sim.get_body_fields())
+    tol = 2e-5 if prec == "f32" else 1e-12
+    assert np.abs(c - c_or).max() < tol
+    assert np.abs(m[:, :nd] - mu1n[:, :nd]).max() < tol
+    assert np.abs(Vg - V).max() < tol * max(1.0, np.abs(V).max())
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("nd,shape,per,body", [
+    (2, (64, 48, 1), (False, False, False), synth.Body("sphere", (20.5, 23.7, 0), 6.2)),
+    (3, (32, 32, 32), (True, True, True), None),
+    (3, (48, 32, 24), (False, False, False), synth.Body("sphere", (16.2, 15.1, 12.3), 5.5)),
+    (2, (70, 36, 1), (False, True, False), None),    # 35x18 after one level: odd coarsest
+])
+def test_poisson_solve_matches_oracle(prec, nd, shape, per, body):
+    case = synth.Case("p", nd, shape, per, False, (0, 0, 0), 0.0, body or synth.Body())
+    g = oracle.grid_from_case(case)
+    mu0 = oracle.measure(g, oracle.make_body(case.body), 0.0)[0] if body else None
+    c = oracle.coeffs(g, mu0)
+    b = synth.random_scalar(3, nd, shape)
+    if prec == "f32":
+        b = b.astype(np.float32).astype(np.float64)
+    p_or, rc, st = oracle.poisson_solve(g, c, b, tol=1e-12, itmax=100)
+    assert rc == 0
+    sim = gpu_sim(case, prec, tol=1e-9 if prec == "f32" else 1e-12, itmax=60)
+    p = np.zeros(b.shape)
+    res, rcg = sim.poisson_solve(_t(b, prec), p)
+    assert res.rel_resid <= (1e-9 if prec == "f32" else 1e-12), res
+    err = np.linalg.norm(p - p_or) / np.linalg.norm(p_or)
+    assert err < (2e-6 if prec == "f32" else 1e-10), (err, res)
+
+
+# ----------------------------------------------------------- whole steps ---
+def _compare(orc, sim, tol_u, tol_p):
+    u, ue, p = gpu_fields(sim)
+    eu = rel_max(u, orc.u)
+    ep = rel_max(p - p.mean(), orc.P - orc.P.mean())
+    assert eu < tol_u, ("u", eu)
+    assert ep < tol_p, ("p", ep)
+    if orc.case.exit_hi_x:
+        assert rel_max(ue, orc.ue) < tol_u
+    return eu, ep
+
+
+def test_config1_circle_fp64_full_size_10_steps():
+    case = synth.config1_circle()
+    orc, sim, st = run_pair(case, 10, "f64", gpu_tol=1e-11, oracle_tol=1e-11)
+    _compare(orc, sim, 1e-9, 1e-8)
+
+
+def test_config2_tgv64_fp32_10_steps():
+    case = synth.config2_tgv(64)
+    orc, sim, st = run_pair(case, 10, "f32")
+    _compare(orc, sim, 1e-5, 1e-5)
+    ke_or, en_or = oracle.diagnostics(orc.g, orc.u, orc.ue)
+    ke, en, md = sim.diagnostics()
+    assert abs(ke / ke_or - 1) < 1e-5 and abs(en / en_or - 1) < 1e-4
+    assert md < 1e-4
+
+
+def test_config3_sphere_reduced_fp32_10_steps():
+    case = synth.config3_sphere((128, 64, 64), D=16.0, centre=(32.0, 32.0, 32.0))
+    orc, sim, st = run_pair(case, 10, "f32")
+    _compare(orc, sim, 1e-5, 1e-5)
+    F_or = oracle.forces(orc.g, orc.b, orc.t, orc.P)
+    F = sim.forces()
+    assert np.abs(F - F_or).max() < 1e-4 * max(np.abs(F_or).max(), 1.0)
+
+
+def test_config4_ellipse_oracle_size_fp32_10_steps():
+    case = synth.config4_ellipse((256, 128), chord=32.0, A=8.0, centre=(64.0, 64.0))
+    orc, sim, st = run_pair(case, 10, "f32")
+    _compare(orc, sim, 1e-5, 1e-5)
+
+
+def test_config5_moving_sphere_reduced_fp32_10_steps():
+    case = synth.config5_moving_sphere((128, 64, 64), D=12.0, centre=(32.0, 32.0, 32.0))
+    orc, sim, st = run_pair(case, 10, "f32")
+    _compare(orc, sim, 1e-5, 1e-5)
+
+
+def test_ragged_sizes_2d_and_3d():
+    c2 = synth.Case("r2", 2, (70, 36, 1), (False, False, False), True, (1.0, 0, 0), 0.05,
+                    synth.Body("sphere", (21.3, 17.9, 0), 5.4), init="noise", seed=3)
+    orc, sim, st = run_pair(c2, 6, "f32")
+    _compare(orc, sim, 1e-5, 1e-5)
+    c3 = synth.Case("r3", 3, (40, 24, 20), (False, False, True), True, (1.0, 0, 0), 0.05,
+                    synth.Body("sphere", (12.2, 11.6, 9.9), 4.1), init="noise", seed=5)
+    orc, sim, st = run_pair(c3, 6, "f32")
+    _compare(orc, sim, 1e-5, 1e-5)
+
+
+def test_adaptive_time_step_matches_oracle_cfl():
+    case = synth.config1_circle((64, 32)).with_(body=synth.Body("sphere", (16.0, 16.0, 0), 4.0))
+    orc, sim, st = run_pair(case, 3, "f64", gpu_tol=1e-11)
+    t, dt_next = sim.get_time()
+    assert dt_next == pytest.approx(orc.dt, rel=1e-10)
+
+
+# ----------------------------------------------------------- failure modes --
+def test_nonfinite_input_is_reported_not_propagated():
+    case = synth.config2_tgv(16)
+    sim = gpu_sim(case, "f32")
+    u = np.zeros((3, 16, 16, 16))
+    u[0, 3, 4, 5] = np.nan
+    sim.set_velocity(_t(u))
+    from paper_2407_16032_b300 import wl
+    with pytest.raises(wl.WLError) as ei:
+        sim.mom_step(0.3)
+    assert ei.value.code == wl.WL_ERR_NONFINITE
+    # the state is still the last good one (the NaN input), time not advanced
+    assert sim.get_time()[0] == 0.0
+
+
+def test_itmax_zero_reports_not_converged():
+    case = synth.config2_tgv(16)
+    sim = gpu_sim(case, "f32", itmax=0)
+    u, ue = synth.initial_velocity(case)
+    sim.set_velocity(_t(u))
+    st, rc = sim.mom_step(0.3, allow_unconverged=True)
+    from paper_2407_16032_b300 import wl
+    assert rc == wl.WL_ERR_NOT_CONVERGED
+
+
+def test_full_size_tgv256_properties_and_flux_sample():
+    # Bench-size workload, bench launch configuration: residual at the target,
+    # projected field divergence-free, momentum conserved, flux equal to the
+    # oracle's on the full grid.
+    case = synth.config2_tgv(256)
+    sim = gpu_sim(case, "f32", tol=1e-6)
+    u, ue = synth.initial_velocity(case)
+    u32 = u.astype(np.float32)
+    sim.set_velocity(_t(u32))
+    r = sim.conv_diff(_t(u32)).double().cpu().numpy()
+    r_or = oracle.conv_diff(oracle.grid_from_case(case), u32.astype(np.float64), ue)
+    assert np.abs(r - r_or).max() <= 32 * np.finfo(np.float32).eps * np.abs(u32).max() ** 2
+    m0 = [float(x) for x in sim.get_velocity()[0].double().sum(dim=(1, 2, 3))]
+    for _ in range(3):
+        st, rc = sim.mom_step()
+        assert st.proj[0].rel_resid <= 1e-6 and st.proj[1].rel_resid <= 1e-6
+    ke, en, md = sim.diagnostics()
+    assert md < 1e-4
+    m1 = [float(x) for x in sim.get_velocity()[0].double().sum(dim=(1, 2, 3))]
+    assert np.allclose(m0, m1, atol=1e-2)
