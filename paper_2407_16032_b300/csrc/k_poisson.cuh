@@ -326,7 +326,11 @@ __global__ void __launch_bounds__(256) k_resid(LevelD<T> L, const T *b, const T 
                     Al += e + tl;
                 }
             }
-            res = (((b[idx] - bm) - Ah) + (bl[idx] - bml)) - Al;
+            // (b - mean) - A p with exact subtractions of the large parts
+            T r1, e1, r2, e2;
+            two_sum(b[idx], -bm, r1, e1);
+            two_sum(r1, -Ah, r2, e2);
+            res = r2 + (((e1 + e2) + (bl[idx] - bml)) - Al);
             acc[0] += res * res;
         }
         L.r[idx] = res;
@@ -376,7 +380,7 @@ __global__ void __launch_bounds__(256) k_pcg_init(LevelD<T> L, GridD gc, const T
     for_cells<NDIM>(L.g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
         const T x0 = xc[lin3(gc, i >> 1, j >> 1, NDIM == 3 ? (k >> 1) : 0)];
         L.x[idx] = x0;
-        const T iD = invd_at<T, NDIM>(L, uni, i, j, k, idx);
+        const T iD = L.invD[idx];
         T s = T(0);
         if (iD != T(0)) {
             long long ip[3], im[3];
@@ -415,10 +419,9 @@ __global__ void __launch_bounds__(256) k_pcg_q(LevelD<T> L, DevScalars *S, doubl
         if (it == 0) {
             d0 = dcur[idx];
         } else {
-            d0 = invd_at<T, NDIM>(L, uni, i, j, k, idx) * L.s[idx] + beta * dprev[idx];
+            d0 = L.invD[idx] * L.s[idx] + beta * dprev[idx];
             dcur[idx] = d0;
         }
-        const int I[3] = {i, j, k};
         T Ad = T(0);
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {
@@ -427,19 +430,8 @@ __global__ void __launch_bounds__(256) k_pcg_q(LevelD<T> L, DevScalars *S, doubl
                 dp = dcur[ip[a]];
                 dm = dcur[im[a]];
             } else {
-                T iDp, iDm;
-                if (uni) {
-                    int P[3] = {I[0], I[1], I[2]}, M[3] = {I[0], I[1], I[2]};
-                    P[a] = (P[a] + 1 == L.g.n[a]) ? (L.g.per[a] ? 0 : P[a]) : P[a] + 1;
-                    M[a] = (M[a] == 0) ? (L.g.per[a] ? L.g.n[a] - 1 : 0) : M[a] - 1;
-                    iDp = invd_uniform<T, NDIM>(L, P[0], P[1], P[2]);
-                    iDm = invd_uniform<T, NDIM>(L, M[0], M[1], M[2]);
-                } else {
-                    iDp = L.invD[ip[a]];
-                    iDm = L.invD[im[a]];
-                }
-                dp = iDp * L.s[ip[a]] + beta * dprev[ip[a]];
-                dm = iDm * L.s[im[a]] + beta * dprev[im[a]];
+                dp = L.invD[ip[a]] * L.s[ip[a]] + beta * dprev[ip[a]];
+                dm = L.invD[im[a]] * L.s[im[a]] + beta * dprev[im[a]];
             }
             Ad += cp[a] * (dp - d0) - cm[a] * (d0 - dm);
         }
@@ -454,34 +446,65 @@ __global__ void __launch_bounds__(256) k_pcg_q(LevelD<T> L, DevScalars *S, doubl
 // PCG step part 2: x += alpha d; s -= alpha q; rho' = <s, D^-1 s>; beta = rho'/rho.
 // On the last iteration only x is updated; on the fine level the correction
 // is added straight into the refinement pressure (ph, pl) instead.
-template <typename T, int NDIM, bool LAST, bool FINE>
+// Purely elementwise: a linear sweep in 16-byte vectors.
+template <typename T> struct V16;
+template <> struct V16<float> { typedef float4 type; static constexpr int n = 4; };
+template <> struct V16<double> { typedef double2 type; static constexpr int n = 2; };
+
+template <typename T, bool LAST, bool FINE>
+__device__ __forceinline__ void pcg_u_elem(T &x, T d, T &s, T q, T iD, T &ph, T &pl, T alpha, T &acc) {
+    const T xn = x + alpha * d;
+    if (LAST && FINE) {
+        T sh, err;
+        two_sum(ph, xn, sh, err);
+        const T lo = pl + err;
+        const T hi = sh + lo;
+        ph = hi;
+        pl = lo - (hi - sh);
+    } else {
+        x = xn;
+    }
+    if (!LAST) {
+        s = s - alpha * q;
+        acc += s * iD * s;
+    }
+}
+
+template <typename T, bool LAST, bool FINE>
 __global__ void __launch_bounds__(256) k_pcg_u(LevelD<T> L, T *ph, T *pl, DevScalars *S, double *part, int lev,
                                                int it) {
+    typedef typename V16<T>::type VT;
+    constexpr int W = V16<T>::n;
     const T *dcur = L.d[it & 1];
     const T alpha = (T)S->alpha[lev];
     T acc[1] = {T(0)};
-    for_cells<NDIM>(L.g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
-        const T xn = L.x[idx] + alpha * dcur[idx];
-        if (LAST && FINE) {
-            T sh, err;
-            two_sum(ph[idx], xn, sh, err);
-            const T lo = pl[idx] + err;
-            const T hi = sh + lo;
-            ph[idx] = hi;
-            pl[idx] = lo - (hi - sh);
-        } else {
-            L.x[idx] = xn;
+    const long long n = L.g.nc;
+    const long long nv = (n % W == 0) ? n / W : 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (long long v = t0; v < nv; v += stride) {
+        VT x = ((VT *)L.x)[v], d = ((const VT *)dcur)[v], s = ((VT *)L.s)[v], q = ((const VT *)L.q)[v];
+        VT iD = ((const VT *)L.invD)[v];
+        VT h, l;
+        if (LAST && FINE) { h = ((VT *)ph)[v]; l = ((VT *)pl)[v]; }
+        T *xe = (T *)&x, *se = (T *)&s, *he = (T *)&h, *le = (T *)&l;
+        const T *de = (const T *)&d, *qe = (const T *)&q, *ie = (const T *)&iD;
+#pragma unroll
+        for (int e = 0; e < W; ++e) pcg_u_elem<T, LAST, FINE>(xe[e], de[e], se[e], qe[e], ie[e], he[e], le[e], alpha, acc[0]);
+        if (LAST && FINE) { ((VT *)ph)[v] = h; ((VT *)pl)[v] = l; }
+        else ((VT *)L.x)[v] = x;
+        if (!LAST) ((VT *)L.s)[v] = s;
+    }
+    if (nv == 0)
+        for (long long e = t0; e < n; e += stride) {
+            T dummyh = T(0), dummyl = T(0);
+            T *hp = (LAST && FINE) ? &ph[e] : &dummyh, *lp = (LAST && FINE) ? &pl[e] : &dummyl;
+            pcg_u_elem<T, LAST, FINE>(L.x[e], dcur[e], L.s[e], L.q[e], L.invD[e], *hp, *lp, alpha, acc[0]);
         }
-        if (!LAST) {
-            const T s = L.s[idx] - alpha * L.q[idx];
-            L.s[idx] = s;
-            acc[0] += s * invd_at<T, NDIM>(L, uni, i, j, k, idx) * s;
-        }
-    });
     if (!LAST) {
         double out[1];
         if (grid_reduce<1, false, T>(acc, part, &S->counters[RS_U], out))
-            if (threadIdx.x == 0 && threadIdx.y == 0) {
+            if (threadIdx.x == 0) {
                 const double rho = S->rho[lev];
                 S->beta[lev] = rho != 0.0 ? out[0] / rho : 0.0;
                 S->rho[lev] = out[0];

@@ -126,6 +126,7 @@ struct Sim : SimBase {
     T *ueA = nullptr, *ueB = nullptr, *ueC = nullptr;
     T *mu1n = nullptr;
     T *Vb[3] = {};
+    // refinement pressure (ph + pl), the warm start of every solve
     T *b = nullptr, *bl = nullptr, *ph = nullptr, *pl = nullptr;
     LevelD<T> lv[WL_MAXLEV];
     T *lc[WL_MAXLEV][3] = {};
@@ -382,9 +383,10 @@ struct Sim : SimBase {
                 E();
                 const bool last = it == k - 1;
                 B(last ? (l == 0 ? "pcg_u_last_fine" : "pcg_u_last") : "pcg_u", l);
-                if (!last) k_pcg_u<T, ND, false, false><<<tgrid(l), tblk(), 0, s>>>(lv[l], ph, pl, S, part, l, it);
-                else if (l > 0) k_pcg_u<T, ND, true, false><<<tgrid(l), tblk(), 0, s>>>(lv[l], ph, pl, S, part, l, it);
-                else k_pcg_u<T, ND, true, true><<<tgrid(l), tblk(), 0, s>>>(lv[l], ph, pl, S, part, l, it);
+                const int vb = blocks((gl[l].nc + 3) / 4);
+                if (!last) k_pcg_u<T, false, false><<<vb, 256, 0, s>>>(lv[l], ph, pl, S, part, l, it);
+                else if (l > 0) k_pcg_u<T, true, false><<<vb, 256, 0, s>>>(lv[l], ph, pl, S, part, l, it);
+                else k_pcg_u<T, true, true><<<vb, 256, 0, s>>>(lv[l], ph, pl, S, part, l, it);
                 E();
             }
         }
