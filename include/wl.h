@@ -217,6 +217,41 @@ WL_API int wl_profile(wl_sim *sim, int on);
  * (NUL-terminated) into buf; *needed (may be NULL) receives the full size. */
 WL_API int wl_profile_report(wl_sim *sim, char *buf, size_t len, size_t *needed);
 
+/* Largest grid (cells) wl_coarse_solve_static accepts: its working memory is
+ * a fixed device array of 5 * WL_STATIC_MAX_CELLS + 8 doubles (~640 KiB) that
+ * every GPU loading this library holds until the process exits. */
+#define WL_STATIC_MAX_CELLS 16384
+
+/* Poisson solve that allocates no device memory (no counterpart in the paper:
+ * an addition for callers that cannot call cudaMalloc when they need the
+ * solve, such as code running during CUDA graph capture, where allocation is
+ * not a capturable call, or applications whose device memory is entirely
+ * owned by their own pool). Solves, on one thread block in double precision,
+ * A x = r - mean(r) with the operator and Jacobi-preconditioned CG of the
+ * library's coarsest multigrid level (the mean is over rows with a nonzero
+ * diagonal; x is returned mean-free over those rows and 0 elsewhere).
+ *   ndim, n[3], periodic[3]: the grid (n[2] ignored in 2D);
+ *   precision: element type of c, r, x (WL_F32 float, WL_F64 double);
+ *   c[a]: device array of the lower a-face coefficients of every cell (the
+ *         layout of include/wl.h fields); the upper faces of non-periodic axes
+ *         are taken as 0, and the caller gives 0 on their lower faces;
+ *   r, x: device arrays (x is written, r is read; they must not alias);
+ *   maxit, rtol: CG iteration limit and relative residual target;
+ *   stream: cudaStream_t (NULL = legacy default stream);
+ *   rel_resid: if not NULL, receives the final relative residual (the call
+ *         then synchronises the stream); if NULL the call only enqueues.
+ * The working memory is one file-scope device array shared by every call: it
+ * keeps the last call's contents and the solve re-initialises what it reads;
+ * calls that may overlap on the GPU (on different streams or host threads)
+ * race on it and must be serialised by the caller. The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.
+ * Errors: WL_ERR_ARG for bad arguments or n[0]*n[1]*n[2] > WL_STATIC_MAX_CELLS,
+ * WL_ERR_CUDA if the address lookup or the launch fails. */
+WL_API int wl_coarse_solve_static(int ndim, const int *n, const int *periodic, int precision,
+                                  const void *const *c, const void *r, void *x, int maxit, double rtol,
+                                  void *stream, double *rel_resid);
+
 WL_API const char *wl_last_error(const wl_sim *sim);
 WL_API const char *wl_status_string(int status);
 

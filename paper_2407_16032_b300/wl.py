@@ -25,7 +25,8 @@ EXPORTS = (
     "wl_config_default", "wl_sim_create", "wl_sim_destroy", "wl_set_velocity", "wl_get_velocity",
     "wl_get_pressure", "wl_set_pressure", "wl_set_time", "wl_get_time", "wl_mom_step", "wl_project",
     "wl_poisson_solve", "wl_conv_diff", "wl_forces", "wl_body_update", "wl_get_body_fields",
-    "wl_diagnostics", "wl_info", "wl_profile", "wl_profile_report", "wl_last_error", "wl_status_string",
+    "wl_diagnostics", "wl_info", "wl_profile", "wl_profile_report", "wl_coarse_solve_static", "wl_last_error",
+    "wl_status_string",
 )
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t)
@@ -90,6 +91,8 @@ def lib() -> C.CDLL:
             "wl_info": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_longlong)], ip),
             "wl_profile": ([vp, ip], ip),
             "wl_profile_report": ([vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)], ip),
+            "wl_coarse_solve_static": ([ip, C.POINTER(C.c_int), C.POINTER(C.c_int), ip, C.POINTER(vp), vp, vp, ip,
+                                        C.c_double, vp, dp], ip),
             "wl_last_error": ([vp], C.c_char_p),
             "wl_status_string": ([ip], C.c_char_p),
         }
@@ -316,3 +319,20 @@ def sim_from_case(case, precision="f32", **kw) -> Sim:
     (ndim, n, periodic, exit_hi_x, U, nu, eps, body, cfl, dt_max, dt0)."""
     return Sim(case.ndim, case.n, case.periodic, case.exit_hi_x, case.U, case.nu, case.eps, precision,
                case.body, cfl=case.cfl, dt_max=case.dt_max, dt_init=case.dt0, **kw)
+
+
+def coarse_solve_static(ndim, n, periodic, c, r, x, maxit=2000, rtol=1e-12, stream=None):
+    """wl_coarse_solve_static: the small Poisson solve that allocates no device
+    memory (for callers that cannot allocate, e.g. during CUDA graph capture).
+    c: sequence of ndim device tensors, r, x: device tensors, all float32 or
+    all float64. Returns (status, final relative residual)."""
+    import torch
+    prec = WL_F32 if r.dtype == torch.float32 else WL_F64
+    nn = (C.c_int * 3)(*(list(n) + [1, 1, 1])[:3])
+    pp = (C.c_int * 3)(*[int(bool(v)) for v in (list(periodic) + [0, 0, 0])[:3]])
+    cp = (C.c_void_p * 3)(*([t.data_ptr() for t in c] + [None] * (3 - len(c))))
+    rel = C.c_double()
+    st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    rc = lib().wl_coarse_solve_static(ndim, nn, pp, prec, cp, r.data_ptr(), x.data_ptr(), int(maxit),
+                                      float(rtol), st, C.byref(rel))
+    return rc, rel.value
