@@ -55,23 +55,27 @@ def describe(case, prec):
             "l2": "inputs larger than L2 (velocity alone > 126 MB)" if case.ncell * 12 > 126e6 else "small"}
 
 
-# bytes per cell of each kernel's algorithmic traffic (T = element size, nd = ndim)
+# Bytes per cell of each kernel's algorithmic traffic (T = element size, nd =
+# ndim): the arrays the method must read and write once per launch. Away from
+# the body the Poisson coefficients are uniform and formed from the position,
+# so the multigrid kernels move no coefficient arrays there (body tiles, a
+# small fraction, also read them: not counted, so the figure is a lower bound).
 def algo_bytes(name, T, nd, has_body=False):
     m1 = nd * nd
     return {
         "flux_pred": 2 * nd * T, "flux_pred_f": 2 * nd * T,
         "flux_corr": 3 * nd * T, "flux_corr_f": 3 * nd * T,
         "blend": (nd + nd + m1 + nd + nd) * T,
-        "div": (nd + 2) * T,
-        "resid": (2 + 1 + nd + 1 + 1) * T,
-        "restrict": 9 * T if nd == 3 else 5 * T,
-        "pcg_init": (1 / 8 + 1 + nd + 1 + 3) * T if nd == 3 else (1 / 4 + 1 + nd + 1 + 3) * T,
-        "pcg_q0": (1 + nd + 1) * T,
-        "pcg_q": (3 + nd + 2) * T,
-        "pcg_u": 7 * T,
-        "pcg_u_last": 3 * T,
-        "pcg_u_last_fine": 6 * T,
-        "grad": (nd + 2 + 2 * nd) * T,
+        "div": (nd + 2) * T,                          # u -> b (pair)
+        "resid": (4 + 1 + 1 / 2 ** nd) * T,           # ph, pl, b, bl -> r, coarse r
+        "restrict": (2 ** nd + 1) * T,                # per coarse cell
+        "pcg_init": (1 / 2 ** nd + 1 + 1 + 3) * T,    # xc, r, 1/D -> x, s, d
+        "pcg_q0": 2 * T,                              # d -> q
+        "pcg_q": 5 * T,                               # s, 1/D, d_prev -> d, q
+        "pcg_u": 7 * T,                               # x, d, s, q, 1/D -> x, s
+        "pcg_u_last": 3 * T,                          # x, d -> x
+        "pcg_u_last_fine": 6 * T,                     # x, d, ph, pl -> ph, pl
+        "grad": (2 + 2 * nd) * T,                     # ph, pl, u -> u
         "cfl": nd * T,
         "measure": ((nd + m1 + nd) if has_body else nd) * T,
     }.get(name)

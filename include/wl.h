@@ -134,7 +134,7 @@ WL_API void wl_config_default(wl_config *cfg, int ndim, const int *n);
 /* Create a simulation (Sec. 3 Simulation(dims, U, L; nu, body)).
  * Allocates all device state on the current device, measures the body at
  * t = 0, sets u = 0 with U on the inflow/wall faces and the exit plane, p = 0.
- * body may be NULL (no body). Errors: WL_ERR_ARG (bad sizes, ndim, eps <= 0,
+ * body may be NULL (no body). Errors: WL_ERR_ARG (bad sizes or 2^31 cells or more, ndim, eps <= 0,
  * nu < 0, ellipse in 3D, exit without non-periodic x), WL_ERR_ALLOC, WL_ERR_CUDA. */
 WL_API int wl_sim_create(const wl_config *cfg, const wl_body *body, wl_sim **out);
 

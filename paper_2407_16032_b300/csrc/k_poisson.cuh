@@ -26,7 +26,7 @@
 #include "wl_common.cuh"
 
 template <int NDIM> struct MT {
-    static constexpr int TX = 32, TY = 8, TZ = NDIM == 3 ? 4 : 1;
+    static constexpr int TX = 32, TY = 8, TZ = NDIM == 3 ? 8 : 1;
 };
 
 struct Tiles {
@@ -283,70 +283,6 @@ __device__ __forceinline__ void face_term(T hN, T lN, T h0, T l0, T c, T &th, T 
     tl = fma(c, dh, -th) + c * dl;
 }
 
-// r = (b - mean) - A (ph + pl) at active rows (0 elsewhere) into the fine-level
-// right-hand side; |r| / |b - mean| -> S->rel.
-template <typename T, int NDIM>
-__global__ void __launch_bounds__(256) k_resid(LevelD<T> L, const T *b, const T *bl, const T *ph, const T *pl,
-                                               DevScalars *S, double *part) {
-    const T bm = (T)S->bmean;
-    const T bml = (T)(S->bmean - (double)bm);
-    T acc[1] = {T(0)};
-    for_cells<NDIM>(L.g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
-        long long ip[3], im[3];
-        T cp[3], cm[3];
-        nb_setup<T, NDIM>(L, uni, i, j, k, idx, ip, im, cp, cm);
-        T res = T(0);
-        if (uni || L.invD[idx] != T(0)) {
-            const T h0 = ph[idx], l0 = pl[idx];
-            T Ah = T(0), Al = T(0);
-#pragma unroll
-            for (int a = 0; a < NDIM; ++a) {
-                if (cp[a] == cm[a]) {
-                    // equal faces: c [(p+ - p) - (p - p-)], the second difference
-                    // formed exactly (two-sums) before the single rounding
-                    T hp, ehp, hm, ehm, s2, es, th, tl, s, e;
-                    two_sum(ph[ip[a]], -h0, hp, ehp);
-                    two_sum(h0, -ph[im[a]], hm, ehm);
-                    two_sum(hp, -hm, s2, es);
-                    const T lo = ((ehp - ehm) + es) + ((pl[ip[a]] - l0) - (l0 - pl[im[a]]));
-                    th = cm[a] * s2;
-                    tl = fma(cm[a], s2, -th) + cm[a] * lo;
-                    two_sum(Ah, th, s, e);
-                    Ah = s;
-                    Al += e + tl;
-                } else {
-                    T th, tl, s, e;
-                    face_term(ph[ip[a]], pl[ip[a]], h0, l0, cp[a], th, tl);
-                    two_sum(Ah, th, s, e);
-                    Ah = s;
-                    Al += e + tl;
-                    face_term(ph[im[a]], pl[im[a]], h0, l0, cm[a], th, tl);
-                    two_sum(Ah, th, s, e);
-                    Ah = s;
-                    Al += e + tl;
-                }
-            }
-            // (b - mean) - A p with exact subtractions of the large parts
-            T r1, e1, r2, e2;
-            two_sum(b[idx], -bm, r1, e1);
-            two_sum(r1, -Ah, r2, e2);
-            res = r2 + (((e1 + e2) + (bl[idx] - bml)) - Al);
-            acc[0] += res * res;
-        }
-        L.r[idx] = res;
-    });
-    double out[1];
-    if (grid_reduce<1, false, T>(acc, part, &S->counters[RS_RESID], out)) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            S->rnorm2 = out[0];
-            const double bn = S->bnorm;
-            const double rel = bn > 0 ? sqrt(out[0]) / bn : (out[0] > 0 ? 1e300 : 0.0);
-            S->rel = rel;
-            if (!(rel == rel) || !(bn == bn) || rel >= 1e300) S->status |= 1;
-        }
-    }
-}
-
 // Restriction: coarse r = sum of the 2^n fine children.
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(256) k_restrict(GridD gf, const T *rf, LevelD<T> C) {
@@ -369,78 +305,6 @@ __device__ __forceinline__ long long parent_off(const GridD &gf, const GridD &gc
     if (I[a] < 0) I[a] = gf.per[a] ? gf.n[a] - 1 : 0;
     if (I[a] >= gf.n[a]) I[a] = gf.per[a] ? 0 : gf.n[a] - 1;
     return lin3(gc, I[0] >> 1, I[1] >> 1, gf.ndim == 3 ? (I[2] >> 1) : 0);
-}
-
-// PCG start on a level after the coarse correction: x = P x_c (injection),
-// s = r - A x, z = D^-1 s, d = z, rho = <s, z>.
-template <typename T, int NDIM>
-__global__ void __launch_bounds__(256) k_pcg_init(LevelD<T> L, GridD gc, const T *xc, DevScalars *S, double *part,
-                                                  int lev) {
-    T acc[1] = {T(0)};
-    for_cells<NDIM>(L.g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
-        const T x0 = xc[lin3(gc, i >> 1, j >> 1, NDIM == 3 ? (k >> 1) : 0)];
-        L.x[idx] = x0;
-        const T iD = L.invD[idx];
-        T s = T(0);
-        if (iD != T(0)) {
-            long long ip[3], im[3];
-            T cp[3], cm[3];
-            nb_setup<T, NDIM>(L, uni, i, j, k, idx, ip, im, cp, cm);
-            T Ax = T(0);
-#pragma unroll
-            for (int a = 0; a < NDIM; ++a)
-                Ax += cp[a] * (xc[parent_off(L.g, gc, i, j, k, a, 1)] - x0) -
-                      cm[a] * (x0 - xc[parent_off(L.g, gc, i, j, k, a, -1)]);
-            s = L.r[idx] - Ax;
-        }
-        const T z = iD * s;
-        L.s[idx] = s;
-        L.d[0][idx] = z;
-        acc[0] += s * z;
-    });
-    double out[1];
-    if (grid_reduce<1, false, T>(acc, part, &S->counters[RS_INIT], out))
-        if (threadIdx.x == 0 && threadIdx.y == 0) S->rho[lev] = out[0];
-}
-
-// PCG step part 1: the search direction d (iteration it > 0: d = D^-1 s + beta
-// d_prev, formed at every stencil point) and q = A d; alpha = rho / <d, q>.
-template <typename T, int NDIM>
-__global__ void __launch_bounds__(256) k_pcg_q(LevelD<T> L, DevScalars *S, double *part, int lev, int it) {
-    const T *dprev = L.d[(it + 1) & 1];
-    T *dcur = L.d[it & 1];
-    const T beta = it > 0 ? (T)S->beta[lev] : T(0);
-    T acc[1] = {T(0)};
-    for_cells<NDIM>(L.g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
-        long long ip[3], im[3];
-        T cp[3], cm[3];
-        nb_setup<T, NDIM>(L, uni, i, j, k, idx, ip, im, cp, cm);
-        T d0;
-        if (it == 0) {
-            d0 = dcur[idx];
-        } else {
-            d0 = L.invD[idx] * L.s[idx] + beta * dprev[idx];
-            dcur[idx] = d0;
-        }
-        T Ad = T(0);
-#pragma unroll
-        for (int a = 0; a < NDIM; ++a) {
-            T dp, dm;
-            if (it == 0) {
-                dp = dcur[ip[a]];
-                dm = dcur[im[a]];
-            } else {
-                dp = L.invD[ip[a]] * L.s[ip[a]] + beta * dprev[ip[a]];
-                dm = L.invD[im[a]] * L.s[im[a]] + beta * dprev[im[a]];
-            }
-            Ad += cp[a] * (dp - d0) - cm[a] * (d0 - dm);
-        }
-        L.q[idx] = Ad;
-        acc[0] += d0 * Ad;
-    });
-    double out[1];
-    if (grid_reduce<1, false, T>(acc, part, &S->counters[RS_Q], out))
-        if (threadIdx.x == 0 && threadIdx.y == 0) S->alpha[lev] = out[0] != 0.0 ? S->rho[lev] / out[0] : 0.0;
 }
 
 // PCG step part 2: x += alpha d; s -= alpha q; rho' = <s, D^-1 s>; beta = rho'/rho.

@@ -10,6 +10,7 @@
 #include "k_flux.cuh"
 #include "k_body.cuh"
 #include "k_poisson.cuh"
+#include "k_mg_march.cuh"
 #include "k_misc.cuh"
 
 #include <cmath>
@@ -361,7 +362,8 @@ struct Sim : SimBase {
         const bool tm = prof.on && s == st;
         auto B = [&](const char *nm, int l) { if (tm) P0(nm, l, gl[l].nc); };
         auto E = [&]() { if (tm) P1(); ++nodes; };
-        for (int l = 0; l + 1 < nlev; ++l) {
+        // level 0 -> 1 restriction is fused into the refinement residual
+        for (int l = 1; l + 1 < nlev; ++l) {
             B("restrict", l + 1);
             k_restrict<T, ND><<<tgrid(l + 1), tblk(), 0, s>>>(gl[l], lv[l].r, lv[l + 1]);
             E();
@@ -375,11 +377,12 @@ struct Sim : SimBase {
         E();
         for (int l = nlev - 2; l >= 0; --l) {
             B("pcg_init", l);
-            k_pcg_init<T, ND><<<tgrid(l), tblk(), 0, s>>>(lv[l], gl[l + 1], lv[l + 1].x, S, part, l);
+            k_pcg_initm<T, ND><<<tgrid(l), tblk(), 0, s>>>(lv[l], gl[l + 1], lv[l + 1].x, S, part, l);
             E();
             for (int it = 0; it < k; ++it) {
                 B(it == 0 ? "pcg_q0" : "pcg_q", l);
-                k_pcg_q<T, ND><<<tgrid(l), tblk(), 0, s>>>(lv[l], S, part, l, it);
+                if (it == 0) k_pcg_qm<T, ND, true><<<tgrid(l), tblk(), 0, s>>>(lv[l], S, part, l, it);
+                else k_pcg_qm<T, ND, false><<<tgrid(l), tblk(), 0, s>>>(lv[l], S, part, l, it);
                 E();
                 const bool last = it == k - 1;
                 B(last ? (l == 0 ? "pcg_u_last_fine" : "pcg_u_last") : "pcg_u", l);
@@ -396,8 +399,14 @@ struct Sim : SimBase {
             E();
         }
         B("resid", 0);
-        k_resid<T, ND><<<tgrid(0), tblk(), 0, s>>>(lv[0], b, bl, ph, pl, S, part);
+        resid_launch(s);
         E();
+    }
+
+    // refinement residual on level 0, restricted into level 1 when there is one
+    void resid_launch(cudaStream_t s) {
+        if (nlev > 1) k_residm<T, ND, true><<<tgrid(0), tblk(), 0, s>>>(lv[0], b, bl, ph, pl, lv[1], S, part);
+        else k_residm<T, ND, false><<<tgrid(0), tblk(), 0, s>>>(lv[0], b, bl, ph, pl, lv[0], S, part);
     }
 
     void build_vcycle_graph() {
@@ -415,7 +424,7 @@ struct Sim : SimBase {
     // b is in place; solve A (ph+pl) = b - mean with warm start; fills stats.
     int solve(wl_solve_stats *sts) {
         P0("resid", 0, g.nc);
-        k_resid<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], b, bl, ph, pl, S, part);
+        resid_launch(st);
         P1();
         WL_LAUNCH_CK();
         ++launches;
@@ -714,7 +723,7 @@ int validate(const wl_config *c, const wl_body *bd, std::string &msg) {
         if (c->n[a] < 2 || c->n[a] > (1 << 20)) { msg = "n[a] must be in [2, 2^20]"; return WL_ERR_ARG; }
     long long nc = 1;
     for (int a = 0; a < c->ndim; ++a) nc *= c->n[a];
-    if (nc > (1LL << 34)) { msg = "grid too large"; return WL_ERR_ARG; }
+    if (nc >= (1LL << 31)) { msg = "grid too large (the kernels index cells with 32-bit integers)"; return WL_ERR_ARG; }
     if (c->precision != WL_F32 && c->precision != WL_F64) { msg = "precision must be WL_F32 or WL_F64"; return WL_ERR_ARG; }
     if (!(c->eps > 0)) { msg = "eps must be positive"; return WL_ERR_ARG; }
     if (!(c->nu >= 0)) { msg = "nu must be >= 0"; return WL_ERR_ARG; }
