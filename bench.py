@@ -70,8 +70,8 @@ def algo_bytes(name, T, nd, has_body=False):
         "resid": (4 + 1 + 1 / 2 ** nd) * T,           # ph, pl, b, bl -> r, coarse r
         "restrict": (2 ** nd + 1) * T,                # per coarse cell
         "pcg_init": (1 / 2 ** nd + 1 + 1 + 3) * T,    # xc, r, 1/D -> x, s, d
-        "pcg_q0": 2 * T,                              # d -> q
-        "pcg_q": 5 * T,                               # s, 1/D, d_prev -> d, q
+        "pcg_d": 4 * T,                               # s, 1/D, d -> d
+        "pcg_q": 2 * T,                               # d -> q
         "pcg_u": 7 * T,                               # x, d, s, q, 1/D -> x, s
         "pcg_u_last": 3 * T,                          # x, d -> x
         "pcg_u_last_fine": 6 * T,                     # x, d, ph, pl -> ph, pl

@@ -90,25 +90,37 @@ __global__ void __launch_bounds__(FluxTile<NDIM>::NT) k_flux(GridD g, FluxArgs<T
                               y0 + TL::TY + TL::H <= n1 &&
                               (NDIM == 2 || (z0 >= TL::H && z0 + TL::TZ + TL::H <= n2));
         __syncthreads();  // previous tile's readers are done
+        // stage the tile: every global load of a component is issued before
+        // its shared-memory stores, so they are all in flight together
+        constexpr int NL = (TL::SN + TL::NT - 1) / TL::NT;
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {
             const T *__restrict__ ua = A.u[a];
             T *sa = s + a * TL::SN;
-            for (int e = tid; e < TL::SN; e += TL::NT) {
-                const int lx = e % TL::SX;
-                const int ly = (e / TL::SX) % TL::SY;
-                const int lz = e / (TL::SX * TL::SY);
-                const int gx = x0 + lx - TL::H, gy = y0 + ly - TL::H;
-                const int gz = NDIM == 3 ? z0 + lz - TL::H : 0;
-                sa[e] = interior ? ua[(long long)gx + (long long)n0 * ((long long)gy + (long long)n1 * gz)]
-                                 : vel_sample<T>(g, ua, A.ue, a, gx, gy, gz);
+            T v[NL];
+#pragma unroll
+            for (int q = 0; q < NL; ++q) {
+                const int e = tid + q * TL::NT;
+                if (e < TL::SN) {
+                    const int lx = e % TL::SX;
+                    const int ly = (e / TL::SX) % TL::SY;
+                    const int lz = e / (TL::SX * TL::SY);
+                    const int gx = x0 + lx - TL::H, gy = y0 + ly - TL::H;
+                    const int gz = NDIM == 3 ? z0 + lz - TL::H : 0;
+                    v[q] = interior ? ua[gx + n0 * (gy + n1 * gz)] : vel_sample<T>(g, ua, A.ue, a, gx, gy, gz);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NL; ++q) {
+                const int e = tid + q * TL::NT;
+                if (e < TL::SN) sa[e] = v[q];
             }
         }
         __syncthreads();
         const int i = x0 + tx, j = y0 + ty, k = z0 + tz;
         if (i >= n0 || j >= n1 || k >= n2) continue;
         const int L = (tx + TL::H) + TL::SX * ((ty + TL::H) + TL::SY * (NDIM == 3 ? tz + TL::H : 0));
-        const long long idx = (long long)i + (long long)n0 * ((long long)j + (long long)n1 * k);
+        const int idx = i + n0 * (j + n1 * k);
         const int I[3] = {i, j, k};
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {

@@ -1,31 +1,17 @@
-// k_mg_march.cuh -- shared-memory z-marching 7-point stencils of the V-cycle.
+// k_mg_march.cuh -- column-marching 7-point stencils of the V-cycle.
 //
 // The operator is the variable-coefficient Poisson operator of the projection
-// (Sec. 2, Sec. 3: u[I,i] -= c[I,i](p[I]-p[I-d(i)]) is its gradient half):
+// (Sec. 2; Sec. 3: u[I,i] -= c[I,i](p[I]-p[I-d(i)]) is its gradient half):
 //   (A p)[I] = sum_a c_a[I+e_a](p[I+e_a]-p[I]) - c_a[I](p[I]-p[I-e_a]).
-// Each 32x8 thread block owns a 32 x 8 x TZ tile. It stages the operand of the
-// tile and a one-cell halo (ZC + 2 planes) in shared memory in one burst of
-// independent coalesced loads, then computes ZC planes from it: every operand
-// value is loaded, or formed (the PCG search direction d = D^-1 s + beta
-// d_prev), once per tile and read by its seven stencil users from shared
-// memory. The domain edge wraps (periodic, any distance) or clamps (the
-// coefficient there is 0).
+// Each thread of a 32x8 block owns one (x, y) column of a 32 x 8 x TZ tile and
+// walks it along z: the z neighbours rotate through registers (one new load per
+// plane), the x and y neighbours are read through L1 at offsets formed once per
+// column (wrapped on periodic axes, clamped elsewhere where the coefficient is
+// 0), and there is no shared-memory staging or barrier in the march.
 #pragma once
 #include "k_poisson.cuh"
 
-template <int NDIM> struct MW {
-    static constexpr int TX = 32, TY = 8, TZ = MT<NDIM>::TZ;
-    static constexpr int WX = TX + 2, WY = TY + 2, WN = WX * WY;
-};
-// Planes computed per slab load (the slab holds ZC + 2 planes in 3D): all of
-// a tile's 8 planes in single precision, half of them in double.
-template <int NDIM, typename T> struct MZ {
-    static constexpr int ZC = NDIM == 3 ? (sizeof(T) == 4 ? MT<NDIM>::TZ : MT<NDIM>::TZ / 2) : 1;
-    static constexpr int NPL = NDIM == 3 ? ZC + 2 : 1;
-};
-
-// Index along an axis of N cells: periodic axes wrap (any distance: the
-// window is wider than small coarse levels), others clamp.
+// Index along an axis of N cells: periodic axes wrap (any distance), others clamp.
 __device__ __forceinline__ int edge_idx(int v, int N, bool per) {
     if (v >= 0 && v < N) return v;
     if (per) {
@@ -35,22 +21,25 @@ __device__ __forceinline__ int edge_idx(int v, int N, bool per) {
     return v < 0 ? 0 : N - 1;
 }
 
-// Load the slab of planes zs-1 .. zs+ZC (3D; the single plane in 2D) of the
-// tile at (x0, y0) with its one-cell xy halo: slab[e] = f(global index). All
-// loads of the slab are independent, so a block keeps them all in flight.
-template <int NDIM, typename T, typename F>
-__device__ __forceinline__ void load_slab(T *slab, const GridD &g, int x0, int y0, int zs, F &&f) {
-    using W = MW<NDIM>;
-    constexpr int NPL = MZ<NDIM, T>::NPL;
-    const int tid = threadIdx.x + 32 * threadIdx.y;
-    for (int e = tid; e < NPL * W::WN; e += 256) {
-        const int pl = e / W::WN, rem = e - pl * W::WN;
-        const int ly = rem / W::WX, lx = rem - ly * W::WX;
-        const int gx = edge_idx(x0 + lx - 1, g.n[0], g.per[0] != 0);
-        const int gy = edge_idx(y0 + ly - 1, g.n[1], g.per[1] != 0);
-        const int gz = NDIM == 3 ? edge_idx(zs - 1 + pl, g.n[2], g.per[2] != 0) : 0;
-        slab[e] = f(gx + g.n[0] * (gy + g.n[1] * gz));
-    }
+// Per-column set-up: cell (i, j) of the plane and the in-plane offsets of its
+// x and y neighbours.
+struct Col {
+    int i, j, oxm, oxp, oym, oyp;
+    bool in;
+};
+
+__device__ __forceinline__ Col column(const GridD &g, int x0, int y0) {
+    Col c;
+    c.i = x0 + threadIdx.x;
+    c.j = y0 + threadIdx.y;
+    c.in = c.i < g.n[0] && c.j < g.n[1];
+    const int i = c.in ? c.i : 0, j = c.in ? c.j : 0;
+    const bool px = g.per[0] != 0, py = g.per[1] != 0;
+    c.oxm = edge_idx(i - 1, g.n[0], px) - i;
+    c.oxp = edge_idx(i + 1, g.n[0], px) - i;
+    c.oym = (edge_idx(j - 1, g.n[1], py) - j) * g.n[0];
+    c.oyp = (edge_idx(j + 1, g.n[1], py) - j) * g.n[0];
+    return c;
 }
 
 // Face coefficients of cell (i,j,k) = idx: uniform tiles from the position,
@@ -74,72 +63,85 @@ __device__ __forceinline__ void coefs(const LevelD<T> &L, bool uni, int i, int j
     }
 }
 
-// The six neighbours of the window centre (tx, ty) of plane slots pm/pc/pp.
-template <int NDIM, typename T>
-struct Nb6 {
-    T c, xm, xp, ym, yp, zm, zp;
-};
-template <int NDIM, typename T>
-__device__ __forceinline__ Nb6<NDIM, T> nb6(const T *pm, const T *pc, const T *pp) {
-    using W = MW<NDIM>;
-    const int o = (threadIdx.y + 1) * W::WX + threadIdx.x + 1;
-    Nb6<NDIM, T> r;
-    r.c = pc[o];
-    r.xm = pc[o - 1];
-    r.xp = pc[o + 1];
-    r.ym = pc[o - W::WX];
-    r.yp = pc[o + W::WX];
-    if (NDIM == 3) { r.zm = pm[o]; r.zp = pp[o]; } else { r.zm = r.zp = T(0); }
-    return r;
-}
-
 // Walk the tiles of a level: body(x0, y0, z0, uniform) for each tile.
 template <int NDIM, typename F>
 __device__ __forceinline__ void for_tiles(const Tiles &tl, const unsigned char *tflag, F &&body) {
     for (int t = blockIdx.x; t < tl.nt; t += gridDim.x) {
         const int bx = t % tl.ntx, rr = t / tl.ntx;
         const int by = rr % tl.nty, bz = rr / tl.nty;
-        body(bx * 32, by * 8, bz * MW<NDIM>::TZ, tflag ? tflag[t] != 0 : false);
+        body(bx * 32, by * 8, bz * MT<NDIM>::TZ, tflag ? tflag[t] != 0 : false);
     }
 }
 
-// q = A d with d formed on the fly (IT0: d as stored; else d = D^-1 s + beta
-// d_prev, written back); alpha = rho / <d, q>.
-template <typename T, int NDIM, bool IT0>
-__global__ void __launch_bounds__(256) k_pcg_qm(LevelD<T> L, DevScalars *S, double *part, int lev, int it) {
-    using W = MW<NDIM>;
-    using Z = MZ<NDIM, T>;
-    __shared__ T slab[Z::NPL * W::WN];
-    const T *dprev = L.d[(it + 1) & 1];
-    T *dcur = L.d[it & 1];
-    const T beta = IT0 ? T(0) : (T)S->beta[lev];
+// Search direction d = D^-1 s + beta d, in place (elementwise, 16-byte vectors).
+template <typename T>
+__global__ void __launch_bounds__(256) k_pcg_d(LevelD<T> L, DevScalars *S, int lev) {
+    typedef typename V16<T>::type VT;
+    constexpr int W = V16<T>::n;
+    const T beta = (T)S->beta[lev];
+    const long long n = L.g.nc;
+    const long long nv = (n % W == 0) ? n / W : 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    T *d = L.d[0];
+    for (long long v = t0; v < nv; v += stride) {
+        const VT s = ((const VT *)L.s)[v], iD = ((const VT *)L.invD)[v];
+        VT dv = ((VT *)d)[v];
+        T *de = (T *)&dv;
+        const T *se = (const T *)&s, *ie = (const T *)&iD;
+#pragma unroll
+        for (int e = 0; e < W; ++e) de[e] = ie[e] * se[e] + beta * de[e];
+        ((VT *)d)[v] = dv;
+    }
+    if (nv == 0)
+        for (long long e = t0; e < n; e += stride) d[e] = L.invD[e] * L.s[e] + beta * d[e];
+}
+
+// q = A d and alpha = rho / <d, q>. Each thread loads its whole column (the
+// TZ + 2 z values and the 4 TZ x/y neighbours) before computing, with
+// restrict-qualified pointers, so all of those loads are in flight at once.
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_pcg_qm(LevelD<T> L, DevScalars *S, double *part, int lev) {
+    constexpr int TZ = MT<NDIM>::TZ;
     const GridD &g = L.g;
-    auto op = [&](int q) -> T { return IT0 ? dcur[q] : L.invD[q] * L.s[q] + beta * dprev[q]; };
+    const T *__restrict__ d = L.d[0];
+    T *__restrict__ q = L.q;
+    const int plane = g.n[0] * g.n[1];
+    const bool pz = g.per[2] != 0;
     T acc[1] = {T(0)};
-    const int i = threadIdx.x, j = threadIdx.y;
     for_tiles<NDIM>(L.tl, L.tflag, [&](int x0, int y0, int z0, bool uni) {
-        const int gi = x0 + i, gj = y0 + j;
-        const bool in = gi < g.n[0] && gj < g.n[1];
-        const int zb = NDIM == 3 ? z0 : 0, zend = NDIM == 3 ? min(z0 + W::TZ, g.n[2]) : 1;
-        for (int zs = zb; zs < zend; zs += Z::ZC) {
-            __syncthreads();
-            load_slab<NDIM, T>(slab, g, x0, y0, zs, op);
-            __syncthreads();
-            if (!in) continue;
-            for (int dz = 0; dz < Z::ZC && zs + dz < zend; ++dz) {
-                const int z = zs + dz;
-                const T *pc = slab + (NDIM == 3 ? (dz + 1) * W::WN : 0);
-                const Nb6<NDIM, T> v = nb6<NDIM>(NDIM == 3 ? pc - W::WN : pc, pc, NDIM == 3 ? pc + W::WN : pc);
-                const int idx = gi + g.n[0] * (gj + g.n[1] * z);
-                T cp[3], cm[3];
-                coefs<T, NDIM>(L, uni, gi, gj, z, idx, cp, cm);
-                T Ad = cp[0] * (v.xp - v.c) - cm[0] * (v.c - v.xm) + cp[1] * (v.yp - v.c) - cm[1] * (v.c - v.ym);
-                if (NDIM == 3) Ad += cp[2] * (v.zp - v.c) - cm[2] * (v.c - v.zm);
-                if (!IT0) dcur[idx] = v.c;
-                L.q[idx] = Ad;
-                acc[0] += v.c * Ad;
-            }
+        const Col c = column(g, x0, y0);
+        if (!c.in) return;
+        const int base = c.i + g.n[0] * c.j;
+        const int zb = NDIM == 3 ? z0 : 0, nz = NDIM == 3 ? min(TZ, g.n[2] - z0) : 1;
+        T vz[TZ + 2], xm[TZ], xp[TZ], ym[TZ], yp[TZ];
+#pragma unroll
+        for (int t = 0; t < TZ + 2; ++t) {
+            vz[t] = T(0);
+            if (NDIM == 3 && t <= nz + 1) vz[t] = d[base + plane * edge_idx(zb - 1 + t, g.n[2], pz)];
         }
+#pragma unroll
+        for (int t = 0; t < TZ; ++t)
+            if (t < nz) {
+                const int idx = base + plane * (zb + t);
+                if (NDIM == 2) vz[1] = d[idx];
+                xm[t] = d[idx + c.oxm];
+                xp[t] = d[idx + c.oxp];
+                ym[t] = d[idx + c.oym];
+                yp[t] = d[idx + c.oyp];
+            }
+#pragma unroll
+        for (int t = 0; t < TZ; ++t)
+            if (t < nz) {
+                const int k = zb + t, idx = base + plane * k;
+                T cp[3], cm[3];
+                coefs<T, NDIM>(L, uni, c.i, c.j, k, idx, cp, cm);
+                const T vc = vz[t + 1];
+                T Ad = cp[0] * (xp[t] - vc) - cm[0] * (vc - xm[t]) + cp[1] * (yp[t] - vc) - cm[1] * (vc - ym[t]);
+                if (NDIM == 3) Ad += cp[2] * (vz[t + 2] - vc) - cm[2] * (vc - vz[t]);
+                q[idx] = Ad;
+                acc[0] += vc * Ad;
+            }
     });
     double out[1];
     if (grid_reduce<1, false, T>(acc, part, &S->counters[RS_Q], out))
@@ -151,46 +153,56 @@ __global__ void __launch_bounds__(256) k_pcg_qm(LevelD<T> L, DevScalars *S, doub
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(256) k_pcg_initm(LevelD<T> L, GridD gc, const T *xc, DevScalars *S, double *part,
                                                    int lev) {
-    using W = MW<NDIM>;
-    using Z = MZ<NDIM, T>;
-    __shared__ T slab[Z::NPL * W::WN];
     const GridD &g = L.g;
-    const int n0 = g.n[0], n01 = g.n[0] * g.n[1];
-    auto op = [&](int q) -> T {
-        const int k = q / n01, rem = q - k * n01, j = rem / n0, i = rem - j * n0;
-        return xc[(i >> 1) + gc.n[0] * ((j >> 1) + gc.n[1] * (NDIM == 3 ? (k >> 1) : 0))];
-    };
     T acc[1] = {T(0)};
-    const int i = threadIdx.x, j = threadIdx.y;
     for_tiles<NDIM>(L.tl, L.tflag, [&](int x0, int y0, int z0, bool uni) {
-        const int gi = x0 + i, gj = y0 + j;
-        const bool in = gi < g.n[0] && gj < g.n[1];
-        const int zb = NDIM == 3 ? z0 : 0, zend = NDIM == 3 ? min(z0 + W::TZ, g.n[2]) : 1;
-        for (int zs = zb; zs < zend; zs += Z::ZC) {
-            __syncthreads();
-            load_slab<NDIM, T>(slab, g, x0, y0, zs, op);
-            __syncthreads();
-            if (!in) continue;
-            for (int dz = 0; dz < Z::ZC && zs + dz < zend; ++dz) {
-                const int z = zs + dz;
-                const T *pc = slab + (NDIM == 3 ? (dz + 1) * W::WN : 0);
-                const Nb6<NDIM, T> v = nb6<NDIM>(NDIM == 3 ? pc - W::WN : pc, pc, NDIM == 3 ? pc + W::WN : pc);
-                const int idx = gi + g.n[0] * (gj + g.n[1] * z);
-                const T iD = L.invD[idx];
-                T sv = T(0);
-                if (iD != T(0)) {
-                    T cp[3], cm[3];
-                    coefs<T, NDIM>(L, uni, gi, gj, z, idx, cp, cm);
-                    T Ax = cp[0] * (v.xp - v.c) - cm[0] * (v.c - v.xm) + cp[1] * (v.yp - v.c) - cm[1] * (v.c - v.ym);
-                    if (NDIM == 3) Ax += cp[2] * (v.zp - v.c) - cm[2] * (v.c - v.zm);
-                    sv = L.r[idx] - Ax;
-                }
-                const T zz = iD * sv;
-                L.x[idx] = v.c;
-                L.s[idx] = sv;
-                L.d[0][idx] = zz;
-                acc[0] += sv * zz;
+        const Col c = column(g, x0, y0);
+        if (!c.in) return;
+        // injection: the operand at a fine cell is its parent's coarse value
+        const int ci = c.i >> 1, cj = c.j >> 1;
+        const int cxm = ((c.i + c.oxm) >> 1) - ci, cxp = ((c.i + c.oxp) >> 1) - ci;
+        const int cym = (((c.j + c.oym / g.n[0]) >> 1) - cj) * gc.n[0];
+        const int cyp = (((c.j + c.oyp / g.n[0]) >> 1) - cj) * gc.n[0];
+        const int cplane = gc.n[0] * gc.n[1];
+        const int cbase = ci + gc.n[0] * cj;
+        const bool pz = g.per[2] != 0;
+        const int zb = NDIM == 3 ? z0 : 0, ze = NDIM == 3 ? min(z0 + MT<NDIM>::TZ, g.n[2]) : 1;
+        constexpr int TZ = MT<NDIM>::TZ;
+        const T *__restrict__ rr = L.r;
+        const T *__restrict__ id = L.invD;
+        T rv[TZ], iv[TZ];
+#pragma unroll
+        for (int t = 0; t < TZ; ++t)
+            if (zb + t < ze) {
+                const int idx = c.i + g.n[0] * (c.j + g.n[1] * (zb + t));
+                rv[t] = rr[idx];
+                iv[t] = id[idx];
             }
+#pragma unroll
+        for (int t = 0; t < TZ; ++t) {
+            const int k = zb + t;
+            if (k >= ze) break;
+            const int cb = cbase + cplane * (NDIM == 3 ? (k >> 1) : 0);
+            const int idx = c.i + g.n[0] * (c.j + g.n[1] * k);
+            const T x0v = xc[cb];
+            L.x[idx] = x0v;
+            const T iD = iv[t];
+            T s = T(0);
+            if (iD != T(0)) {
+                T cp[3], cm[3];
+                coefs<T, NDIM>(L, uni, c.i, c.j, k, idx, cp, cm);
+                T Ax = cp[0] * (xc[cb + cxp] - x0v) - cm[0] * (x0v - xc[cb + cxm]) + cp[1] * (xc[cb + cyp] - x0v) -
+                       cm[1] * (x0v - xc[cb + cym]);
+                if (NDIM == 3) {
+                    const int kp = edge_idx(k + 1, g.n[2], pz) >> 1, km = edge_idx(k - 1, g.n[2], pz) >> 1;
+                    Ax += cp[2] * (xc[cbase + cplane * kp] - x0v) - cm[2] * (x0v - xc[cbase + cplane * km]);
+                }
+                s = rv[t] - Ax;
+            }
+            const T z = iD * s;
+            L.s[idx] = s;
+            L.d[0][idx] = z;
+            acc[0] += s * z;
         }
     });
     double out[1];
@@ -201,90 +213,111 @@ __global__ void __launch_bounds__(256) k_pcg_initm(LevelD<T> L, GridD gc, const 
 // Refinement residual r = (b - mean) - A (ph + pl), compensated (exact
 // differences, FMA products, two-sum accumulation), at active rows; written to
 // the fine level and, when RESTRICT, summed over the 2^n children straight into
-// the next level's right-hand side; |r| / |b - mean| -> S->rel.
+// the next level's right-hand side; |r| / |b - mean| -> S->rel. A column is
+// processed in batches of HB planes whose loads are all issued first.
 template <typename T, int NDIM, bool RESTRICT>
-__global__ void __launch_bounds__(256) k_residm(LevelD<T> L, const T *b, const T *bl, const T *ph, const T *pl,
-                                                LevelD<T> C, DevScalars *S, double *part) {
-    using W = MW<NDIM>;
-    using Z = MZ<NDIM, T>;
-    __shared__ T sh_[Z::NPL * W::WN], sl_[Z::NPL * W::WN];
+__global__ void __launch_bounds__(256) k_residm(LevelD<T> L, const T *__restrict__ b, const T *__restrict__ bl,
+                                                const T *__restrict__ ph, const T *__restrict__ pl, LevelD<T> C,
+                                                DevScalars *S, double *part) {
+    constexpr int TZ = MT<NDIM>::TZ;
+    constexpr int HB = NDIM == 3 ? 2 : 1;
     __shared__ T rpl[8][33];
     const GridD &g = L.g;
     const T bm = (T)S->bmean;
     const T bml = (T)(S->bmean - (double)bm);
-    auto oph = [&](int q) -> T { return ph[q]; };
-    auto opl = [&](int q) -> T { return pl[q]; };
+    const int plane = g.n[0] * g.n[1];
+    const bool pz = g.per[2] != 0;
+    T *__restrict__ rout = L.r;
     T acc[1] = {T(0)};
-    const int i = threadIdx.x, j = threadIdx.y;
     for_tiles<NDIM>(L.tl, L.tflag, [&](int x0, int y0, int z0, bool uni) {
-        const int gi = x0 + i, gj = y0 + j;
-        const bool in = gi < g.n[0] && gj < g.n[1];
-        const int zb = NDIM == 3 ? z0 : 0, zend = NDIM == 3 ? min(z0 + W::TZ, g.n[2]) : 1;
-        T csum = T(0);  // restriction partial over a z pair
-        for (int zs = zb; zs < zend; zs += Z::ZC) {
-            __syncthreads();
-            load_slab<NDIM, T>(sh_, g, x0, y0, zs, oph);
-            load_slab<NDIM, T>(sl_, g, x0, y0, zs, opl);
-            __syncthreads();
-            for (int dz = 0; dz < Z::ZC && zs + dz < zend; ++dz) {
-                const int z = zs + dz;
+        const Col c = column(g, x0, y0);
+        const int base = (c.in ? c.i : 0) + g.n[0] * (c.in ? c.j : 0);
+        const int zb = NDIM == 3 ? z0 : 0, nz = NDIM == 3 ? min(TZ, g.n[2] - z0) : 1;
+        T csum = T(0);
+        for (int hb = 0; hb < nz; hb += HB) {
+            // batch loads: z column (HB + 2), x/y neighbours, b pair
+            T hz[HB + 2], lz[HB + 2], hx[4][HB], lx[4][HB], bv[HB], blv[HB];
+#pragma unroll
+            for (int t = 0; t < HB + 2; ++t) {
+                hz[t] = lz[t] = T(0);
+                if (c.in && (NDIM == 3 ? hb + t <= nz + 1 - 0 && hb + t - 1 <= nz : t == 1)) {
+                    const int q = NDIM == 3 ? base + plane * edge_idx(zb + hb - 1 + t, g.n[2], pz) : base;
+                    hz[t] = ph[q];
+                    lz[t] = pl[q];
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < HB; ++t)
+                if (c.in && hb + t < nz) {
+                    const int idx = base + plane * (zb + hb + t);
+                    const int off[4] = {c.oxm, c.oxp, c.oym, c.oyp};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        hx[u][t] = ph[idx + off[u]];
+                        lx[u][t] = pl[idx + off[u]];
+                    }
+                    bv[t] = b[idx];
+                    blv[t] = bl[idx];
+                }
+#pragma unroll
+            for (int t = 0; t < HB; ++t) {
+                const int k = zb + hb + t;
+                const bool live = hb + t < nz;
+                const int idx = base + plane * k;
                 T res = T(0);
-                if (in) {
-                    const int idx = gi + g.n[0] * (gj + g.n[1] * z);
+                if (c.in && live) {
                     if (uni || L.invD[idx] != T(0)) {
-                        const T *hc = sh_ + (NDIM == 3 ? (dz + 1) * W::WN : 0);
-                        const T *lc = sl_ + (NDIM == 3 ? (dz + 1) * W::WN : 0);
-                        const Nb6<NDIM, T> h = nb6<NDIM>(NDIM == 3 ? hc - W::WN : hc, hc, NDIM == 3 ? hc + W::WN : hc);
-                        const Nb6<NDIM, T> l = nb6<NDIM>(NDIM == 3 ? lc - W::WN : lc, lc, NDIM == 3 ? lc + W::WN : lc);
                         T cp[3], cm[3];
-                        coefs<T, NDIM>(L, uni, gi, gj, z, idx, cp, cm);
-                        const T hP[3] = {h.xp, h.yp, h.zp}, hM[3] = {h.xm, h.ym, h.zm};
-                        const T lP[3] = {l.xp, l.yp, l.zp}, lM[3] = {l.xm, l.ym, l.zm};
+                        coefs<T, NDIM>(L, uni, c.i, c.j, k, idx, cp, cm);
+                        const T hc = hz[t + 1], lc = lz[t + 1];
+                        const T hP[3] = {hx[1][t], hx[3][t], hz[t + 2]}, hM[3] = {hx[0][t], hx[2][t], hz[t]};
+                        const T lP[3] = {lx[1][t], lx[3][t], lz[t + 2]}, lM[3] = {lx[0][t], lx[2][t], lz[t]};
                         T Ah = T(0), Al = T(0);
 #pragma unroll
                         for (int a = 0; a < NDIM; ++a) {
                             T th, tl, s, e;
                             if (cp[a] == cm[a]) {
                                 // equal faces: c [(p+ - p) - (p - p-)] formed exactly
-                                T hp, ehp, hm, ehm, s2, es;
-                                two_sum(hP[a], -h.c, hp, ehp);
-                                two_sum(h.c, -hM[a], hm, ehm);
-                                two_sum(hp, -hm, s2, es);
-                                const T lo = ((ehp - ehm) + es) + ((lP[a] - l.c) - (l.c - lM[a]));
+                                T d1, e1, d2, e2, s2, es;
+                                two_sum(hP[a], -hc, d1, e1);
+                                two_sum(hc, -hM[a], d2, e2);
+                                two_sum(d1, -d2, s2, es);
+                                const T lo = ((e1 - e2) + es) + ((lP[a] - lc) - (lc - lM[a]));
                                 th = cm[a] * s2;
                                 tl = fma(cm[a], s2, -th) + cm[a] * lo;
                                 two_sum(Ah, th, s, e);
                                 Ah = s;
                                 Al += e + tl;
                             } else {
-                                face_term(hP[a], lP[a], h.c, l.c, cp[a], th, tl);
+                                face_term(hP[a], lP[a], hc, lc, cp[a], th, tl);
                                 two_sum(Ah, th, s, e);
                                 Ah = s;
                                 Al += e + tl;
-                                face_term(hM[a], lM[a], h.c, l.c, cm[a], th, tl);
+                                face_term(hM[a], lM[a], hc, lc, cm[a], th, tl);
                                 two_sum(Ah, th, s, e);
                                 Ah = s;
                                 Al += e + tl;
                             }
                         }
                         T r1, e1, r2, e2;
-                        two_sum(b[idx], -bm, r1, e1);
+                        two_sum(bv[t], -bm, r1, e1);
                         two_sum(r1, -Ah, r2, e2);
-                        res = r2 + (((e1 + e2) + (bl[idx] - bml)) - Al);
+                        res = r2 + (((e1 + e2) + (blv[t] - bml)) - Al);
                         acc[0] += res * res;
                     }
-                    L.r[idx] = res;
+                    rout[idx] = res;
                 }
-                if (RESTRICT) {
+                if (RESTRICT && live) {
                     // children (2i..2i+1, 2j..2j+1, 2k..2k+1): x pairs by shuffle,
                     // y pairs through shared memory, z pairs in a register
+                    const int i = threadIdx.x, j = threadIdx.y;
                     const T v = res + __shfl_xor_sync(0xffffffffu, res, 1);
                     rpl[j][i] = v;
                     __syncthreads();
                     if ((i & 1) == 0 && (j & 1) == 0) {
                         csum += v + rpl[j + 1][i];
-                        if (NDIM == 2 || (z & 1) == 1) {
-                            const int ci = gi >> 1, cj = gj >> 1, ck = NDIM == 3 ? (z >> 1) : 0;
+                        if (NDIM == 2 || (k & 1) == 1) {
+                            const int ci = c.i >> 1, cj = c.j >> 1, ck = NDIM == 3 ? (k >> 1) : 0;
                             if (ci < C.g.n[0] && cj < C.g.n[1]) C.r[ci + C.g.n[0] * (cj + C.g.n[1] * ck)] = csum;
                             csum = T(0);
                         }

@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(256) k_pcg_u(LevelD<T> L, T *ph, T *pl, DevSca
                                                int it) {
     typedef typename V16<T>::type VT;
     constexpr int W = V16<T>::n;
-    const T *dcur = L.d[it & 1];
+    const T *dcur = L.d[0];
     const T alpha = (T)S->alpha[lev];
     T acc[1] = {T(0)};
     const long long n = L.g.nc;

@@ -380,9 +380,13 @@ struct Sim : SimBase {
             k_pcg_initm<T, ND><<<tgrid(l), tblk(), 0, s>>>(lv[l], gl[l + 1], lv[l + 1].x, S, part, l);
             E();
             for (int it = 0; it < k; ++it) {
-                B(it == 0 ? "pcg_q0" : "pcg_q", l);
-                if (it == 0) k_pcg_qm<T, ND, true><<<tgrid(l), tblk(), 0, s>>>(lv[l], S, part, l, it);
-                else k_pcg_qm<T, ND, false><<<tgrid(l), tblk(), 0, s>>>(lv[l], S, part, l, it);
+                if (it > 0) {
+                    B("pcg_d", l);
+                    k_pcg_d<T><<<blocks((gl[l].nc + 3) / 4), 256, 0, s>>>(lv[l], S, l);
+                    E();
+                }
+                B("pcg_q", l);
+                k_pcg_qm<T, ND><<<tgrid(l), tblk(), 0, s>>>(lv[l], S, part, l);
                 E();
                 const bool last = it == k - 1;
                 B(last ? (l == 0 ? "pcg_u_last_fine" : "pcg_u_last") : "pcg_u", l);
