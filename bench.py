@@ -89,23 +89,21 @@ def load_peaks():
     return 6400.0, "fallback"
 
 
-def source_hash():
+def source_hash(files):
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2407_16032_b300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def traffic_for(kernel):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
+    the kernel's current source files (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
-    e = d.get(kernel)
-    if not e or e.get("source_hash") != source_hash():
+    e = json.load(open(p)).get(kernel)
+    if not e or e.get("source_hash") != source_hash(e.get("source_files", [])):
         return None
     return e.get("dram_bytes_per_launch")
 

@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256) k_residm(LevelD<T> L, const T *__restrict
                                                 const T *__restrict__ ph, const T *__restrict__ pl, LevelD<T> C,
                                                 DevScalars *S, double *part) {
     constexpr int TZ = MT<NDIM>::TZ;
-    constexpr int HB = NDIM == 3 ? 2 : 1;
+    constexpr int HB = 1;
     __shared__ T rpl[8][33];
     const GridD &g = L.g;
     const T bm = (T)S->bmean;
