@@ -206,6 +206,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -291,6 +292,51 @@ def main():
                 "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": src,
                 "algorithmic_bytes_per_launch": int(bpl), "traffic": traffic_for(nm)}
 
+    # ---- learned Poisson guess vs plain multigrid on the same workload: the
+    # network is set up, fed by the solver's own converged projections,
+    # trained on the GPU, then the same number of steps is timed with it on
+    learned = None
+    if not args.no_learned:
+        lev = 2
+        sim.guess_setup(level=lev, capacity=64)
+        sim.guess_mode(collect=True)
+        for _ in range(16):
+            sim.mom_step()
+        sim.guess_mode(collect=False)
+        t0 = time.perf_counter()
+        loss0, loss1 = sim.guess_train(iters=300, lr=2e-3, batch=4, seed=0)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        res = {}
+        su, _ = sim.get_velocity()
+        sp = sim.get_pressure()
+        tt, dtt = sim.get_time()
+        for use in (False, True):
+            sim.set_velocity(su)
+            sim.set_pressure(sp)
+            sim.set_time(tt, dtt)
+            sim.guess_mode(use=use)
+            sim.mom_step()
+            torch.cuda.synchronize()
+            a, bq = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            vc, r0 = [], []
+            a.record(stream)
+            for _ in range(args.steps):
+                st, rc = sim.mom_step()
+                vc.append(st.proj[0].vcycles + st.proj[1].vcycles)
+                r0.append(0.5 * (st.proj[0].rel_initial + st.proj[1].rel_initial))
+            bq.record(stream)
+            torch.cuda.synchronize()
+            res[use] = (case.ncell * args.steps / (a.elapsed_time(bq) / 1000.0), statistics.mean(vc), statistics.mean(r0))
+        sim.guess_mode(use=False)
+        learned = {"value": res[True][0], "plain_mg_value": res[False][0], "unit": UNIT,
+                   "speedup": res[True][0] / res[False][0],
+                   "vcycles_per_step": {"plain": res[False][1], "learned": res[True][1]},
+                   "initial_rel_residual": {"plain": res[False][2], "learned": res[True][2]},
+                   "net": "bias-free ReLU 3D CNN 1-16-16-1, 3^3 kernels, BF16 mma.sync, on MG level 2",
+                   "train": {"samples": 32, "adam_steps": 300, "batch": 4, "loss_first": loss0, "loss_last": loss1,
+                             "seconds": t_train}}
+
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -324,7 +370,7 @@ def main():
                "config": describe(case, prec) | {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                                                  "vcycles_per_step_mean": statistics.mean(vcyc)},
                "hbm_GBps_dominant_kernel": roof["achieved"] if roof else None,
-               "roofline": roof, "kernels": kernels[:10], "cpu_baseline": cpu, "e2e": e2e,
+               "roofline": roof, "kernels": kernels[:10], "learned_guess": learned, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": l1 - l0, "clocks": clocks,
                "paper_context": {"ns_per_cell_step": 1.57, "cell_steps_per_s": 6.4e8,
                                  "hw": "NVIDIA H100, FP32, TGV 134M cells (Sec. 4.1)"}}

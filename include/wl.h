@@ -118,6 +118,7 @@ typedef struct {
     int vcycles;           /* V-cycles used */
     double rel_resid;      /* final |b - A p|_2 / |b|_2 over active rows */
     double bnorm;          /* |b|_2 of the mean-free right-hand side */
+    double rel_initial;    /* relative residual of the initial guess (after the learned guess, if used) */
 } wl_solve_stats;
 
 typedef struct {
@@ -216,6 +217,39 @@ WL_API int wl_profile(wl_sim *sim, int on);
  * "name level launches total_ms cells_per_launch". Writes at most len bytes
  * (NUL-terminated) into buf; *needed (may be NULL) receives the full size. */
 WL_API int wl_profile_report(wl_sim *sim, char *buf, size_t len, size_t *needed);
+
+/* Learned Poisson initial guess (no counterpart in the paper; its data-driven
+ * multigrid reference, Sec. 3, is the precedent). A bias-free ReLU 3D
+ * convolutional network with 3x3x3 kernels and channels 1 -> 16 -> 16 -> 1 runs
+ * on multigrid level `level` (1/2^level of each axis): it maps the restricted
+ * residual of the warm start to a coarse pressure correction, which is added to
+ * the pressure by injection before the V-cycles; the V-cycles then converge to
+ * the same tolerance (plain multigrid stays the judge of the error).
+ * Convolutions run on BF16 tensor cores (mma.sync) with FP32 accumulation;
+ * weights are kept in FP32 (Adam) and copied to BF16.
+ *   wl_guess_setup: allocate the network and room for `capacity` samples.
+ *   wl_guess_mode: collect != 0 records (restricted residual, coarse mean of
+ *     the converged-minus-initial pressure) of every converged projection;
+ *     use != 0 applies the trained network to every projection.
+ *   wl_guess_train: `iters` Adam steps of `batch` samples each on the GPU;
+ *     loss = sum (y - t)^2 / sum t^2; first and last losses returned.
+ *   wl_guess_weights: set (in) and/or get (out) the FP32 weights,
+ *     3 x 27 x 16 x 16 floats [layer][tap z,y,x][in][out] (host or device).
+ *   wl_guess_info: level, number of samples held, output gain. */
+WL_API int wl_guess_setup(wl_sim *sim, int level, int capacity);
+WL_API int wl_guess_mode(wl_sim *sim, int collect, int use);
+WL_API int wl_guess_train(wl_sim *sim, int iters, double lr, int batch, unsigned seed, double *loss_first,
+                          double *loss_last);
+WL_API int wl_guess_weights(wl_sim *sim, const float *in, float *out);
+WL_API int wl_guess_info(wl_sim *sim, int *level, int *samples, double *gain);
+
+/* One forward and backward pass of the guess network on a single sample (for
+ * checking the kernels): grid ndim, n[3]; weights w (3 x 27 x 16 x 16 floats);
+ * input x and target t (n[0]*n[1]*n[2] floats, t may be NULL for forward
+ * only); outputs y (forward result), dw (gradient of the loss w.r.t. w) and
+ * the loss. All host or device pointers. Allocates its own device buffers. */
+WL_API int wl_net_eval(int ndim, const int *n, const float *w, const float *x, const float *t, float *y, float *dw,
+                       double *loss);
 
 /* Largest grid (cells) wl_coarse_solve_static accepts: its working memory is
  * a fixed device array of 5 * WL_STATIC_MAX_CELLS + 8 doubles (~640 KiB) that

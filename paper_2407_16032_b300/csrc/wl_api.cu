@@ -12,11 +12,14 @@
 #include "k_poisson.cuh"
 #include "k_mg_march.cuh"
 #include "k_misc.cuh"
+#include "k_net.cuh"
 
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
+#include <random>
 #include <new>
 #include <string>
 #include <utility>
@@ -64,6 +67,11 @@ struct SimBase {
     virtual void diagnostics(double *ke, double *ens, double *maxdiv) = 0;
     virtual void info(int *levels, long long *launches) = 0;
     virtual void profile(int on) = 0;
+    virtual void guess_setup(int level, int capacity) = 0;
+    virtual void guess_mode(int collect, int use) = 0;
+    virtual void guess_train(int iters, double lr, int batch, unsigned seed, double *l0, double *l1) = 0;
+    virtual void guess_weights(const float *in, float *out) = 0;
+    virtual void guess_info(int *level, int *samples, double *gain) = 0;
     virtual std::string profile_report() = 0;
     double t = 0.0, dt_next = 0.25;
 };
@@ -142,6 +150,20 @@ struct Sim : SimBase {
     bool has_body = false, moving = false;
     double body_t = -1.0;
     int np = 1;
+    // learned initial guess (network on multigrid level gq.lev)
+    struct GuessState {
+        int lev = -1, shift = 0, cap = 0, count = 0, next = 0, step = 0;
+        bool collect = false, use = false, ready = false;
+        double gain = 1.0;
+        NetGrid ng{};
+        float *dx = nullptr, *dt = nullptr;  // samples: inputs, targets (cap x V)
+        double *dn = nullptr;                 // per-sample sums of squares (x, t)
+        float *W = nullptr, *G = nullptr, *m = nullptr, *v = nullptr, *Y = nullptr, *Z1 = nullptr, *Z2 = nullptr;
+        float *fx = nullptr, *tt = nullptr;   // network input and scaled target (one sample)
+        __nv_bfloat16 *Wf = nullptr, *Wb = nullptr, *A0 = nullptr, *A1 = nullptr, *A2 = nullptr, *dY = nullptr;
+        double *loss = nullptr;
+        T *ph0 = nullptr, *pl0 = nullptr;
+    } gq;
     Prof prof;
     void P0(const char *name, int level, long long cells) { prof.beg(st, name, level, cells); }
     void P1() { prof.end(st); }
@@ -432,7 +454,10 @@ struct Sim : SimBase {
         P1();
         WL_LAUNCH_CK();
         ++launches;
+        const bool collecting = gq.collect && gq.cap > 0;
+        if (collecting || (gq.use && gq.ready)) guess_begin(collecting);
         read_scalars();
+        const double rel0 = hS->rel;
         int it = 0;
         while (hS->rel > cfg.tol && it < cfg.itmax && !(hS->status & 1)) {
             if (prof.on) {
@@ -447,7 +472,8 @@ struct Sim : SimBase {
             read_scalars();
             ++it;
         }
-        if (sts) { sts->vcycles = it; sts->rel_resid = hS->rel; sts->bnorm = hS->bnorm; }
+        if (sts) { sts->vcycles = it; sts->rel_resid = hS->rel; sts->bnorm = hS->bnorm; sts->rel_initial = rel0; }
+        if (collecting && !(hS->status & 1) && hS->rel <= cfg.tol) guess_end();
         if (hS->status & 1) return WL_ERR_NONFINITE;
         if (hS->rel > cfg.tol) return WL_ERR_NOT_CONVERGED;
         return WL_OK;
@@ -714,6 +740,228 @@ struct Sim : SimBase {
         return out;
     }
 
+    // ---------------------------------------------------------- learned guess
+    void guess_setup(int level, int capacity) override {
+        if (level < 1 || level >= nlev) throw Err{WL_ERR_ARG, "guess level must be a coarse multigrid level"};
+        if (capacity < 0 || capacity > 100000) throw Err{WL_ERR_ARG, "bad sample capacity"};
+        if (gq.lev >= 0) throw Err{WL_ERR_STATE, "learned guess already set up"};
+        gq.lev = level;
+        gq.shift = level;
+        gq.ng.nx = gl[level].n[0];
+        gq.ng.ny = gl[level].n[1];
+        gq.ng.nz = gl[level].n[2];
+        gq.ng.V = (int)gl[level].nc;
+        const size_t V = gq.ng.V;
+        gq.cap = capacity;
+        if (capacity > 0) {
+            gq.dx = alloc_n<float>((size_t)capacity * V);
+            gq.dt = alloc_n<float>((size_t)capacity * V);
+            gq.dn = alloc_n<double>(2 * (size_t)capacity);
+            gq.ph0 = alloc_n<T>(g.nc);
+            gq.pl0 = alloc_n<T>(g.nc);
+        }
+        gq.W = alloc_n<float>(3 * NET_WL);
+        gq.G = alloc_n<float>(3 * NET_WL);
+        gq.m = alloc_n<float>(3 * NET_WL);
+        gq.v = alloc_n<float>(3 * NET_WL);
+        gq.Wf = alloc_n<__nv_bfloat16>(3 * NET_WL);
+        gq.Wb = alloc_n<__nv_bfloat16>(3 * NET_WL);
+        gq.fx = alloc_n<float>(V);
+        gq.tt = alloc_n<float>(V);
+        gq.Y = alloc_n<float>(V * NET_C);
+        gq.Z1 = alloc_n<float>(V * NET_C);
+        gq.Z2 = alloc_n<float>(V * NET_C);
+        gq.A0 = alloc_n<__nv_bfloat16>(V * NET_C);
+        gq.A1 = alloc_n<__nv_bfloat16>(V * NET_C);
+        gq.A2 = alloc_n<__nv_bfloat16>(V * NET_C);
+        gq.dY = alloc_n<__nv_bfloat16>(V * NET_C);
+        gq.loss = alloc_n<double>(1);
+        WL_CK(cudaStreamSynchronize(st));
+    }
+
+    void guess_mode(int collect, int use) override {
+        if (gq.lev < 0) throw Err{WL_ERR_STATE, "learned guess not set up"};
+        if (use && !gq.ready) throw Err{WL_ERR_STATE, "learned guess has no trained weights"};
+        gq.collect = collect != 0;
+        gq.use = use != 0;
+    }
+
+    void guess_weights(const float *in, float *out) override {
+        if (gq.lev < 0) throw Err{WL_ERR_STATE, "learned guess not set up"};
+        if (in) {
+            WL_CK(cudaMemcpyAsync(gq.W, in, 3 * NET_WL * sizeof(float), cudaMemcpyDefault, st));
+            k_net_weights<<<blocks(3 * NET_WL), 256, 0, st>>>(gq.W, gq.Wf, gq.Wb);
+            WL_LAUNCH_CK();
+            gq.ready = true;
+        }
+        if (out) WL_CK(cudaMemcpyAsync(out, gq.W, 3 * NET_WL * sizeof(float), cudaMemcpyDefault, st));
+        WL_CK(cudaStreamSynchronize(st));
+    }
+
+    void guess_info(int *level, int *samples, double *gain) override {
+        if (level) *level = gq.lev;
+        if (samples) *samples = gq.count;
+        if (gain) *gain = gq.gain;
+    }
+
+    // restrict the current fine residual (already on level 1) down to the net level
+    void restrict_to_guess_level() {
+        for (int l = 1; l < gq.lev; ++l) {
+            k_restrict<T, ND><<<tgrid(l + 1), tblk(), 0, st>>>(gl[l], lv[l].r, lv[l + 1]);
+            WL_LAUNCH_CK();
+            ++launches;
+        }
+    }
+
+    // network forward on fx (FP32 input) -> Y (channel 0 = output)
+    void net_forward(const float *x) {
+        const NetGrid &ng = gq.ng;
+        const int nb = (ng.V + 63) / 64, cb = nb < 2048 ? nb : 2048;
+        k_net_input<<<blocks(ng.V), 256, 0, st>>>(ng.V, x, gq.A0);
+        k_conv_fwd<<<cb, 128, 0, st>>>(ng, gq.A0, gq.Wf, gq.Z1, gq.A1);
+        k_conv_fwd<<<cb, 128, 0, st>>>(ng, gq.A1, gq.Wf + NET_WL, gq.Z2, gq.A2);
+        k_conv_fwd<<<cb, 128, 0, st>>>(ng, gq.A2, gq.Wf + 2 * NET_WL, gq.Y, nullptr);
+        WL_LAUNCH_CK();
+        launches += 4;
+    }
+
+    // At the start of a solve (after the first residual): record the sample
+    // input and the warm start (collecting), or apply the network's correction
+    // and recompute the residual (using).
+    void guess_begin(bool collecting) {
+        restrict_to_guess_level();
+        const size_t V = gq.ng.V;
+        if (collecting) {
+            float *xs = gq.dx + (size_t)gq.next * V;
+            if (sizeof(T) == sizeof(float)) WL_CK(cudaMemcpyAsync(xs, lv[gq.lev].r, V * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            else k_to_float<T><<<blocks(V), 256, 0, st>>>((long long)V, lv[gq.lev].r, xs);
+            WL_CK(cudaMemcpyAsync(gq.ph0, ph, g.nc * sizeof(T), cudaMemcpyDeviceToDevice, st));
+            WL_CK(cudaMemcpyAsync(gq.pl0, pl, g.nc * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        } else {
+            if (sizeof(T) == sizeof(float)) WL_CK(cudaMemcpyAsync(gq.fx, lv[gq.lev].r, V * sizeof(float), cudaMemcpyDeviceToDevice, st));
+            else k_to_float<T><<<blocks(V), 256, 0, st>>>((long long)V, lv[gq.lev].r, gq.fx);
+            P0("guess_net", gq.lev, (long long)V);
+            net_forward(gq.fx);
+            P1();
+            P0("guess_apply", 0, g.nc);
+            k_guess_apply<T><<<blocks(g.nc), 256, 0, st>>>(g, gq.shift, gq.ng, (float)gq.gain, gq.Y, ph, pl);
+            P1();
+            P0("resid", 0, g.nc);
+            resid_launch(st);
+            P1();
+            WL_LAUNCH_CK();
+            launches += 3;
+        }
+    }
+
+    // After a converged solve: the target (coarse mean of p_converged - p_warm),
+    // mean-free, and the sample's norms.
+    void guess_end() {
+        const size_t V = gq.ng.V;
+        float *ts = gq.dt + (size_t)gq.next * V;
+        k_guess_target<T><<<blocks(V), 256, 0, st>>>(g, gq.shift, gq.ng, ph, pl, gq.ph0, gq.pl0, ts);
+        k_demean<<<1, 1024, 0, st>>>(gq.ng.V, ts);
+        WL_CK(cudaMemsetAsync(gq.dn + 2 * gq.next, 0, 2 * sizeof(double), st));
+        k_sumsq<<<blocks(V), 256, 0, st>>>(gq.ng.V, gq.dx + (size_t)gq.next * V, gq.dn + 2 * gq.next);
+        k_sumsq<<<blocks(V), 256, 0, st>>>(gq.ng.V, ts, gq.dn + 2 * gq.next + 1);
+        WL_LAUNCH_CK();
+        launches += 4;
+        gq.next = (gq.next + 1) % gq.cap;
+        if (gq.count < gq.cap) ++gq.count;
+    }
+
+    // Adam on the collected samples (inputs scaled to unit RMS, targets by the
+    // same factor and by the dataset gain; the bias-free ReLU network is
+    // positively homogeneous, so at inference y = gain * net(r)).
+    void guess_train(int iters, double lr, int batch, unsigned seed, double *l0, double *l1) override {
+        if (gq.lev < 0 || gq.count < 1) throw Err{WL_ERR_STATE, "no collected samples to train on"};
+        const size_t V = gq.ng.V;
+        const int n = gq.count;
+        std::vector<double> hn(2 * n);
+        WL_CK(cudaMemcpyAsync(hn.data(), gq.dn, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        WL_CK(cudaStreamSynchronize(st));
+        std::vector<double> ratio, sx(n);
+        for (int i = 0; i < n; ++i) {
+            sx[i] = std::sqrt(hn[2 * i] / V);
+            if (hn[2 * i] > 0 && hn[2 * i + 1] > 0) ratio.push_back(std::sqrt(hn[2 * i + 1] / hn[2 * i]));
+        }
+        if (ratio.empty()) throw Err{WL_ERR_STATE, "collected samples are all zero"};
+        std::nth_element(ratio.begin(), ratio.begin() + ratio.size() / 2, ratio.end());
+        const double gain = ratio[ratio.size() / 2];
+        std::vector<double> tn2(n);
+        if (!gq.ready) {
+            // He-style initial weights, seeded
+            std::mt19937 rng(seed);
+            std::normal_distribution<float> nd(0.f, 1.f);
+            std::vector<float> w(3 * NET_WL, 0.f);
+            for (int l = 0; l < 3; ++l)
+                for (int t = 0; t < NET_TAPS; ++t)
+                    for (int i = 0; i < NET_C; ++i)
+                        for (int o = 0; o < NET_C; ++o) {
+                            if ((l == 0 && i > 0) || (l == 2 && o > 0)) continue;
+                            const float fan = (float)(NET_TAPS * (l == 0 ? 1 : NET_C));
+                            w[(l * NET_TAPS + t) * NET_C * NET_C + i * NET_C + o] = nd(rng) * std::sqrt(2.f / fan);
+                        }
+            WL_CK(cudaMemcpyAsync(gq.W, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+            WL_CK(cudaMemsetAsync(gq.m, 0, 3 * NET_WL * sizeof(float), st));
+            WL_CK(cudaMemsetAsync(gq.v, 0, 3 * NET_WL * sizeof(float), st));
+            gq.step = 0;
+        }
+        k_net_weights<<<blocks(3 * NET_WL), 256, 0, st>>>(gq.W, gq.Wf, gq.Wb);
+        std::mt19937 pick(seed + 1);
+        std::uniform_int_distribution<int> ud(0, n - 1);
+        float *tt = gq.tt;
+        double *dtn = gq.loss;
+        std::vector<double> hl(1);
+        double *tnorm = nullptr;
+        tnorm = alloc_n<double>(1);
+        const NetGrid &ng = gq.ng;
+        const int nbk = (ng.V + 63) / 64, cb = nbk < 2048 ? nbk : 2048;
+        const int wb = (ng.V + 16 * 4 * 16 - 1) / (16 * 4 * 16);
+        const dim3 dwg(wb < 1 ? 1 : (wb > 512 ? 512 : wb), NET_TAPS);
+        for (int itn = 0; itn < iters; ++itn) {
+            WL_CK(cudaMemsetAsync(gq.G, 0, 3 * NET_WL * sizeof(float), st));
+            WL_CK(cudaMemsetAsync(dtn, 0, sizeof(double), st));
+            for (int bi = 0; bi < batch; ++bi) {
+                const int sm = ud(pick);
+                const float sxi = sx[sm] > 0 ? (float)(1.0 / sx[sm]) : 1.f;
+                // input x / s, target t / (s gain)
+                k_scale_copy<<<blocks(V), 256, 0, st>>>(ng.V, sxi, gq.dx + (size_t)sm * V, gq.fx);
+                k_scale_copy<<<blocks(V), 256, 0, st>>>(ng.V, (float)(sxi / gain), gq.dt + (size_t)sm * V, tt);
+                WL_CK(cudaMemsetAsync(tnorm, 0, sizeof(double), st));
+                k_sumsq<<<blocks(V), 256, 0, st>>>(ng.V, tt, tnorm);
+                net_forward(gq.fx);
+                k_net_loss<<<blocks(V), 256, 0, st>>>(ng.V, gq.Y, tt, tnorm, gq.dY, dtn);
+                // layer 3
+                k_conv_dw<<<dwg, 128, 0, st>>>(ng, gq.A2, gq.dY, gq.G + 2 * NET_WL);
+                k_conv_fwd<<<cb, 128, 0, st>>>(ng, gq.dY, gq.Wb + 2 * NET_WL, gq.Y, nullptr);
+                k_relu_bwd<<<blocks(V * NET_C), 256, 0, st>>>((int)(V * NET_C), gq.Y, gq.Z2, gq.A2);
+                // layer 2 (A2 now holds dZ2)
+                k_conv_dw<<<dwg, 128, 0, st>>>(ng, gq.A1, gq.A2, gq.G + NET_WL);
+                k_conv_fwd<<<cb, 128, 0, st>>>(ng, gq.A2, gq.Wb + NET_WL, gq.Y, nullptr);
+                k_relu_bwd<<<blocks(V * NET_C), 256, 0, st>>>((int)(V * NET_C), gq.Y, gq.Z1, gq.A1);
+                // layer 1 (A1 now holds dZ1)
+                k_conv_dw<<<dwg, 128, 0, st>>>(ng, gq.A0, gq.A1, gq.G);
+                WL_LAUNCH_CK();
+                launches += 14;
+            }
+            ++gq.step;
+            k_adam<<<blocks(3 * NET_WL), 256, 0, st>>>(gq.W, gq.G, gq.m, gq.v, gq.step, (float)lr, (float)batch);
+            k_net_weights<<<blocks(3 * NET_WL), 256, 0, st>>>(gq.W, gq.Wf, gq.Wb);
+            WL_LAUNCH_CK();
+            launches += 2;
+            if (itn == 0 || itn == iters - 1) {
+                WL_CK(cudaMemcpyAsync(hl.data(), dtn, sizeof(double), cudaMemcpyDeviceToHost, st));
+                WL_CK(cudaStreamSynchronize(st));
+                if (itn == 0 && l0) *l0 = hl[0] / batch;
+                if (itn == iters - 1 && l1) *l1 = hl[0] / batch;
+            }
+        }
+        gq.gain = gain;
+        gq.ready = true;
+        WL_CK(cudaStreamSynchronize(st));
+    }
+
     void info(int *levels, long long *nl) override {
         if (levels) *levels = nlev;
         if (nl) *nl = launches;
@@ -894,6 +1142,85 @@ int wl_profile_report(wl_sim *s, char *buf, size_t len, size_t *needed) {
         return (int)WL_OK;
     });
 }
+int wl_guess_setup(wl_sim *s, int level, int capacity) {
+    return guard(s, [&] { s->impl->guess_setup(level, capacity); return (int)WL_OK; });
+}
+int wl_guess_mode(wl_sim *s, int collect, int use) {
+    return guard(s, [&] { s->impl->guess_mode(collect, use); return (int)WL_OK; });
+}
+int wl_guess_train(wl_sim *s, int iters, double lr, int batch, unsigned seed, double *loss_first, double *loss_last) {
+    if (iters < 1 || batch < 1 || !(lr > 0)) return WL_ERR_ARG;
+    return guard(s, [&] { s->impl->guess_train(iters, lr, batch, seed, loss_first, loss_last); return (int)WL_OK; });
+}
+int wl_guess_weights(wl_sim *s, const float *in, float *out) {
+    return guard(s, [&] { s->impl->guess_weights(in, out); return (int)WL_OK; });
+}
+int wl_guess_info(wl_sim *s, int *level, int *samples, double *gain) {
+    return guard(s, [&] { s->impl->guess_info(level, samples, gain); return (int)WL_OK; });
+}
+
+// One forward and backward pass of the network on a given sample (test entry).
+int wl_net_eval(int ndim, const int *n, const float *w, const float *x, const float *t, float *y, float *dw,
+                double *loss) {
+    if ((ndim != 2 && ndim != 3) || !n || !w || !x) return WL_ERR_ARG;
+    NetGrid ng{n[0], n[1], ndim == 3 ? n[2] : 1, 0};
+    if (ng.nx < 1 || ng.ny < 1 || ng.nz < 1 || (long long)ng.nx * ng.ny * ng.nz > (1LL << 28)) return WL_ERR_ARG;
+    ng.V = ng.nx * ng.ny * ng.nz;
+    const size_t V = ng.V;
+    std::vector<void *> bufs;
+    bool ok = true;
+    auto dal = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) { ok = false; return nullptr; }
+        bufs.push_back(p);
+        return p;
+    };
+    float *W = (float *)dal(3 * NET_WL * 4), *fx = (float *)dal(V * 4), *ft = (float *)dal(V * 4);
+    float *Y = (float *)dal(V * NET_C * 4), *Z1 = (float *)dal(V * NET_C * 4), *Z2 = (float *)dal(V * NET_C * 4);
+    float *G = (float *)dal(3 * NET_WL * 4), *yo = (float *)dal(V * 4);
+    __nv_bfloat16 *Wf = (__nv_bfloat16 *)dal(3 * NET_WL * 2), *Wb = (__nv_bfloat16 *)dal(3 * NET_WL * 2);
+    __nv_bfloat16 *A0 = (__nv_bfloat16 *)dal(V * NET_C * 2), *A1 = (__nv_bfloat16 *)dal(V * NET_C * 2);
+    __nv_bfloat16 *A2 = (__nv_bfloat16 *)dal(V * NET_C * 2), *dY = (__nv_bfloat16 *)dal(V * NET_C * 2);
+    double *dl = (double *)dal(2 * sizeof(double));
+    int rc = ok ? WL_OK : WL_ERR_ALLOC;
+    if (rc == WL_OK) {
+        cudaMemcpy(W, w, 3 * NET_WL * 4, cudaMemcpyDefault);
+        cudaMemcpy(fx, x, V * 4, cudaMemcpyDefault);
+        if (t) cudaMemcpy(ft, t, V * 4, cudaMemcpyDefault);
+        cudaMemset(G, 0, 3 * NET_WL * 4);
+        cudaMemset(dl, 0, 2 * sizeof(double));
+        const int eb = (int)((V + 255) / 256), vb = (int)((V * NET_C + 255) / 256);
+        const int nb = (int)((V + 63) / 64), cb = nb < 2048 ? nb : 2048;
+        const int wb = (int)((V + 1023) / 1024);
+        const dim3 dwg(wb < 1 ? 1 : (wb > 512 ? 512 : wb), NET_TAPS);
+        k_net_weights<<<(3 * NET_WL + 255) / 256, 256>>>(W, Wf, Wb);
+        k_net_input<<<eb, 256>>>(ng.V, fx, A0);
+        k_conv_fwd<<<cb, 128>>>(ng, A0, Wf, Z1, A1);
+        k_conv_fwd<<<cb, 128>>>(ng, A1, Wf + NET_WL, Z2, A2);
+        k_conv_fwd<<<cb, 128>>>(ng, A2, Wf + 2 * NET_WL, Y, nullptr);
+        k_channel0<<<eb, 256>>>(ng.V, Y, yo);
+        if (t) {
+            k_sumsq<<<eb, 256>>>(ng.V, ft, dl + 1);
+            k_net_loss<<<eb, 256>>>(ng.V, Y, ft, dl + 1, dY, dl);
+            k_conv_dw<<<dwg, 128>>>(ng, A2, dY, G + 2 * NET_WL);
+            k_conv_fwd<<<cb, 128>>>(ng, dY, Wb + 2 * NET_WL, Y, nullptr);
+            k_relu_bwd<<<vb, 256>>>(ng.V * NET_C, Y, Z2, A2);
+            k_conv_dw<<<dwg, 128>>>(ng, A1, A2, G + NET_WL);
+            k_conv_fwd<<<cb, 128>>>(ng, A2, Wb + NET_WL, Y, nullptr);
+            k_relu_bwd<<<vb, 256>>>(ng.V * NET_C, Y, Z1, A1);
+            k_conv_dw<<<dwg, 128>>>(ng, A0, A1, G);
+        }
+        if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) rc = WL_ERR_CUDA;
+        if (rc == WL_OK) {
+            if (y) cudaMemcpy(y, yo, V * 4, cudaMemcpyDefault);
+            if (dw && t) cudaMemcpy(dw, G, 3 * NET_WL * 4, cudaMemcpyDefault);
+            if (loss && t) cudaMemcpy(loss, dl, sizeof(double), cudaMemcpyDeviceToHost);
+        }
+    }
+    for (void *p : bufs) cudaFree(p);
+    return rc;
+}
+
 const char *wl_last_error(const wl_sim *s) { return s ? s->err.c_str() : "null sim"; }
 const char *wl_status_string(int st) {
     switch (st) {

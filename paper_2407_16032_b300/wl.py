@@ -25,7 +25,8 @@ EXPORTS = (
     "wl_config_default", "wl_sim_create", "wl_sim_destroy", "wl_set_velocity", "wl_get_velocity",
     "wl_get_pressure", "wl_set_pressure", "wl_set_time", "wl_get_time", "wl_mom_step", "wl_project",
     "wl_poisson_solve", "wl_conv_diff", "wl_forces", "wl_body_update", "wl_get_body_fields",
-    "wl_diagnostics", "wl_info", "wl_profile", "wl_profile_report", "wl_coarse_solve_static", "wl_last_error",
+    "wl_diagnostics", "wl_info", "wl_profile", "wl_profile_report", "wl_coarse_solve_static", "wl_guess_setup",
+    "wl_guess_mode", "wl_guess_train", "wl_guess_weights", "wl_guess_info", "wl_net_eval", "wl_last_error",
     "wl_status_string",
 )
 
@@ -52,7 +53,7 @@ class Body(C.Structure):
 
 
 class SolveStats(C.Structure):
-    _fields_ = [("vcycles", C.c_int), ("rel_resid", C.c_double), ("bnorm", C.c_double)]
+    _fields_ = [("vcycles", C.c_int), ("rel_resid", C.c_double), ("bnorm", C.c_double), ("rel_initial", C.c_double)]
 
 
 class StepStats(C.Structure):
@@ -93,6 +94,12 @@ def lib() -> C.CDLL:
             "wl_profile_report": ([vp, C.c_char_p, C.c_size_t, C.POINTER(C.c_size_t)], ip),
             "wl_coarse_solve_static": ([ip, C.POINTER(C.c_int), C.POINTER(C.c_int), ip, C.POINTER(vp), vp, vp, ip,
                                         C.c_double, vp, dp], ip),
+            "wl_guess_setup": ([vp, ip, ip], ip),
+            "wl_guess_mode": ([vp, ip, ip], ip),
+            "wl_guess_train": ([vp, ip, C.c_double, ip, C.c_uint, dp, dp], ip),
+            "wl_guess_weights": ([vp, vp, vp], ip),
+            "wl_guess_info": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int), dp], ip),
+            "wl_net_eval": ([ip, C.POINTER(C.c_int), vp, vp, vp, vp, vp, dp], ip),
             "wl_last_error": ([vp], C.c_char_p),
             "wl_status_string": ([ip], C.c_char_p),
         }
@@ -126,6 +133,7 @@ class SolveResult:
     vcycles: int
     rel_resid: float
     bnorm: float
+    rel_initial: float = 0.0
 
 
 class Sim:
@@ -259,13 +267,13 @@ class Sim:
     def project(self, w, dt):
         st = SolveStats()
         self._check(lib().wl_project(self._h, float(w), float(dt), C.byref(st)), "wl_project")
-        return SolveResult(st.vcycles, st.rel_resid, st.bnorm)
+        return SolveResult(st.vcycles, st.rel_resid, st.bnorm, st.rel_initial)
 
     def poisson_solve(self, b, p):
         st = SolveStats()
         rc = lib().wl_poisson_solve(self._h, _ptr(b), _ptr(p), C.byref(st))
         self._check(rc, "wl_poisson_solve", (WL_OK, WL_ERR_NOT_CONVERGED))
-        return SolveResult(st.vcycles, st.rel_resid, st.bnorm), rc
+        return SolveResult(st.vcycles, st.rel_resid, st.bnorm, st.rel_initial), rc
 
     def conv_diff(self, u, ue=None, r=None):
         r = self.torch.empty_like(u) if r is None else r
@@ -308,6 +316,30 @@ class Sim:
             rows.append((nm, int(lv), int(n), float(ms), int(cells)))
         return rows
 
+    # ------------------------------------------------------ learned guess
+    def guess_setup(self, level=2, capacity=64):
+        self._check(lib().wl_guess_setup(self._h, int(level), int(capacity)), "wl_guess_setup")
+
+    def guess_mode(self, collect=False, use=False):
+        self._check(lib().wl_guess_mode(self._h, int(bool(collect)), int(bool(use))), "wl_guess_mode")
+
+    def guess_train(self, iters=200, lr=1e-3, batch=4, seed=0):
+        l0, l1 = C.c_double(), C.c_double()
+        self._check(lib().wl_guess_train(self._h, int(iters), float(lr), int(batch), int(seed), C.byref(l0),
+                                         C.byref(l1)), "wl_guess_train")
+        return l0.value, l1.value
+
+    def guess_weights(self, set_to=None):
+        out = np.zeros(3 * 27 * 16 * 16, dtype=np.float32)
+        src = None if set_to is None else np.ascontiguousarray(set_to, dtype=np.float32)
+        self._check(lib().wl_guess_weights(self._h, _ptr(src), _ptr(out)), "wl_guess_weights")
+        return out.reshape(3, 27, 16, 16)
+
+    def guess_info(self):
+        lv, ns, gn = C.c_int(), C.c_int(), C.c_double()
+        self._check(lib().wl_guess_info(self._h, C.byref(lv), C.byref(ns), C.byref(gn)), "wl_guess_info")
+        return lv.value, ns.value, gn.value
+
     def info(self):
         lv, nl = C.c_int(), C.c_longlong()
         self._check(lib().wl_info(self._h, C.byref(lv), C.byref(nl)), "wl_info")
@@ -336,3 +368,19 @@ def coarse_solve_static(ndim, n, periodic, c, r, x, maxit=2000, rtol=1e-12, stre
     rc = lib().wl_coarse_solve_static(ndim, nn, pp, prec, cp, r.data_ptr(), x.data_ptr(), int(maxit),
                                       float(rtol), st, C.byref(rel))
     return rc, rel.value
+
+
+def net_eval(ndim, n, w, x, t=None):
+    """wl_net_eval: one forward/backward pass of the guess network (host arrays).
+    w: (3, 27, 16, 16) float32; x, t: grid-shaped float32. Returns (y, dw, loss)."""
+    nn = (C.c_int * 3)(*(list(n) + [1, 1, 1])[:3])
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    tt = None if t is None else np.ascontiguousarray(t, dtype=np.float32)
+    y = np.zeros(x.shape, dtype=np.float32)
+    dw = np.zeros(w.shape, dtype=np.float32)
+    loss = C.c_double()
+    rc = lib().wl_net_eval(ndim, nn, _ptr(w), _ptr(x), _ptr(tt), _ptr(y), _ptr(dw), C.byref(loss))
+    if rc != WL_OK:
+        raise WLError(rc, "wl_net_eval failed")
+    return y, dw, loss.value
