@@ -87,6 +87,8 @@ def lib():
             ("orc_forces", [C.POINTER(Grid), C.POINTER(BodyS), C.c_double, _P, _P], None),
             ("orc_step", [C.POINTER(Grid), C.POINTER(BodyS), C.c_double, C.c_double, _P, _P, _P, C.POINTER(Solver), C.POINTER(Stats)], C.c_int),
             ("orc_diagnostics", [C.POINTER(Grid), _P, _P, _P, _P], None),
+            ("orc_conv_diff_vjp", [C.POINTER(Grid), _P, _P, _P, _P, _P], None),
+            ("orc_step_vjp", [C.POINTER(Grid), C.POINTER(BodyS), C.c_double, C.c_double, _P, _P, _P, _P, _P, _P, _P], None),
         ]:
             f = getattr(L, name)
             f.argtypes = args
@@ -276,6 +278,33 @@ def diagnostics(g, u, ue):
     en = np.zeros(1)
     lib().orc_diagnostics(C.byref(g), _p(_d(u)), _p(_d(ue)), _p(ke), _p(en))
     return ke[0], en[0]
+
+
+def conv_diff_vjp(g, u, ue, lam):
+    """(J_R(u, ue))^T lam -> (ubar, uebar)."""
+    ub = np.zeros_like(_d(u))
+    ueb = np.zeros(max(plane_size(g), 1))
+    lib().orc_conv_diff_vjp(C.byref(g), _p(_d(u)), _p(_d(ue)), _p(_d(lam)), _p(ub), _p(ueb))
+    return ub, ueb
+
+
+def step_vjp(g, body_s, t, dt, u0, ue0, P0, lu, le):
+    """Vector-Jacobian product of one step (orc_step) w.r.t. (u0, ue0)."""
+    ub = np.zeros_like(_d(u0))
+    ueb = np.zeros(max(plane_size(g), 1))
+    le = _d(le) if le is not None else np.zeros(max(plane_size(g), 1))
+    lib().orc_step_vjp(C.byref(g), C.byref(body_s), float(t), float(dt), _p(_d(u0)), _p(_d(ue0)), _p(_d(P0)),
+                       _p(_d(lu)), _p(le), _p(ub), _p(ueb))
+    return ub, ueb
+
+
+def step_fn(g, body_s, t, dt, u0, ue0, P0, tol=1e-13):
+    """One orc_step on copies: returns (u, ue, P)."""
+    u, ue, P = _d(u0).copy(), _d(ue0).copy(), _d(P0).copy()
+    S = make_solver(tol, 200, 4)
+    st = (Stats * 2)()
+    lib().orc_step(C.byref(g), C.byref(body_s), float(t), float(dt), _p(u), _p(ue), _p(P), C.byref(S), st)
+    return u, ue, P
 
 
 @dataclass

@@ -819,3 +819,300 @@ void orc_diagnostics(const orc_grid *g, const double *u, const double *ue, doubl
     *ke = s / (double)nc;
     *ens = w / (double)nc;
 }
+
+/* ======================================================================== */
+/* Discrete adjoint of one step (vector-Jacobian product) w.r.t. the start  */
+/* velocity u0 and exit plane ue0, at fixed dt and fixed body, with the      */
+/* limiter branches frozen at the evaluation point (subgradient at ties).    */
+/* ======================================================================== */
+
+/* Where a velocity sample comes from: kind 0 stored face (index into u),
+ * 1 exit plane (index into ue), 2 constant. Mirrors su(). */
+static void su_loc(const orc_grid *g, int a, int i, int j, int k, int *kind, size_t *index)
+{
+    int idx[3] = {i, j, k};
+    int upper = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+        int N = g->n[ax];
+        if (ax >= g->ndim) { idx[ax] = 0; continue; }
+        if (g->periodic[ax]) idx[ax] = ((idx[ax] % N) + N) % N;
+        else if (ax == a) {
+            if (idx[ax] < 0) idx[ax] = 0;
+            if (idx[ax] >= N) { idx[ax] = N; upper = 1; }
+        } else {
+            if (idx[ax] < 0) idx[ax] = 0;
+            if (idx[ax] > N - 1) idx[ax] = N - 1;
+        }
+    }
+    if (upper) {
+        if (a == 0 && g->exit_hi_x) { *kind = 1; *index = (size_t)idx[1] + (size_t)g->n[1] * idx[2]; }
+        else { *kind = 2; *index = 0; }
+        return;
+    }
+    *kind = 0;
+    *index = (size_t)a * ncell(g) + lin(g, idx[0], idx[1], idx[2]);
+}
+
+static void scatter(int kind, size_t index, double v, double *ub, double *ueb)
+{
+    if (kind == 0) ub[index] += v;
+    else if (kind == 1) ueb[index] += v;
+}
+
+/* median3 with the index (0, 1, 2) of the argument it returns */
+static double median3_w(double a, double b, double c, int *w)
+{
+    double m1 = a <= b ? a : b; int w1 = a <= b ? 0 : 1;
+    double M1 = a <= b ? b : a; int wM = a <= b ? 1 : 0;
+    double m2 = M1 <= c ? M1 : c; int w2 = M1 <= c ? wM : 2;
+    if (m1 >= m2) { *w = w1; return m1; }
+    *w = w2;
+    return m2;
+}
+
+/* Partial derivatives of the limited QUICK value w.r.t. (uu, c, d). */
+static double quick_d(double uu, double c, double d, double *g)
+{
+    double phi = (5.0 * c + 2.0 * d - uu) / 6.0;
+    int wi, wo;
+    double inner = median3_w(10.0 * c - 9.0 * uu, c, d, &wi);
+    double val = median3_w(phi, c, inner, &wo);
+    g[0] = g[1] = g[2] = 0.0;
+    if (wo == 0) { g[0] = -1.0 / 6.0; g[1] = 5.0 / 6.0; g[2] = 2.0 / 6.0; }
+    else if (wo == 1) g[1] = 1.0;
+    else {
+        if (wi == 0) { g[0] = -9.0; g[1] = 10.0; }
+        else if (wi == 1) g[1] = 1.0;
+        else g[2] = 1.0;
+    }
+    return val;
+}
+
+/* mu * dF/d(inputs) of the face flux of u_a through the lower b-face of the
+ * control volume of cell I, scattered to the adjoint arrays. */
+static void face_flux_vjp(const orc_grid *g, const double *u, const double *ue, int a, int b, int i, int j, int k,
+                          double mu, double *ub, double *ueb)
+{
+    int db[3] = {0, 0, 0}, da[3] = {0, 0, 0};
+    db[b] = 1; da[a] = 1;
+    int P[6][3] = {{i, j, k}, {i - da[0], j - da[1], k - da[2]},
+                   {i - 2 * db[0], j - 2 * db[1], k - 2 * db[2]}, {i - db[0], j - db[1], k - db[2]},
+                   {i, j, k}, {i + db[0], j + db[1], k + db[2]}};
+    int comp[6] = {b, b, a, a, a, a};
+    double v[6];
+    int kind[6];
+    size_t ix[6];
+    for (int q = 0; q < 6; ++q) {
+        v[q] = su(g, u, ue, comp[q], P[q][0], P[q][1], P[q][2]);
+        su_loc(g, comp[q], P[q][0], P[q][1], P[q][2], &kind[q], &ix[q]);
+    }
+    double Uf = 0.5 * (v[0] + v[1]);
+    double gq[3], phi;
+    /* (uu, c, d) = (sm2, sm1, s0) if Uf > 0 else (sp1, s0, sm1) */
+    int map[3];
+    if (Uf > 0.0) { phi = quick_d(v[2], v[3], v[4], gq); map[0] = 2; map[1] = 3; map[2] = 4; }
+    else { phi = quick_d(v[5], v[4], v[3], gq); map[0] = 5; map[1] = 4; map[2] = 3; }
+    scatter(kind[0], ix[0], mu * 0.5 * phi, ub, ueb);
+    scatter(kind[1], ix[1], mu * 0.5 * phi, ub, ueb);
+    for (int q = 0; q < 3; ++q) scatter(kind[map[q]], ix[map[q]], mu * Uf * gq[q], ub, ueb);
+    scatter(kind[4], ix[4], -mu * g->nu, ub, ueb);
+    scatter(kind[3], ix[3], mu * g->nu, ub, ueb);
+}
+
+/* (ub, ueb) += J_R(u, ue)^T lam */
+void orc_conv_diff_vjp(const orc_grid *g, const double *u, const double *ue, const double *lam, double *ub, double *ueb)
+{
+    size_t nc = ncell(g);
+    for (int a = 0; a < g->ndim; ++a)
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i) {
+                    int I[3] = {i, j, k};
+                    if (!g->periodic[a] && I[a] == 0) continue;
+                    double l = lam[(size_t)a * nc + lin(g, i, j, k)];
+                    if (l == 0.0) continue;
+                    for (int b = 0; b < g->ndim; ++b) {
+                        int db[3] = {0, 0, 0};
+                        db[b] = 1;
+                        face_flux_vjp(g, u, ue, a, b, i, j, k, l, ub, ueb);
+                        face_flux_vjp(g, u, ue, a, b, i + db[0], j + db[1], k + db[2], -l, ub, ueb);
+                    }
+                }
+}
+
+/* fb += B^T gbar (blend transposed; boundary faces carry constants). */
+static void bdim_vjp(const orc_grid *g, const double *mu0, const double *mu1n, const double *gbar, double *fb)
+{
+    size_t nc = ncell(g);
+    for (int a = 0; a < g->ndim; ++a)
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i) {
+                    int I[3] = {i, j, k};
+                    if (!g->periodic[a] && I[a] == 0) continue;
+                    size_t L = (size_t)a * nc + lin(g, i, j, k);
+                    double gv = gbar[L];
+                    if (!mu0) { fb[L] += gv; continue; }
+                    fb[L] += mu0[L] * gv;
+                    for (int b = 0; b < g->ndim; ++b) {
+                        double m = mu1n[(size_t)(a * 3 + b) * nc + lin(g, i, j, k)];
+                        if (m == 0.0) continue;
+                        int P[3] = {i, j, k}, M[3] = {i, j, k};
+                        P[b] += 1; M[b] -= 1;
+                        for (int ax = 0; ax < 3; ++ax) {
+                            if (ax >= g->ndim) continue;
+                            int N = g->n[ax];
+                            if (g->periodic[ax]) { P[ax] = ((P[ax] % N) + N) % N; M[ax] = ((M[ax] % N) + N) % N; }
+                            else {
+                                if (P[ax] > N - 1) P[ax] = N - 1;
+                                if (M[ax] < 0) M[ax] = 0;
+                            }
+                        }
+                        fb[(size_t)a * nc + lin(g, P[0], P[1], P[2])] += 0.5 * m * gv;
+                        fb[(size_t)a * nc + lin(g, M[0], M[1], M[2])] -= 0.5 * m * gv;
+                    }
+                }
+}
+
+/* Exit condition transposed: given ueb_out, accumulate into ue0b, ueGb, uGb (last
+ * interior x faces) and uesb (corrector). */
+static void exit_vjp(const orc_grid *g, double dt, int corrector, const double *ueb_out, double *ue0b, double *ueGb,
+                     double *uGb, double *uesb)
+{
+    if (!g->exit_hi_x) return;
+    int np = g->n[1] * g->n[2], n0 = g->n[0];
+    double m = 0.0;
+    for (int p = 0; p < np; ++p) m += ueb_out[p];
+    m /= np;
+    double Ubar = g->U[0], w = corrector ? 0.5 : 1.0;
+    for (int p = 0; p < np; ++p) {
+        int j = p % g->n[1], k = p / g->n[1];
+        double e = ueb_out[p] - m;
+        ue0b[p] += w * e;
+        ueGb[p] += -w * dt * Ubar * e;
+        uGb[lin(g, n0 - 1, j, k)] += w * dt * Ubar * e;
+        if (corrector) uesb[p] += 0.5 * e;
+    }
+}
+
+/* Projection transposed: (ub, ueb) = (lu, le) + D^T q/(w dt), with
+ * q = solve(-w dt G^T lu) (the solve's mean removal is symmetric). */
+static void project_vjp(const orc_grid *g, const double *c, const double *lu, const double *le, double w, double dt,
+                        double *ub, double *ueb)
+{
+    size_t nc = ncell(g);
+    int np = g->n[1] * g->n[2];
+    orc_level L = fine_level(g, (double *)c);
+    double *rhs = calloc(nc, sizeof(double)), *q = calloc(nc, sizeof(double));
+    double wdt = w * dt;
+    for (int k = 0; k < g->n[2]; ++k)
+        for (int j = 0; j < g->n[1]; ++j)
+            for (int i = 0; i < g->n[0]; ++i) {
+                int I[3] = {i, j, k};
+                double s = 0.0;
+                for (int a = 0; a < g->ndim; ++a) {
+                    int Ip[3] = {i, j, k};
+                    Ip[a] += 1;
+                    s += c[(size_t)a * nc + lin(g, i, j, k)] * lu[(size_t)a * nc + lin(g, i, j, k)];
+                    double cp = lv_c(&L, a, Ip);
+                    if (cp != 0.0) {
+                        int J[3] = {Ip[0], Ip[1], Ip[2]};
+                        if (J[a] == g->n[a]) J[a] = 0;
+                        s -= cp * lu[(size_t)a * nc + lin(g, J[0], J[1], J[2])];
+                    }
+                    (void)I;
+                }
+                rhs[lin(g, i, j, k)] = -wdt * s;
+            }
+    orc_solver S = {1e-13, 200, 4};
+    orc_poisson_solve(g, c, rhs, q, &S, NULL);
+    for (size_t e = 0; e < (size_t)g->ndim * nc; ++e) ub[e] = lu[e];
+    for (int p = 0; p < np; ++p) ueb[p] = le ? le[p] : 0.0;
+    for (int a = 0; a < g->ndim; ++a)
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i) {
+                    int I[3] = {i, j, k};
+                    size_t F = (size_t)a * nc + lin(g, i, j, k);
+                    double qm = 0.0;
+                    if (I[a] > 0 || g->periodic[a]) {
+                        int M[3] = {i, j, k};
+                        M[a] -= 1;
+                        if (M[a] < 0) M[a] += g->n[a];
+                        qm = q[lin(g, M[0], M[1], M[2])];
+                    }
+                    ub[F] += (qm - q[lin(g, i, j, k)]) / wdt;
+                    if (a == 0 && g->exit_hi_x && i == g->n[0] - 1) ueb[j + g->n[1] * k] += q[lin(g, i, j, k)] / wdt;
+                }
+    free(rhs); free(q);
+}
+
+/* Vector-Jacobian product of orc_step: given (lu, le) for the step's output
+ * (u, ue), return (ub, ueb) for its input (u0, ue0). The state arrays are not
+ * changed; P (warm start) is used for the forward recomputation. */
+void orc_step_vjp(const orc_grid *g, const orc_body *B, double t, double dt, const double *u0, const double *ue0,
+                  const double *P0, const double *lu, const double *le, double *ub, double *ueb)
+{
+    size_t nc = ncell(g);
+    size_t nu = (size_t)g->ndim * nc;
+    int np = g->n[1] * g->n[2];
+    double *c = malloc(nu * sizeof(double));
+    double *mu0 = NULL, *mu1n = NULL, *V = NULL;
+    if (B && B->kind != 0) {
+        mu0 = malloc(nu * sizeof(double)); mu1n = malloc(9 * nc * sizeof(double)); V = malloc(nu * sizeof(double));
+        orc_measure(g, B, t + dt, mu0, mu1n, V);
+    }
+    orc_coeffs(g, mu0, c);
+    orc_solver S = {1e-13, 200, 4};
+    /* forward predictor: u* and ue* */
+    double *r = malloc(nu * sizeof(double)), *us = malloc(nu * sizeof(double));
+    double *ues = malloc((size_t)np * sizeof(double)), *P = malloc(nc * sizeof(double));
+    memcpy(P, P0, nc * sizeof(double));
+    orc_conv_diff(g, u0, ue0, r);
+    orc_bdim(g, u0, r, dt, mu0, mu1n, V, NULL, us);
+    memcpy(ues, ue0, (size_t)np * sizeof(double));
+    orc_exit_bc(g, ue0, u0, ue0, dt, 0, NULL, us, ues);
+    orc_project(g, c, us, ues, P, 1.0, dt, &S, NULL);
+    /* reverse */
+    double *u2b = calloc(nu, sizeof(double)), *ue2b = calloc((size_t)np + 1, sizeof(double));
+    double *usb = calloc(nu, sizeof(double)), *uesb = calloc((size_t)np + 1, sizeof(double));
+    double *fb = calloc(nu, sizeof(double)), *u1b = calloc(nu, sizeof(double)), *ue1b = calloc((size_t)np + 1, sizeof(double));
+    double *tmp = calloc(nu, sizeof(double)), *tmpe = calloc((size_t)np + 1, sizeof(double));
+    for (size_t e = 0; e < nu; ++e) ub[e] = 0.0;
+    for (int p = 0; p < np; ++p) ueb[p] = 0.0;
+    /* corrector projection (w = 1/2) */
+    project_vjp(g, c, lu, le, 0.5, dt, u2b, ue2b);
+    /* corrector exit: ue2 from ue0, ue*, u* */
+    exit_vjp(g, dt, 1, ue2b, ueb, uesb, usb, uesb);
+    /* corrector blend: u2 = (u* + B(u0 + dt R(u*)))/2 on non-boundary faces */
+    for (int a = 0; a < g->ndim; ++a)
+        for (size_t e = 0; e < nc; ++e) {
+            size_t F = (size_t)a * nc + e;
+            int i = (int)(e % g->n[0]), j = (int)((e / g->n[0]) % g->n[1]), k = (int)(e / ((size_t)g->n[0] * g->n[1]));
+            int I[3] = {i, j, k};
+            double v = (!g->periodic[a] && I[a] == 0) ? 0.0 : 0.5 * u2b[F];
+            tmp[F] = v;
+            usb[F] += v;
+        }
+    bdim_vjp(g, mu0, mu1n, tmp, fb);
+    for (size_t e = 0; e < nu; ++e) { ub[e] += fb[e]; fb[e] *= dt; }
+    orc_conv_diff_vjp(g, us, ues, fb, usb, uesb);
+    /* predictor projection (w = 1) */
+    project_vjp(g, c, usb, uesb, 1.0, dt, u1b, ue1b);
+    /* predictor exit: ue1 from ue0 (twice) and u0 */
+    exit_vjp(g, dt, 0, ue1b, ueb, ueb, ub, NULL);
+    /* predictor blend: u1 = B(u0 + dt R(u0)) */
+    for (size_t e = 0; e < nu; ++e) { fb[e] = 0.0; tmp[e] = 0.0; }
+    for (int a = 0; a < g->ndim; ++a)
+        for (size_t e = 0; e < nc; ++e) {
+            size_t F = (size_t)a * nc + e;
+            int i = (int)(e % g->n[0]), j = (int)((e / g->n[0]) % g->n[1]), k = (int)(e / ((size_t)g->n[0] * g->n[1]));
+            int I[3] = {i, j, k};
+            tmp[F] = (!g->periodic[a] && I[a] == 0) ? 0.0 : u1b[F];
+        }
+    bdim_vjp(g, mu0, mu1n, tmp, fb);
+    for (size_t e = 0; e < nu; ++e) { ub[e] += fb[e]; fb[e] *= dt; }
+    orc_conv_diff_vjp(g, u0, ue0, fb, ub, ueb);
+    free(c); free(mu0); free(mu1n); free(V); free(r); free(us); free(ues); free(P);
+    free(u2b); free(ue2b); free(usb); free(uesb); free(fb); free(u1b); free(ue1b); free(tmp); free(tmpe);
+}

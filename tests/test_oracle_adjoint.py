@@ -1,0 +1,122 @@
+"""Pins of the FP64 oracle's discrete adjoint of one step (the vector-Jacobian
+product with respect to the start velocity and exit plane, fixed dt and body).
+
+Expected values come from central finite differences of the oracle's forward
+step (an independent computation: the forward code never calls the adjoint)
+and from a structural property of the projection, not from the adjoint's own
+formulas.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+RNG = np.random.default_rng(99)
+
+
+def _case(kind):
+    B = synth.Body()
+    if kind == "periodic2d":
+        g = oracle.make_grid(2, (24, 16), (True, True), False, (0.0, 0.0), 0.01)
+        u0 = synth.random_field(11, 2, (24, 16), amp=0.5)
+    elif kind == "channel_exit":
+        g = oracle.make_grid(2, (20, 12), (False, True), True, (1.0, 0.0), 0.005)
+        u0 = synth.random_field(12, 2, (20, 12), amp=0.2, offset=(1.0, 0.0))
+    elif kind == "circle":
+        g = oracle.make_grid(2, (28, 20), (False, False), True, (1.0, 0.0), 0.01)
+        u0 = synth.random_field(13, 2, (28, 20), amp=0.2, offset=(1.0, 0.0))
+        B = synth.Body(kind="sphere", centre=(10.0, 10.3, 0.0), radius=4.2)
+    elif kind == "walled3d":
+        g = oracle.make_grid(3, (12, 10, 8), (True, True, False), False, (0.0, 0.0, 0.0), 0.02)
+        u0 = synth.random_field(14, 3, (12, 10, 8), amp=0.4)
+    else:
+        raise KeyError(kind)
+    ue0 = np.zeros(max(oracle.plane_size(g), 1))
+    if g.exit_hi_x:
+        ue0 = 1.0 + 0.1 * (2 * synth.uniform01(21, 0, ue0.size) - 1)
+    return g, oracle.make_body(B), u0, ue0
+
+
+def _dot(a, b):
+    return float(np.sum(np.asarray(a) * np.asarray(b)))
+
+
+def _fd_step(g, B, t, dt, u0, ue0, P0, lu, le, v, ve):
+    """Central differences of <(lu, le), step(u0 + h v, ue0 + h ve)> at two
+    small h. A limiter branch switch (a kink of the piecewise-smooth step) within
+    h of the point spoils one of them; both are returned."""
+    out = []
+    for h in (1e-6, 1e-7):
+        up, uep, _ = oracle.step_fn(g, B, t, dt, u0 + h * v, ue0 + h * ve, P0)
+        um, uem, _ = oracle.step_fn(g, B, t, dt, u0 - h * v, ue0 - h * ve, P0)
+        out.append((_dot(lu, up - um) + _dot(le[: uep.size], uep - uem)) / (2 * h))
+    return out
+
+
+def _close_to_one(got, fds, rel, abs_):
+    return any(abs(got - f) <= rel * abs(f) + abs_ for f in fds)
+
+
+@pytest.mark.parametrize("kind", ["periodic2d", "channel_exit", "circle", "walled3d"])
+def test_conv_diff_vjp_matches_central_differences(kind):
+    g, _, u0, ue0 = _case(kind)
+    lam = RNG.normal(size=u0.shape)
+    ub, ueb = oracle.conv_diff_vjp(g, u0, ue0, lam)
+    for _ in range(3):
+        v = RNG.normal(size=u0.shape)
+        ve = RNG.normal(size=ue0.shape) if g.exit_hi_x else np.zeros_like(ue0)
+        h = 1e-6
+        rp = oracle.conv_diff(g, u0 + h * v, ue0 + h * ve)
+        rm = oracle.conv_diff(g, u0 - h * v, ue0 - h * ve)
+        fd = _dot(lam, (rp - rm) / (2 * h))
+        # the flux is piecewise quadratic: the central difference is exact up to rounding
+        assert _dot(ub, v) + _dot(ueb, ve) == pytest.approx(fd, rel=1e-7, abs=1e-9)
+
+
+@pytest.mark.parametrize("kind", ["periodic2d", "channel_exit", "circle", "walled3d"])
+def test_step_vjp_matches_central_differences(kind):
+    g, B, u0, ue0 = _case(kind)
+    dt, t = 0.3, 0.0
+    P0 = np.zeros(u0.shape[1:])
+    lu = RNG.normal(size=u0.shape)
+    le = RNG.normal(size=ue0.shape) if g.exit_hi_x else np.zeros_like(ue0)
+    ub, ueb = oracle.step_vjp(g, B, t, dt, u0, ue0, P0, lu, le)
+    assert np.all(np.isfinite(ub)) and np.all(np.isfinite(ueb))
+    for _ in range(2):
+        v = RNG.normal(size=u0.shape)
+        ve = RNG.normal(size=ue0.shape) if g.exit_hi_x else np.zeros_like(ue0)
+        fds = _fd_step(g, B, t, dt, u0, ue0, P0, lu, le, v, ve)
+        got = _dot(ub, v) + _dot(ueb, ve)
+        assert _close_to_one(got, fds, 1e-6, 1e-6), (got, fds)
+
+
+def test_step_vjp_single_entries_match_finite_differences():
+    # unit directions on a few faces, including the lower wall face and exit plane
+    g, B, u0, ue0 = _case("channel_exit")
+    dt, P0 = 0.25, np.zeros(u0.shape[1:])
+    lu = RNG.normal(size=u0.shape)
+    le = RNG.normal(size=ue0.shape)
+    ub, ueb = oracle.step_vjp(g, B, 0.0, dt, u0, ue0, P0, lu, le)
+    zu, ze = np.zeros_like(u0), np.zeros_like(ue0)
+    for idx in [(0, 5, 0), (0, 3, 19), (1, 7, 10), (0, 0, 1)]:
+        v = zu.copy()
+        v[idx] = 1.0
+        fds = _fd_step(g, B, 0.0, dt, u0, ue0, P0, lu, le, v, ze)
+        assert _close_to_one(ub[idx], fds, 1e-5, 1e-7), (idx, ub[idx], fds)
+    for p in (0, 5, 11):
+        ve = ze.copy()
+        ve[p] = 1.0
+        fds = _fd_step(g, B, 0.0, dt, u0, ue0, P0, lu, le, zu, ve)
+        assert _close_to_one(ueb[p], fds, 1e-5, 1e-7), (p, ueb[p], fds)
+
+
+def test_step_vjp_annihilates_gradients_on_periodic_grid():
+    # Body-free periodic grid: the corrector ends with the orthogonal projector
+    # onto divergence-free fields, which maps every discrete gradient to zero,
+    # so a cotangent that is a gradient has a zero pull-back.
+    g, B, u0, ue0 = _case("periodic2d")
+    phi = RNG.normal(size=u0.shape[1:])
+    lu = np.stack([phi - np.roll(phi, 1, axis=-1), phi - np.roll(phi, 1, axis=-2)])
+    ub, _ = oracle.step_vjp(g, B, 0.0, 0.3, u0, ue0, np.zeros(u0.shape[1:]), lu, None)
+    assert np.max(np.abs(ub)) < 1e-10 * np.max(np.abs(lu))
