@@ -251,6 +251,34 @@ WL_API int wl_guess_info(wl_sim *sim, int *level, int *samples, double *gain);
 WL_API int wl_net_eval(int ndim, const int *n, const float *w, const float *x, const float *t, float *y, float *dw,
                        double *loss);
 
+/* Adjoint of one time step (no counterpart in the paper, which differentiates
+ * the solver in forward mode with dual numbers, Sec. 3 / Sec. 5.3): the
+ * vector-Jacobian product of wl_mom_step with the fixed step dt from the start
+ * state (u0, ue0) at time t, the body measured at t + dt as the step does.
+ * Given the cotangents lu (velocity), le (exit plane, may be NULL) and lP
+ * (reported pressure, nc doubles, may be NULL) of the step's outputs, returns
+ * ub, ueb = J^T (lu, le, lP) for (u0, ue0). The Jacobian is taken with the
+ * flux limiter's branches frozen at the evaluation point. Transposes: the
+ * convection-diffusion flux (scattered), the BDIM blend (gathered), the exit
+ * condition, and each projection through one Poisson solve on div(c lam) with
+ * the same symmetric multigrid, converged to relative residual `tol` (the
+ * forward projection inside is solved to `tol` too).
+ *   u0, lu, ub: ndim arrays of nc (cfg.precision type); ue0, le, ueb: the exit
+ *   plane (ignored / may be NULL without an exit); P0: warm start of the
+ *   forward projection (nc doubles, may be NULL = 0). All host or device.
+ * The sim's velocity, pressure, time and body are unchanged on return.
+ * stats (may be NULL): the two adjoint solves (predictor, corrector).
+ * Errors: WL_ERR_ARG, WL_ERR_NOT_CONVERGED, WL_ERR_NONFINITE, WL_ERR_CUDA. */
+WL_API int wl_step_vjp(wl_sim *sim, double t, double dt, const void *u0, const void *ue0, const double *P0,
+                       const void *lu, const void *le, const double *lP, double tol, void *ub, void *ueb,
+                       wl_solve_stats *stats);
+
+/* Derivative of the pressure force (wl_forces) component `axis` with respect
+ * to the reported pressure, times `scale`: g[I] = -scale n_axis(x_I)
+ * K_eps(d(x_I)) on active cells (0 elsewhere), body at its last measured time.
+ * g: nc doubles, host or device. */
+WL_API int wl_force_dp(wl_sim *sim, int axis, double scale, double *g);
+
 /* Largest grid (cells) wl_coarse_solve_static accepts: its working memory is
  * a fixed device array of 5 * WL_STATIC_MAX_CELLS + 8 doubles (~640 KiB) that
  * every GPU loading this library holds until the process exits. */

@@ -88,7 +88,13 @@ def lib():
             ("orc_step", [C.POINTER(Grid), C.POINTER(BodyS), C.c_double, C.c_double, _P, _P, _P, C.POINTER(Solver), C.POINTER(Stats)], C.c_int),
             ("orc_diagnostics", [C.POINTER(Grid), _P, _P, _P, _P], None),
             ("orc_conv_diff_vjp", [C.POINTER(Grid), _P, _P, _P, _P, _P], None),
-            ("orc_step_vjp", [C.POINTER(Grid), C.POINTER(BodyS), C.c_double, C.c_double, _P, _P, _P, _P, _P, _P, _P], None),
+            ("orc_force_dp", [C.POINTER(Grid), C.POINTER(BodyS), C.c_double, C.c_int, _P], None),
+            ("orc_step_fields", [C.POINTER(Grid), _P, _P, _P, C.c_double, _P, _P, _P, C.POINTER(Solver),
+                                 C.POINTER(Stats)], C.c_int),
+            ("orc_step_vjp_fields", [C.POINTER(Grid), _P, _P, _P, C.c_double, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                     _P, _P], None),
+            ("orc_step_vjp", [C.POINTER(Grid), C.POINTER(BodyS), C.c_double, C.c_double, _P, _P, _P, _P, _P, _P, _P, _P],
+             None),
         ]:
             f = getattr(L, name)
             f.argtypes = args
@@ -280,6 +286,13 @@ def diagnostics(g, u, ue):
     return ke[0], en[0]
 
 
+def force_dp(g, body_s, t, axis):
+    """dF_axis/dp per cell (the force is linear in the pressure)."""
+    out = np.zeros(_shape(g))
+    lib().orc_force_dp(C.byref(g), C.byref(body_s), float(t), int(axis), _p(out))
+    return out
+
+
 def conv_diff_vjp(g, u, ue, lam):
     """(J_R(u, ue))^T lam -> (ubar, uebar)."""
     ub = np.zeros_like(_d(u))
@@ -288,14 +301,43 @@ def conv_diff_vjp(g, u, ue, lam):
     return ub, ueb
 
 
-def step_vjp(g, body_s, t, dt, u0, ue0, P0, lu, le):
-    """Vector-Jacobian product of one step (orc_step) w.r.t. (u0, ue0)."""
+def step_vjp(g, body_s, t, dt, u0, ue0, P0, lu, le, lP=None):
+    """Vector-Jacobian product of one step (orc_step) w.r.t. (u0, ue0), given
+    the cotangents (lu, le, lP) of its outputs (u, ue, P); lP may be None."""
     ub = np.zeros_like(_d(u0))
     ueb = np.zeros(max(plane_size(g), 1))
     le = _d(le) if le is not None else np.zeros(max(plane_size(g), 1))
+    lPd = _d(lP) if lP is not None else None
     lib().orc_step_vjp(C.byref(g), C.byref(body_s), float(t), float(dt), _p(_d(u0)), _p(_d(ue0)), _p(_d(P0)),
-                       _p(_d(lu)), _p(le), _p(ub), _p(ueb))
+                       _p(_d(lu)), _p(le), _p(lPd) if lPd is not None else None, _p(ub), _p(ueb))
     return ub, ueb
+
+
+def step_fields_fn(g, fields, dt, u0, ue0, P0, tol=1e-13):
+    """One orc_step_fields on copies with explicit face fields (mu0, mu1n, V)
+    (None: no body): returns (u, ue, P)."""
+    u, ue, P = _d(u0).copy(), _d(ue0).copy(), _d(P0).copy()
+    S = make_solver(tol, 200, 4)
+    st = (Stats * 2)()
+    fk = [None, None, None] if fields is None else [_d(x) for x in fields]
+    lib().orc_step_fields(C.byref(g), *[(_p(x) if x is not None else None) for x in fk], float(dt), _p(u), _p(ue),
+                          _p(P), C.byref(S), st)
+    return u, ue, P
+
+
+def step_vjp_fields(g, fields, dt, u0, ue0, P0, lu, le, lP=None):
+    """Vector-Jacobian product of orc_step_fields: returns (ub, ueb, mu0b,
+    mu1nb, Vb), the last three the cotangents of the face fields."""
+    mu0, mu1n, V = (_d(x) for x in fields)
+    ub = np.zeros_like(_d(u0))
+    ueb = np.zeros(max(plane_size(g), 1))
+    le = _d(le) if le is not None else np.zeros(max(plane_size(g), 1))
+    lPd = _d(lP) if lP is not None else None
+    mu0b, mu1nb, Vb = np.zeros_like(mu0), np.zeros_like(mu1n), np.zeros_like(V)
+    lib().orc_step_vjp_fields(C.byref(g), _p(mu0), _p(mu1n), _p(V), float(dt), _p(_d(u0)), _p(_d(ue0)),
+                              _p(_d(P0)), _p(_d(lu)), _p(le), _p(lPd) if lPd is not None else None, _p(ub), _p(ueb),
+                              _p(mu0b), _p(mu1nb), _p(Vb))
+    return ub, ueb, mu0b, mu1nb, Vb
 
 
 def step_fn(g, body_s, t, dt, u0, ue0, P0, tol=1e-13):

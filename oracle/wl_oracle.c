@@ -741,15 +741,31 @@ void orc_forces(const orc_grid *g, const orc_body *B, double t, const double *p,
             }
 }
 
-/* One Heun predictor-corrector step with projections (Sec. 2).
+/* Derivative of the force component `axis` with respect to each cell's
+ * pressure: the force is linear in p, dF_axis/dp_I = -n_axis(x_I) K_eps(d(x_I)). */
+void orc_force_dp(const orc_grid *g, const orc_body *B, double t, int axis, double *out)
+{
+    for (int k = 0; k < g->n[2]; ++k)
+        for (int j = 0; j < g->n[1]; ++j)
+            for (int i = 0; i < g->n[0]; ++i) {
+                double x[3] = {i + 0.5, j + 0.5, k + 0.5};
+                double d, nrm[3], v[3];
+                out[lin(g, i, j, k)] = 0.0;
+                if (B->kind == 0) continue;
+                orc_body_eval(B, g->ndim, x, t, &d, nrm, v);
+                out[lin(g, i, j, k)] = -nrm[axis] * orc_kernel(d, g->eps);
+            }
+}
+
+/* One Heun predictor-corrector step with projections (Sec. 2), with the body
+ * given by its measured face fields (mu0, mu1n, V; all NULL without a body).
  * State: u (ndim x nc), ue (exit plane), P (pressure, warm start in/out).
- * Body measured at t + dt (the end of the step) and held for both stages.
  *   u0 = u
  *   predictor:  u = B(u0 + dt R(u0)); BC; exit; project(w = 1)      -> u*
  *   corrector:  u = (u* + B(u0 + dt R(u*)))/2; BC; exit; project(w = 1/2)
  * Returns the number of projections that did not converge. */
-int orc_step(const orc_grid *g, const orc_body *B, double t, double dt,
-             double *u, double *ue, double *P, const orc_solver *S, orc_stats *st2)
+int orc_step_fields(const orc_grid *g, const double *mu0, const double *mu1n, const double *V, double dt,
+                    double *u, double *ue, double *P, const orc_solver *S, orc_stats *st2)
 {
     size_t nc = ncell(g);
     size_t nu = (size_t)g->ndim * nc;
@@ -757,13 +773,6 @@ int orc_step(const orc_grid *g, const orc_body *B, double t, double dt,
     double *u0 = malloc(nu * sizeof(double)), *r = malloc(nu * sizeof(double));
     double *ue0 = malloc((size_t)np * sizeof(double)), *ues = malloc((size_t)np * sizeof(double));
     double *c = malloc(nu * sizeof(double));
-    double *mu0 = NULL, *mu1n = NULL, *V = NULL;
-    if (B && B->kind != 0) {
-        mu0 = malloc(nu * sizeof(double));
-        mu1n = malloc(9 * nc * sizeof(double));
-        V = malloc(nu * sizeof(double));
-        orc_measure(g, B, t + dt, mu0, mu1n, V);
-    }
     orc_coeffs(g, mu0, c);
     memcpy(u0, u, nu * sizeof(double));
     memcpy(ue0, ue, (size_t)np * sizeof(double));
@@ -782,6 +791,24 @@ int orc_step(const orc_grid *g, const orc_body *B, double t, double dt,
     orc_exit_bc(g, ue0, us, ues, dt, 1, ues, u, ue);
     bad += orc_project(g, c, u, ue, P, 0.5, dt, S, st2 ? &st2[1] : NULL);
     free(us); free(u0); free(r); free(ue0); free(ues); free(c);
+    return bad;
+}
+
+/* The step with the body measured at t + dt (the end of the step), held for
+ * both stages. */
+int orc_step(const orc_grid *g, const orc_body *B, double t, double dt,
+             double *u, double *ue, double *P, const orc_solver *S, orc_stats *st2)
+{
+    size_t nc = ncell(g);
+    size_t nu = (size_t)g->ndim * nc;
+    double *mu0 = NULL, *mu1n = NULL, *V = NULL;
+    if (B && B->kind != 0) {
+        mu0 = malloc(nu * sizeof(double));
+        mu1n = malloc(9 * nc * sizeof(double));
+        V = malloc(nu * sizeof(double));
+        orc_measure(g, B, t + dt, mu0, mu1n, V);
+    }
+    int bad = orc_step_fields(g, mu0, mu1n, V, dt, u, ue, P, S, st2);
     free(mu0); free(mu1n); free(V);
     return bad;
 }
@@ -996,9 +1023,15 @@ static void exit_vjp(const orc_grid *g, double dt, int corrector, const double *
 }
 
 /* Projection transposed: (ub, ueb) = (lu, le) + D^T q/(w dt), with
- * q = solve(-w dt G^T lu) (the solve's mean removal is symmetric). */
-static void project_vjp(const orc_grid *g, const double *c, const double *lu, const double *le, double w, double dt,
-                        double *ub, double *ueb)
+ * q = solve(lP - w dt G^T lu) (the solve's mean removal is symmetric); lP,
+ * the cotangent of the returned pressure, may be NULL.
+ * With the projection's own pressure P (u_out = u - w dt c grad P) and cb not
+ * NULL, also the cotangent of the coefficients, through both the gradient
+ * update and the operator A(c) (d(A^+ b) = -A^+ dA P):
+ *   cb_a[I] += (P[I] - P[I-e_a]) ((q[I] - q[I-e_a]) - w dt lu_a[I])
+ * on faces whose coefficient is the body's mu0 (not a non-periodic boundary). */
+static void project_vjp(const orc_grid *g, const double *c, const double *lu, const double *le, const double *lP,
+                        double w, double dt, double *ub, double *ueb, const double *P, double *cb)
 {
     size_t nc = ncell(g);
     int np = g->n[1] * g->n[2];
@@ -1022,7 +1055,7 @@ static void project_vjp(const orc_grid *g, const double *c, const double *lu, co
                     }
                     (void)I;
                 }
-                rhs[lin(g, i, j, k)] = -wdt * s;
+                rhs[lin(g, i, j, k)] = -wdt * s + (lP ? lP[lin(g, i, j, k)] : 0.0);
             }
     orc_solver S = {1e-13, 200, 4};
     orc_poisson_solve(g, c, rhs, q, &S, NULL);
@@ -1043,45 +1076,109 @@ static void project_vjp(const orc_grid *g, const double *c, const double *lu, co
                     }
                     ub[F] += (qm - q[lin(g, i, j, k)]) / wdt;
                     if (a == 0 && g->exit_hi_x && i == g->n[0] - 1) ueb[j + g->n[1] * k] += q[lin(g, i, j, k)] / wdt;
+                    if (cb && P && (I[a] > 0 || g->periodic[a])) {
+                        int M[3] = {i, j, k};
+                        M[a] -= 1;
+                        if (M[a] < 0) M[a] += g->n[a];
+                        double dP = P[lin(g, i, j, k)] - P[lin(g, M[0], M[1], M[2])];
+                        cb[F] += dP * ((q[lin(g, i, j, k)] - qm) - wdt * lu[F]);
+                    }
                 }
     free(rhs); free(q);
 }
 
-/* Vector-Jacobian product of orc_step: given (lu, le) for the step's output
- * (u, ue), return (ub, ueb) for its input (u0, ue0). The state arrays are not
- * changed; P (warm start) is used for the forward recomputation. */
-void orc_step_vjp(const orc_grid *g, const orc_body *B, double t, double dt, const double *u0, const double *ue0,
-                  const double *P0, const double *lu, const double *le, double *ub, double *ueb)
+/* Neighbour along b (dir = +1 or -1) of face (i,j,k), wrapped on periodic
+ * axes and clamped to the stored range otherwise (the blend's samples). */
+static size_t blend_nb(const orc_grid *g, int i, int j, int k, int b, int dir)
+{
+    int P[3] = {i, j, k};
+    P[b] += dir;
+    for (int ax = 0; ax < g->ndim; ++ax) {
+        int N = g->n[ax];
+        if (g->periodic[ax]) P[ax] = ((P[ax] % N) + N) % N;
+        else if (P[ax] < 0) P[ax] = 0;
+        else if (P[ax] > N - 1) P[ax] = N - 1;
+    }
+    return lin(g, P[0], P[1], P[2]);
+}
+
+/* Cotangents of the blend's face fields, given the blend input f and the
+ * (masked) cotangent gbar of its output u = V + mu0 (f - V) + mu1 n.grad(f - V):
+ *   mu0b += gbar (f - V);  mu1nb[a,b] += gbar (f - V)(P_b) - (f - V)(M_b)) / 2;
+ *   Vb += gbar (1 - mu0), and the gradient term's -/+ gbar mu1 n_b / 2 at P_b / M_b. */
+static void bdim_field_vjp(const orc_grid *g, const double *f, const double *mu0, const double *mu1n, const double *V,
+                           const double *gbar, double *mu0b, double *mu1nb, double *Vb)
+{
+    size_t nc = ncell(g);
+    for (int a = 0; a < g->ndim; ++a)
+        for (int k = 0; k < g->n[2]; ++k)
+            for (int j = 0; j < g->n[1]; ++j)
+                for (int i = 0; i < g->n[0]; ++i) {
+                    size_t L = (size_t)a * nc + lin(g, i, j, k);
+                    double gv = gbar[L];
+                    if (gv == 0.0) continue;
+                    mu0b[L] += gv * (f[L] - V[L]);
+                    Vb[L] += gv * (1.0 - mu0[L]);
+                    for (int b = 0; b < g->ndim; ++b) {
+                        size_t up = (size_t)a * nc + blend_nb(g, i, j, k, b, +1);
+                        size_t dn = (size_t)a * nc + blend_nb(g, i, j, k, b, -1);
+                        size_t m = (size_t)(a * 3 + b) * nc + lin(g, i, j, k);
+                        mu1nb[m] += gv * 0.5 * ((f[up] - V[up]) - (f[dn] - V[dn]));
+                        Vb[up] -= gv * 0.5 * mu1n[m];
+                        Vb[dn] += gv * 0.5 * mu1n[m];
+                    }
+                }
+}
+
+/* Vector-Jacobian product of orc_step_fields: given (lu, le, lP) for the
+ * step's output (u, ue, P), return (ub, ueb) for its input (u0, ue0); lP may
+ * be NULL. When mu0b, mu1nb, Vb are not NULL, the cotangents of the face
+ * fields (mu0 through the blends and the Poisson coefficients, mu1 n, V) are
+ * added to them (layout of orc_measure). The state arrays are not changed;
+ * P0 (warm start) is used for the forward recomputation (the converged step
+ * does not depend on it). */
+void orc_step_vjp_fields(const orc_grid *g, const double *mu0, const double *mu1n, const double *V, double dt,
+                         const double *u0, const double *ue0, const double *P0, const double *lu, const double *le,
+                         const double *lP, double *ub, double *ueb, double *mu0b, double *mu1nb, double *Vb)
 {
     size_t nc = ncell(g);
     size_t nu = (size_t)g->ndim * nc;
     int np = g->n[1] * g->n[2];
+    int fields = mu0 && mu0b && mu1nb && Vb;
     double *c = malloc(nu * sizeof(double));
-    double *mu0 = NULL, *mu1n = NULL, *V = NULL;
-    if (B && B->kind != 0) {
-        mu0 = malloc(nu * sizeof(double)); mu1n = malloc(9 * nc * sizeof(double)); V = malloc(nu * sizeof(double));
-        orc_measure(g, B, t + dt, mu0, mu1n, V);
-    }
     orc_coeffs(g, mu0, c);
     orc_solver S = {1e-13, 200, 4};
-    /* forward predictor: u* and ue* */
+    /* forward: predictor (u*, ue*, P1) and corrector (P2), keeping the blend inputs */
     double *r = malloc(nu * sizeof(double)), *us = malloc(nu * sizeof(double));
-    double *ues = malloc((size_t)np * sizeof(double)), *P = malloc(nc * sizeof(double));
-    memcpy(P, P0, nc * sizeof(double));
+    double *f1 = malloc(nu * sizeof(double)), *f2 = malloc(nu * sizeof(double));
+    double *ues = malloc((size_t)np * sizeof(double)), *P1 = malloc(nc * sizeof(double));
+    double *P2 = malloc(nc * sizeof(double)), *u2 = malloc(nu * sizeof(double));
+    double *ue2 = malloc((size_t)np * sizeof(double));
+    memcpy(P1, P0, nc * sizeof(double));
     orc_conv_diff(g, u0, ue0, r);
+    for (size_t e = 0; e < nu; ++e) f1[e] = u0[e] + dt * r[e];
     orc_bdim(g, u0, r, dt, mu0, mu1n, V, NULL, us);
     memcpy(ues, ue0, (size_t)np * sizeof(double));
     orc_exit_bc(g, ue0, u0, ue0, dt, 0, NULL, us, ues);
-    orc_project(g, c, us, ues, P, 1.0, dt, &S, NULL);
+    orc_project(g, c, us, ues, P1, 1.0, dt, &S, NULL);
+    if (fields) {
+        orc_conv_diff(g, us, ues, r);
+        for (size_t e = 0; e < nu; ++e) f2[e] = u0[e] + dt * r[e];
+        orc_bdim(g, u0, r, dt, mu0, mu1n, V, us, u2);
+        memcpy(ue2, ues, (size_t)np * sizeof(double));
+        orc_exit_bc(g, ue0, us, ues, dt, 1, ues, u2, ue2);
+        memcpy(P2, P1, nc * sizeof(double));
+        orc_project(g, c, u2, ue2, P2, 0.5, dt, &S, NULL);
+    }
     /* reverse */
     double *u2b = calloc(nu, sizeof(double)), *ue2b = calloc((size_t)np + 1, sizeof(double));
     double *usb = calloc(nu, sizeof(double)), *uesb = calloc((size_t)np + 1, sizeof(double));
     double *fb = calloc(nu, sizeof(double)), *u1b = calloc(nu, sizeof(double)), *ue1b = calloc((size_t)np + 1, sizeof(double));
-    double *tmp = calloc(nu, sizeof(double)), *tmpe = calloc((size_t)np + 1, sizeof(double));
+    double *tmp = calloc(nu, sizeof(double));
     for (size_t e = 0; e < nu; ++e) ub[e] = 0.0;
     for (int p = 0; p < np; ++p) ueb[p] = 0.0;
     /* corrector projection (w = 1/2) */
-    project_vjp(g, c, lu, le, 0.5, dt, u2b, ue2b);
+    project_vjp(g, c, lu, le, lP, 0.5, dt, u2b, ue2b, fields ? P2 : NULL, fields ? mu0b : NULL);
     /* corrector exit: ue2 from ue0, ue*, u* */
     exit_vjp(g, dt, 1, ue2b, ueb, uesb, usb, uesb);
     /* corrector blend: u2 = (u* + B(u0 + dt R(u*)))/2 on non-boundary faces */
@@ -1094,11 +1191,12 @@ void orc_step_vjp(const orc_grid *g, const orc_body *B, double t, double dt, con
             tmp[F] = v;
             usb[F] += v;
         }
+    if (fields) bdim_field_vjp(g, f2, mu0, mu1n, V, tmp, mu0b, mu1nb, Vb);
     bdim_vjp(g, mu0, mu1n, tmp, fb);
     for (size_t e = 0; e < nu; ++e) { ub[e] += fb[e]; fb[e] *= dt; }
     orc_conv_diff_vjp(g, us, ues, fb, usb, uesb);
     /* predictor projection (w = 1) */
-    project_vjp(g, c, usb, uesb, 1.0, dt, u1b, ue1b);
+    project_vjp(g, c, usb, uesb, NULL, 1.0, dt, u1b, ue1b, fields ? P1 : NULL, fields ? mu0b : NULL);
     /* predictor exit: ue1 from ue0 (twice) and u0 */
     exit_vjp(g, dt, 0, ue1b, ueb, ueb, ub, NULL);
     /* predictor blend: u1 = B(u0 + dt R(u0)) */
@@ -1110,9 +1208,25 @@ void orc_step_vjp(const orc_grid *g, const orc_body *B, double t, double dt, con
             int I[3] = {i, j, k};
             tmp[F] = (!g->periodic[a] && I[a] == 0) ? 0.0 : u1b[F];
         }
+    if (fields) bdim_field_vjp(g, f1, mu0, mu1n, V, tmp, mu0b, mu1nb, Vb);
     bdim_vjp(g, mu0, mu1n, tmp, fb);
     for (size_t e = 0; e < nu; ++e) { ub[e] += fb[e]; fb[e] *= dt; }
     orc_conv_diff_vjp(g, u0, ue0, fb, ub, ueb);
-    free(c); free(mu0); free(mu1n); free(V); free(r); free(us); free(ues); free(P);
-    free(u2b); free(ue2b); free(usb); free(uesb); free(fb); free(u1b); free(ue1b); free(tmp); free(tmpe);
+    free(c); free(r); free(us); free(f1); free(f2); free(ues); free(P1); free(P2); free(u2); free(ue2);
+    free(u2b); free(ue2b); free(usb); free(uesb); free(fb); free(u1b); free(ue1b); free(tmp);
+}
+
+/* The same with the body measured at t + dt (as orc_step does). */
+void orc_step_vjp(const orc_grid *g, const orc_body *B, double t, double dt, const double *u0, const double *ue0,
+                  const double *P0, const double *lu, const double *le, const double *lP, double *ub, double *ueb)
+{
+    size_t nc = ncell(g);
+    size_t nu = (size_t)g->ndim * nc;
+    double *mu0 = NULL, *mu1n = NULL, *V = NULL;
+    if (B && B->kind != 0) {
+        mu0 = malloc(nu * sizeof(double)); mu1n = malloc(9 * nc * sizeof(double)); V = malloc(nu * sizeof(double));
+        orc_measure(g, B, t + dt, mu0, mu1n, V);
+    }
+    orc_step_vjp_fields(g, mu0, mu1n, V, dt, u0, ue0, P0, lu, le, lP, ub, ueb, NULL, NULL, NULL);
+    free(mu0); free(mu1n); free(V);
 }

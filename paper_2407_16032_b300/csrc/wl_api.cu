@@ -13,6 +13,7 @@
 #include "k_mg_march.cuh"
 #include "k_misc.cuh"
 #include "k_net.cuh"
+#include "k_adjoint.cuh"
 
 #include <cmath>
 #include <cstdio>
@@ -73,6 +74,9 @@ struct SimBase {
     virtual void guess_weights(const float *in, float *out) = 0;
     virtual void guess_info(int *level, int *samples, double *gain) = 0;
     virtual std::string profile_report() = 0;
+    virtual int step_vjp(double t0, double dt, const void *u0, const void *ue0, const double *P0, const void *lu,
+                         const void *le, const double *lP, double tol, void *ub, void *ueb, wl_solve_stats *st) = 0;
+    virtual void force_dp(int axis, double scale, double *g) = 0;
     double t = 0.0, dt_next = 0.25;
 };
 
@@ -164,6 +168,14 @@ struct Sim : SimBase {
         double *loss = nullptr;
         T *ph0 = nullptr, *pl0 = nullptr;
     } gq;
+    // adjoint of one step: forward copies, cotangents, and a backup of the state
+    struct AdjState {
+        bool ready = false;
+        T *u0[3] = {}, *us[3] = {}, *lu[3] = {}, *x[3] = {}, *usb[3] = {}, *fb[3] = {}, *ub[3] = {}, *bku[3] = {};
+        T *ue0 = nullptr, *ues = nullptr, *le = nullptr, *xe = nullptr, *uesb = nullptr, *ueb = nullptr, *bkue = nullptr;
+        T *bkph = nullptr, *bkpl = nullptr;
+        double *lP = nullptr;
+    } ad;
     Prof prof;
     void P0(const char *name, int level, long long cells) { prof.beg(st, name, level, cells); }
     void P1() { prof.end(st); }
@@ -962,6 +974,193 @@ struct Sim : SimBase {
         WL_CK(cudaStreamSynchronize(st));
     }
 
+    // ------------------------------------------------------------ adjoint
+    void adj_alloc() {
+        if (ad.ready) return;
+        const long long nc = g.nc;
+        for (int a = 0; a < g.ndim; ++a) {
+            ad.u0[a] = alloc_n<T>(nc); ad.us[a] = alloc_n<T>(nc); ad.lu[a] = alloc_n<T>(nc);
+            ad.x[a] = alloc_n<T>(nc); ad.usb[a] = alloc_n<T>(nc); ad.fb[a] = alloc_n<T>(nc);
+            ad.ub[a] = alloc_n<T>(nc); ad.bku[a] = alloc_n<T>(nc);
+        }
+        ad.ue0 = alloc_n<T>(np); ad.ues = alloc_n<T>(np); ad.le = alloc_n<T>(np); ad.xe = alloc_n<T>(np);
+        ad.uesb = alloc_n<T>(np); ad.ueb = alloc_n<T>(np); ad.bkue = alloc_n<T>(np);
+        ad.bkph = alloc_n<T>(nc); ad.bkpl = alloc_n<T>(nc);
+        ad.lP = alloc_n<double>(nc);
+        if (!pout) pout = alloc_n<double>(nc);
+        ad.ready = true;
+    }
+    static CVec3P<T> cvp(T *const (&p)[3]) { CVec3P<T> r{}; for (int a = 0; a < 3; ++a) r.p[a] = p[a]; return r; }
+    static Vec3P<T> vvp(T *const (&p)[3]) { Vec3P<T> r{}; for (int a = 0; a < 3; ++a) r.p[a] = p[a]; return r; }
+    void zero_vec(T *const (&p)[3]) {
+        for (int a = 0; a < g.ndim; ++a) WL_CK(cudaMemsetAsync(p[a], 0, g.nc * sizeof(T), st));
+    }
+    void copy_vec(T *const (&dst)[3], T *const (&src)[3]) {
+        for (int a = 0; a < g.ndim; ++a)
+            WL_CK(cudaMemcpyAsync(dst[a], src[a], g.nc * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    }
+
+    // Projection transposed: (out, oute) = (lam, le) + D^T A^+ (div(c lam) + lP/(w dt)).
+    int proj_vjp(T *const (&lam)[3], const T *le, const double *lP, double w, double dt, T *const (&out)[3], T *oute,
+                 wl_solve_stats *sts) {
+        P0("adj_rhs", 0, g.nc);
+        k_adj_rhs<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], cvp(lam), lP, 1.0 / (w * dt), b, bl);
+        P1();
+        k_bstats<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], b, S, part);
+        WL_CK(cudaMemsetAsync(ph, 0, g.nc * sizeof(T), st));
+        WL_CK(cudaMemsetAsync(pl, 0, g.nc * sizeof(T), st));
+        WL_LAUNCH_CK();
+        launches += 2;
+        const int rc = solve(sts);
+        pmean();
+        P0("adj_grad", 0, g.nc);
+        k_adj_grad<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], ph, pl, S, cvp(lam), le, vvp(out), oute);
+        P1();
+        WL_LAUNCH_CK();
+        ++launches;
+        return rc;
+    }
+
+    void adj_flux(T *const (&u)[3], const T *ue, T *const (&lam)[3], T *const (&ub)[3], T *ueb) {
+        P0("adj_flux", 0, g.nc);
+        k_adj_flux<T, ND><<<blocks(g.nc), 256, 0, st>>>(g, cvp(u), ue, cvp(lam), vvp(ub), ueb);
+        P1();
+        WL_LAUNCH_CK();
+        ++launches;
+    }
+
+    void adj_blend(T *const (&gin)[3], double s, T *const *ustar_b, T *const (&ub)[3], T *const (&fb)[3], double dt) {
+        Vec3P<T> sb{};
+        for (int a = 0; a < 3; ++a) sb.p[a] = ustar_b ? ustar_b[a] : nullptr;
+        P0("adj_blend", 0, g.nc);
+        k_adj_blend<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], cvp(gin), (T)s, mu1n, (long long)g.nc, has_body, sb,
+                                                        vvp(ub), vvp(fb), (T)dt);
+        P1();
+        WL_LAUNCH_CK();
+        ++launches;
+    }
+
+    // Vector-Jacobian product of one step (mom_step with a fixed dt, body
+    // measured at t0 + dt) at the start state (u0, ue0), warm start P0: given
+    // the cotangents (lu, le) of the step's velocity and exit plane and lP of
+    // its reported pressure, returns (ub, ueb) for (u0, ue0). The sim's state
+    // (velocity, exit plane, pressure, time, body) is left as it was.
+    int step_vjp(double t0, double dt, const void *u0, const void *ue0, const double *P0in, const void *lu,
+                 const void *le, const double *lP, double tol, void *ub, void *ueb, wl_solve_stats *sts) override {
+        if (!(dt > 0)) throw Err{WL_ERR_ARG, "step_vjp: dt must be positive"};
+        adj_alloc();
+        const size_t vb = g.nc * sizeof(T), pb = (size_t)np * sizeof(T);
+        // back up the state
+        copy_vec(ad.bku, vel[cur]);
+        WL_CK(cudaMemcpyAsync(ad.bkue, ueA, pb, cudaMemcpyDeviceToDevice, st));
+        WL_CK(cudaMemcpyAsync(ad.bkph, ph, vb, cudaMemcpyDeviceToDevice, st));
+        WL_CK(cudaMemcpyAsync(ad.bkpl, pl, vb, cudaMemcpyDeviceToDevice, st));
+        const double body_t0 = body_t, tol0 = cfg.tol;
+        const bool gc = gq.collect, gu = gq.use;
+        gq.collect = gq.use = false;
+        int rc = WL_OK;
+        // inputs
+        for (int a = 0; a < g.ndim; ++a) {
+            WL_CK(cudaMemcpyAsync(ad.u0[a], (const char *)u0 + a * vb, vb, cudaMemcpyDefault, st));
+            WL_CK(cudaMemcpyAsync(ad.lu[a], (const char *)lu + a * vb, vb, cudaMemcpyDefault, st));
+        }
+        if (g.exit_x) {
+            if (ue0) WL_CK(cudaMemcpyAsync(ad.ue0, ue0, pb, cudaMemcpyDefault, st));
+            else k_fill<T><<<blocks(np), 256, 0, st>>>((long long)np, (T)g.U[0], ad.ue0);
+            if (le) WL_CK(cudaMemcpyAsync(ad.le, le, pb, cudaMemcpyDefault, st));
+            else WL_CK(cudaMemsetAsync(ad.le, 0, pb, st));
+        }
+        if (lP) WL_CK(cudaMemcpyAsync(ad.lP, lP, g.nc * sizeof(double), cudaMemcpyDefault, st));
+        if (P0in) {
+            WL_CK(cudaMemcpyAsync(pout, P0in, g.nc * sizeof(double), cudaMemcpyDefault, st));
+            k_pin<T><<<blocks(g.nc), 256, 0, st>>>(g, pout, ph, pl);
+            WL_LAUNCH_CK();
+            ++launches;
+        } else {
+            WL_CK(cudaMemsetAsync(ph, 0, vb, st));
+            WL_CK(cudaMemsetAsync(pl, 0, vb, st));
+        }
+        if (has_body && (moving || body_t != t0 + dt)) body_update(t0 + dt);
+        wl_solve_stats s[2] = {};
+        // forward predictor: u* and u_e*
+        copy_vec(vel[cur], ad.u0);
+        if (g.exit_x) {
+            WL_CK(cudaMemcpyAsync(ueA, ad.ue0, pb, cudaMemcpyDeviceToDevice, st));
+            WL_CK(cudaMemcpyAsync(ueB, ad.ue0, pb, cudaMemcpyDeviceToDevice, st));
+        }
+        const int A0 = cur, B1 = (cur + 1) & 3, C2 = (cur + 2) & 3;
+        int ustar;
+        if (!has_body) {
+            flux<FM_PRED_U>(fargs(A0, ueB, -1, B1, dt));
+            ustar = B1;
+        } else {
+            flux<FM_PRED_F>(fargs(A0, ueB, -1, B1, dt));
+            blend(false, B1, -1, C2);
+            ustar = C2;
+        }
+        exit_stage(false, A0, dt);
+        cfg.tol = tol;
+        int r0 = project_buf(ustar, ueA, 1.0, dt, nullptr);
+        copy_vec(ad.us, vel[ustar]);
+        if (g.exit_x) WL_CK(cudaMemcpyAsync(ad.ues, ueA, pb, cudaMemcpyDeviceToDevice, st));
+        // reverse: corrector projection, exit, blend, flux at u*
+        int r1 = proj_vjp(ad.lu, g.exit_x ? ad.le : nullptr, lP ? ad.lP : nullptr, 0.5, dt, ad.x, ad.xe, &s[1]);
+        zero_vec(ad.ub);
+        zero_vec(ad.usb);
+        if (g.exit_x) {
+            WL_CK(cudaMemsetAsync(ad.ueb, 0, pb, st));
+            WL_CK(cudaMemsetAsync(ad.uesb, 0, pb, st));
+            k_adj_exit<T, true><<<1, 1024, 0, st>>>(g, ad.xe, (T)dt, ad.ueb, ad.uesb, ad.usb[0]);
+            WL_LAUNCH_CK();
+            ++launches;
+        }
+        adj_blend(ad.x, 0.5, ad.usb, ad.ub, ad.fb, dt);
+        adj_flux(ad.us, ad.ues, ad.fb, ad.usb, ad.uesb);
+        // predictor projection, exit, blend, flux at u0
+        int r2 = proj_vjp(ad.usb, g.exit_x ? ad.uesb : nullptr, nullptr, 1.0, dt, ad.x, ad.xe, &s[0]);
+        if (g.exit_x) {
+            k_adj_exit<T, false><<<1, 1024, 0, st>>>(g, ad.xe, (T)dt, ad.ueb, ad.ueb, ad.ub[0]);
+            WL_LAUNCH_CK();
+            ++launches;
+        }
+        adj_blend(ad.x, 1.0, nullptr, ad.ub, ad.fb, dt);
+        adj_flux(ad.u0, ad.ue0, ad.fb, ad.ub, ad.ueb);
+        // outputs
+        for (int a = 0; a < g.ndim; ++a) WL_CK(cudaMemcpyAsync((char *)ub + a * vb, ad.ub[a], vb, cudaMemcpyDefault, st));
+        if (ueb && g.exit_x) WL_CK(cudaMemcpyAsync(ueb, ad.ueb, pb, cudaMemcpyDefault, st));
+        // restore the state
+        cfg.tol = tol0;
+        gq.collect = gc;
+        gq.use = gu;
+        copy_vec(vel[cur], ad.bku);
+        WL_CK(cudaMemcpyAsync(ueA, ad.bkue, pb, cudaMemcpyDeviceToDevice, st));
+        WL_CK(cudaMemcpyAsync(ph, ad.bkph, vb, cudaMemcpyDeviceToDevice, st));
+        WL_CK(cudaMemcpyAsync(pl, ad.bkpl, vb, cudaMemcpyDeviceToDevice, st));
+        if (has_body && body_t != body_t0 && body_t0 >= 0) body_update(body_t0);
+        WL_CK(cudaStreamSynchronize(st));
+        prof.flush();
+        if (sts) { sts[0] = s[0]; sts[1] = s[1]; }
+        for (int r : {r0, r1, r2})
+            if (r != WL_OK && rc == WL_OK) rc = r;
+        if (rc == WL_ERR_NONFINITE) err = "non-finite values in the adjoint step";
+        else if (rc == WL_ERR_NOT_CONVERGED) err = "a Poisson solve of the adjoint step did not reach tol";
+        return rc;
+    }
+
+    void force_dp(int axis, double scale, double *gout) override {
+        if (axis < 0 || axis >= g.ndim) throw Err{WL_ERR_ARG, "force_dp: axis out of range"};
+        adj_alloc();
+        if (!has_body) {
+            WL_CK(cudaMemsetAsync(ad.lP, 0, g.nc * sizeof(double), st));
+        } else {
+            k_force_dp<T><<<blocks(g.nc), 256, 0, st>>>(g, body_state(body_t), lv[0].invD, axis, scale, ad.lP);
+            WL_LAUNCH_CK();
+            ++launches;
+        }
+        WL_CK(cudaMemcpyAsync(gout, ad.lP, g.nc * sizeof(double), cudaMemcpyDefault, st));
+        WL_CK(cudaStreamSynchronize(st));
+    }
+
     void info(int *levels, long long *nl) override {
         if (levels) *levels = nlev;
         if (nl) *nl = launches;
@@ -1219,6 +1418,16 @@ int wl_net_eval(int ndim, const int *n, const float *w, const float *x, const fl
     }
     for (void *p : bufs) cudaFree(p);
     return rc;
+}
+
+int wl_step_vjp(wl_sim *s, double t, double dt, const void *u0, const void *ue0, const double *P0, const void *lu,
+                const void *le, const double *lP, double tol, void *ub, void *ueb, wl_solve_stats *stats) {
+    if (!u0 || !lu || !ub || !(tol > 0)) return WL_ERR_ARG;
+    return guard(s, [&] { return s->impl->step_vjp(t, dt, u0, ue0, P0, lu, le, lP, tol, ub, ueb, stats); });
+}
+int wl_force_dp(wl_sim *s, int axis, double scale, double *g) {
+    if (!g) return WL_ERR_ARG;
+    return guard(s, [&] { s->impl->force_dp(axis, scale, g); return (int)WL_OK; });
 }
 
 const char *wl_last_error(const wl_sim *s) { return s ? s->err.c_str() : "null sim"; }

@@ -26,8 +26,8 @@ EXPORTS = (
     "wl_get_pressure", "wl_set_pressure", "wl_set_time", "wl_get_time", "wl_mom_step", "wl_project",
     "wl_poisson_solve", "wl_conv_diff", "wl_forces", "wl_body_update", "wl_get_body_fields",
     "wl_diagnostics", "wl_info", "wl_profile", "wl_profile_report", "wl_coarse_solve_static", "wl_guess_setup",
-    "wl_guess_mode", "wl_guess_train", "wl_guess_weights", "wl_guess_info", "wl_net_eval", "wl_last_error",
-    "wl_status_string",
+    "wl_guess_mode", "wl_guess_train", "wl_guess_weights", "wl_guess_info", "wl_net_eval", "wl_step_vjp",
+    "wl_force_dp", "wl_last_error", "wl_status_string",
 )
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t)
@@ -100,6 +100,9 @@ def lib() -> C.CDLL:
             "wl_guess_weights": ([vp, vp, vp], ip),
             "wl_guess_info": ([vp, C.POINTER(C.c_int), C.POINTER(C.c_int), dp], ip),
             "wl_net_eval": ([ip, C.POINTER(C.c_int), vp, vp, vp, vp, vp, dp], ip),
+            "wl_step_vjp": ([vp, C.c_double, C.c_double, vp, vp, vp, vp, vp, vp, C.c_double, vp, vp,
+                             C.POINTER(SolveStats)], ip),
+            "wl_force_dp": ([vp, ip, C.c_double, vp], ip),
             "wl_last_error": ([vp], C.c_char_p),
             "wl_status_string": ([ip], C.c_char_p),
         }
@@ -339,6 +342,25 @@ class Sim:
         lv, ns, gn = C.c_int(), C.c_int(), C.c_double()
         self._check(lib().wl_guess_info(self._h, C.byref(lv), C.byref(ns), C.byref(gn)), "wl_guess_info")
         return lv.value, ns.value, gn.value
+
+    # ------------------------------------------------------------ adjoint
+    def step_vjp(self, t, dt, u0, ue0, P0, lu, le=None, lP=None, tol=1e-8, ub=None, ueb=None):
+        """wl_step_vjp: (ub, ueb) = J^T (lu, le, lP) of one step from (u0, ue0)
+        at time t with step dt. Returns (ub, ueb, [predictor, corrector] solve
+        results of the adjoint solves)."""
+        ub = self.torch.empty_like(lu) if ub is None else ub
+        if ueb is None and self.exit:
+            ueb = self.new_plane(device=lu.is_cuda)
+        st = (SolveStats * 2)()
+        self._check(lib().wl_step_vjp(self._h, float(t), float(dt), _ptr(u0), _ptr(ue0), _ptr(P0), _ptr(lu),
+                                      _ptr(le), _ptr(lP), float(tol), _ptr(ub), _ptr(ueb), st), "wl_step_vjp")
+        return ub, ueb, [SolveResult(x.vcycles, x.rel_resid, x.bnorm, x.rel_initial) for x in st]
+
+    def force_dp(self, axis, scale=1.0, out=None):
+        """wl_force_dp: scale * dF_axis/dp per cell (float64)."""
+        out = self.torch.zeros(self._shape(), dtype=self.torch.float64, device=self.device) if out is None else out
+        self._check(lib().wl_force_dp(self._h, int(axis), float(scale), _ptr(out)), "wl_force_dp")
+        return out
 
     def info(self):
         lv, nl = C.c_int(), C.c_longlong()

@@ -42,15 +42,18 @@ def _dot(a, b):
     return float(np.sum(np.asarray(a) * np.asarray(b)))
 
 
-def _fd_step(g, B, t, dt, u0, ue0, P0, lu, le, v, ve):
-    """Central differences of <(lu, le), step(u0 + h v, ue0 + h ve)> at two
+def _fd_step(g, B, t, dt, u0, ue0, P0, lu, le, v, ve, lP=None):
+    """Central differences of <(lu, le, lP), step(u0 + h v, ue0 + h ve)> at two
     small h. A limiter branch switch (a kink of the piecewise-smooth step) within
     h of the point spoils one of them; both are returned."""
     out = []
     for h in (1e-6, 1e-7):
-        up, uep, _ = oracle.step_fn(g, B, t, dt, u0 + h * v, ue0 + h * ve, P0)
-        um, uem, _ = oracle.step_fn(g, B, t, dt, u0 - h * v, ue0 - h * ve, P0)
-        out.append((_dot(lu, up - um) + _dot(le[: uep.size], uep - uem)) / (2 * h))
+        up, uep, Pp = oracle.step_fn(g, B, t, dt, u0 + h * v, ue0 + h * ve, P0)
+        um, uem, Pm = oracle.step_fn(g, B, t, dt, u0 - h * v, ue0 - h * ve, P0)
+        d = _dot(lu, up - um) + _dot(le[: uep.size], uep - uem)
+        if lP is not None:
+            d += _dot(lP, Pp - Pm)
+        out.append(d / (2 * h))
     return out
 
 
@@ -120,3 +123,109 @@ def test_step_vjp_annihilates_gradients_on_periodic_grid():
     lu = np.stack([phi - np.roll(phi, 1, axis=-1), phi - np.roll(phi, 1, axis=-2)])
     ub, _ = oracle.step_vjp(g, B, 0.0, 0.3, u0, ue0, np.zeros(u0.shape[1:]), lu, None)
     assert np.max(np.abs(ub)) < 1e-10 * np.max(np.abs(lu))
+
+
+@pytest.mark.parametrize("kind", ["circle", "channel_exit", "walled3d"])
+def test_step_vjp_with_pressure_cotangent_matches_central_differences(kind):
+    # the reported pressure (mean-free over active cells) enters force
+    # objectives; its cotangent joins the corrector projection's adjoint solve
+    g, B, u0, ue0 = _case(kind)
+    dt, t = 0.3, 0.0
+    P0 = np.zeros(u0.shape[1:])
+    lu = np.zeros(u0.shape)
+    le = np.zeros_like(ue0)
+    lP = RNG.normal(size=u0.shape[1:])
+    ub, ueb = oracle.step_vjp(g, B, t, dt, u0, ue0, P0, lu, le, lP)
+    assert np.max(np.abs(ub)) > 0
+    for _ in range(2):
+        v = RNG.normal(size=u0.shape)
+        ve = RNG.normal(size=ue0.shape) if g.exit_hi_x else np.zeros_like(ue0)
+        fds = _fd_step(g, B, t, dt, u0, ue0, P0, lu, le, v, ve, lP)
+        got = _dot(ub, v) + _dot(ueb, ve)
+        assert _close_to_one(got, fds, 1e-6, 1e-6), (got, fds)
+
+
+def _fields_case(kind):
+    if kind == "circle":
+        g, B, u0, ue0 = _case("circle")
+        body = synth.Body(kind="sphere", centre=(10.0, 10.3, 0.0), radius=4.2)
+    else:
+        g = oracle.make_grid(2, (40, 28), (False, False), True, (1.0, 0.0), 0.02)
+        u0 = synth.random_field(17, 2, (40, 28), amp=0.1, offset=(1.0, 0.0))
+        ue0 = 1.0 + 0.1 * (2 * synth.uniform01(23, 0, 28) - 1)
+        body = synth.Body("ellipse", (15.2, 14.1, 0.0), 0.0, (8.0, 1.6), heave_amp=2.0, pitch_amp=0.3, omega=0.05)
+        B = oracle.make_body(body)
+    return g, B, body, u0, ue0
+
+
+@pytest.mark.parametrize("kind", ["circle", "ellipse"])
+def test_field_cotangents_match_central_differences(kind):
+    # the step's dependence on the measured face fields (mu0 in the blend and
+    # in the Poisson coefficients, mu1 n and V in the blend), checked against
+    # central differences of the step run with perturbed explicit fields
+    g, B, body, u0, ue0 = _fields_case(kind)
+    dt, t = 0.3, 1.0
+    fields = oracle.measure(g, B, t + dt)
+    P0 = np.zeros(u0.shape[1:])
+    lu = RNG.normal(size=u0.shape)
+    le = RNG.normal(size=ue0.shape)
+    lP = RNG.normal(size=u0.shape[1:])
+    ub, ueb, mu0b, mu1nb, Vb = oracle.step_vjp_fields(g, fields, dt, u0, ue0, P0, lu, le, lP)
+    ub2, ueb2 = oracle.step_vjp(g, B, t, dt, u0, ue0, P0, lu, le, lP)
+    assert np.array_equal(ub, ub2) and np.array_equal(ueb, ueb2)
+    mu0, mu1n, V = fields
+    band = (mu0 > 0.05) & (mu0 < 1.0)          # keep the active set of the solve fixed
+    assert band.sum() > 10
+    for _ in range(2):
+        d0 = np.where(band, RNG.normal(size=mu0.shape), 0.0)
+        d1 = np.zeros_like(mu1n)
+        d1[:, : g.ndim] = np.where(band[:, None], RNG.normal(size=mu1n[:, : g.ndim].shape), 0.0)
+        dV = np.where(band, RNG.normal(size=V.shape), 0.0)
+        got = _dot(mu0b, d0) + _dot(mu1nb, d1) + _dot(Vb, dV)
+        fds = []
+        for h in (1e-6, 1e-7):
+            outs = []
+            for sgn in (1, -1):
+                f = (mu0 + sgn * h * d0, mu1n + sgn * h * d1, V + sgn * h * dV)
+                u, ue, P = oracle.step_fields_fn(g, f, dt, u0, ue0, P0)
+                outs.append(_dot(lu, u) + _dot(le, ue) + _dot(lP, P))
+            fds.append((outs[0] - outs[1]) / (2 * h))
+        assert _close_to_one(got, fds, 1e-6, 1e-6), (got, fds)
+
+
+def test_window_parameter_gradient_matches_central_differences():
+    # mean thrust of a heaving and pitching ellipse over a few steps: the
+    # adjoint gradient with respect to the heave and pitch amplitudes against
+    # central differences of complete forward runs
+    from oracle import adjoint
+    case = synth.Case("el", 2, (48, 32, 1), (False, False, False), True, (1.0, 0.0, 0.0), 0.02,
+                      synth.Body("ellipse", (16.3, 15.8, 0.0), 0.0, (8.0, 1.6), heave_amp=2.0, pitch_amp=0.3,
+                                 omega=0.06))
+    g = oracle.grid_from_case(case)
+    u0 = synth.random_field(31, 2, (48, 32, 1), amp=0.05, offset=(1.0, 0.0))
+    u0[0][:, 0] = 1.0
+    u0[1][0, :] = 0.0
+    ue0 = np.ones(32)
+    P0 = np.zeros((32, 48))
+    dts = [0.25, 0.3, 0.3, 0.3]
+    w = (-1.0 / len(dts), 0.0)
+    J, du0, due0, grads = adjoint.window_gradient(case, u0, ue0, P0, 0.5, dts, w, ("heave_amp", "pitch_amp"))
+    assert np.isfinite(J) and J != 0.0
+    for name in ("heave_amp", "pitch_amp"):
+        fds = []
+        for h in (1e-4, 1e-5):
+            v = getattr(case.body, name)
+            Jp, _ = adjoint.window_forward(case, u0, ue0, P0, 0.5, dts, w, adjoint._with(case.body, name, v + h))
+            Jm, _ = adjoint.window_forward(case, u0, ue0, P0, 0.5, dts, w, adjoint._with(case.body, name, v - h))
+            fds.append((Jp - Jm) / (2 * h))
+        assert _close_to_one(grads[name], fds, 1e-5, 1e-8), (name, grads[name], fds)
+    # and the initial-velocity gradient along a random direction
+    v = RNG.normal(size=u0.shape)
+    v[0][:, 0] = 0.0
+    v[1][0, :] = 0.0
+    fds = []
+    for h in (1e-6, 1e-7):
+        Jp, _ = adjoint.window_forward(case, u0 + h * v, ue0, P0, 0.5, dts, w)
+        Jm, _ = adjoint.window_forward(case, u0 - h * v, ue0, P0, 0.5, dts, w)
+        fds.append((Jp - Jm) / (2 * h))
+    assert _close_to_one(_dot(du0, v), fds, 1e-5, 1e-9), (_dot(du0, v), fds)
