@@ -69,9 +69,9 @@ def algo_bytes(name, T, nd, has_body=False):
         "div": (nd + 2) * T,                          # u -> b (pair)
         "resid": (4 + 1 + 1 / 2 ** nd) * T,           # ph, pl, b, bl -> r, coarse r
         "restrict": (2 ** nd + 1) * T,                # per coarse cell
-        "pcg_init": (1 / 2 ** nd + 1 + 1 + 3) * T,    # xc, r, 1/D -> x, s, d
-        "pcg_d": 4 * T,                               # s, 1/D, d -> d
-        "pcg_q": 2 * T,                               # d -> q
+        "pcg_init": (1 / 2 ** nd + 1 + 1 + 2) * T,    # xc, r, 1/D -> x, s
+        "pcg_dq1": 3 * T,                             # s -> d, q (first iteration)
+        "pcg_dq": 4 * T,                              # s, d_old -> d, q
         "pcg_u": 7 * T,                               # x, d, s, q, 1/D -> x, s
         "pcg_u_last": 3 * T,                          # x, d -> x
         "pcg_u_last_fine": 6 * T,                     # x, d, ph, pl -> ph, pl
@@ -207,6 +207,8 @@ def main():
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-spinup", type=int, default=2000)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -337,6 +339,38 @@ def main():
                    "train": {"samples": 32, "adam_steps": 300, "batch": 4, "loss_first": loss0, "loss_last": loss1,
                              "seconds": t_train}}
 
+    # ---- adjoint of the flapping-foil window: heaving + pitching ellipse,
+    # 1024 x 512 FP32, spun up from rest, then the mean thrust over a 400-step
+    # window and its gradient with respect to the heave and pitch amplitudes
+    # (checkpoints every 20 steps; backward = recomputation + adjoint sweep)
+    adjoint = None
+    if not args.no_adjoint:
+        c4 = synth.config4_ellipse()
+        s4 = sim_from_case(c4, "f32", tol=1e-6, itmax=32)
+        u4, ue4 = synth.initial_velocity(c4)
+        s4.set_velocity(torch.tensor(u4, dtype=torch.float32, device="cuda"),
+                        torch.tensor(ue4, dtype=torch.float32, device="cuda"))
+        for _ in range(args.adjoint_spinup):
+            s4.mom_step(allow_unconverged=True)
+        nwin, ck = 400, 20
+        a0, a1, a2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        a0.record(s4.stream)
+        J, dts = s4.window_forward(nwin, ck, None, (-1.0 / nwin, 0.0, 0.0))
+        a1.record(s4.stream)
+        _, _, dp = s4.window_backward(1.0, tol=1e-6)
+        a2.record(s4.stream)
+        torch.cuda.synchronize()
+        tf, tb = a0.elapsed_time(a1) / 1000.0, a1.elapsed_time(a2) / 1000.0
+        adjoint = {"workload": f"ellipse2d {c4.n[0]}x{c4.n[1]} FP32, {args.adjoint_spinup}-step spin-up, "
+                               f"{nwin}-step window, checkpoints every {ck}",
+                   "objective": "mean thrust -(1/N) sum F_x", "J": J,
+                   "dJ_dheave_amp": float(dp[0]), "dJ_dpitch_amp": float(dp[1]),
+                   "forward_cell_steps_per_s": c4.ncell * nwin / tf,
+                   "backward_cell_steps_per_s": c4.ncell * nwin / tb,
+                   "backward_over_forward": tb / tf, "forward_s": tf, "backward_s": tb}
+        s4.close()
+
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -370,7 +404,7 @@ def main():
                "config": describe(case, prec) | {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                                                  "vcycles_per_step_mean": statistics.mean(vcyc)},
                "hbm_GBps_dominant_kernel": roof["achieved"] if roof else None,
-               "roofline": roof, "kernels": kernels[:10], "learned_guess": learned, "cpu_baseline": cpu, "e2e": e2e,
+               "roofline": roof, "kernels": kernels[:10], "learned_guess": learned, "adjoint": adjoint, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": l1 - l0, "clocks": clocks,
                "paper_context": {"ns_per_cell_step": 1.57, "cell_steps_per_s": 6.4e8,
                                  "hw": "NVIDIA H100, FP32, TGV 134M cells (Sec. 4.1)"}}

@@ -279,6 +279,39 @@ WL_API int wl_step_vjp(wl_sim *sim, double t, double dt, const void *u0, const v
  * g: nc doubles, host or device. */
 WL_API int wl_force_dp(wl_sim *sim, int axis, double scale, double *g);
 
+/* Gradient over a window of time steps, with checkpointed recomputation (no
+ * counterpart in the paper; its forward-mode dual numbers, Sec. 3 / Sec. 5.3,
+ * are replaced by the step's hand-written adjoint, wl_step_vjp). Objective:
+ *   J = sum_{n=1..nsteps} w . F_n  (+ <lu, u_N> + <le, ue_N> in the backward call)
+ * with F_n the pressure force of wl_forces after step n (mean thrust of a
+ * flapping foil: w = (-1/nsteps, 0, 0)).
+ *   wl_window_forward: runs nsteps steps from the current state with the time
+ *     steps dts (nsteps doubles; NULL = the adaptive CFL steps, which are then
+ *     held fixed for the gradient), storing a checkpoint of the state every
+ *     ckpt_every steps on the device (ceil(nsteps/ckpt_every) + ckpt_every + 1
+ *     states of velocity, exit plane and pressure). Returns J (may be NULL) and
+ *     the steps taken (dts_out, may be NULL). w: 3 doubles (NULL = 0).
+ *   wl_window_backward: the reverse sweep. Each segment is recomputed from its
+ *     checkpoint, then the steps are pulled back with wl_step_vjp's kernels,
+ *     the adjoint Poisson solves converged to `tol`. Inputs: gJ (the cotangent
+ *     of J), lu / le (cotangents of the final velocity and exit plane, may be
+ *     NULL = 0). Outputs (each may be NULL): du0, due0 (gradient with respect
+ *     to the window's start velocity and exit plane, layout of wl_set_velocity)
+ *     and dparams = (dJ/d heave_amp, dJ/d pitch_amp) of the body (host, 2
+ *     doubles), through the measured face fields, the Poisson coefficients and
+ *     the force's own dependence on the body. The sim is left in the state
+ *     after the window. Errors: WL_ERR_STATE (no forward window held),
+ *     WL_ERR_NONFINITE, WL_ERR_ARG, WL_ERR_CUDA; a forward step that fails
+ *     returns its status from wl_window_forward. */
+WL_API int wl_window_forward(wl_sim *sim, int nsteps, int ckpt_every, const double *dts, const double *w, double *J,
+                             double *dts_out);
+WL_API int wl_window_backward(wl_sim *sim, double gJ, const void *lu, const void *le, double tol, void *du0,
+                              void *due0, double *dparams);
+
+/* Replace the body's parameters (same kind; e.g. new heave / pitch amplitudes)
+ * and re-measure it at the time it was last measured. Drops a held window. */
+WL_API int wl_set_body(wl_sim *sim, const wl_body *body);
+
 /* Largest grid (cells) wl_coarse_solve_static accepts: its working memory is
  * a fixed device array of 5 * WL_STATIC_MAX_CELLS + 8 doubles (~640 KiB) that
  * every GPU loading this library holds until the process exits. */

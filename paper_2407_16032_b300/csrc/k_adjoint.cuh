@@ -304,12 +304,12 @@ __global__ void k_adj_exit(GridD g, const T *ein, T dt, T *ue0b, T *ueGb, T *uGx
     }
 }
 
-// Pressure derivative of the force on the body, component `axis`:
+// Pressure derivative of the weighted force w . F on the body:
 // F = -sum_I (p_I - mean) n(x_I) K_eps(d(x_I)) over active cells, so
-// dF/dp_I = -n_axis K on active cells of the kernel band (the mean's share is
-// removed by the adjoint solve, whose right-hand side is made mean-free).
+// d(w.F)/dp_I = -(w . n) K on active cells of the kernel band (the mean's share
+// is removed by the adjoint solve, whose right-hand side is made mean-free).
 template <typename T>
-__global__ void k_force_dp(GridD g, BodyState B, const T *invD, int axis, double scale, double *out) {
+__global__ void k_force_dp(GridD g, BodyState B, const T *invD, double w0, double w1, double w2, double *out) {
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nc;
          idx += (long long)gridDim.x * blockDim.x) {
         int i, j, k;
@@ -318,8 +318,232 @@ __global__ void k_force_dp(GridD g, BodyState B, const T *invD, int axis, double
         if (invD[idx] != T(0)) {
             double pd[3] = {i + 0.5, j + 0.5, k + 0.5}, dd, nd[3], vd[3];
             body_eval<double>(B, g.ndim, pd, dd, nd, vd);
-            v = -scale * nd[axis] * kkernel<double>(dd, B.eps);
+            v = -(w0 * nd[0] + w1 * nd[1] + w2 * nd[2]) * kkernel<double>(dd, B.eps);
         }
         out[idx] = v;
     }
+}
+
+// ------------------------------------------------ body-parameter tangents
+// Tangent of the body state with respect to one motion parameter: the heave
+// amplitude moves the centre by sin(omega t + phase) along the heave axis and
+// its velocity by omega cos(omega t + phase); the pitch amplitude moves the
+// angle by sin(omega t + phase + pi/2) and the rate by omega cos(...).
+struct BodyTangent {
+    double dc[3];      // centre
+    double dvc[3];     // centre velocity
+    double dth, dthd;  // pitch angle and rate
+};
+
+// Signed distance, normal and velocity at point x (double) and their tangents
+// along dB (same formulas as body_eval, differentiated by hand).
+__device__ __forceinline__ void body_tangent(const BodyState &B, const BodyTangent &dB, int ndim, const double (&x)[3],
+                                             double &d, double (&n)[3], double (&V)[3], double &dd,
+                                             double (&dn)[3], double (&dV)[3]) {
+    double rv[3], drv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        rv[a] = a < ndim ? (x[a] - B.chi[a]) - B.clo[a] : 0.0;
+        drv[a] = a < ndim ? -dB.dc[a] : 0.0;
+        n[a] = dn[a] = 0.0;
+        V[a] = B.vc[a];
+        dV[a] = dB.dvc[a];
+    }
+    d = 1e30;
+    dd = 0.0;
+    if (B.kind == 1) {
+        const double rr = sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
+        d = rr - B.radius;
+        if (rr > 0.0) {
+            double nd = 0.0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) { n[a] = rv[a] / rr; nd += n[a] * drv[a]; }
+            dd = nd;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) dn[a] = (drv[a] - n[a] * nd) / rr;
+        } else {
+            n[0] = 1.0;
+        }
+    } else if (B.kind == 2) {
+        const double ct = B.cth, st = B.sth, sa2 = B.sa * B.sa, sb2 = B.sb * B.sb;
+        const double xp = ct * rv[0] + st * rv[1], yp = -st * rv[0] + ct * rv[1];
+        const double dxp = ct * drv[0] + st * drv[1] + yp * dB.dth;
+        const double dyp = -st * drv[0] + ct * drv[1] - xp * dB.dth;
+        const double q = sqrt(xp * xp / sa2 + yp * yp / sb2);
+        const double gx = xp / sa2, gy = yp / sb2;
+        const double gn = sqrt(gx * gx + gy * gy);
+        if (gn > 0.0) {
+            const double dq = q > 0.0 ? (xp * dxp / sa2 + yp * dyp / sb2) / q : 0.0;
+            const double dgx = dxp / sa2, dgy = dyp / sb2;
+            const double dgn = (gx * dgx + gy * dgy) / gn;
+            d = (q - 1.0) * q / gn;
+            dd = ((2.0 * q - 1.0) * dq * gn - (q - 1.0) * q * dgn) / (gn * gn);
+            const double nx = gx / gn, ny = gy / gn;
+            const double dnx = (dgx * gn - gx * dgn) / (gn * gn), dny = (dgy * gn - gy * dgn) / (gn * gn);
+            n[0] = ct * nx - st * ny;
+            n[1] = st * nx + ct * ny;
+            dn[0] = ct * dnx - st * dny - dB.dth * n[1];
+            dn[1] = st * dnx + ct * dny + dB.dth * n[0];
+        } else {
+            d = -B.sb;
+            n[0] = 1.0;
+        }
+        V[0] += -B.thd * rv[1];
+        V[1] += B.thd * rv[0];
+        dV[0] += -dB.dthd * rv[1] - B.thd * drv[1];
+        dV[1] += dB.dthd * rv[0] + B.thd * drv[0];
+    }
+}
+
+// Face fields (mu0, mu1 n, V) of component a at stored face (i,j,k) and their
+// tangents along dB (double). mu0' = K, mu1' = -d K.
+struct FaceTan {
+    double mu0, m[3], V, dmu0, dm[3], dV;
+};
+__device__ __forceinline__ FaceTan face_tangent(const BodyState &B, const BodyTangent &dB, int ndim, int a, int i, int j,
+                                                int k) {
+    double x[3] = {i + 0.5, j + 0.5, k + 0.5};
+    x[a] -= 0.5;
+    double d, n[3], V[3], dd, dn[3], dV[3];
+    body_tangent(B, dB, ndim, x, d, n, V, dd, dn, dV);
+    FaceTan f;
+    const double K = kkernel<double>(d, B.eps);
+    const double m1 = kmu1<double>(d, B.eps);
+    f.mu0 = kmu0<double>(d, B.eps);
+    f.dmu0 = K * dd;
+    const double dm1 = -d * K * dd;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        f.m[b] = b < ndim ? m1 * n[b] : 0.0;
+        f.dm[b] = b < ndim ? dm1 * n[b] + m1 * dn[b] : 0.0;
+    }
+    f.V = V[a];
+    f.dV = dV[a];
+    return f;
+}
+
+// Tangent of the blended velocity along two parameter directions, contracted
+// with the blend's cotangent: acc[p] += sum_faces s gin * du/dtheta_p, with
+//   du = dV + dmu0 (f - V) - mu0 dV + sum_b [dm_b (f - V)(P_b) - (f - V)(M_b)) / 2
+//                                            - m_b (dV(P_b) - dV(M_b)) / 2]
+// (P_b / M_b the clamped / wrapped neighbours along b). Only faces of tiles
+// with non-uniform coefficients can carry a body term. Adds into out[0..1].
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_adj_param_blend(LevelD<T> L, CVec3P<T> gin, T s, CVec3P<T> f, CVec3P<T> Vf,
+                                                         BodyState B, BodyTangent dB0, BodyTangent dB1,
+                                                         DevScalars *S, double *part, double *out) {
+    const GridD &g = L.g;
+    double acc[2] = {0.0, 0.0};
+    for_cells<NDIM>(g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
+        if (uni) return;
+        const int J[3] = {i, j, k};
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            if (!g.per[a] && J[a] == 0) continue;
+            const double gv = (double)s * (double)gin.p[a][idx];
+            if (gv == 0.0) continue;
+            const FaceTan c0 = face_tangent(B, dB0, NDIM, a, i, j, k);
+            if (c0.mu0 >= 1.0 && c0.dmu0 == 0.0 && c0.m[0] == 0.0 && c0.m[1] == 0.0 && c0.m[2] == 0.0) continue;
+            const FaceTan c1 = face_tangent(B, dB1, NDIM, a, i, j, k);
+            const double fv = (double)f.p[a][idx] - (double)Vf.p[a][idx];
+            double du0 = c0.dV + c0.dmu0 * fv - c0.mu0 * c0.dV;
+            double du1 = c1.dV + c1.dmu0 * fv - c1.mu0 * c1.dV;
+#pragma unroll
+            for (int b = 0; b < NDIM; ++b) {
+                int P[3] = {i, j, k}, M[3] = {i, j, k};
+                P[b] += 1;
+                M[b] -= 1;
+#pragma unroll
+                for (int ax = 0; ax < NDIM; ++ax) {
+                    const int N = g.n[ax];
+                    if (g.per[ax]) { P[ax] = wrapi(P[ax], N); M[ax] = wrapi(M[ax], N); }
+                    else { P[ax] = P[ax] > N - 1 ? N - 1 : P[ax]; M[ax] = M[ax] < 0 ? 0 : M[ax]; }
+                }
+                const long long ip = lin3(g, P[0], P[1], P[2]), im = lin3(g, M[0], M[1], M[2]);
+                const double dfv = ((double)f.p[a][ip] - (double)Vf.p[a][ip]) - ((double)f.p[a][im] - (double)Vf.p[a][im]);
+                const FaceTan p0 = face_tangent(B, dB0, NDIM, a, P[0], P[1], P[2]);
+                const FaceTan m0 = face_tangent(B, dB0, NDIM, a, M[0], M[1], M[2]);
+                const FaceTan p1 = face_tangent(B, dB1, NDIM, a, P[0], P[1], P[2]);
+                const FaceTan m1 = face_tangent(B, dB1, NDIM, a, M[0], M[1], M[2]);
+                du0 += 0.5 * (c0.dm[b] * dfv - c0.m[b] * (p0.dV - m0.dV));
+                du1 += 0.5 * (c1.dm[b] * dfv - c1.m[b] * (p1.dV - m1.dV));
+            }
+            acc[0] += gv * du0;
+            acc[1] += gv * du1;
+        }
+    });
+    double red[2];
+    if (grid_reduce<2, false, double>(acc, part, &S->counters[RS_MISC], red))
+        if (threadIdx.x == 0 && threadIdx.y == 0) { out[0] += red[0]; out[1] += red[1]; }
+}
+
+// Coefficient part of the projection's parameter derivative: with the forward
+// pressure P of the projection (pair Ph + Pl), the adjoint solution q' (pair
+// qh + ql) and the cotangent lam of the projected velocity,
+//   dJ/dc_a[I] = w dt (P[I] - P[I-e_a]) ((q'[I] - q'[I-e_a]) - lam_a[I]),
+// contracted with dc = dmu0 on faces whose coefficient is mu0. Adds into out.
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_adj_param_coef(LevelD<T> L, const T *Ph, const T *Pl, const T *qh,
+                                                        const T *ql, CVec3P<T> lam, double wdt, BodyState B,
+                                                        BodyTangent dB0, BodyTangent dB1, DevScalars *S, double *part,
+                                                        double *out) {
+    const GridD &g = L.g;
+    double acc[2] = {0.0, 0.0};
+    for_cells<NDIM>(g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
+        if (uni) return;
+        long long ip[3], im[3];
+        T cp[3], cm[3];
+        nb_setup<T, NDIM>(L, false, i, j, k, idx, ip, im, cp, cm);
+        const int I[3] = {i, j, k};
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            if (!g.per[a] && I[a] == 0) continue;
+            const FaceTan t0 = face_tangent(B, dB0, NDIM, a, i, j, k);
+            const FaceTan t1 = face_tangent(B, dB1, NDIM, a, i, j, k);
+            if (t0.dmu0 == 0.0 && t1.dmu0 == 0.0) continue;
+            const double dP = ((double)Ph[idx] - (double)Ph[im[a]]) + ((double)Pl[idx] - (double)Pl[im[a]]);
+            const double dq = ((double)qh[idx] - (double)qh[im[a]]) + ((double)ql[idx] - (double)ql[im[a]]);
+            const double cb = wdt * dP * (dq - (double)lam.p[a][idx]);
+            acc[0] += cb * t0.dmu0;
+            acc[1] += cb * t1.dmu0;
+        }
+    });
+    double red[2];
+    if (grid_reduce<2, false, double>(acc, part, &S->counters[RS_MISC], red))
+        if (threadIdx.x == 0 && threadIdx.y == 0) { out[0] += red[0]; out[1] += red[1]; }
+}
+
+// Direct parameter derivative of the weighted force w.F at fixed pressure:
+// F = -sum_I (p_I - mean) n(x_I) K(d(x_I)) over active cells, so
+// d(w.F) = -sum_I (p_I - mean) sum_a w_a (dn_a K + n_a K' dd). Adds into out.
+template <typename T>
+__global__ void k_force_dparam(GridD g, BodyState B, BodyTangent dB0, BodyTangent dB1, const T *ph, const T *pl,
+                               const T *invD, double w0, double w1, double w2, DevScalars *S, double *part,
+                               double *out) {
+    const double pm = S->pmean;
+    const double w[3] = {w0, w1, w2};
+    double acc[2] = {0.0, 0.0};
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nc;
+         idx += (long long)gridDim.x * blockDim.x) {
+        if (invD[idx] == T(0)) continue;
+        int i, j, k;
+        decode(g, idx, i, j, k);
+        const double x[3] = {i + 0.5, j + 0.5, k + 0.5};
+        const double p = ((double)ph[idx] - pm) + (double)pl[idx];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            double d, n[3], V[3], dd, dn[3], dV[3];
+            body_tangent(B, q == 0 ? dB0 : dB1, g.ndim, x, d, n, V, dd, dn, dV);
+            const double r = d / B.eps;
+            if (!(r > -1.0 && r < 1.0)) continue;
+            const double K = kkernel<double>(d, B.eps);
+            const double Kp = -0.5 * 3.14159265358979323846 * sinpi(r) / (B.eps * B.eps);
+            double s = 0.0;
+            for (int a = 0; a < g.ndim; ++a) s += w[a] * (dn[a] * K + n[a] * Kp * dd);
+            acc[q] -= p * s;
+        }
+    }
+    double red[2];
+    if (grid_reduce<2, false, double>(acc, part, &S->counters[RS_MISC], red))
+        if (threadIdx.x == 0) { out[0] += red[0]; out[1] += red[1]; }
 }

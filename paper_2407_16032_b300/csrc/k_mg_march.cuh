@@ -73,75 +73,120 @@ __device__ __forceinline__ void for_tiles(const Tiles &tl, const unsigned char *
     }
 }
 
-// Search direction d = D^-1 s + beta d, in place (elementwise, 16-byte vectors).
-template <typename T>
-__global__ void __launch_bounds__(256) k_pcg_d(LevelD<T> L, DevScalars *S, int lev) {
-    typedef typename V16<T>::type VT;
-    constexpr int W = V16<T>::n;
-    const T beta = (T)S->beta[lev];
-    const long long n = L.g.nc;
-    const long long nv = (n % W == 0) ? n / W : 0;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    T *d = L.d[0];
-    for (long long v = t0; v < nv; v += stride) {
-        const VT s = ((const VT *)L.s)[v], iD = ((const VT *)L.invD)[v];
-        VT dv = ((VT *)d)[v];
-        T *de = (T *)&dv;
-        const T *se = (const T *)&s, *ie = (const T *)&iD;
-#pragma unroll
-        for (int e = 0; e < W; ++e) de[e] = ie[e] * se[e] + beta * de[e];
-        ((VT *)d)[v] = dv;
-    }
-    if (nv == 0)
-        for (long long e = t0; e < n; e += stride) d[e] = L.invD[e] * L.s[e] + beta * d[e];
-}
-
-// q = A d and alpha = rho / <d, q>. Each thread loads its whole column (the
-// TZ + 2 z values and the 4 TZ x/y neighbours) before computing, with
-// restrict-qualified pointers, so all of those loads are in flight at once.
-template <typename T, int NDIM>
-__global__ void __launch_bounds__(256) k_pcg_qm(LevelD<T> L, DevScalars *S, double *part, int lev) {
+// Search direction and operator in one pass (a PCG iteration's first half):
+//   d = D^-1 s + beta d_old   (d = D^-1 s on the first iteration),
+//   q = A d,   alpha = rho / <d, q>.
+// d_old and d are different buffers (dold, dnew): a tile's ring reads d_old of
+// the neighbouring tiles while they write their d. Each thread owns one
+// (x, y) column of a 32 x 8 x TZ tile and issues all its column's loads (s and
+// d_old over TZ + 2 planes) before forming d into a shared (TZ + 2) x 10 x 34
+// tile; the in-plane ring is formed by warps 0 and 7 (rows below / above the
+// tile) and 16 lanes of warp 1 (columns left / right), each loading its ring
+// cell over the TZ planes at once. After one barrier the operator is applied
+// from shared memory. Uniform tiles form 1/D and the coefficients from the
+// position.
+template <typename T, int NDIM, bool FIRST>
+__global__ void __launch_bounds__(256, 3) k_pcg_dq(LevelD<T> L, const T *__restrict__ dold, T *__restrict__ dnew,
+                                               DevScalars *S, double *part, int lev) {
     constexpr int TZ = MT<NDIM>::TZ;
+    constexpr int PZ = NDIM == 3 ? TZ + 2 : 1;   // planes held (with the z ring)
+    constexpr int Z0 = NDIM == 3 ? 1 : 0;        // smem plane of the tile's first plane
+    __shared__ T sd[PZ][10][34];
+    __shared__ T idtab[8];
     const GridD &g = L.g;
-    const T *__restrict__ d = L.d[0];
+    const T beta = FIRST ? T(0) : (T)S->beta[lev];
+    const T *__restrict__ s = L.s;
+    const T *__restrict__ iD = L.invD;
     T *__restrict__ q = L.q;
-    const int plane = g.n[0] * g.n[1];
-    const bool pz = g.per[2] != 0;
+    const int n0 = g.n[0], n1 = g.n[1], plane = g.n[0] * g.n[1];
+    const bool px = g.per[0] != 0, py = g.per[1] != 0, pz = g.per[2] != 0;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    // 1/D of a uniform-tile cell: -1 / (faces * cu), faces = 2n minus its
+    // non-periodic domain faces
+    if (tx < 8 && ty == 0) idtab[tx] = tx > 0 ? T(-1) / (T(tx) * L.cu) : T(0);
+    __syncthreads();
+    auto idu = [&](int ii, int jj, int kk) -> T {
+        const int I[3] = {ii, jj, kk};
+        int nf = 2 * NDIM;
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a)
+            if (!g.per[a]) nf -= (I[a] == 0) + (I[a] == g.n[a] - 1);
+        return idtab[nf];
+    };
     T acc[1] = {T(0)};
     for_tiles<NDIM>(L.tl, L.tflag, [&](int x0, int y0, int z0, bool uni) {
-        const Col c = column(g, x0, y0);
-        if (!c.in) return;
-        const int base = c.i + g.n[0] * c.j;
+        const int nx = min(32, n0 - x0), ny = min(8, n1 - y0);
         const int zb = NDIM == 3 ? z0 : 0, nz = NDIM == 3 ? min(TZ, g.n[2] - z0) : 1;
-        T vz[TZ + 2], xm[TZ], xp[TZ], ym[TZ], yp[TZ];
-#pragma unroll
-        for (int t = 0; t < TZ + 2; ++t) {
-            vz[t] = T(0);
-            if (NDIM == 3 && t <= nz + 1) vz[t] = d[base + plane * edge_idx(zb - 1 + t, g.n[2], pz)];
+        const int i = x0 + tx, j = y0 + ty;
+        const bool in = tx < nx && ty < ny;
+        // uniform tiles away from every non-periodic domain face take one 1/D
+        const bool plain = uni && (px || (x0 > 0 && x0 + nx < n0)) && (py || (y0 > 0 && y0 + ny < n1)) &&
+                           (NDIM == 2 || pz || (zb > 0 && zb + nz < g.n[2]));
+        const T idc = idtab[2 * NDIM];
+        auto dform = [&](int id, int ii, int jj, int kk, T sv, T dv) -> T {
+            const T iv = !uni ? iD[id] : (plain ? idc : idu(ii, jj, kk));
+            return FIRST ? iv * sv : iv * sv + beta * dv;
+        };
+        // this thread's ring cell (role 0: none, 1 below, 2 above, 3 left, 4 right)
+        int role = 0, ri = 0, rj = 0, sy = 0, sx = 0;
+        if (ty == 0 && tx < nx) { role = 1; ri = i; rj = edge_idx(y0 - 1, n1, py); sy = 0; sx = tx + 1; }
+        else if (ty == 7 && tx < nx) { role = 2; ri = i; rj = edge_idx(y0 + ny, n1, py); sy = ny + 1; sx = tx + 1; }
+        else if (ty == 1 && tx < 8 && tx < ny) { role = 3; ri = edge_idx(x0 - 1, n0, px); rj = y0 + tx; sy = tx + 1; sx = 0; }
+        else if (ty == 1 && tx >= 8 && tx < 16 && tx - 8 < ny) {
+            role = 4; ri = edge_idx(x0 + nx, n0, px); rj = y0 + tx - 8; sy = tx - 7; sx = nx + 1;
         }
+        __syncthreads();   // the previous tile's readers of sd are done
+        int kz[PZ];
 #pragma unroll
-        for (int t = 0; t < TZ; ++t)
-            if (t < nz) {
-                const int idx = base + plane * (zb + t);
-                if (NDIM == 2) vz[1] = d[idx];
-                xm[t] = d[idx + c.oxm];
-                xp[t] = d[idx + c.oxp];
-                ym[t] = d[idx + c.oym];
-                yp[t] = d[idx + c.oyp];
-            }
+        for (int t = 0; t < PZ; ++t) kz[t] = NDIM == 3 ? edge_idx(zb - 1 + t, g.n[2], pz) : 0;
+        T sv[PZ], dv[PZ], rs[TZ], rd[TZ];
+        // all loads of the column and of the ring cell first
+        if (in) {
 #pragma unroll
-        for (int t = 0; t < TZ; ++t)
-            if (t < nz) {
-                const int k = zb + t, idx = base + plane * k;
-                T cp[3], cm[3];
-                coefs<T, NDIM>(L, uni, c.i, c.j, k, idx, cp, cm);
-                const T vc = vz[t + 1];
-                T Ad = cp[0] * (xp[t] - vc) - cm[0] * (vc - xm[t]) + cp[1] * (yp[t] - vc) - cm[1] * (vc - ym[t]);
-                if (NDIM == 3) Ad += cp[2] * (vz[t + 2] - vc) - cm[2] * (vc - vz[t]);
-                q[idx] = Ad;
-                acc[0] += vc * Ad;
-            }
+            for (int t = 0; t < PZ; ++t)
+                if (t < nz + 2 * Z0) {
+                    const int id = i + n0 * j + plane * kz[t];
+                    sv[t] = s[id];
+                    dv[t] = FIRST ? T(0) : dold[id];
+                }
+        }
+        if (role) {
+#pragma unroll
+            for (int t = 0; t < TZ; ++t)
+                if (t < nz) {
+                    const int id = ri + n0 * rj + plane * kz[t + Z0];
+                    rs[t] = s[id];
+                    rd[t] = FIRST ? T(0) : dold[id];
+                }
+        }
+        if (in) {
+#pragma unroll
+            for (int t = 0; t < PZ; ++t)
+                if (t < nz + 2 * Z0)
+                    sd[t][ty + 1][tx + 1] = dform(i + n0 * j + plane * kz[t], i, j, kz[t], sv[t], dv[t]);
+        }
+        if (role) {
+#pragma unroll
+            for (int t = 0; t < TZ; ++t)
+                if (t < nz) sd[t + Z0][sy][sx] = dform(ri + n0 * rj + plane * kz[t + Z0], ri, rj, kz[t + Z0], rs[t], rd[t]);
+        }
+        __syncthreads();
+        if (in) {
+#pragma unroll
+            for (int t = 0; t < TZ; ++t)
+                if (t < nz) {
+                    const int k = zb + t, idx = i + n0 * j + plane * k;
+                    T cp[3], cm[3];
+                    coefs<T, NDIM>(L, uni, i, j, k, idx, cp, cm);
+                    const T dc = sd[t + Z0][ty + 1][tx + 1];
+                    T Ad = cp[0] * (sd[t + Z0][ty + 1][tx + 2] - dc) - cm[0] * (dc - sd[t + Z0][ty + 1][tx]) +
+                           cp[1] * (sd[t + Z0][ty + 2][tx + 1] - dc) - cm[1] * (dc - sd[t + Z0][ty][tx + 1]);
+                    if (NDIM == 3) Ad += cp[2] * (sd[t + 2 * Z0][ty + 1][tx + 1] - dc) - cm[2] * (dc - sd[t][ty + 1][tx + 1]);
+                    dnew[idx] = dc;
+                    q[idx] = Ad;
+                    acc[0] += dc * Ad;
+                }
+        }
     });
     double out[1];
     if (grid_reduce<1, false, T>(acc, part, &S->counters[RS_Q], out))
@@ -149,7 +194,7 @@ __global__ void __launch_bounds__(256) k_pcg_qm(LevelD<T> L, DevScalars *S, doub
 }
 
 // PCG start after the coarse correction: x = P x_c (injection), s = r - A x,
-// d = D^-1 s, rho = <s, d>.
+// rho = <s, D^-1 s> (the first search direction D^-1 s is formed by k_pcg_dq).
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(256) k_pcg_initm(LevelD<T> L, GridD gc, const T *xc, DevScalars *S, double *part,
                                                    int lev) {
@@ -199,10 +244,8 @@ __global__ void __launch_bounds__(256) k_pcg_initm(LevelD<T> L, GridD gc, const 
                 }
                 s = rv[t] - Ax;
             }
-            const T z = iD * s;
             L.s[idx] = s;
-            L.d[0][idx] = z;
-            acc[0] += s * z;
+            acc[0] += s * (iD * s);
         }
     });
     double out[1];

@@ -335,11 +335,10 @@ __device__ __forceinline__ void pcg_u_elem(T &x, T d, T &s, T q, T iD, T &ph, T 
 }
 
 template <typename T, bool LAST, bool FINE>
-__global__ void __launch_bounds__(256) k_pcg_u(LevelD<T> L, T *ph, T *pl, DevScalars *S, double *part, int lev,
-                                               int it) {
+__global__ void __launch_bounds__(256) k_pcg_u(LevelD<T> L, const T *dcur, T *ph, T *pl, DevScalars *S, double *part,
+                                               int lev, int it) {
     typedef typename V16<T>::type VT;
     constexpr int W = V16<T>::n;
-    const T *dcur = L.d[0];
     const T alpha = (T)S->alpha[lev];
     T acc[1] = {T(0)};
     const long long n = L.g.nc;

@@ -77,6 +77,10 @@ struct SimBase {
     virtual int step_vjp(double t0, double dt, const void *u0, const void *ue0, const double *P0, const void *lu,
                          const void *le, const double *lP, double tol, void *ub, void *ueb, wl_solve_stats *st) = 0;
     virtual void force_dp(int axis, double scale, double *g) = 0;
+    virtual int window_forward(int nsteps, int ckpt, const double *dts, const double *w, double *J, double *dts_out) = 0;
+    virtual int window_backward(double gJ, const void *lu, const void *le, double tol, void *du0, void *due0,
+                                double *dparams) = 0;
+    virtual void set_body(const wl_body *bd) = 0;
     double t = 0.0, dt_next = 0.25;
 };
 
@@ -170,12 +174,26 @@ struct Sim : SimBase {
     } gq;
     // adjoint of one step: forward copies, cotangents, and a backup of the state
     struct AdjState {
-        bool ready = false;
+        bool ready = false, pready = false;
         T *u0[3] = {}, *us[3] = {}, *lu[3] = {}, *x[3] = {}, *usb[3] = {}, *fb[3] = {}, *ub[3] = {}, *bku[3] = {};
         T *ue0 = nullptr, *ues = nullptr, *le = nullptr, *xe = nullptr, *uesb = nullptr, *ueb = nullptr, *bkue = nullptr;
         T *bkph = nullptr, *bkpl = nullptr;
         double *lP = nullptr;
+        // parameter mode: blend inputs and pressures of both stages, gradient
+        T *f1[3] = {}, *f2[3] = {}, *P1h = nullptr, *P1l = nullptr, *P2h = nullptr, *P2l = nullptr;
+        double *dpar = nullptr;
     } ad;
+    // checkpointed time window (forward run kept for the reverse sweep)
+    struct Snap { T *u[3]; T *ue; T *ph; T *pl; double t; };
+    struct Window {
+        bool active = false;
+        int n = 0, k = 0;
+        double w[3] = {0, 0, 0};
+        std::vector<double> dts, t0s;
+        std::vector<Snap> ck, seg;
+        Snap fin{};
+        double fin_dt_next = 0.0;
+    } win;
     Prof prof;
     void P0(const char *name, int level, long long cells) { prof.beg(st, name, level, cells); }
     void P1() { prof.end(st); }
@@ -414,20 +432,19 @@ struct Sim : SimBase {
             k_pcg_initm<T, ND><<<tgrid(l), tblk(), 0, s>>>(lv[l], gl[l + 1], lv[l + 1].x, S, part, l);
             E();
             for (int it = 0; it < k; ++it) {
-                if (it > 0) {
-                    B("pcg_d", l);
-                    k_pcg_d<T><<<blocks((gl[l].nc + 3) / 4), 256, 0, s>>>(lv[l], S, l);
-                    E();
-                }
-                B("pcg_q", l);
-                k_pcg_qm<T, ND><<<tgrid(l), tblk(), 0, s>>>(lv[l], S, part, l);
+                // d alternates between the two buffers (the next pass reads the
+                // previous direction of neighbouring tiles while writing its own)
+                T *dnew = lv[l].d[it & 1], *dold = lv[l].d[(it + 1) & 1];
+                B(it == 0 ? "pcg_dq1" : "pcg_dq", l);
+                if (it == 0) k_pcg_dq<T, ND, true><<<tgrid(l), tblk(), 0, s>>>(lv[l], dold, dnew, S, part, l);
+                else k_pcg_dq<T, ND, false><<<tgrid(l), tblk(), 0, s>>>(lv[l], dold, dnew, S, part, l);
                 E();
                 const bool last = it == k - 1;
                 B(last ? (l == 0 ? "pcg_u_last_fine" : "pcg_u_last") : "pcg_u", l);
                 const int vb = blocks((gl[l].nc + 3) / 4);
-                if (!last) k_pcg_u<T, false, false><<<vb, 256, 0, s>>>(lv[l], ph, pl, S, part, l, it);
-                else if (l > 0) k_pcg_u<T, true, false><<<vb, 256, 0, s>>>(lv[l], ph, pl, S, part, l, it);
-                else k_pcg_u<T, true, true><<<vb, 256, 0, s>>>(lv[l], ph, pl, S, part, l, it);
+                if (!last) k_pcg_u<T, false, false><<<vb, 256, 0, s>>>(lv[l], dnew, ph, pl, S, part, l, it);
+                else if (l > 0) k_pcg_u<T, true, false><<<vb, 256, 0, s>>>(lv[l], dnew, ph, pl, S, part, l, it);
+                else k_pcg_u<T, true, true><<<vb, 256, 0, s>>>(lv[l], dnew, ph, pl, S, part, l, it);
                 E();
             }
         }
@@ -987,8 +1004,16 @@ struct Sim : SimBase {
         ad.uesb = alloc_n<T>(np); ad.ueb = alloc_n<T>(np); ad.bkue = alloc_n<T>(np);
         ad.bkph = alloc_n<T>(nc); ad.bkpl = alloc_n<T>(nc);
         ad.lP = alloc_n<double>(nc);
+        ad.dpar = alloc_n<double>(2);
         if (!pout) pout = alloc_n<double>(nc);
         ad.ready = true;
+    }
+    void adj_alloc_params() {
+        adj_alloc();
+        if (ad.pready) return;
+        for (int a = 0; a < g.ndim; ++a) { ad.f1[a] = alloc_n<T>(g.nc); ad.f2[a] = alloc_n<T>(g.nc); }
+        ad.P1h = alloc_n<T>(g.nc); ad.P1l = alloc_n<T>(g.nc); ad.P2h = alloc_n<T>(g.nc); ad.P2l = alloc_n<T>(g.nc);
+        ad.pready = true;
     }
     static CVec3P<T> cvp(T *const (&p)[3]) { CVec3P<T> r{}; for (int a = 0; a < 3; ++a) r.p[a] = p[a]; return r; }
     static Vec3P<T> vvp(T *const (&p)[3]) { Vec3P<T> r{}; for (int a = 0; a < 3; ++a) r.p[a] = p[a]; return r; }
@@ -999,10 +1024,31 @@ struct Sim : SimBase {
         for (int a = 0; a < g.ndim; ++a)
             WL_CK(cudaMemcpyAsync(dst[a], src[a], g.nc * sizeof(T), cudaMemcpyDeviceToDevice, st));
     }
+    void dcopy(T *dst, const T *src, size_t n) {
+        WL_CK(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    }
+
+    // Tangents of the body state at time tt along the heave and pitch amplitudes.
+    void param_tangents(double tt, BodyTangent &h, BodyTangent &p) const {
+        std::memset(&h, 0, sizeof(h));
+        std::memset(&p, 0, sizeof(p));
+        const int ax = body.heave_axis;
+        if (ax >= 0 && ax < 3) {
+            h.dc[ax] = std::sin(body.omega * tt + body.phase);
+            h.dvc[ax] = body.omega * std::cos(body.omega * tt + body.phase);
+        }
+        if (body.kind == WL_BODY_ELLIPSE) {
+            p.dth = std::sin(body.omega * tt + body.phase + 0.5 * PI);
+            p.dthd = body.omega * std::cos(body.omega * tt + body.phase + 0.5 * PI);
+        }
+    }
 
     // Projection transposed: (out, oute) = (lam, le) + D^T A^+ (div(c lam) + lP/(w dt)).
+    // With the stage's forward pressure (Ph, Pl) and params, also the
+    // coefficient part of the parameter gradient.
     int proj_vjp(T *const (&lam)[3], const T *le, const double *lP, double w, double dt, T *const (&out)[3], T *oute,
-                 wl_solve_stats *sts) {
+                 wl_solve_stats *sts, const T *Ph = nullptr, const T *Pl = nullptr, const BodyTangent *dB = nullptr,
+                 double tt = 0.0) {
         P0("adj_rhs", 0, g.nc);
         k_adj_rhs<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], cvp(lam), lP, 1.0 / (w * dt), b, bl);
         P1();
@@ -1012,6 +1058,14 @@ struct Sim : SimBase {
         WL_LAUNCH_CK();
         launches += 2;
         const int rc = solve(sts);
+        if (Ph && dB) {
+            P0("adj_param_coef", 0, g.nc);
+            k_adj_param_coef<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], Ph, Pl, ph, pl, cvp(lam), w * dt,
+                                                                 body_state(tt), dB[0], dB[1], S, part, ad.dpar);
+            P1();
+            WL_LAUNCH_CK();
+            ++launches;
+        }
         pmean();
         P0("adj_grad", 0, g.nc);
         k_adj_grad<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], ph, pl, S, cvp(lam), le, vvp(out), oute);
@@ -1040,6 +1094,131 @@ struct Sim : SimBase {
         ++launches;
     }
 
+    void adj_param_blend(T *const (&gin)[3], double s, T *const (&f)[3], const BodyTangent *dB, double tt) {
+        CVec3P<T> V{};
+        for (int a = 0; a < 3; ++a) V.p[a] = Vb[a];
+        P0("adj_param_blend", 0, g.nc);
+        k_adj_param_blend<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], cvp(gin), (T)s, cvp(f), V, body_state(tt),
+                                                              dB[0], dB[1], S, part, ad.dpar);
+        P1();
+        WL_LAUNCH_CK();
+        ++launches;
+    }
+
+    // Core of the step's adjoint on device buffers. In: ad.u0 / ad.ue0 (start
+    // state), ph / pl (warm start), ad.lu / ad.le (cotangents of the step's
+    // velocity and exit plane), ad.lP when haveP (of its pressure). Out:
+    // ad.ub / ad.ueb. With params, the heave / pitch amplitude derivative of
+    // the step (and of wF . F of its pressure, wF may be null) is added into
+    // ad.dpar. Leaves the velocity slots, exit planes and ph / pl changed.
+    int vjp_core(double t0, double dt, bool haveP, double tol, bool params, const double *wF, wl_solve_stats *sts) {
+        const size_t pb = (size_t)np * sizeof(T);
+        const double t1 = t0 + dt;
+        const double tol0 = cfg.tol;
+        const bool gc = gq.collect, gu = gq.use;
+        gq.collect = gq.use = false;
+        cfg.tol = tol;
+        if (has_body && (moving || body_t != t1)) body_update(t1);
+        params = params && has_body;
+        BodyTangent dB[2];
+        if (params) { adj_alloc_params(); param_tangents(t1, dB[0], dB[1]); }
+        wl_solve_stats s[2] = {};
+        // forward predictor: u*, u_e* (and its blend input and pressure)
+        copy_vec(vel[cur], ad.u0);
+        if (g.exit_x) {
+            dcopy(ueA, ad.ue0, np);
+            dcopy(ueB, ad.ue0, np);
+        }
+        const int A0 = cur, B1 = (cur + 1) & 3, C2 = (cur + 2) & 3, D3 = (cur + 3) & 3;
+        int ustar;
+        if (!has_body) {
+            flux<FM_PRED_U>(fargs(A0, ueB, -1, B1, dt));
+            ustar = B1;
+        } else {
+            flux<FM_PRED_F>(fargs(A0, ueB, -1, B1, dt));
+            if (params) copy_vec(ad.f1, vel[B1]);
+            blend(false, B1, -1, C2);
+            ustar = C2;
+        }
+        exit_stage(false, A0, dt);
+        int r0 = project_buf(ustar, ueA, 1.0, dt, nullptr);
+        copy_vec(ad.us, vel[ustar]);
+        if (g.exit_x) dcopy(ad.ues, ueA, np);
+        int r0c = WL_OK;
+        if (params) {
+            // forward corrector: its blend input and pressure
+            dcopy(ad.P1h, ph, g.nc);
+            dcopy(ad.P1l, pl, g.nc);
+            flux<FM_CORR_F>(fargs(ustar, ueA, A0, B1, dt));
+            copy_vec(ad.f2, vel[B1]);
+            blend(true, B1, ustar, D3);
+            exit_stage(true, ustar, dt);
+            r0c = project_buf(D3, ueA, 0.5, dt, nullptr);
+            dcopy(ad.P2h, ph, g.nc);
+            dcopy(ad.P2l, pl, g.nc);
+            if (wF) {
+                // direct dependence of wF . F on the body at fixed pressure
+                pmean();
+                P0("force_dparam", 0, g.nc);
+                k_force_dparam<T><<<blocks(g.nc), 256, 0, st>>>(g, body_state(t1), dB[0], dB[1], ph, pl, lv[0].invD,
+                                                                wF[0], wF[1], wF[2], S, part, ad.dpar);
+                P1();
+                WL_LAUNCH_CK();
+                ++launches;
+            }
+        }
+        // reverse: corrector projection, exit, blend, flux at u*
+        int r1 = proj_vjp(ad.lu, g.exit_x ? ad.le : nullptr, haveP ? ad.lP : nullptr, 0.5, dt, ad.x, ad.xe, &s[1],
+                          params ? ad.P2h : nullptr, params ? ad.P2l : nullptr, params ? dB : nullptr, t1);
+        zero_vec(ad.ub);
+        zero_vec(ad.usb);
+        if (g.exit_x) {
+            WL_CK(cudaMemsetAsync(ad.ueb, 0, pb, st));
+            WL_CK(cudaMemsetAsync(ad.uesb, 0, pb, st));
+            k_adj_exit<T, true><<<1, 1024, 0, st>>>(g, ad.xe, (T)dt, ad.ueb, ad.uesb, ad.usb[0]);
+            WL_LAUNCH_CK();
+            ++launches;
+        }
+        if (params) adj_param_blend(ad.x, 0.5, ad.f2, dB, t1);
+        adj_blend(ad.x, 0.5, ad.usb, ad.ub, ad.fb, dt);
+        adj_flux(ad.us, ad.ues, ad.fb, ad.usb, ad.uesb);
+        // predictor projection, exit, blend, flux at u0
+        int r2 = proj_vjp(ad.usb, g.exit_x ? ad.uesb : nullptr, nullptr, 1.0, dt, ad.x, ad.xe, &s[0],
+                          params ? ad.P1h : nullptr, params ? ad.P1l : nullptr, params ? dB : nullptr, t1);
+        if (g.exit_x) {
+            k_adj_exit<T, false><<<1, 1024, 0, st>>>(g, ad.xe, (T)dt, ad.ueb, ad.ueb, ad.ub[0]);
+            WL_LAUNCH_CK();
+            ++launches;
+        }
+        if (params) adj_param_blend(ad.x, 1.0, ad.f1, dB, t1);
+        adj_blend(ad.x, 1.0, nullptr, ad.ub, ad.fb, dt);
+        adj_flux(ad.u0, ad.ue0, ad.fb, ad.ub, ad.ueb);
+        cfg.tol = tol0;
+        gq.collect = gc;
+        gq.use = gu;
+        if (sts) { sts[0] = s[0]; sts[1] = s[1]; }
+        int rc = WL_OK;
+        for (int r : {r0, r0c, r1, r2})
+            if (r != WL_OK && rc == WL_OK) rc = r;
+        if (rc == WL_ERR_NONFINITE) err = "non-finite values in the adjoint step";
+        else if (rc == WL_ERR_NOT_CONVERGED) err = "a Poisson solve of the adjoint step did not reach tol";
+        return rc;
+    }
+
+    void backup_state() {
+        copy_vec(ad.bku, vel[cur]);
+        dcopy(ad.bkue, ueA, np);
+        dcopy(ad.bkph, ph, g.nc);
+        dcopy(ad.bkpl, pl, g.nc);
+    }
+    void restore_state(double body_t0) {
+        copy_vec(vel[cur], ad.bku);
+        dcopy(ueA, ad.bkue, np);
+        dcopy(ph, ad.bkph, g.nc);
+        dcopy(pl, ad.bkpl, g.nc);
+        if (has_body && body_t != body_t0 && body_t0 >= 0) body_update(body_t0);
+    }
+
     // Vector-Jacobian product of one step (mom_step with a fixed dt, body
     // measured at t0 + dt) at the start state (u0, ue0), warm start P0: given
     // the cotangents (lu, le) of the step's velocity and exit plane and lP of
@@ -1050,16 +1229,8 @@ struct Sim : SimBase {
         if (!(dt > 0)) throw Err{WL_ERR_ARG, "step_vjp: dt must be positive"};
         adj_alloc();
         const size_t vb = g.nc * sizeof(T), pb = (size_t)np * sizeof(T);
-        // back up the state
-        copy_vec(ad.bku, vel[cur]);
-        WL_CK(cudaMemcpyAsync(ad.bkue, ueA, pb, cudaMemcpyDeviceToDevice, st));
-        WL_CK(cudaMemcpyAsync(ad.bkph, ph, vb, cudaMemcpyDeviceToDevice, st));
-        WL_CK(cudaMemcpyAsync(ad.bkpl, pl, vb, cudaMemcpyDeviceToDevice, st));
-        const double body_t0 = body_t, tol0 = cfg.tol;
-        const bool gc = gq.collect, gu = gq.use;
-        gq.collect = gq.use = false;
-        int rc = WL_OK;
-        // inputs
+        const double body_t0 = body_t;
+        backup_state();
         for (int a = 0; a < g.ndim; ++a) {
             WL_CK(cudaMemcpyAsync(ad.u0[a], (const char *)u0 + a * vb, vb, cudaMemcpyDefault, st));
             WL_CK(cudaMemcpyAsync(ad.lu[a], (const char *)lu + a * vb, vb, cudaMemcpyDefault, st));
@@ -1080,84 +1251,162 @@ struct Sim : SimBase {
             WL_CK(cudaMemsetAsync(ph, 0, vb, st));
             WL_CK(cudaMemsetAsync(pl, 0, vb, st));
         }
-        if (has_body && (moving || body_t != t0 + dt)) body_update(t0 + dt);
-        wl_solve_stats s[2] = {};
-        // forward predictor: u* and u_e*
-        copy_vec(vel[cur], ad.u0);
-        if (g.exit_x) {
-            WL_CK(cudaMemcpyAsync(ueA, ad.ue0, pb, cudaMemcpyDeviceToDevice, st));
-            WL_CK(cudaMemcpyAsync(ueB, ad.ue0, pb, cudaMemcpyDeviceToDevice, st));
-        }
-        const int A0 = cur, B1 = (cur + 1) & 3, C2 = (cur + 2) & 3;
-        int ustar;
-        if (!has_body) {
-            flux<FM_PRED_U>(fargs(A0, ueB, -1, B1, dt));
-            ustar = B1;
-        } else {
-            flux<FM_PRED_F>(fargs(A0, ueB, -1, B1, dt));
-            blend(false, B1, -1, C2);
-            ustar = C2;
-        }
-        exit_stage(false, A0, dt);
-        cfg.tol = tol;
-        int r0 = project_buf(ustar, ueA, 1.0, dt, nullptr);
-        copy_vec(ad.us, vel[ustar]);
-        if (g.exit_x) WL_CK(cudaMemcpyAsync(ad.ues, ueA, pb, cudaMemcpyDeviceToDevice, st));
-        // reverse: corrector projection, exit, blend, flux at u*
-        int r1 = proj_vjp(ad.lu, g.exit_x ? ad.le : nullptr, lP ? ad.lP : nullptr, 0.5, dt, ad.x, ad.xe, &s[1]);
-        zero_vec(ad.ub);
-        zero_vec(ad.usb);
-        if (g.exit_x) {
-            WL_CK(cudaMemsetAsync(ad.ueb, 0, pb, st));
-            WL_CK(cudaMemsetAsync(ad.uesb, 0, pb, st));
-            k_adj_exit<T, true><<<1, 1024, 0, st>>>(g, ad.xe, (T)dt, ad.ueb, ad.uesb, ad.usb[0]);
-            WL_LAUNCH_CK();
-            ++launches;
-        }
-        adj_blend(ad.x, 0.5, ad.usb, ad.ub, ad.fb, dt);
-        adj_flux(ad.us, ad.ues, ad.fb, ad.usb, ad.uesb);
-        // predictor projection, exit, blend, flux at u0
-        int r2 = proj_vjp(ad.usb, g.exit_x ? ad.uesb : nullptr, nullptr, 1.0, dt, ad.x, ad.xe, &s[0]);
-        if (g.exit_x) {
-            k_adj_exit<T, false><<<1, 1024, 0, st>>>(g, ad.xe, (T)dt, ad.ueb, ad.ueb, ad.ub[0]);
-            WL_LAUNCH_CK();
-            ++launches;
-        }
-        adj_blend(ad.x, 1.0, nullptr, ad.ub, ad.fb, dt);
-        adj_flux(ad.u0, ad.ue0, ad.fb, ad.ub, ad.ueb);
-        // outputs
+        const int rc = vjp_core(t0, dt, lP != nullptr, tol, false, nullptr, sts);
         for (int a = 0; a < g.ndim; ++a) WL_CK(cudaMemcpyAsync((char *)ub + a * vb, ad.ub[a], vb, cudaMemcpyDefault, st));
         if (ueb && g.exit_x) WL_CK(cudaMemcpyAsync(ueb, ad.ueb, pb, cudaMemcpyDefault, st));
-        // restore the state
-        cfg.tol = tol0;
-        gq.collect = gc;
-        gq.use = gu;
-        copy_vec(vel[cur], ad.bku);
-        WL_CK(cudaMemcpyAsync(ueA, ad.bkue, pb, cudaMemcpyDeviceToDevice, st));
-        WL_CK(cudaMemcpyAsync(ph, ad.bkph, vb, cudaMemcpyDeviceToDevice, st));
-        WL_CK(cudaMemcpyAsync(pl, ad.bkpl, vb, cudaMemcpyDeviceToDevice, st));
-        if (has_body && body_t != body_t0 && body_t0 >= 0) body_update(body_t0);
+        restore_state(body_t0);
         WL_CK(cudaStreamSynchronize(st));
         prof.flush();
-        if (sts) { sts[0] = s[0]; sts[1] = s[1]; }
-        for (int r : {r0, r1, r2})
-            if (r != WL_OK && rc == WL_OK) rc = r;
-        if (rc == WL_ERR_NONFINITE) err = "non-finite values in the adjoint step";
-        else if (rc == WL_ERR_NOT_CONVERGED) err = "a Poisson solve of the adjoint step did not reach tol";
         return rc;
+    }
+
+    // Weighted pressure derivative of the force into ad.lP: scale * sum_a w_a dF_a/dp.
+    void force_dp_w(double tt, const double *w, double scale) {
+        adj_alloc();
+        if (!has_body) {
+            WL_CK(cudaMemsetAsync(ad.lP, 0, g.nc * sizeof(double), st));
+            return;
+        }
+        k_force_dp<T><<<blocks(g.nc), 256, 0, st>>>(g, body_state(tt), lv[0].invD, w[0] * scale, w[1] * scale,
+                                                    w[2] * scale, ad.lP);
+        WL_LAUNCH_CK();
+        ++launches;
     }
 
     void force_dp(int axis, double scale, double *gout) override {
         if (axis < 0 || axis >= g.ndim) throw Err{WL_ERR_ARG, "force_dp: axis out of range"};
-        adj_alloc();
-        if (!has_body) {
-            WL_CK(cudaMemsetAsync(ad.lP, 0, g.nc * sizeof(double), st));
-        } else {
-            k_force_dp<T><<<blocks(g.nc), 256, 0, st>>>(g, body_state(body_t), lv[0].invD, axis, scale, ad.lP);
-            WL_LAUNCH_CK();
-            ++launches;
-        }
+        double w[3] = {0, 0, 0};
+        w[axis] = 1.0;
+        force_dp_w(body_t, w, scale);
         WL_CK(cudaMemcpyAsync(gout, ad.lP, g.nc * sizeof(double), cudaMemcpyDefault, st));
+        WL_CK(cudaStreamSynchronize(st));
+    }
+
+    // ------------------------------------------------- checkpointed window
+    Snap snap_alloc() {
+        Snap s{};
+        for (int a = 0; a < g.ndim; ++a) s.u[a] = alloc_n<T>(g.nc);
+        s.ue = alloc_n<T>(np);
+        s.ph = alloc_n<T>(g.nc);
+        s.pl = alloc_n<T>(g.nc);
+        return s;
+    }
+    void snap_take(Snap &s) {
+        copy_vec(s.u, vel[cur]);
+        dcopy(s.ue, ueA, np);
+        dcopy(s.ph, ph, g.nc);
+        dcopy(s.pl, pl, g.nc);
+        s.t = t;
+    }
+    void snap_put(const Snap &s) {
+        copy_vec(vel[cur], s.u);
+        dcopy(ueA, s.ue, np);
+        dcopy(ph, s.ph, g.nc);
+        dcopy(pl, s.pl, g.nc);
+        t = s.t;
+    }
+
+    int window_forward(int nsteps, int ckpt, const double *dts, const double *w, double *J, double *dts_out) override {
+        if (nsteps < 1 || ckpt < 1) throw Err{WL_ERR_ARG, "window: nsteps and ckpt_every must be >= 1"};
+        adj_alloc();
+        const int nck = (nsteps + ckpt - 1) / ckpt;
+        if ((int)win.ck.size() < nck) while ((int)win.ck.size() < nck) win.ck.push_back(snap_alloc());
+        if ((int)win.seg.size() < ckpt) while ((int)win.seg.size() < ckpt) win.seg.push_back(snap_alloc());
+        if (!win.fin.ue) win.fin = snap_alloc();
+        win.active = false;
+        win.n = nsteps;
+        win.k = ckpt;
+        for (int a = 0; a < 3; ++a) win.w[a] = w ? w[a] : 0.0;
+        win.dts.assign(nsteps, 0.0);
+        double Jv = 0.0;
+        for (int n = 0; n < nsteps; ++n) {
+            if (n % ckpt == 0) snap_take(win.ck[n / ckpt]);
+            const double dt = dts ? dts[n] : dt_next;
+            win.dts[n] = dt;
+            const int rc = mom_step(dt, nullptr);
+            if (rc != WL_OK) return rc;
+            if (w && has_body) {
+                double F[3];
+                forces(F);
+                Jv += w[0] * F[0] + w[1] * F[1] + w[2] * F[2];
+            }
+        }
+        snap_take(win.fin);
+        win.fin_dt_next = dt_next;
+        WL_CK(cudaStreamSynchronize(st));
+        if (J) *J = Jv;
+        if (dts_out) for (int n = 0; n < nsteps; ++n) dts_out[n] = win.dts[n];
+        win.active = true;
+        return WL_OK;
+    }
+
+    int window_backward(double gJ, const void *luf, const void *lef, double tol, void *du0, void *due0,
+                        double *dparams) override {
+        if (!win.active) throw Err{WL_ERR_STATE, "window_backward: no forward window is held"};
+        adj_alloc();
+        const size_t vb = g.nc * sizeof(T), pb = (size_t)np * sizeof(T);
+        const bool params = dparams != nullptr && has_body;
+        const bool force = has_body && (win.w[0] != 0 || win.w[1] != 0 || win.w[2] != 0) && gJ != 0.0;
+        double wF[3] = {gJ * win.w[0], gJ * win.w[1], gJ * win.w[2]};
+        // final cotangents
+        for (int a = 0; a < g.ndim; ++a) {
+            if (luf) WL_CK(cudaMemcpyAsync(ad.lu[a], (const char *)luf + a * vb, vb, cudaMemcpyDefault, st));
+            else WL_CK(cudaMemsetAsync(ad.lu[a], 0, vb, st));
+        }
+        if (g.exit_x) {
+            if (lef) WL_CK(cudaMemcpyAsync(ad.le, lef, pb, cudaMemcpyDefault, st));
+            else WL_CK(cudaMemsetAsync(ad.le, 0, pb, st));
+        }
+        WL_CK(cudaMemsetAsync(ad.dpar, 0, 2 * sizeof(double), st));
+        int rc = WL_OK;
+        const int nseg = (win.n + win.k - 1) / win.k;
+        for (int sgi = nseg - 1; sgi >= 0 && rc == WL_OK; --sgi) {
+            const int n0 = sgi * win.k, n1 = std::min(win.n, n0 + win.k);
+            // recompute the segment's start states from its checkpoint
+            snap_put(win.ck[sgi]);
+            for (int n = n0; n < n1; ++n) {
+                snap_take(win.seg[n - n0]);
+                if (n + 1 < n1) {
+                    const int r = mom_step(win.dts[n], nullptr);
+                    if (r != WL_OK && r != WL_ERR_NOT_CONVERGED) { rc = r; break; }
+                }
+            }
+            for (int n = n1 - 1; n >= n0 && rc == WL_OK; --n) {
+                const Snap &s = win.seg[n - n0];
+                const double dt = win.dts[n];
+                copy_vec(ad.u0, s.u);
+                dcopy(ad.ue0, s.ue, np);
+                dcopy(ph, s.ph, g.nc);
+                dcopy(pl, s.pl, g.nc);
+                if (has_body && (moving || body_t != s.t + dt)) body_update(s.t + dt);
+                if (force) force_dp_w(s.t + dt, win.w, gJ);
+                const int r = vjp_core(s.t, dt, force, tol, params, force ? wF : nullptr, nullptr);
+                if (r == WL_ERR_NONFINITE) rc = r;
+                for (int a = 0; a < 3; ++a) std::swap(ad.lu[a], ad.ub[a]);
+                std::swap(ad.le, ad.ueb);
+            }
+        }
+        if (rc == WL_OK) {
+            for (int a = 0; a < g.ndim; ++a)
+                if (du0) WL_CK(cudaMemcpyAsync((char *)du0 + a * vb, ad.lu[a], vb, cudaMemcpyDefault, st));
+            if (due0 && g.exit_x) WL_CK(cudaMemcpyAsync(due0, ad.le, pb, cudaMemcpyDefault, st));
+            if (dparams) WL_CK(cudaMemcpyAsync(dparams, ad.dpar, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        }
+        // back to the state after the window
+        snap_put(win.fin);
+        dt_next = win.fin_dt_next;
+        if (has_body && (moving || body_t != t)) body_update(t);
+        WL_CK(cudaStreamSynchronize(st));
+        prof.flush();
+        return rc;
+    }
+
+    void set_body(const wl_body *bd) override {
+        if (!bd || bd->kind != body.kind) throw Err{WL_ERR_ARG, "set_body: the body kind cannot change"};
+        body = *bd;
+        moving = has_body && (body.heave_amp != 0.0 || body.pitch_amp != 0.0);
+        win.active = false;
+        if (has_body) body_update(body_t >= 0 ? body_t : t);
         WL_CK(cudaStreamSynchronize(st));
     }
 
@@ -1424,6 +1673,18 @@ int wl_step_vjp(wl_sim *s, double t, double dt, const void *u0, const void *ue0,
                 const void *le, const double *lP, double tol, void *ub, void *ueb, wl_solve_stats *stats) {
     if (!u0 || !lu || !ub || !(tol > 0)) return WL_ERR_ARG;
     return guard(s, [&] { return s->impl->step_vjp(t, dt, u0, ue0, P0, lu, le, lP, tol, ub, ueb, stats); });
+}
+int wl_window_forward(wl_sim *s, int nsteps, int ckpt_every, const double *dts, const double *w, double *J,
+                      double *dts_out) {
+    return guard(s, [&] { return s->impl->window_forward(nsteps, ckpt_every, dts, w, J, dts_out); });
+}
+int wl_window_backward(wl_sim *s, double gJ, const void *lu, const void *le, double tol, void *du0, void *due0,
+                       double *dparams) {
+    if (!(tol > 0)) return WL_ERR_ARG;
+    return guard(s, [&] { return s->impl->window_backward(gJ, lu, le, tol, du0, due0, dparams); });
+}
+int wl_set_body(wl_sim *s, const wl_body *body) {
+    return guard(s, [&] { s->impl->set_body(body); return (int)WL_OK; });
 }
 int wl_force_dp(wl_sim *s, int axis, double scale, double *g) {
     if (!g) return WL_ERR_ARG;

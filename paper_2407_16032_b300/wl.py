@@ -27,7 +27,7 @@ EXPORTS = (
     "wl_poisson_solve", "wl_conv_diff", "wl_forces", "wl_body_update", "wl_get_body_fields",
     "wl_diagnostics", "wl_info", "wl_profile", "wl_profile_report", "wl_coarse_solve_static", "wl_guess_setup",
     "wl_guess_mode", "wl_guess_train", "wl_guess_weights", "wl_guess_info", "wl_net_eval", "wl_step_vjp",
-    "wl_force_dp", "wl_last_error", "wl_status_string",
+    "wl_force_dp", "wl_window_forward", "wl_window_backward", "wl_set_body", "wl_last_error", "wl_status_string",
 )
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t)
@@ -103,6 +103,9 @@ def lib() -> C.CDLL:
             "wl_step_vjp": ([vp, C.c_double, C.c_double, vp, vp, vp, vp, vp, vp, C.c_double, vp, vp,
                              C.POINTER(SolveStats)], ip),
             "wl_force_dp": ([vp, ip, C.c_double, vp], ip),
+            "wl_window_forward": ([vp, ip, ip, vp, vp, dp, vp], ip),
+            "wl_window_backward": ([vp, C.c_double, vp, vp, C.c_double, vp, vp, vp], ip),
+            "wl_set_body": ([vp, C.POINTER(Body)], ip),
             "wl_last_error": ([vp], C.c_char_p),
             "wl_status_string": ([ip], C.c_char_p),
         }
@@ -129,6 +132,20 @@ def _ptr(x) -> Optional[int]:
         return x.ctypes.data
     assert x.is_contiguous()
     return x.data_ptr()
+
+
+def _body_struct(body) -> Body:
+    """wl_body from a body description (kind, centre, radius, semi, heave_amp,
+    pitch_amp, omega, phase, heave_axis)."""
+    bd = Body()
+    bd.kind = BODY_KIND[body.kind]
+    for a in range(3):
+        bd.centre[a] = float(body.centre[a])
+    bd.radius = float(body.radius)
+    bd.semi[0], bd.semi[1] = float(body.semi[0]), float(body.semi[1])
+    bd.heave_amp, bd.pitch_amp = float(body.heave_amp), float(body.pitch_amp)
+    bd.omega, bd.phase, bd.heave_axis = float(body.omega), float(body.phase), int(body.heave_axis)
+    return bd
 
 
 @dataclass
@@ -189,20 +206,14 @@ class Sim:
             cfg.allocator.alloc, cfg.allocator.free = self._alloc_cb, self._free_cb
         bd = None
         if body is not None and getattr(body, "kind", "none") != "none":
-            bd = Body()
-            bd.kind = BODY_KIND[body.kind]
-            for a in range(3):
-                bd.centre[a] = float(body.centre[a])
-            bd.radius = float(body.radius)
-            bd.semi[0], bd.semi[1] = float(body.semi[0]), float(body.semi[1])
-            bd.heave_amp, bd.pitch_amp = float(body.heave_amp), float(body.pitch_amp)
-            bd.omega, bd.phase, bd.heave_axis = float(body.omega), float(body.phase), int(body.heave_axis)
+            bd = _body_struct(body)
         self._h = C.c_void_p()
         with torch.cuda.device(self.device):
             rc = L.wl_sim_create(C.byref(cfg), C.byref(bd) if bd is not None else None, C.byref(self._h))
         if rc != WL_OK:
             raise WLError(rc, "wl_sim_create failed: " + L.wl_status_string(rc).decode())
         self.cfg = cfg
+        self.body = body
 
     # -------------------------------------------------------------- plumbing
     def _check(self, rc, what, ok=(WL_OK,)):
@@ -361,6 +372,30 @@ class Sim:
         out = self.torch.zeros(self._shape(), dtype=self.torch.float64, device=self.device) if out is None else out
         self._check(lib().wl_force_dp(self._h, int(axis), float(scale), _ptr(out)), "wl_force_dp")
         return out
+
+    def window_forward(self, nsteps, ckpt_every=20, dts=None, w=(0.0, 0.0, 0.0)):
+        """wl_window_forward: returns (J, dts taken)."""
+        J = C.c_double()
+        out = np.zeros(int(nsteps))
+        d = None if dts is None else np.ascontiguousarray(dts, dtype=np.float64)
+        ww = np.ascontiguousarray((list(w) + [0.0, 0.0, 0.0])[:3], dtype=np.float64)
+        self._check(lib().wl_window_forward(self._h, int(nsteps), int(ckpt_every), _ptr(d), _ptr(ww), C.byref(J),
+                                            _ptr(out)), "wl_window_forward")
+        return J.value, out
+
+    def window_backward(self, gJ=1.0, lu=None, le=None, tol=1e-7, params=True):
+        """wl_window_backward: returns (du0, due0, dparams or None)."""
+        du0 = self.new_velocity()
+        due0 = self.new_plane() if self.exit else None
+        dp = np.zeros(2) if params else None
+        self._check(lib().wl_window_backward(self._h, float(gJ), _ptr(lu), _ptr(le), float(tol), _ptr(du0),
+                                             _ptr(due0), _ptr(dp)), "wl_window_backward")
+        return du0, due0, dp
+
+    def set_body(self, body):
+        """wl_set_body with a body description (kind unchanged)."""
+        self._check(lib().wl_set_body(self._h, C.byref(_body_struct(body))), "wl_set_body")
+        self.body = body
 
     def info(self):
         lv, nl = C.c_int(), C.c_longlong()
