@@ -51,7 +51,7 @@ def describe(case, prec):
             "cells": case.ncell, "nu": case.nu, "body": case.body.kind,
             "bc": "periodic" if all(case.periodic[:case.ndim]) else "inflow/slip/convective-exit",
             "precision": prec, "poisson_tol": 1e-6, "smoother": "PCG x4 per level, V(0,4)",
-            "guess": "warm start (previous pressure)",
+            "guess": "warm start (previous pressure); learned guess in learned_guess",
             "l2": "inputs larger than L2 (velocity alone > 126 MB)" if case.ncell * 12 > 126e6 else "small"}
 
 
@@ -294,31 +294,39 @@ def main():
                 "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": src,
                 "algorithmic_bytes_per_launch": int(bpl), "traffic": traffic_for(nm)}
 
-    # ---- learned Poisson guess vs plain multigrid on the same workload: the
-    # network is set up, fed by the solver's own converged projections,
-    # trained on the GPU, then the same number of steps is timed with it on
+    # ---- learned Poisson guess vs plain multigrid on the same workload. Both
+    # learned parts are fitted on the solver's own converged projections: the
+    # temporal guess (a 1x1x1 convolution over each stage's pressure history,
+    # least squares in the residual norm) and the coarse-level CNN (Adam on
+    # the GPU). Arms from the same state, each timed over the same steps after
+    # three untimed steps (the temporal guess needs two steps of history).
     learned = None
     if not args.no_learned:
-        lev = 2
-        sim.guess_setup(level=lev, capacity=64)
+        sim.tguess_mode(collect=True, use=False)
+        sim.guess_setup(level=2, capacity=64)
         sim.guess_mode(collect=True)
         for _ in range(16):
             sim.mom_step()
         sim.guess_mode(collect=False)
+        sim.tguess_mode(collect=False, use=False)
+        tw, tratio = sim.tguess_fit()
         t0 = time.perf_counter()
         loss0, loss1 = sim.guess_train(iters=300, lr=2e-3, batch=4, seed=0)
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
-        res = {}
-        su, _ = sim.get_velocity()
+        su, sue = sim.get_velocity()
         sp = sim.get_pressure()
         tt, dtt = sim.get_time()
-        for use in (False, True):
-            sim.set_velocity(su)
+        arms = {"plain": (False, False), "temporal": (True, False), "temporal+cnn": (True, True)}
+        res = {}
+        for name, (tgu, cnn) in arms.items():
+            sim.set_velocity(su, sue)
             sim.set_pressure(sp)
             sim.set_time(tt, dtt)
-            sim.guess_mode(use=use)
-            sim.mom_step()
+            sim.tguess_mode(collect=False, use=tgu)
+            sim.guess_mode(use=cnn)
+            for _ in range(3):
+                sim.mom_step()
             torch.cuda.synchronize()
             a, bq = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             vc, r0 = [], []
@@ -329,15 +337,18 @@ def main():
                 r0.append(0.5 * (st.proj[0].rel_initial + st.proj[1].rel_initial))
             bq.record(stream)
             torch.cuda.synchronize()
-            res[use] = (case.ncell * args.steps / (a.elapsed_time(bq) / 1000.0), statistics.mean(vc), statistics.mean(r0))
+            res[name] = {"value": case.ncell * args.steps / (a.elapsed_time(bq) / 1000.0),
+                         "vcycles_per_step": statistics.mean(vc), "initial_rel_residual": statistics.mean(r0)}
         sim.guess_mode(use=False)
-        learned = {"value": res[True][0], "plain_mg_value": res[False][0], "unit": UNIT,
-                   "speedup": res[True][0] / res[False][0],
-                   "vcycles_per_step": {"plain": res[False][1], "learned": res[True][1]},
-                   "initial_rel_residual": {"plain": res[False][2], "learned": res[True][2]},
-                   "net": "bias-free ReLU 3D CNN 1-16-16-1, 3^3 kernels, BF16 mma.sync, on MG level 2",
-                   "train": {"samples": 32, "adam_steps": 300, "batch": 4, "loss_first": loss0, "loss_last": loss1,
-                             "seconds": t_train}}
+        sim.tguess_mode(collect=False, use=False)
+        learned = {"value": res["temporal"]["value"], "plain_mg_value": res["plain"]["value"], "unit": UNIT,
+                   "speedup": res["temporal"]["value"] / res["plain"]["value"], "arms": res,
+                   "temporal": {"net": "1x1x1 conv over (H1, H1 - H2, Ho - H1) per projection stage",
+                                "weights": {"predictor": tw[0].tolist(), "corrector": tw[1].tolist()},
+                                "fit_residual_ratio": tratio.tolist(), "projections_fitted": 30},
+                   "cnn": {"net": "bias-free ReLU 3D CNN 1-16-16-1, 3^3 kernels, BF16 mma.sync, on MG level 2",
+                           "train": {"samples": 32, "adam_steps": 300, "batch": 4, "loss_first": loss0,
+                                     "loss_last": loss1, "seconds": t_train}}}
 
     # ---- adjoint of the flapping-foil window: heaving + pitching ellipse,
     # 1024 x 512 FP32, spun up from rest, then the mean thrust over a 400-step

@@ -243,6 +243,28 @@ WL_API int wl_guess_train(wl_sim *sim, int iters, double lr, int batch, unsigned
 WL_API int wl_guess_weights(wl_sim *sim, const float *in, float *out);
 WL_API int wl_guess_info(wl_sim *sim, int *level, int *samples, double *gain);
 
+/* Learned temporal guess (no counterpart in the paper): a 1x1x1 convolution
+ * over the pressure history of each projection stage (predictor, corrector),
+ *   guess = H1 + w1 (H1 - H2) + w2 (Ho - H1),
+ * H1, H2 the stage's last two converged pressures, Ho the other stage's latest
+ * (w = (0, 1) is the plain warm start from the previous projection). It
+ * replaces the warm start of each wl_mom_step projection once two steps of
+ * history exist; the V-cycles then converge to the same tolerance (plain
+ * multigrid stays the judge of the error). When both learned guesses are on,
+ * this one is applied first and the network's coarse correction after it.
+ *   wl_tguess_mode: collect != 0 gathers, at every converged projection, the
+ *     normal equations of the weights' least-squares fit in the residual norm
+ *     |A (P - guess)| (entering collection clears them); use != 0 applies
+ *     the weights. The history restarts after wl_set_velocity/_pressure.
+ *   wl_tguess_fit: fits (w1, w2) per stage from the gathered equations; w:
+ *     4 doubles (predictor w1, w2, corrector w1, w2), ratio: 2 doubles, the
+ *     fitted guess's residual norm over the plain warm start's on the
+ *     collected projections (either may be NULL).
+ *   wl_tguess_weights: set (in) and / or get (out) the 4 weights (host). */
+WL_API int wl_tguess_mode(wl_sim *sim, int collect, int use);
+WL_API int wl_tguess_fit(wl_sim *sim, double *w, double *ratio);
+WL_API int wl_tguess_weights(wl_sim *sim, const double *in, double *out);
+
 /* One forward and backward pass of the guess network on a single sample (for
  * checking the kernels): grid ndim, n[3]; weights w (3 x 27 x 16 x 16 floats);
  * input x and target t (n[0]*n[1]*n[2] floats, t may be NULL for forward

@@ -85,9 +85,9 @@ __device__ __forceinline__ void for_tiles(const Tiles &tl, const unsigned char *
 // cell over the TZ planes at once. After one barrier the operator is applied
 // from shared memory. Uniform tiles form 1/D and the coefficients from the
 // position.
-template <typename T, int NDIM, bool FIRST>
-__global__ void __launch_bounds__(256, 3) k_pcg_dq(LevelD<T> L, const T *__restrict__ dold, T *__restrict__ dnew,
-                                               DevScalars *S, double *part, int lev) {
+template <typename T, int NDIM>
+__device__ __forceinline__ void pcg_dq_run(const LevelD<T> &L, const T *__restrict__ dold, T *__restrict__ dnew,
+                                           DevScalars *S, double *part, int lev, const bool FIRST) {
     constexpr int TZ = MT<NDIM>::TZ;
     constexpr int PZ = NDIM == 3 ? TZ + 2 : 1;   // planes held (with the z ring)
     constexpr int Z0 = NDIM == 3 ? 1 : 0;        // smem plane of the tile's first plane
@@ -192,12 +192,17 @@ __global__ void __launch_bounds__(256, 3) k_pcg_dq(LevelD<T> L, const T *__restr
     if (grid_reduce<1, false, T>(acc, part, &S->counters[RS_Q], out))
         if (threadIdx.x == 0 && threadIdx.y == 0) S->alpha[lev] = out[0] != 0.0 ? S->rho[lev] / out[0] : 0.0;
 }
+template <typename T, int NDIM, bool FIRST>
+__global__ void __launch_bounds__(256, 3) k_pcg_dq(LevelD<T> L, const T *dold, T *dnew,
+                                                   DevScalars *S, double *part, int lev) {
+    pcg_dq_run<T, NDIM>(L, dold, dnew, S, part, lev, FIRST);
+}
 
 // PCG start after the coarse correction: x = P x_c (injection), s = r - A x,
 // rho = <s, D^-1 s> (the first search direction D^-1 s is formed by k_pcg_dq).
 template <typename T, int NDIM>
-__global__ void __launch_bounds__(256) k_pcg_initm(LevelD<T> L, GridD gc, const T *xc, DevScalars *S, double *part,
-                                                   int lev) {
+__device__ __forceinline__ void pcg_init_run(const LevelD<T> &L, const GridD &gc, const T *xc, DevScalars *S,
+                                             double *part, int lev) {
     const GridD &g = L.g;
     T acc[1] = {T(0)};
     for_tiles<NDIM>(L.tl, L.tflag, [&](int x0, int y0, int z0, bool uni) {
@@ -251,6 +256,11 @@ __global__ void __launch_bounds__(256) k_pcg_initm(LevelD<T> L, GridD gc, const 
     double out[1];
     if (grid_reduce<1, false, T>(acc, part, &S->counters[RS_INIT], out))
         if (threadIdx.x == 0 && threadIdx.y == 0) S->rho[lev] = out[0];
+}
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_pcg_initm(LevelD<T> L, GridD gc, const T *xc, DevScalars *S, double *part,
+                                                   int lev) {
+    pcg_init_run<T, NDIM>(L, gc, xc, S, part, lev);
 }
 
 // Refinement residual r = (b - mean) - A (ph + pl), compensated (exact

@@ -13,6 +13,7 @@
 #pragma once
 #include <cuda_bf16.h>
 #include "wl_common.cuh"
+#include "k_poisson.cuh"
 
 #define NET_C 16
 #define NET_TAPS 27
@@ -319,4 +320,76 @@ __global__ void k_scale_ch0(int V, float s, float *Y) {
 }
 __global__ void k_channel0(int V, const float *__restrict__ Y, float *y) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) y[v] = Y[v * NET_C];
+}
+
+// ------------------------------------------------- learned temporal guess
+// A 1x1x1 convolution over the pressure history of the same projection stage:
+//   guess = H1 + w1 (H1 - H2) + w2 (Ho - H1)
+// with H1, H2 the stage's last two converged pressures and Ho the other
+// stage's latest (w = (0, 1) is the plain warm start). The weights are fitted
+// to the solver's own projections by least squares in the residual norm
+// (k_tguess_stats gathers the 2x2 normal equations). Pressures are (hi, lo)
+// pairs; the differences are small next to the values and taken in T.
+template <typename T>
+__global__ void k_tguess_apply(long long n, const T *H1h, const T *H1l, const T *H2h, const T *H2l, const T *Hoh,
+                               const T *Hol, T w1, T w2, T *ph, T *pl) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const T b = H1h[i], bl = H1l[i];
+        const T D1 = (b - H2h[i]) + (bl - H2l[i]);
+        const T D2 = (Hoh[i] - b) + (Hol[i] - bl);
+        const T c = w1 * D1 + w2 * D2;
+        T s, e;
+        two_sum(b, c, s, e);
+        const T lo = bl + e;
+        const T hi = s + lo;
+        ph[i] = hi;
+        pl[i] = lo - (hi - s);
+    }
+}
+
+// Normal equations of the fit, for one converged projection P: with
+// d = P - H1, D1 = H1 - H2, D2 = Ho - H1, accumulates
+//   (A D1)^2, (A D1)(A D2), (A D2)^2, (A D1)(A d), (A D2)(A d), (A d)^2
+// over active rows into out[0..5] (the initial residual of the guess is
+// A (d - w1 D1 - w2 D2), up to the mean removal).
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_tguess_stats(LevelD<T> L, const T *Ph, const T *Pl, const T *H1h,
+                                                      const T *H1l, const T *H2h, const T *H2l, const T *Hoh,
+                                                      const T *Hol, DevScalars *S, double *part, double *out) {
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    auto diffs = [&](long long id, double &d, double &D1, double &D2) {
+        const double b = (double)H1h[id] + (double)H1l[id];
+        d = ((double)Ph[id] + (double)Pl[id]) - b;
+        D1 = b - ((double)H2h[id] + (double)H2l[id]);
+        D2 = ((double)Hoh[id] + (double)Hol[id]) - b;
+    };
+    for_cells<NDIM>(L.g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
+        if (!uni && L.invD[idx] == T(0)) return;
+        long long ip[3], im[3];
+        T cp[3], cm[3];
+        nb_setup<T, NDIM>(L, uni, i, j, k, idx, ip, im, cp, cm);
+        double d0, a0, b0;
+        diffs(idx, d0, a0, b0);
+        double Ad = 0, A1 = 0, A2 = 0;
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            double dp, ap, bp, dm, am, bm;
+            diffs(ip[a], dp, ap, bp);
+            diffs(im[a], dm, am, bm);
+            const double c1 = (double)cp[a], c0 = (double)cm[a];
+            Ad += c1 * (dp - d0) - c0 * (d0 - dm);
+            A1 += c1 * (ap - a0) - c0 * (a0 - am);
+            A2 += c1 * (bp - b0) - c0 * (b0 - bm);
+        }
+        acc[0] += A1 * A1;
+        acc[1] += A1 * A2;
+        acc[2] += A2 * A2;
+        acc[3] += A1 * Ad;
+        acc[4] += A2 * Ad;
+        acc[5] += Ad * Ad;
+    });
+    double red[6];
+    if (grid_reduce<6, false, double>(acc, part, &S->counters[RS_MISC], red))
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            for (int q = 0; q < 6; ++q) out[q] += red[q];
 }

@@ -200,6 +200,10 @@ __global__ void __launch_bounds__(256) k_div(LevelD<T> L, CVec3P<T> u, const T *
                                              DevScalars *S, double *part) {
     const GridD &g = L.g;
     T acc[2] = {T(0), T(0)};
+    // distinct arrays: the loads of all planes of a column may be issued together
+    const T *__restrict__ ux = u.p[0], *__restrict__ uy = u.p[1], *__restrict__ uz = u.p[2];
+    const T *__restrict__ uep = ue;
+    T *__restrict__ bo = b, *__restrict__ blo = bl;
     for_cells<NDIM>(g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
         const int I[3] = {i, j, k};
         const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
@@ -208,12 +212,13 @@ __global__ void __launch_bounds__(256) k_div(LevelD<T> L, CVec3P<T> u, const T *
         T sh = T(0), sl = T(0);
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {
+            const T *__restrict__ ua = a == 0 ? ux : (a == 1 ? uy : uz);
             T up;
-            if (I[a] + 1 < g.n[a]) up = u.p[a][idx + st[a]];
-            else if (g.per[a]) up = u.p[a][idx - (long long)(g.n[a] - 1) * st[a]];
-            else up = (a == 0 && g.exit_x) ? ue[j + (long long)g.n[1] * k] : (T)g.U[a];
+            if (I[a] + 1 < g.n[a]) up = ua[idx + st[a]];
+            else if (g.per[a]) up = ua[idx - (long long)(g.n[a] - 1) * st[a]];
+            else up = (a == 0 && g.exit_x) ? uep[j + (long long)g.n[1] * k] : (T)g.U[a];
             T d, de, s2, e2;
-            two_sum(up, -u.p[a][idx], d, de);
+            two_sum(up, -ua[idx], d, de);
             two_sum(sh, d, s2, e2);
             sh = s2;
             sl += e2 + de;
@@ -221,10 +226,10 @@ __global__ void __launch_bounds__(256) k_div(LevelD<T> L, CVec3P<T> u, const T *
         T h = sh + sl;
         T l = sl - (h - sh);
         const T bh = h * inv_wdt;
-        const T blo = fma(h, inv_wdt, -bh) + l * inv_wdt;
-        const T s = bh + blo;
-        b[idx] = s;
-        bl[idx] = blo - (s - bh);
+        const T blo_ = fma(h, inv_wdt, -bh) + l * inv_wdt;
+        const T s = bh + blo_;
+        bo[idx] = s;
+        blo[idx] = blo_ - (s - bh);
         if (uni || L.invD[idx] != T(0)) { acc[0] += s; acc[1] += s * s; }
     });
     double out[2];
@@ -285,7 +290,7 @@ __device__ __forceinline__ void face_term(T hN, T lN, T h0, T l0, T c, T &th, T 
 
 // Restriction: coarse r = sum of the 2^n fine children.
 template <typename T, int NDIM>
-__global__ void __launch_bounds__(256) k_restrict(GridD gf, const T *rf, LevelD<T> C) {
+__device__ __forceinline__ void restrict_run(const GridD &gf, const T *rf, const LevelD<T> &C) {
     for_cells<NDIM>(C.g, C.tl, nullptr, [&](int i, int j, int k, long long idx, bool) {
         T s = T(0);
         for (int oz = 0; oz < (NDIM == 3 ? 2 : 1); ++oz)
@@ -295,6 +300,10 @@ __global__ void __launch_bounds__(256) k_restrict(GridD gf, const T *rf, LevelD<
             }
         C.r[idx] = s;
     });
+}
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_restrict(GridD gf, const T *rf, LevelD<T> C) {
+    restrict_run<T, NDIM>(gf, rf, C);
 }
 
 // Parent (injection) index of the fine cell (i,j,k) offset by o along axis a,
@@ -335,16 +344,18 @@ __device__ __forceinline__ void pcg_u_elem(T &x, T d, T &s, T q, T iD, T &ph, T 
 }
 
 template <typename T, bool LAST, bool FINE>
-__global__ void __launch_bounds__(256) k_pcg_u(LevelD<T> L, const T *dcur, T *ph, T *pl, DevScalars *S, double *part,
-                                               int lev, int it) {
+__device__ __forceinline__ void pcg_u_run(const LevelD<T> &L, const T *dcur, T *ph, T *pl, DevScalars *S,
+                                          double *part, int lev) {
     typedef typename V16<T>::type VT;
     constexpr int W = V16<T>::n;
     const T alpha = (T)S->alpha[lev];
     T acc[1] = {T(0)};
     const long long n = L.g.nc;
     const long long nv = (n % W == 0) ? n / W : 0;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int nthr = blockDim.x * blockDim.y;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const long long stride = (long long)gridDim.x * nthr;
+    const long long t0 = blockIdx.x * (long long)nthr + tid;
     for (long long v = t0; v < nv; v += stride) {
         VT x = ((VT *)L.x)[v], d = ((const VT *)dcur)[v], s = ((VT *)L.s)[v], q = ((const VT *)L.q)[v];
         VT iD = ((const VT *)L.invD)[v];
@@ -367,12 +378,18 @@ __global__ void __launch_bounds__(256) k_pcg_u(LevelD<T> L, const T *dcur, T *ph
     if (!LAST) {
         double out[1];
         if (grid_reduce<1, false, T>(acc, part, &S->counters[RS_U], out))
-            if (threadIdx.x == 0) {
+            if (tid == 0) {
                 const double rho = S->rho[lev];
                 S->beta[lev] = rho != 0.0 ? out[0] / rho : 0.0;
                 S->rho[lev] = out[0];
             }
     }
+}
+
+template <typename T, bool LAST, bool FINE>
+__global__ void __launch_bounds__(256) k_pcg_u(LevelD<T> L, const T *dcur, T *ph, T *pl, DevScalars *S, double *part,
+                                               int lev, int it) {
+    pcg_u_run<T, LAST, FINE>(L, dcur, ph, pl, S, part, lev);
 }
 
 // Single-level case: the coarse solve itself is the fine correction.
@@ -393,12 +410,12 @@ __global__ void k_padd(GridD g, const T *x, T *ph, T *pl) {
 // of the right-hand side over active rows, to 1e-12 relative or maxit; the
 // mean-free solution is written to L.x. w: 4*nc doubles of scratch.
 template <typename T>
-__global__ void k_coarsest(LevelD<T> L, double *w, int maxit) {
+__device__ __forceinline__ void coarsest_run(const LevelD<T> &L, double *w, int maxit) {
     const GridD &g = L.g;
     const long long n = g.nc;
     double *xs = w, *ss = w + n, *ds = w + 2 * n, *qs = w + 3 * n;
     __shared__ double sh[64];
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
     const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
     double v1[1], o1[1];
     double sr = 0.0, na = 0.0;
@@ -486,11 +503,17 @@ __global__ void k_coarsest(LevelD<T> L, double *w, int maxit) {
     const double xm = nact > 0 ? sh[40] / nact : 0.0;
     for (long long e = tid; e < n; e += nt) L.x[e] = L.invD[e] != T(0) ? (T)(xs[e] - xm) : T(0);
 }
+template <typename T>
+__global__ void k_coarsest(LevelD<T> L, double *w, int maxit) {
+    coarsest_run<T>(L, w, maxit);
+}
 
 // ------------------------------------------------------------- projection
 // Pressure-gradient update (Sec. 3 listing): u_a[I] -= w dt c_a[I] (p[I] - p[I-e_a]).
 template <typename T, int NDIM>
-__global__ void __launch_bounds__(256) k_grad(LevelD<T> L, const T *ph, const T *pl, T wdt, Vec3P<T> u) {
+__global__ void __launch_bounds__(256) k_grad(LevelD<T> L, const T *__restrict__ ph, const T *__restrict__ pl, T wdt,
+                                              Vec3P<T> u) {
+    T *__restrict__ ux = u.p[0], *__restrict__ uy = u.p[1], *__restrict__ uz = u.p[2];
     for_cells<NDIM>(L.g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
         long long ip[3], im[3];
         T cp[3], cm[3];
@@ -499,8 +522,9 @@ __global__ void __launch_bounds__(256) k_grad(LevelD<T> L, const T *ph, const T 
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {
             if (cm[a] == T(0)) continue;
+            T *__restrict__ ua = a == 0 ? ux : (a == 1 ? uy : uz);
             const T dp = (h0 - ph[im[a]]) + (l0 - pl[im[a]]);
-            u.p[a][idx] -= wdt * cm[a] * dp;
+            ua[idx] -= wdt * cm[a] * dp;
         }
     });
 }

@@ -81,6 +81,9 @@ struct SimBase {
     virtual int window_backward(double gJ, const void *lu, const void *le, double tol, void *du0, void *due0,
                                 double *dparams) = 0;
     virtual void set_body(const wl_body *bd) = 0;
+    virtual void tguess_mode(int collect, int use) = 0;
+    virtual void tguess_fit(double *w, double *ratio) = 0;
+    virtual void tguess_weights(const double *in, double *out) = 0;
     double t = 0.0, dt_next = 0.25;
 };
 
@@ -183,6 +186,16 @@ struct Sim : SimBase {
         T *f1[3] = {}, *f2[3] = {}, *P1h = nullptr, *P1l = nullptr, *P2h = nullptr, *P2l = nullptr;
         double *dpar = nullptr;
     } ad;
+    // learned temporal guess: per projection stage (0 predictor, 1 corrector)
+    // its last two converged pressures (hi, lo), the fitted weights and the
+    // gathered normal equations
+    struct TGuess {
+        bool collect = false, use = false, ready = false;
+        T *H[2][2][2] = {};       // [stage][age][hi / lo]
+        int count[2] = {0, 0};
+        double w[2][2] = {{0.0, 1.0}, {0.0, 1.0}};
+        double *stats = nullptr;  // 2 x 6 doubles on the device
+    } tg;
     // checkpointed time window (forward run kept for the reverse sweep)
     struct Snap { T *u[3]; T *ue; T *ph; T *pl; double t; };
     struct Window {
@@ -309,6 +322,7 @@ struct Sim : SimBase {
             L.cu = (T)std::pow(2.0, (double)l * (ND - 2));
         }
         cw = alloc_n<double>(4 * gl[nlev - 1].nc);
+
         // initial state: u = 0 with U on boundary normal faces, exit plane U_x
         t = 0.0;
         dt_next = c.dt_init;
@@ -508,13 +522,16 @@ struct Sim : SimBase {
         return WL_OK;
     }
 
-    int project_buf(int q, const T *ue, double w, double dt, wl_solve_stats *sts) {
+    int project_buf(int q, const T *ue, double w, double dt, wl_solve_stats *sts, int stage = -1) {
         P0("div", 0, g.nc);
         k_div<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], cv(q), ue, (T)(1.0 / (w * dt)), b, bl, S, part);
         P1();
         WL_LAUNCH_CK();
         ++launches;
+        const bool tgs = stage >= 0 && tg.ready;
+        if (tgs && tg.use && tg.count[stage] >= 2 && tg.count[1 - stage] >= 1) tguess_apply(stage);
         int rc = solve(sts);
+        if (tgs && rc == WL_OK) tguess_push(stage);
         P0("grad", 0, g.nc);
         k_grad<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], ph, pl, (T)(w * dt), vv(q));
         P1();
@@ -522,6 +539,92 @@ struct Sim : SimBase {
         ++launches;
         return rc;
     }
+
+    // ---------------------------------------------- learned temporal guess
+    void tguess_alloc() {
+        if (tg.ready) return;
+        for (int sg = 0; sg < 2; ++sg)
+            for (int a = 0; a < 2; ++a)
+                for (int h = 0; h < 2; ++h) tg.H[sg][a][h] = alloc_n<T>(g.nc);
+        tg.stats = alloc_n<double>(12);
+        tg.ready = true;
+    }
+    void tguess_apply(int sg) {
+        const int o = 1 - sg;
+        P0("tguess_apply", 0, g.nc);
+        k_tguess_apply<T><<<blocks(g.nc), 256, 0, st>>>(g.nc, tg.H[sg][0][0], tg.H[sg][0][1], tg.H[sg][1][0],
+                                                        tg.H[sg][1][1], tg.H[o][0][0], tg.H[o][0][1],
+                                                        (T)tg.w[sg][0], (T)tg.w[sg][1], ph, pl);
+        P1();
+        WL_LAUNCH_CK();
+        ++launches;
+        // the first residual is of the guess
+        P0("resid", 0, g.nc);
+        resid_launch(st);
+        P1();
+        WL_LAUNCH_CK();
+        ++launches;
+    }
+    // after a converged projection of stage sg: gather the fit's normal
+    // equations (collecting) and push the solution into the stage's history
+    void tguess_push(int sg) {
+        const int o = 1 - sg;
+        if (tg.collect && tg.count[sg] >= 2 && tg.count[o] >= 1) {
+            k_tguess_stats<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], ph, pl, tg.H[sg][0][0], tg.H[sg][0][1],
+                                                               tg.H[sg][1][0], tg.H[sg][1][1], tg.H[o][0][0],
+                                                               tg.H[o][0][1], S, part, tg.stats + 6 * sg);
+            WL_LAUNCH_CK();
+            ++launches;
+        }
+        std::swap(tg.H[sg][0][0], tg.H[sg][1][0]);
+        std::swap(tg.H[sg][0][1], tg.H[sg][1][1]);
+        WL_CK(cudaMemcpyAsync(tg.H[sg][0][0], ph, g.nc * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        WL_CK(cudaMemcpyAsync(tg.H[sg][0][1], pl, g.nc * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        if (tg.count[sg] < 2) ++tg.count[sg];
+    }
+    void tguess_mode(int collect, int use) override {
+        tguess_alloc();
+        if (collect && !tg.collect) WL_CK(cudaMemsetAsync(tg.stats, 0, 12 * sizeof(double), st));
+        tg.collect = collect != 0;
+        tg.use = use != 0;
+        WL_CK(cudaStreamSynchronize(st));
+    }
+    // least-squares weights per stage from the gathered normal equations;
+    // ratio[sg]: predicted initial-residual norm of the fitted guess over the
+    // plain warm start's on the collected projections
+    void tguess_fit(double *w, double *ratio) override {
+        tguess_alloc();
+        double h[12];
+        WL_CK(cudaMemcpyAsync(h, tg.stats, sizeof(h), cudaMemcpyDeviceToHost, st));
+        WL_CK(cudaStreamSynchronize(st));
+        for (int sg = 0; sg < 2; ++sg) {
+            const double *m = h + 6 * sg;
+            const double G11 = m[0], G12 = m[1], G22 = m[2], c1 = m[3], c2 = m[4], dd = m[5];
+            const double ridge = 1e-12 * (G11 + G22);
+            const double a = G11 + ridge, d = G22 + ridge, det = a * d - G12 * G12;
+            double w1 = 0.0, w2 = 1.0;
+            if (det > 0 && G11 > 0 && G22 > 0) {
+                w1 = (d * c1 - G12 * c2) / det;
+                w2 = (a * c2 - G12 * c1) / det;
+            }
+            tg.w[sg][0] = w1;
+            tg.w[sg][1] = w2;
+            auto loss = [&](double x1, double x2) {
+                return dd - 2 * (x1 * c1 + x2 * c2) + x1 * x1 * G11 + 2 * x1 * x2 * G12 + x2 * x2 * G22;
+            };
+            const double lp = loss(0.0, 1.0), lf = loss(w1, w2);
+            if (w) { w[2 * sg] = w1; w[2 * sg + 1] = w2; }
+            if (ratio) ratio[sg] = lp > 0 ? std::sqrt(std::max(lf, 0.0) / lp) : 1.0;
+        }
+    }
+    void tguess_weights(const double *in, double *out) override {
+        tguess_alloc();
+        for (int q = 0; q < 4; ++q) {
+            if (in) tg.w[q / 2][q % 2] = in[q];
+            if (out) out[q] = tg.w[q / 2][q % 2];
+        }
+    }
+    void tguess_reset() { tg.count[0] = tg.count[1] = 0; }
 
     // ------------------------------------------------------------ stages
     template <int NDIM, int MODE>
@@ -611,7 +714,7 @@ struct Sim : SimBase {
             ustar = C2;
         }
         exit_stage(false, A0, dt);
-        rc0 = project_buf(ustar, ueA, 1.0, dt, &s0);
+        rc0 = project_buf(ustar, ueA, 1.0, dt, &s0, 0);
         if (rc0 == WL_ERR_NONFINITE) return fail_restore(rc0, "non-finite values in the predictor projection");
         if (!has_body) {
             flux<FM_CORR_U>(fargs(ustar, ueA, A0, C2, dt));
@@ -622,7 +725,7 @@ struct Sim : SimBase {
             unew = D3;
         }
         exit_stage(true, ustar, dt);
-        rc1 = project_buf(unew, ueA, 0.5, dt, &s1);
+        rc1 = project_buf(unew, ueA, 0.5, dt, &s1, 1);
         if (rc1 == WL_ERR_NONFINITE) return fail_restore(rc1, "non-finite values in the corrector projection");
         // CFL for the next step
         P0("cfl", 0, g.nc);
@@ -688,6 +791,7 @@ struct Sim : SimBase {
     }
 
     void set_velocity(const void *u, const void *ue) override {
+        tguess_reset();
         const size_t bytes = g.nc * sizeof(T);
         for (int a = 0; a < g.ndim; ++a) WL_CK(cudaMemcpyAsync(vel[cur][a], (const char *)u + a * bytes, bytes, cudaMemcpyDefault, st));
         fill_boundary(cur);
@@ -719,6 +823,7 @@ struct Sim : SimBase {
     }
 
     void set_pressure(const double *p) override {
+        tguess_reset();
         if (!pout) pout = alloc_n<double>(g.nc);
         WL_CK(cudaMemcpyAsync(pout, p, g.nc * sizeof(double), cudaMemcpyDefault, st));
         k_pin<T><<<blocks(g.nc), 256, 0, st>>>(g, pout, ph, pl);
@@ -1314,6 +1419,12 @@ struct Sim : SimBase {
         if ((int)win.seg.size() < ckpt) while ((int)win.seg.size() < ckpt) win.seg.push_back(snap_alloc());
         if (!win.fin.ue) win.fin = snap_alloc();
         win.active = false;
+        // the learned guesses change the converged fields only within the
+        // solver tolerance, but the backward sweep's recomputation must repeat
+        // this forward run exactly: both stay off over the window
+        const bool tgu = tg.use, gqu = gq.use;
+        tg.use = gq.use = false;
+        struct Restore { bool &a, &b; bool va, vb; ~Restore() { a = va; b = vb; } } rs{tg.use, gq.use, tgu, gqu};
         win.n = nsteps;
         win.k = ckpt;
         for (int a = 0; a < 3; ++a) win.w[a] = w ? w[a] : 0.0;
@@ -1358,6 +1469,9 @@ struct Sim : SimBase {
             else WL_CK(cudaMemsetAsync(ad.le, 0, pb, st));
         }
         WL_CK(cudaMemsetAsync(ad.dpar, 0, 2 * sizeof(double), st));
+        const bool tgu = tg.use, gqu = gq.use;
+        tg.use = gq.use = false;
+        struct Restore { bool &a, &b; bool va, vb; ~Restore() { a = va; b = vb; } } rs{tg.use, gq.use, tgu, gqu};
         int rc = WL_OK;
         const int nseg = (win.n + win.k - 1) / win.k;
         for (int sgi = nseg - 1; sgi >= 0 && rc == WL_OK; --sgi) {
@@ -1682,6 +1796,15 @@ int wl_window_backward(wl_sim *s, double gJ, const void *lu, const void *le, dou
                        double *dparams) {
     if (!(tol > 0)) return WL_ERR_ARG;
     return guard(s, [&] { return s->impl->window_backward(gJ, lu, le, tol, du0, due0, dparams); });
+}
+int wl_tguess_mode(wl_sim *s, int collect, int use) {
+    return guard(s, [&] { s->impl->tguess_mode(collect, use); return (int)WL_OK; });
+}
+int wl_tguess_fit(wl_sim *s, double *w, double *ratio) {
+    return guard(s, [&] { s->impl->tguess_fit(w, ratio); return (int)WL_OK; });
+}
+int wl_tguess_weights(wl_sim *s, const double *in, double *out) {
+    return guard(s, [&] { s->impl->tguess_weights(in, out); return (int)WL_OK; });
 }
 int wl_set_body(wl_sim *s, const wl_body *body) {
     return guard(s, [&] { s->impl->set_body(body); return (int)WL_OK; });

@@ -27,7 +27,8 @@ EXPORTS = (
     "wl_poisson_solve", "wl_conv_diff", "wl_forces", "wl_body_update", "wl_get_body_fields",
     "wl_diagnostics", "wl_info", "wl_profile", "wl_profile_report", "wl_coarse_solve_static", "wl_guess_setup",
     "wl_guess_mode", "wl_guess_train", "wl_guess_weights", "wl_guess_info", "wl_net_eval", "wl_step_vjp",
-    "wl_force_dp", "wl_window_forward", "wl_window_backward", "wl_set_body", "wl_last_error", "wl_status_string",
+    "wl_force_dp", "wl_window_forward", "wl_window_backward", "wl_set_body", "wl_tguess_mode", "wl_tguess_fit",
+    "wl_tguess_weights", "wl_last_error", "wl_status_string",
 )
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t)
@@ -106,6 +107,9 @@ def lib() -> C.CDLL:
             "wl_window_forward": ([vp, ip, ip, vp, vp, dp, vp], ip),
             "wl_window_backward": ([vp, C.c_double, vp, vp, C.c_double, vp, vp, vp], ip),
             "wl_set_body": ([vp, C.POINTER(Body)], ip),
+            "wl_tguess_mode": ([vp, ip, ip], ip),
+            "wl_tguess_fit": ([vp, vp, vp], ip),
+            "wl_tguess_weights": ([vp, vp, vp], ip),
             "wl_last_error": ([vp], C.c_char_p),
             "wl_status_string": ([ip], C.c_char_p),
         }
@@ -396,6 +400,22 @@ class Sim:
         """wl_set_body with a body description (kind unchanged)."""
         self._check(lib().wl_set_body(self._h, C.byref(_body_struct(body))), "wl_set_body")
         self.body = body
+
+    # ------------------------------------------------ learned temporal guess
+    def tguess_mode(self, collect=False, use=False):
+        self._check(lib().wl_tguess_mode(self._h, int(bool(collect)), int(bool(use))), "wl_tguess_mode")
+
+    def tguess_fit(self):
+        """Returns (weights (2, 2): [stage][w1, w2], residual ratio per stage)."""
+        w, r = np.zeros(4), np.zeros(2)
+        self._check(lib().wl_tguess_fit(self._h, _ptr(w), _ptr(r)), "wl_tguess_fit")
+        return w.reshape(2, 2), r
+
+    def tguess_weights(self, set_to=None):
+        out = np.zeros(4)
+        src = None if set_to is None else np.ascontiguousarray(set_to, dtype=np.float64).ravel()
+        self._check(lib().wl_tguess_weights(self._h, _ptr(src), _ptr(out)), "wl_tguess_weights")
+        return out.reshape(2, 2)
 
     def info(self):
         lv, nl = C.c_int(), C.c_longlong()
