@@ -86,34 +86,53 @@ __global__ void __launch_bounds__(FluxTile<NDIM>::NT) k_flux(GridD g, FluxArgs<T
         const int by = (int)((t / ntx) % nty);
         const int bz = (int)(t / ((long long)ntx * nty));
         const int x0 = bx * TL::TX, y0 = by * TL::TY, z0 = bz * TL::TZ;
-        const bool interior = x0 >= TL::H && x0 + TL::TX + TL::H <= n0 && y0 >= TL::H &&
-                              y0 + TL::TY + TL::H <= n1 &&
-                              (NDIM == 2 || (z0 >= TL::H && z0 + TL::TZ + TL::H <= n2));
         __syncthreads();  // previous tile's readers are done
-        // stage the tile: every global load of a component is issued before
-        // its shared-memory stores, so they are all in flight together
-        constexpr int NL = (TL::SN + TL::NT - 1) / TL::NT;
+        // stage the tile row by row (a row: SX samples along x): the threads
+        // of one x-row of the block take a staged row each, lanes 0..2H-1 also
+        // its last 2H samples. Indices wrap on periodic axes (a shift of at
+        // most H); samples beyond a non-periodic domain edge take the
+        // boundary rule of vel_sample. Every load of a component is issued
+        // before its shared-memory stores.
+        constexpr int NROW = TL::SY * TL::SZ;
+        constexpr int RPI = TL::TY * TL::TZ;            // rows staged per pass
+        constexpr int NPASS = (NROW + RPI - 1) / RPI;
+        const int r0 = ty + TL::TY * tz;
+        auto wrap = [](int v, int N) { return v < 0 ? v + N : (v >= N ? v - N : v); };
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {
             const T *__restrict__ ua = A.u[a];
             T *sa = s + a * TL::SN;
-            T v[NL];
+            T v[NPASS][2];
 #pragma unroll
-            for (int q = 0; q < NL; ++q) {
-                const int e = tid + q * TL::NT;
-                if (e < TL::SN) {
-                    const int lx = e % TL::SX;
-                    const int ly = (e / TL::SX) % TL::SY;
-                    const int lz = e / (TL::SX * TL::SY);
-                    const int gx = x0 + lx - TL::H, gy = y0 + ly - TL::H;
-                    const int gz = NDIM == 3 ? z0 + lz - TL::H : 0;
-                    v[q] = interior ? ua[gx + n0 * (gy + n1 * gz)] : vel_sample<T>(g, ua, A.ue, a, gx, gy, gz);
+            for (int q = 0; q < NPASS; ++q) {
+                const int rr = r0 + q * RPI;
+                if (rr < NROW) {
+                    const int ly = rr % TL::SY, lz = rr / TL::SY;
+                    int gy = y0 + ly - TL::H;
+                    int gz = NDIM == 3 ? z0 + lz - TL::H : 0;
+                    bool ok = true;
+                    if (gy < 0 || gy >= n1) { if (g.per[1]) gy = wrap(gy, n1); else ok = false; }
+                    if (NDIM == 3 && (gz < 0 || gz >= n2)) { if (g.per[2]) gz = wrap(gz, n2); else ok = false; }
+                    const long long rowb = (long long)n0 * (gy + (long long)n1 * gz);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int lx = h == 0 ? tx : TL::TX + tx;
+                        if (h == 1 && tx >= 2 * TL::H) continue;
+                        int gx = x0 + lx - TL::H;
+                        bool okx = ok;
+                        if (gx < 0 || gx >= n0) { if (g.per[0]) gx = wrap(gx, n0); else okx = false; }
+                        const int gyr = y0 + ly - TL::H, gzr = NDIM == 3 ? z0 + lz - TL::H : 0;
+                        v[q][h] = okx ? ua[gx + rowb] : vel_sample<T>(g, ua, A.ue, a, x0 + lx - TL::H, gyr, gzr);
+                    }
                 }
             }
 #pragma unroll
-            for (int q = 0; q < NL; ++q) {
-                const int e = tid + q * TL::NT;
-                if (e < TL::SN) sa[e] = v[q];
+            for (int q = 0; q < NPASS; ++q) {
+                const int rr = r0 + q * RPI;
+                if (rr < NROW) {
+                    sa[rr * TL::SX + tx] = v[q][0];
+                    if (tx < 2 * TL::H) sa[rr * TL::SX + TL::TX + tx] = v[q][1];
+                }
             }
         }
         __syncthreads();

@@ -63,15 +63,6 @@ __device__ __forceinline__ void coefs(const LevelD<T> &L, bool uni, int i, int j
     }
 }
 
-// Walk the tiles of a level: body(x0, y0, z0, uniform) for each tile.
-template <int NDIM, typename F>
-__device__ __forceinline__ void for_tiles(const Tiles &tl, const unsigned char *tflag, F &&body) {
-    for (int t = blockIdx.x; t < tl.nt; t += gridDim.x) {
-        const int bx = t % tl.ntx, rr = t / tl.ntx;
-        const int by = rr % tl.nty, bz = rr / tl.nty;
-        body(bx * 32, by * 8, bz * MT<NDIM>::TZ, tflag ? tflag[t] != 0 : false);
-    }
-}
 
 // Search direction and operator in one pass (a PCG iteration's first half):
 //   d = D^-1 s + beta d_old   (d = D^-1 s on the first iteration),
@@ -193,7 +184,7 @@ __device__ __forceinline__ void pcg_dq_run(const LevelD<T> &L, const T *__restri
         if (threadIdx.x == 0 && threadIdx.y == 0) S->alpha[lev] = out[0] != 0.0 ? S->rho[lev] / out[0] : 0.0;
 }
 template <typename T, int NDIM, bool FIRST>
-__global__ void __launch_bounds__(256, 3) k_pcg_dq(LevelD<T> L, const T *dold, T *dnew,
+__global__ void __launch_bounds__(256, 4) k_pcg_dq(LevelD<T> L, const T *dold, T *dnew,
                                                    DevScalars *S, double *part, int lev) {
     pcg_dq_run<T, NDIM>(L, dold, dnew, S, part, lev, FIRST);
 }
@@ -218,35 +209,47 @@ __device__ __forceinline__ void pcg_init_run(const LevelD<T> &L, const GridD &gc
         const bool pz = g.per[2] != 0;
         const int zb = NDIM == 3 ? z0 : 0, ze = NDIM == 3 ? min(z0 + MT<NDIM>::TZ, g.n[2]) : 1;
         constexpr int TZ = MT<NDIM>::TZ;
+        constexpr int PZ = NDIM == 3 ? TZ + 2 : 1;
         const T *__restrict__ rr = L.r;
         const T *__restrict__ id = L.invD;
-        T rv[TZ], iv[TZ];
+        const T *__restrict__ xcr = xc;
+        // every load of the column first: r and 1/D of its cells, the parent
+        // value of fine planes zb-1 .. zb+TZ, and the parent of the x and of
+        // the y neighbour that has another parent (the other side of each
+        // pair shares the cell's parent: at most one offset is nonzero)
+        const int cxn = cxm ? cxm : cxp, cyn = cym ? cym : cyp;
+        T rv[TZ], iv[TZ], pv[PZ], xn[TZ], yn[TZ];
+#pragma unroll
+        for (int t = 0; t < PZ; ++t) {
+            const int kf = NDIM == 3 ? edge_idx(zb - 1 + t, g.n[2], pz) : 0;
+            if (NDIM == 2 || zb - 1 + t <= ze) pv[t] = xcr[cbase + cplane * (kf >> 1)];
+        }
 #pragma unroll
         for (int t = 0; t < TZ; ++t)
             if (zb + t < ze) {
                 const int idx = c.i + g.n[0] * (c.j + g.n[1] * (zb + t));
                 rv[t] = rr[idx];
                 iv[t] = id[idx];
+                const int cb = cbase + cplane * (NDIM == 3 ? ((zb + t) >> 1) : 0);
+                xn[t] = cxn ? xcr[cb + cxn] : T(0);
+                yn[t] = cyn ? xcr[cb + cyn] : T(0);
             }
 #pragma unroll
         for (int t = 0; t < TZ; ++t) {
             const int k = zb + t;
             if (k >= ze) break;
-            const int cb = cbase + cplane * (NDIM == 3 ? (k >> 1) : 0);
             const int idx = c.i + g.n[0] * (c.j + g.n[1] * k);
-            const T x0v = xc[cb];
+            const T x0v = pv[t + (NDIM == 3 ? 1 : 0)];
             L.x[idx] = x0v;
             const T iD = iv[t];
             T s = T(0);
             if (iD != T(0)) {
                 T cp[3], cm[3];
                 coefs<T, NDIM>(L, uni, c.i, c.j, k, idx, cp, cm);
-                T Ax = cp[0] * (xc[cb + cxp] - x0v) - cm[0] * (x0v - xc[cb + cxm]) + cp[1] * (xc[cb + cyp] - x0v) -
-                       cm[1] * (x0v - xc[cb + cym]);
-                if (NDIM == 3) {
-                    const int kp = edge_idx(k + 1, g.n[2], pz) >> 1, km = edge_idx(k - 1, g.n[2], pz) >> 1;
-                    Ax += cp[2] * (xc[cbase + cplane * kp] - x0v) - cm[2] * (x0v - xc[cbase + cplane * km]);
-                }
+                const T vxm = cxm ? xn[t] : x0v, vxp = cxp ? xn[t] : x0v;
+                const T vym = cym ? yn[t] : x0v, vyp = cyp ? yn[t] : x0v;
+                T Ax = cp[0] * (vxp - x0v) - cm[0] * (x0v - vxm) + cp[1] * (vyp - x0v) - cm[1] * (x0v - vym);
+                if (NDIM == 3) Ax += cp[2] * (pv[t + 2] - x0v) - cm[2] * (x0v - pv[t]);
                 s = rv[t] - Ax;
             }
             L.s[idx] = s;
@@ -258,7 +261,7 @@ __device__ __forceinline__ void pcg_init_run(const LevelD<T> &L, const GridD &gc
         if (threadIdx.x == 0 && threadIdx.y == 0) S->rho[lev] = out[0];
 }
 template <typename T, int NDIM>
-__global__ void __launch_bounds__(256) k_pcg_initm(LevelD<T> L, GridD gc, const T *xc, DevScalars *S, double *part,
+__global__ void __launch_bounds__(256, 3) k_pcg_initm(LevelD<T> L, GridD gc, const T *xc, DevScalars *S, double *part,
                                                    int lev) {
     pcg_init_run<T, NDIM>(L, gc, xc, S, part, lev);
 }
@@ -274,7 +277,7 @@ __global__ void __launch_bounds__(256) k_residm(LevelD<T> L, const T *__restrict
                                                 DevScalars *S, double *part) {
     constexpr int TZ = MT<NDIM>::TZ;
     constexpr int HB = 1;
-    __shared__ T rpl[8][33];
+    __shared__ T rpl[2][8][33];   // double-buffered by plane parity (3D)
     const GridD &g = L.g;
     const T bm = (T)S->bmean;
     const T bml = (T)(S->bmean - (double)bm);
@@ -364,18 +367,21 @@ __global__ void __launch_bounds__(256) k_residm(LevelD<T> L, const T *__restrict
                     // children (2i..2i+1, 2j..2j+1, 2k..2k+1): x pairs by shuffle,
                     // y pairs through shared memory, z pairs in a register
                     const int i = threadIdx.x, j = threadIdx.y;
+                    const int pb = NDIM == 3 ? (k & 1) : 0;
                     const T v = res + __shfl_xor_sync(0xffffffffu, res, 1);
-                    rpl[j][i] = v;
+                    rpl[pb][j][i] = v;
                     __syncthreads();
                     if ((i & 1) == 0 && (j & 1) == 0) {
-                        csum += v + rpl[j + 1][i];
+                        csum += v + rpl[pb][j + 1][i];
                         if (NDIM == 2 || (k & 1) == 1) {
                             const int ci = c.i >> 1, cj = c.j >> 1, ck = NDIM == 3 ? (k >> 1) : 0;
                             if (ci < C.g.n[0] && cj < C.g.n[1]) C.r[ci + C.g.n[0] * (cj + C.g.n[1] * ck)] = csum;
                             csum = T(0);
                         }
                     }
-                    __syncthreads();
+                    // (3D: the next plane writes the other buffer, and the one
+                    // after it is written only past the next plane's barrier)
+                    if (NDIM == 2) __syncthreads();
                 }
             }
         }

@@ -72,6 +72,16 @@ __device__ __forceinline__ void for_cells(const GridD &g, const Tiles &tl, const
     }
 }
 
+// Walk the tiles of a level: body(x0, y0, z0, uniform) for each tile.
+template <int NDIM, typename F>
+__device__ __forceinline__ void for_tiles(const Tiles &tl, const unsigned char *tflag, F &&body) {
+    for (int t = blockIdx.x; t < tl.nt; t += gridDim.x) {
+        const int bx = t % tl.ntx, rr = t / tl.ntx;
+        const int by = rr % tl.nty, bz = rr / tl.nty;
+        body(bx * 32, by * 8, bz * MT<NDIM>::TZ, tflag ? tflag[t] != 0 : false);
+    }
+}
+
 // Neighbour indices and face coefficients of cell (i,j,k) = idx. In uniform
 // tiles the coefficients come from the position (cu, or 0 on a non-periodic
 // domain face); elsewhere they are loaded.
@@ -198,39 +208,68 @@ __device__ __forceinline__ void two_sum(T a, T b, T &s, T &e);
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(256) k_div(LevelD<T> L, CVec3P<T> u, const T *ue, T inv_wdt, T *b, T *bl,
                                              DevScalars *S, double *part) {
+    constexpr int TZ = MT<NDIM>::TZ;
     const GridD &g = L.g;
     T acc[2] = {T(0), T(0)};
-    // distinct arrays: the loads of all planes of a column may be issued together
     const T *__restrict__ ux = u.p[0], *__restrict__ uy = u.p[1], *__restrict__ uz = u.p[2];
     const T *__restrict__ uep = ue;
+    const T *__restrict__ iDp = L.invD;
     T *__restrict__ bo = b, *__restrict__ blo = bl;
-    for_cells<NDIM>(g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
-        const int I[3] = {i, j, k};
-        const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
-        // divergence of the stored velocity as an unevaluated pair (exact
-        // face differences, two-sum accumulation), then scaled by 1/(w dt)
-        T sh = T(0), sl = T(0);
+    const long long plane = (long long)g.n[0] * g.n[1];
+    for_tiles<NDIM>(L.tl, L.tflag, [&](int x0, int y0, int z0, bool uni) {
+        const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
+        if (i >= g.n[0] || j >= g.n[1]) return;
+        const int zb = NDIM == 3 ? z0 : 0, nz = NDIM == 3 ? min(TZ, g.n[2] - z0) : 1;
+        const long long base = i + (long long)g.n[0] * j;
+        // upper faces: the next cell, the periodic image, or the boundary value
+        // (U_a, or the exit plane for u_x)
+        const bool xin = i + 1 < g.n[0], yin = j + 1 < g.n[1];
+        const long long ox = xin ? 1 : (g.per[0] ? -(long long)(g.n[0] - 1) : 0);
+        const long long oy = yin ? g.n[0] : (g.per[1] ? -(long long)(g.n[1] - 1) * g.n[0] : 0);
+        const bool xb = !xin && !g.per[0], yb = !yin && !g.per[1];
+        // every load of the column first
+        T vx[TZ], vxp[TZ], vy[TZ], vyp[TZ], vz[TZ + 1], iv[TZ];
 #pragma unroll
-        for (int a = 0; a < NDIM; ++a) {
-            const T *__restrict__ ua = a == 0 ? ux : (a == 1 ? uy : uz);
-            T up;
-            if (I[a] + 1 < g.n[a]) up = ua[idx + st[a]];
-            else if (g.per[a]) up = ua[idx - (long long)(g.n[a] - 1) * st[a]];
-            else up = (a == 0 && g.exit_x) ? uep[j + (long long)g.n[1] * k] : (T)g.U[a];
-            T d, de, s2, e2;
-            two_sum(up, -ua[idx], d, de);
-            two_sum(sh, d, s2, e2);
-            sh = s2;
-            sl += e2 + de;
+        for (int t = 0; t < TZ; ++t)
+            if (t < nz) {
+                const long long idx = base + plane * (zb + t);
+                vx[t] = ux[idx];
+                vxp[t] = xb ? (g.exit_x ? uep[j + (long long)g.n[1] * (zb + t)] : (T)g.U[0]) : ux[idx + ox];
+                vy[t] = uy[idx];
+                vyp[t] = yb ? (T)g.U[1] : uy[idx + oy];
+                if (NDIM == 3) vz[t] = uz[idx];
+                iv[t] = uni ? T(1) : iDp[idx];
+            }
+        if (NDIM == 3) {
+            const int kt = zb + nz;
+            vz[nz < TZ ? nz : TZ] = kt < g.n[2] ? uz[base + plane * kt] : (g.per[2] ? uz[base] : (T)g.U[2]);
         }
-        T h = sh + sl;
-        T l = sl - (h - sh);
-        const T bh = h * inv_wdt;
-        const T blo_ = fma(h, inv_wdt, -bh) + l * inv_wdt;
-        const T s = bh + blo_;
-        bo[idx] = s;
-        blo[idx] = blo_ - (s - bh);
-        if (uni || L.invD[idx] != T(0)) { acc[0] += s; acc[1] += s * s; }
+#pragma unroll
+        for (int t = 0; t < TZ; ++t)
+            if (t < nz) {
+                const long long idx = base + plane * (zb + t);
+                // divergence as an unevaluated pair (exact face differences,
+                // two-sum accumulation over the axes in order), scaled by 1/(w dt)
+                const T up[3] = {vxp[t], vyp[t], NDIM == 3 ? vz[t + 1] : T(0)};
+                const T lo[3] = {vx[t], vy[t], NDIM == 3 ? vz[t] : T(0)};
+                T sh = T(0), sl = T(0);
+#pragma unroll
+                for (int a = 0; a < NDIM; ++a) {
+                    T d, de, s2, e2;
+                    two_sum(up[a], -lo[a], d, de);
+                    two_sum(sh, d, s2, e2);
+                    sh = s2;
+                    sl += e2 + de;
+                }
+                T h = sh + sl;
+                T l = sl - (h - sh);
+                const T bh = h * inv_wdt;
+                const T blo_ = fma(h, inv_wdt, -bh) + l * inv_wdt;
+                const T sv = bh + blo_;
+                bo[idx] = sv;
+                blo[idx] = blo_ - (sv - bh);
+                if (iv[t] != T(0)) { acc[0] += sv; acc[1] += sv * sv; }
+            }
     });
     double out[2];
     if (grid_reduce<2, false, T>(acc, part, &S->counters[RS_DIV], out)) {
@@ -508,23 +547,106 @@ __global__ void k_coarsest(LevelD<T> L, double *w, int maxit) {
     coarsest_run<T>(L, w, maxit);
 }
 
+// Coarsest level by a precomputed dense solution operator (one block, FP64):
+// x = M (r - mean r) over active rows, M the active block of the inverse of
+// the operator bordered by the mean constraint, [A 1; 1^T 0]; x is made
+// mean-free over active rows like the PCG solve's. M: n x n doubles, zero on
+// inactive rows and columns.
+template <typename T>
+__global__ void k_coarsest_dense(LevelD<T> L, const double *__restrict__ M) {
+    const int n = (int)L.g.nc;
+    __shared__ double rr[512];
+    __shared__ double sh[64];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double v2[2] = {0.0, 0.0}, o2[2];
+    for (int e = tid; e < n; e += nt)
+        if (L.invD[e] != T(0)) { v2[0] += (double)L.r[e]; v2[1] += 1.0; }
+    block_reduce<2, false, double>(v2, o2, sh);
+    if (tid == 0) { sh[40] = o2[0]; sh[41] = o2[1]; }
+    __syncthreads();
+    const double nact = sh[41], rmean = nact > 0 ? sh[40] / nact : 0.0;
+    for (int e = tid; e < n; e += nt) rr[e] = L.invD[e] != T(0) ? (double)L.r[e] - rmean : 0.0;
+    __syncthreads();
+    double xs[2] = {0.0, 0.0};
+    double sx = 0.0;
+    for (int q = 0, e = tid; e < n; e += nt, ++q) {
+        const double *row = M + (long long)e * n;
+        double acc = 0.0;
+        for (int c = 0; c < n; ++c) acc = fma(row[c], rr[c], acc);
+        if (q < 2) xs[q] = acc;
+        if (L.invD[e] != T(0)) sx += acc;
+    }
+    double v1[1] = {sx}, o1[1];
+    block_reduce<1, false, double>(v1, o1, sh);
+    if (tid == 0) sh[40] = o1[0];
+    __syncthreads();
+    const double xm = nact > 0 ? sh[40] / nact : 0.0;
+    for (int q = 0, e = tid; e < n; e += nt, ++q) L.x[e] = L.invD[e] != T(0) ? (T)(xs[q] - xm) : T(0);
+}
+
 // ------------------------------------------------------------- projection
 // Pressure-gradient update (Sec. 3 listing): u_a[I] -= w dt c_a[I] (p[I] - p[I-e_a]).
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(256) k_grad(LevelD<T> L, const T *__restrict__ ph, const T *__restrict__ pl, T wdt,
                                               Vec3P<T> u) {
+    constexpr int TZ = MT<NDIM>::TZ;
+    constexpr int HB = NDIM == 3 ? 2 : 1;   // planes whose loads are issued together
+    const GridD &g = L.g;
     T *__restrict__ ux = u.p[0], *__restrict__ uy = u.p[1], *__restrict__ uz = u.p[2];
-    for_cells<NDIM>(L.g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
-        long long ip[3], im[3];
-        T cp[3], cm[3];
-        nb_setup<T, NDIM>(L, uni, i, j, k, idx, ip, im, cp, cm);
-        const T h0 = ph[idx], l0 = pl[idx];
+    const long long plane = (long long)g.n[0] * g.n[1];
+    for_tiles<NDIM>(L.tl, L.tflag, [&](int x0, int y0, int z0, bool uni) {
+        const int i = x0 + threadIdx.x, j = y0 + threadIdx.y;
+        if (i >= g.n[0] || j >= g.n[1]) return;
+        const int zb = NDIM == 3 ? z0 : 0, nz = NDIM == 3 ? min(TZ, g.n[2] - z0) : 1;
+        const long long base = i + (long long)g.n[0] * j;
+        // lower neighbours: the previous cell or the periodic image (a
+        // non-periodic lower domain face has coefficient 0: no update)
+        const long long om0 = i > 0 ? 1 : (long long)(g.n[0] - 1), om1 = j > 0 ? g.n[0] : (long long)(g.n[1] - 1) * g.n[0];
+        const bool fx = i > 0 || g.per[0], fy = j > 0 || g.per[1];
+        const long long sx = i > 0 ? -om0 : om0, sy = j > 0 ? -om1 : om1;
+        for (int hb = 0; hb < nz; hb += HB) {
+            T h0[HB], l0[HB], hx[HB], lx[HB], hy[HB], ly[HB], hz[HB], lz[HB], cx[HB], cy[HB], cz[HB];
+            T vx[HB], vy[HB], vz[HB];
 #pragma unroll
-        for (int a = 0; a < NDIM; ++a) {
-            if (cm[a] == T(0)) continue;
-            T *__restrict__ ua = a == 0 ? ux : (a == 1 ? uy : uz);
-            const T dp = (h0 - ph[im[a]]) + (l0 - pl[im[a]]);
-            ua[idx] -= wdt * cm[a] * dp;
+            for (int t = 0; t < HB; ++t)
+                if (hb + t < nz) {
+                    const int k = zb + hb + t;
+                    const long long idx = base + plane * k;
+                    h0[t] = ph[idx];
+                    l0[t] = pl[idx];
+                    vx[t] = ux[idx];
+                    vy[t] = uy[idx];
+                    if (NDIM == 3) vz[t] = uz[idx];
+                    hx[t] = ph[idx + sx];
+                    lx[t] = pl[idx + sx];
+                    hy[t] = ph[idx + sy];
+                    ly[t] = pl[idx + sy];
+                    if (NDIM == 3) {
+                        const long long km = k > 0 ? idx - plane : idx + plane * (g.n[2] - 1);
+                        hz[t] = ph[km];
+                        lz[t] = pl[km];
+                    }
+                    if (!uni) {
+                        cx[t] = L.c[0][idx];
+                        cy[t] = L.c[1][idx];
+                        if (NDIM == 3) cz[t] = L.c[2][idx];
+                    }
+                }
+#pragma unroll
+            for (int t = 0; t < HB; ++t)
+                if (hb + t < nz) {
+                    const int k = zb + hb + t;
+                    const long long idx = base + plane * k;
+                    const bool fz = NDIM == 3 && (k > 0 || g.per[2]);
+                    const T c0 = uni ? (fx ? L.cu : T(0)) : cx[t];
+                    const T c1 = uni ? (fy ? L.cu : T(0)) : cy[t];
+                    if (c0 != T(0)) ux[idx] = vx[t] - wdt * c0 * ((h0[t] - hx[t]) + (l0[t] - lx[t]));
+                    if (c1 != T(0)) uy[idx] = vy[t] - wdt * c1 * ((h0[t] - hy[t]) + (l0[t] - ly[t]));
+                    if (NDIM == 3) {
+                        const T c2 = uni ? (fz ? L.cu : T(0)) : cz[t];
+                        if (c2 != T(0)) uz[idx] = vz[t] - wdt * c2 * ((h0[t] - hz[t]) + (l0[t] - lz[t]));
+                    }
+                }
         }
     });
 }

@@ -152,6 +152,8 @@ struct Sim : SimBase {
     T *lc[WL_MAXLEV][3] = {};
     unsigned char *tfl[WL_MAXLEV] = {};
     double *cw = nullptr;   // coarsest scratch
+    double *cM = nullptr;   // dense solution operator of the coarsest level (static coefficients)
+    bool cdense = false;
     double *pout = nullptr; // reported pressure scratch
     DevScalars *S = nullptr, *hS = nullptr;
     double *part = nullptr;
@@ -185,6 +187,10 @@ struct Sim : SimBase {
         // parameter mode: blend inputs and pressures of both stages, gradient
         T *f1[3] = {}, *f2[3] = {}, *P1h = nullptr, *P1l = nullptr, *P2h = nullptr, *P2l = nullptr;
         double *dpar = nullptr;
+        // warm starts of the adjoint solves over a window (per stage: the
+        // previous reverse step's solution)
+        T *qh[2] = {}, *ql[2] = {};
+        bool qwarm = false, qvalid[2] = {false, false};
     } ad;
     // learned temporal guess: per projection stage (0 predictor, 1 corrector)
     // its last two converged pressures (hi, lo), the fitted weights and the
@@ -328,6 +334,9 @@ struct Sim : SimBase {
         dt_next = c.dt_init;
         set_velocity_fill();
         body_update(0.0);
+        // a small coarsest level with coefficients that never change (no body
+        // or a fixed one) is solved by a precomputed dense operator
+        cdense = gl[nlev - 1].nc <= 256 && !moving && coarse_dense_build();
         build_vcycle_graph();
         WL_CK(cudaStreamSynchronize(st));
     }
@@ -439,7 +448,8 @@ struct Sim : SimBase {
         int maxit = (int)(2 * ncl + 200);
         if (maxit > 2000) maxit = 2000;
         B("coarsest", L);
-        k_coarsest<T><<<1, ncl >= 512 ? 512 : 256, 0, s>>>(lv[L], cw, maxit);
+        if (cdense) k_coarsest_dense<T><<<1, 256, 0, s>>>(lv[L], cM);
+        else k_coarsest<T><<<1, ncl >= 512 ? 512 : 256, 0, s>>>(lv[L], cw, maxit);
         E();
         for (int l = nlev - 2; l >= 0; --l) {
             B("pcg_init", l);
@@ -478,7 +488,85 @@ struct Sim : SimBase {
         else k_residm<T, ND, false><<<tgrid(0), tblk(), 0, s>>>(lv[0], b, bl, ph, pl, lv[0], S, part);
     }
 
+    // Dense solution operator of the coarsest level: the inverse of the active
+    // operator bordered by the mean constraint, [A 1; 1^T 0], by Gauss-Jordan
+    // elimination with partial pivoting in double on the host. Returns false
+    // (PCG stays) if the bordered matrix is singular (a disconnected active set).
+    bool coarse_dense_build() {
+        const int L = nlev - 1;
+        const GridD &cg = gl[L];
+        const int n = (int)cg.nc;
+        std::vector<T> hc[3], hinv(n);
+        for (int a = 0; a < g.ndim; ++a) {
+            hc[a].resize(n);
+            WL_CK(cudaMemcpyAsync(hc[a].data(), lc[L][a], n * sizeof(T), cudaMemcpyDeviceToHost, st));
+        }
+        WL_CK(cudaMemcpyAsync(hinv.data(), lv[L].invD, n * sizeof(T), cudaMemcpyDeviceToHost, st));
+        WL_CK(cudaStreamSynchronize(st));
+        std::vector<int> act;
+        std::vector<int> pos(n, -1);
+        for (int e = 0; e < n; ++e)
+            if (hinv[e] != T(0)) { pos[e] = (int)act.size(); act.push_back(e); }
+        const int m = (int)act.size();
+        if (m == 0) return false;
+        const int K = m + 1;
+        std::vector<double> A((size_t)K * K, 0.0), X((size_t)K * K, 0.0);
+        const int st3[3] = {1, cg.n[0], cg.n[0] * cg.n[1]};
+        double amax = 0.0;
+        for (int r = 0; r < m; ++r) {
+            const int e = act[r];
+            const int I[3] = {e % cg.n[0], (e / cg.n[0]) % cg.n[1], e / (cg.n[0] * cg.n[1])};
+            for (int a = 0; a < g.ndim; ++a) {
+                const int N = cg.n[a];
+                const bool per = cg.per[a] != 0;
+                const int ep = I[a] == N - 1 ? (per ? e - (N - 1) * st3[a] : -1) : e + st3[a];
+                const int em = I[a] == 0 ? (per ? e + (N - 1) * st3[a] : -1) : e - st3[a];
+                const double cp = ep >= 0 ? (double)hc[a][ep] : 0.0, cm = (double)hc[a][e];
+                A[(size_t)r * K + r] -= cp + cm;
+                if (ep >= 0 && pos[ep] >= 0) A[(size_t)r * K + pos[ep]] += cp;
+                if (em >= 0 && pos[em] >= 0) A[(size_t)r * K + pos[em]] += cm;
+            }
+            amax = std::max(amax, std::fabs(A[(size_t)r * K + r]));
+            A[(size_t)r * K + m] = 1.0;
+            A[(size_t)m * K + r] = 1.0;
+        }
+        for (int r = 0; r < K; ++r) X[(size_t)r * K + r] = 1.0;
+        for (int c = 0; c < K; ++c) {
+            int piv = c;
+            for (int r = c + 1; r < K; ++r)
+                if (std::fabs(A[(size_t)r * K + c]) > std::fabs(A[(size_t)piv * K + c])) piv = r;
+            if (!(std::fabs(A[(size_t)piv * K + c]) > 1e-10 * std::max(amax, 1.0))) return false;
+            if (piv != c)
+                for (int q = 0; q < K; ++q) {
+                    std::swap(A[(size_t)c * K + q], A[(size_t)piv * K + q]);
+                    std::swap(X[(size_t)c * K + q], X[(size_t)piv * K + q]);
+                }
+            const double inv = 1.0 / A[(size_t)c * K + c];
+            for (int q = 0; q < K; ++q) { A[(size_t)c * K + q] *= inv; X[(size_t)c * K + q] *= inv; }
+            for (int r = 0; r < K; ++r) {
+                if (r == c) continue;
+                const double f = A[(size_t)r * K + c];
+                if (f == 0.0) continue;
+                for (int q = 0; q < K; ++q) {
+                    A[(size_t)r * K + q] -= f * A[(size_t)c * K + q];
+                    X[(size_t)r * K + q] -= f * X[(size_t)c * K + q];
+                }
+            }
+        }
+        std::vector<double> Mh((size_t)n * n, 0.0);
+        for (int r = 0; r < m; ++r)
+            for (int q = 0; q < m; ++q) Mh[(size_t)act[r] * n + act[q]] = X[(size_t)r * K + q];
+        if (!cM) cM = alloc_n<double>((size_t)256 * 256);
+        WL_CK(cudaMemcpyAsync(cM, Mh.data(), Mh.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        WL_CK(cudaStreamSynchronize(st));
+        return true;
+    }
+
     void build_vcycle_graph() {
+        if (vexec) {
+            WL_CK(cudaGraphExecDestroy(vexec));
+            vexec = nullptr;
+        }
         cudaGraph_t graph;
         long long nodes = 0;
         WL_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
@@ -1110,6 +1198,7 @@ struct Sim : SimBase {
         ad.bkph = alloc_n<T>(nc); ad.bkpl = alloc_n<T>(nc);
         ad.lP = alloc_n<double>(nc);
         ad.dpar = alloc_n<double>(2);
+        for (int q = 0; q < 2; ++q) { ad.qh[q] = alloc_n<T>(nc); ad.ql[q] = alloc_n<T>(nc); }
         if (!pout) pout = alloc_n<double>(nc);
         ad.ready = true;
     }
@@ -1153,16 +1242,29 @@ struct Sim : SimBase {
     // coefficient part of the parameter gradient.
     int proj_vjp(T *const (&lam)[3], const T *le, const double *lP, double w, double dt, T *const (&out)[3], T *oute,
                  wl_solve_stats *sts, const T *Ph = nullptr, const T *Pl = nullptr, const BodyTangent *dB = nullptr,
-                 double tt = 0.0) {
+                 double tt = 0.0, int stage = -1) {
         P0("adj_rhs", 0, g.nc);
         k_adj_rhs<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], cvp(lam), lP, 1.0 / (w * dt), b, bl);
         P1();
         k_bstats<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], b, S, part);
-        WL_CK(cudaMemsetAsync(ph, 0, g.nc * sizeof(T), st));
-        WL_CK(cudaMemsetAsync(pl, 0, g.nc * sizeof(T), st));
         WL_LAUNCH_CK();
         launches += 2;
+        // warm start: the same stage's solution of the previous reverse step
+        // over a window (any start converges to the same solution), else 0
+        const bool warm = stage >= 0 && ad.qwarm && ad.qvalid[stage];
+        if (warm) {
+            dcopy(ph, ad.qh[stage], g.nc);
+            dcopy(pl, ad.ql[stage], g.nc);
+        } else {
+            WL_CK(cudaMemsetAsync(ph, 0, g.nc * sizeof(T), st));
+            WL_CK(cudaMemsetAsync(pl, 0, g.nc * sizeof(T), st));
+        }
         const int rc = solve(sts);
+        if (stage >= 0 && ad.qwarm) {
+            dcopy(ad.qh[stage], ph, g.nc);
+            dcopy(ad.ql[stage], pl, g.nc);
+            ad.qvalid[stage] = true;
+        }
         if (Ph && dB) {
             P0("adj_param_coef", 0, g.nc);
             k_adj_param_coef<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], Ph, Pl, ph, pl, cvp(lam), w * dt,
@@ -1274,7 +1376,7 @@ struct Sim : SimBase {
         }
         // reverse: corrector projection, exit, blend, flux at u*
         int r1 = proj_vjp(ad.lu, g.exit_x ? ad.le : nullptr, haveP ? ad.lP : nullptr, 0.5, dt, ad.x, ad.xe, &s[1],
-                          params ? ad.P2h : nullptr, params ? ad.P2l : nullptr, params ? dB : nullptr, t1);
+                          params ? ad.P2h : nullptr, params ? ad.P2l : nullptr, params ? dB : nullptr, t1, 1);
         zero_vec(ad.ub);
         zero_vec(ad.usb);
         if (g.exit_x) {
@@ -1289,7 +1391,7 @@ struct Sim : SimBase {
         adj_flux(ad.us, ad.ues, ad.fb, ad.usb, ad.uesb);
         // predictor projection, exit, blend, flux at u0
         int r2 = proj_vjp(ad.usb, g.exit_x ? ad.uesb : nullptr, nullptr, 1.0, dt, ad.x, ad.xe, &s[0],
-                          params ? ad.P1h : nullptr, params ? ad.P1l : nullptr, params ? dB : nullptr, t1);
+                          params ? ad.P1h : nullptr, params ? ad.P1l : nullptr, params ? dB : nullptr, t1, 0);
         if (g.exit_x) {
             k_adj_exit<T, false><<<1, 1024, 0, st>>>(g, ad.xe, (T)dt, ad.ueb, ad.ueb, ad.ub[0]);
             WL_LAUNCH_CK();
@@ -1472,6 +1574,9 @@ struct Sim : SimBase {
         const bool tgu = tg.use, gqu = gq.use;
         tg.use = gq.use = false;
         struct Restore { bool &a, &b; bool va, vb; ~Restore() { a = va; b = vb; } } rs{tg.use, gq.use, tgu, gqu};
+        ad.qwarm = true;
+        ad.qvalid[0] = ad.qvalid[1] = false;
+        struct QOff { bool &q; ~QOff() { q = false; } } qoff{ad.qwarm};
         int rc = WL_OK;
         const int nseg = (win.n + win.k - 1) / win.k;
         for (int sgi = nseg - 1; sgi >= 0 && rc == WL_OK; --sgi) {
@@ -1521,6 +1626,11 @@ struct Sim : SimBase {
         moving = has_body && (body.heave_amp != 0.0 || body.pitch_amp != 0.0);
         win.active = false;
         if (has_body) body_update(body_t >= 0 ? body_t : t);
+        // the coarsest level's dense operator follows the new coefficients
+        const bool want = gl[nlev - 1].nc <= 256 && !moving;
+        const bool was = cdense;
+        cdense = want && coarse_dense_build();
+        if (cdense != was) build_vcycle_graph();
         WL_CK(cudaStreamSynchronize(st));
     }
 
