@@ -42,6 +42,7 @@ def workload(name):
         "msphere": lambda: synth.config5_moving_sphere(),
         "circle": lambda: synth.config1_circle(),
         "ellipse": lambda: synth.config4_ellipse(),
+        "cylinder64": lambda: synth.cylinder_benchmark(64),
     }
     return table[name]()
 

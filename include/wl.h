@@ -67,7 +67,7 @@ typedef enum {
 
 typedef enum { WL_F32 = 0, WL_F64 = 1 } wl_precision;
 
-typedef enum { WL_BODY_NONE = 0, WL_BODY_SPHERE = 1, WL_BODY_ELLIPSE = 2 } wl_body_kind;
+typedef enum { WL_BODY_NONE = 0, WL_BODY_SPHERE = 1, WL_BODY_ELLIPSE = 2, WL_BODY_CYLINDER = 3 } wl_body_kind;
 
 /* Optional device allocator (e.g. a framework's caching allocator).
  * alloc returns a device pointer of at least `bytes` (256-byte aligned) or
@@ -100,7 +100,9 @@ typedef struct {
 } wl_config;
 
 /* Analytic immersed body (Sec. 3 AutoBody: signed distance + motion map).
- * SPHERE is a circle in 2D. The centre heaves along heave_axis as
+ * SPHERE is a circle in 2D. CYLINDER (3D) is a circular cylinder of the given
+ * radius with its axis along z through (centre[0], centre[1]) (the moving
+ * cylinder benchmark of Sec. 4, spanwise periodic). The centre heaves along heave_axis as
  * centre + heave_amp sin(omega t + phase); ELLIPSE (2D) has semi-axes semi[0]
  * (chord/2, along x at zero pitch) and semi[1] (thickness/2) and pitches about
  * its centre by pitch_amp sin(omega t + phase + pi/2). Signed distance d > 0 in

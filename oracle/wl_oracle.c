@@ -211,12 +211,14 @@ void orc_body_eval(const orc_body *B, int ndim, const double *x, double t, doubl
     nrm[0] = nrm[1] = nrm[2] = 0.0;
     V[0] = cdot[0]; V[1] = cdot[1]; V[2] = cdot[2];
     if (B->kind == 0) { *d = 1e30; return; }
-    if (B->kind == 1) {
+    if (B->kind == 1 || B->kind == 3) {
+        /* sphere (circle in 2D); cylinder: the same in the x-y plane, axis along z */
         double r2 = 0.0, rv[3] = {0, 0, 0};
-        for (int a = 0; a < ndim; ++a) { rv[a] = x[a] - c[a]; r2 += rv[a] * rv[a]; }
+        int na = B->kind == 3 ? 2 : ndim;
+        for (int a = 0; a < na; ++a) { rv[a] = x[a] - c[a]; r2 += rv[a] * rv[a]; }
         double rr = sqrt(r2);
         *d = rr - B->radius;
-        if (rr > 0.0) for (int a = 0; a < ndim; ++a) nrm[a] = rv[a] / rr;
+        if (rr > 0.0) for (int a = 0; a < na; ++a) nrm[a] = rv[a] / rr;
         else nrm[0] = 1.0;
         return;
     }

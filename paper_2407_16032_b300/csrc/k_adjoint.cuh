@@ -351,7 +351,8 @@ __device__ __forceinline__ void body_tangent(const BodyState &B, const BodyTange
     }
     d = 1e30;
     dd = 0.0;
-    if (B.kind == 1) {
+    if (B.kind == 1 || B.kind == 3) {
+        if (B.kind == 3) { rv[2] = 0.0; drv[2] = 0.0; }   // cylinder: in-plane distance
         const double rr = sqrt(rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2]);
         d = rr - B.radius;
         if (rr > 0.0) {

@@ -17,7 +17,7 @@
 // The centre is split into an integer part and a remainder so that face
 // offsets x - c stay accurate in single precision.
 struct BodyState {
-    int kind;          // 0 none, 1 sphere/circle, 2 ellipse (2D)
+    int kind;          // 0 none, 1 sphere/circle, 2 ellipse (2D), 3 cylinder along z (3D)
     double chi[3];     // integer part of the centre
     double clo[3];     // centre - chi
     double radius;
@@ -66,7 +66,8 @@ __device__ __forceinline__ void body_eval(const BodyState &B, int ndim, const T 
         nrm[a] = T(0);
         V[a] = (T)B.vc[a];
     }
-    if (B.kind == 1) {
+    if (B.kind == 1 || B.kind == 3) {
+        if (B.kind == 3) rv[2] = T(0);   // cylinder: distance in the x-y plane
         T r2 = rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
         T rr = sqrt(r2);
         d = rr - (T)B.radius;

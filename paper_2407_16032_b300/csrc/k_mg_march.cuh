@@ -118,20 +118,45 @@ __device__ __forceinline__ void pcg_dq_run(const LevelD<T> &L, const T *__restri
             const T iv = !uni ? iD[id] : (plain ? idc : idu(ii, jj, kk));
             return FIRST ? iv * sv : iv * sv + beta * dv;
         };
-        // this thread's ring cell (role 0: none, 1 below, 2 above, 3 left, 4 right)
-        int role = 0, ri = 0, rj = 0, sy = 0, sx = 0;
-        if (ty == 0 && tx < nx) { role = 1; ri = i; rj = edge_idx(y0 - 1, n1, py); sy = 0; sx = tx + 1; }
-        else if (ty == 7 && tx < nx) { role = 2; ri = i; rj = edge_idx(y0 + ny, n1, py); sy = ny + 1; sx = tx + 1; }
-        else if (ty == 1 && tx < 8 && tx < ny) { role = 3; ri = edge_idx(x0 - 1, n0, px); rj = y0 + tx; sy = tx + 1; sx = 0; }
-        else if (ty == 1 && tx >= 8 && tx < 16 && tx - 8 < ny) {
-            role = 4; ri = edge_idx(x0 + nx, n0, px); rj = y0 + tx - 8; sy = tx - 7; sx = nx + 1;
+        // ring work. 2D (one plane): warps 0 and 7 take the rows below and
+        // above the tile, lanes 0..15 of warp 1 its left and right columns.
+        // 3D: spread over all warps: warp w takes two planes (2 (w mod 4) and
+        // the next) of the row below (w < 4) or above (w >= 4), and lanes
+        // 0..15 of warp w the left / right column cells of plane w.
+        int rrow = -1, rrj = 0, rsy = 0, rp0 = 0;       // row cell (x = i), planes rp0, rp0 + 1
+        int rcol = -1, rci = 0, rcj = 0, rcy = 0, rcx = 0;  // column cell, plane ty
+        if (NDIM == 3) {
+            if (tx < nx) {
+                rrow = ty < 4 ? 0 : 1;
+                rrj = rrow == 0 ? edge_idx(y0 - 1, n1, py) : edge_idx(y0 + ny, n1, py);
+                rsy = rrow == 0 ? 0 : ny + 1;
+                rp0 = 2 * (ty & 3);
+            }
+            if (tx < 16 && (tx & 7) < ny && ty < nz) {
+                rcol = tx < 8 ? 0 : 1;
+                rci = rcol == 0 ? edge_idx(x0 - 1, n0, px) : edge_idx(x0 + nx, n0, px);
+                rcj = y0 + (tx & 7);
+                rcy = (tx & 7) + 1;
+                rcx = rcol == 0 ? 0 : nx + 1;
+            }
+        } else {
+            if (ty == 0 && tx < nx) { rrow = 0; rrj = edge_idx(y0 - 1, n1, py); rsy = 0; }
+            else if (ty == 7 && tx < nx) { rrow = 1; rrj = edge_idx(y0 + ny, n1, py); rsy = ny + 1; }
+            else if (ty == 1 && tx < 16 && (tx & 7) < ny) {
+                rcol = tx < 8 ? 0 : 1;
+                rci = rcol == 0 ? edge_idx(x0 - 1, n0, px) : edge_idx(x0 + nx, n0, px);
+                rcj = y0 + (tx & 7);
+                rcy = (tx & 7) + 1;
+                rcx = rcol == 0 ? 0 : nx + 1;
+            }
         }
+        const int NRP = NDIM == 3 ? 2 : 1;              // row planes per thread
         __syncthreads();   // the previous tile's readers of sd are done
         int kz[PZ];
 #pragma unroll
         for (int t = 0; t < PZ; ++t) kz[t] = NDIM == 3 ? edge_idx(zb - 1 + t, g.n[2], pz) : 0;
-        T sv[PZ], dv[PZ], rs[TZ], rd[TZ];
-        // all loads of the column and of the ring cell first
+        T sv[PZ], dv[PZ], rs[2], rd[2], cs = T(0), cd = T(0);
+        // all loads of the column and of the ring cells first
         if (in) {
 #pragma unroll
             for (int t = 0; t < PZ; ++t)
@@ -141,14 +166,22 @@ __device__ __forceinline__ void pcg_dq_run(const LevelD<T> &L, const T *__restri
                     dv[t] = FIRST ? T(0) : dold[id];
                 }
         }
-        if (role) {
+        if (rrow >= 0) {
 #pragma unroll
-            for (int t = 0; t < TZ; ++t)
-                if (t < nz) {
-                    const int id = ri + n0 * rj + plane * kz[t + Z0];
-                    rs[t] = s[id];
-                    rd[t] = FIRST ? T(0) : dold[id];
+            for (int h = 0; h < NRP; ++h)
+                if (rp0 + h < nz) {
+                    const int kk = NDIM == 3 ? edge_idx(zb + rp0 + h, g.n[2], pz) : 0;   // (no run-time index into kz)
+                    const int id = i + n0 * rrj + plane * kk;
+                    rs[h] = s[id];
+                    rd[h] = FIRST ? T(0) : dold[id];
                 }
+        }
+        const int cz = NDIM == 3 ? ty : 0;
+        if (rcol >= 0) {
+            const int kk = NDIM == 3 ? edge_idx(zb + cz, g.n[2], pz) : 0;
+            const int id = rci + n0 * rcj + plane * kk;
+            cs = s[id];
+            cd = FIRST ? T(0) : dold[id];
         }
         if (in) {
 #pragma unroll
@@ -156,10 +189,17 @@ __device__ __forceinline__ void pcg_dq_run(const LevelD<T> &L, const T *__restri
                 if (t < nz + 2 * Z0)
                     sd[t][ty + 1][tx + 1] = dform(i + n0 * j + plane * kz[t], i, j, kz[t], sv[t], dv[t]);
         }
-        if (role) {
+        if (rrow >= 0) {
 #pragma unroll
-            for (int t = 0; t < TZ; ++t)
-                if (t < nz) sd[t + Z0][sy][sx] = dform(ri + n0 * rj + plane * kz[t + Z0], ri, rj, kz[t + Z0], rs[t], rd[t]);
+            for (int h = 0; h < NRP; ++h)
+                if (rp0 + h < nz) {
+                    const int kk = NDIM == 3 ? edge_idx(zb + rp0 + h, g.n[2], pz) : 0;
+                    sd[rp0 + h + Z0][rsy][tx + 1] = dform(i + n0 * rrj + plane * kk, i, rrj, kk, rs[h], rd[h]);
+                }
+        }
+        if (rcol >= 0) {
+            const int kk = NDIM == 3 ? edge_idx(zb + cz, g.n[2], pz) : 0;
+            sd[cz + Z0][rcy][rcx] = dform(rci + n0 * rcj + plane * kk, rci, rcj, kk, cs, cd);
         }
         __syncthreads();
         if (in) {
@@ -167,12 +207,22 @@ __device__ __forceinline__ void pcg_dq_run(const LevelD<T> &L, const T *__restri
             for (int t = 0; t < TZ; ++t)
                 if (t < nz) {
                     const int k = zb + t, idx = i + n0 * j + plane * k;
-                    T cp[3], cm[3];
-                    coefs<T, NDIM>(L, uni, i, j, k, idx, cp, cm);
                     const T dc = sd[t + Z0][ty + 1][tx + 1];
-                    T Ad = cp[0] * (sd[t + Z0][ty + 1][tx + 2] - dc) - cm[0] * (dc - sd[t + Z0][ty + 1][tx]) +
-                           cp[1] * (sd[t + Z0][ty + 2][tx + 1] - dc) - cm[1] * (dc - sd[t + Z0][ty][tx + 1]);
-                    if (NDIM == 3) Ad += cp[2] * (sd[t + 2 * Z0][ty + 1][tx + 1] - dc) - cm[2] * (dc - sd[t][ty + 1][tx + 1]);
+                    T Ad;
+                    if (plain) {
+                        // every face carries cu: A d = cu (sum of the 2n neighbours - 2n d)
+                        T nb = (sd[t + Z0][ty + 1][tx + 2] + sd[t + Z0][ty + 1][tx]) +
+                               (sd[t + Z0][ty + 2][tx + 1] + sd[t + Z0][ty][tx + 1]);
+                        if (NDIM == 3) nb += sd[t + 2 * Z0][ty + 1][tx + 1] + sd[t][ty + 1][tx + 1];
+                        Ad = L.cu * (nb - T(2 * NDIM) * dc);
+                    } else {
+                        T cp[3], cm[3];
+                        coefs<T, NDIM>(L, uni, i, j, k, idx, cp, cm);
+                        Ad = cp[0] * (sd[t + Z0][ty + 1][tx + 2] - dc) - cm[0] * (dc - sd[t + Z0][ty + 1][tx]) +
+                             cp[1] * (sd[t + Z0][ty + 2][tx + 1] - dc) - cm[1] * (dc - sd[t + Z0][ty][tx + 1]);
+                        if (NDIM == 3)
+                            Ad += cp[2] * (sd[t + 2 * Z0][ty + 1][tx + 1] - dc) - cm[2] * (dc - sd[t][ty + 1][tx + 1]);
+                    }
                     dnew[idx] = dc;
                     q[idx] = Ad;
                     acc[0] += dc * Ad;
@@ -210,6 +260,9 @@ __device__ __forceinline__ void pcg_init_run(const LevelD<T> &L, const GridD &gc
         const int zb = NDIM == 3 ? z0 : 0, ze = NDIM == 3 ? min(z0 + MT<NDIM>::TZ, g.n[2]) : 1;
         constexpr int TZ = MT<NDIM>::TZ;
         constexpr int PZ = NDIM == 3 ? TZ + 2 : 1;
+        // uniform tile away from every non-periodic domain face
+        const bool plain = uni && (g.per[0] || (x0 > 0 && x0 + 32 < g.n[0])) &&
+                           (g.per[1] || (y0 > 0 && y0 + 8 < g.n[1])) && (NDIM == 2 || pz || (zb > 0 && ze < g.n[2]));
         const T *__restrict__ rr = L.r;
         const T *__restrict__ id = L.invD;
         const T *__restrict__ xcr = xc;
@@ -244,12 +297,20 @@ __device__ __forceinline__ void pcg_init_run(const LevelD<T> &L, const GridD &gc
             const T iD = iv[t];
             T s = T(0);
             if (iD != T(0)) {
-                T cp[3], cm[3];
-                coefs<T, NDIM>(L, uni, c.i, c.j, k, idx, cp, cm);
                 const T vxm = cxm ? xn[t] : x0v, vxp = cxp ? xn[t] : x0v;
                 const T vym = cym ? yn[t] : x0v, vyp = cyp ? yn[t] : x0v;
-                T Ax = cp[0] * (vxp - x0v) - cm[0] * (x0v - vxm) + cp[1] * (vyp - x0v) - cm[1] * (x0v - vym);
-                if (NDIM == 3) Ax += cp[2] * (pv[t + 2] - x0v) - cm[2] * (x0v - pv[t]);
+                T Ax;
+                if (plain) {
+                    // every face carries cu: A x = cu (sum of the 2n neighbours - 2n x)
+                    T nb = (vxp + vxm) + (vyp + vym);
+                    if (NDIM == 3) nb += pv[t + 2] + pv[t];
+                    Ax = L.cu * (nb - T(2 * NDIM) * x0v);
+                } else {
+                    T cp[3], cm[3];
+                    coefs<T, NDIM>(L, uni, c.i, c.j, k, idx, cp, cm);
+                    Ax = cp[0] * (vxp - x0v) - cm[0] * (x0v - vxm) + cp[1] * (vyp - x0v) - cm[1] * (x0v - vym);
+                    if (NDIM == 3) Ax += cp[2] * (pv[t + 2] - x0v) - cm[2] * (x0v - pv[t]);
+                }
                 s = rv[t] - Ax;
             }
             L.s[idx] = s;

@@ -1655,7 +1655,9 @@ int validate(const wl_config *c, const wl_body *bd, std::string &msg) {
     if (!(c->tol > 0) || c->itmax < 0 || c->smooth_iters < 1 || c->smooth_iters > 64) { msg = "bad solver settings"; return WL_ERR_ARG; }
     if (!(c->dt_init > 0) || !(c->dt_max > 0) || !(c->cfl > 0)) { msg = "bad time-step settings"; return WL_ERR_ARG; }
     if (bd) {
-        if (bd->kind < 0 || bd->kind > 2) { msg = "unknown body kind"; return WL_ERR_ARG; }
+        if (bd->kind < 0 || bd->kind > 3) { msg = "unknown body kind"; return WL_ERR_ARG; }
+        if (bd->kind == WL_BODY_CYLINDER && c->ndim != 3) { msg = "cylinder body is 3D only (use a sphere in 2D)"; return WL_ERR_ARG; }
+        if (bd->kind == WL_BODY_CYLINDER && !(bd->radius > 0)) { msg = "cylinder radius must be positive"; return WL_ERR_ARG; }
         if (bd->kind == WL_BODY_ELLIPSE && c->ndim != 2) { msg = "ellipse body is 2D only"; return WL_ERR_ARG; }
         if (bd->kind == WL_BODY_SPHERE && !(bd->radius > 0)) { msg = "sphere radius must be positive"; return WL_ERR_ARG; }
         if (bd->kind == WL_BODY_ELLIPSE && !(bd->semi[0] > 0 && bd->semi[1] > 0)) { msg = "ellipse semi-axes must be positive"; return WL_ERR_ARG; }

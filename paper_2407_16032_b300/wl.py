@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libwl.so")
 
 WL_OK, WL_ERR_ARG, WL_ERR_CUDA, WL_ERR_ALLOC, WL_ERR_NOT_CONVERGED, WL_ERR_NONFINITE, WL_ERR_UNSTABLE, WL_ERR_STATE = range(8)
 WL_F32, WL_F64 = 0, 1
-BODY_KIND = {"none": 0, "sphere": 1, "ellipse": 2}
+BODY_KIND = {"none": 0, "sphere": 1, "ellipse": 2, "cylinder": 3}
 
 EXPORTS = (
     "wl_config_default", "wl_sim_create", "wl_sim_destroy", "wl_set_velocity", "wl_get_velocity",

@@ -46,7 +46,8 @@ def uniform01(seed: int, comp: int, count: int) -> np.ndarray:
 class Body:
     """Analytic immersed body (Sec. 3: AutoBody = signed distance + motion map).
 
-    kind: "none", "sphere" (a circle when ndim == 2) or "ellipse" (2D only).
+    kind: "none", "sphere" (a circle when ndim == 2), "ellipse" (2D only) or
+    "cylinder" (3D, axis along z through the centre's x and y).
     Motion: centre moves along ``heave_axis`` as
     ``centre + heave_amp * sin(omega * t + phase)``; the ellipse pitches about
     its centre by ``pitch_amp * sin(omega * t + phase + pi/2)``.
@@ -63,7 +64,7 @@ class Body:
 
     @property
     def kind_id(self) -> int:
-        return {"none": 0, "sphere": 1, "ellipse": 2}[self.kind]
+        return {"none": 0, "sphere": 1, "ellipse": 2, "cylinder": 3}[self.kind]
 
 
 @dataclass
@@ -201,6 +202,19 @@ def config5_moving_sphere(n=(512, 256, 256), D=48.0, centre=(128.0, 128.0, 128.0
                 (1.0, 0.0, 0.0), D / 5000.0,
                 Body("sphere", centre, D / 2.0, heave_amp=0.25 * D, omega=omega, heave_axis=1),
                 init="noise", steps=1000)
+
+
+def cylinder_benchmark(L=64, moving=True) -> Case:
+    """The paper's moving-cylinder benchmark shape (Sec. 4): D = L, domain
+    9L x 6L x 2L, spanwise periodic, Re = 1000 on D. Readings: centre at
+    (2L, 3L), transverse heave of 0.25 D at St = 0.2 (as the moving sphere)."""
+    D = float(L)
+    omega = 2.0 * math.pi * 0.2 / D if moving else 0.0
+    return Case(f"cylinder{L}", 3, (9 * L, 6 * L, 2 * L), (False, False, True), True,
+                (1.0, 0.0, 0.0), D / 1000.0,
+                Body("cylinder", (2.0 * D, 3.0 * D, 0.0), D / 2.0, heave_amp=0.25 * D if moving else 0.0,
+                     omega=omega, heave_axis=1),
+                init="noise", steps=100)
 
 
 def scaled(case: Case, factor: float) -> Case:

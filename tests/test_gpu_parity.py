@@ -58,6 +58,7 @@ def test_conv_diff_matches_oracle(prec, shape, per, exit):
     (synth.Body("sphere", (30.6, 20.1, 0.0), 9.1), 2, (70, 40, 1), 0.0),
     (synth.Body("ellipse", (40.2, 30.7, 0.0), 0.0, (16.0, 3.84), heave_amp=4.0, pitch_amp=0.26, omega=0.03), 2,
      (96, 64, 1), 7.0),
+    (synth.Body("cylinder", (20.6, 17.3, 0.0), 6.2, heave_amp=2.0, omega=0.07, heave_axis=1), 3, (48, 36, 10), 3.0),
 ])
 def test_body_measure_matches_oracle(prec, body, nd, shape, t):
     case = synth.Case("m", nd, shape, (False,) * 3, True, (1.0, 0, 0), 0.01, body)
@@ -153,6 +154,10 @@ def test_config4_ellipse_oracle_size_fp32_10_steps():
     case = synth.config4_ellipse((256, 128), chord=32.0, A=8.0, centre=(64.0, 64.0))
     orc, sim, st = run_pair(case, 10, "f32")
     _compare(orc, sim, 1e-5, 1e-5)
+    # the pressure force (thrust / lift) on the moving foil at the step's end
+    F_or = oracle.forces(orc.g, orc.b, orc.t, orc.P)
+    F = sim.forces()
+    assert np.abs(F - F_or).max() < 1e-5 * max(np.abs(F_or).max(), 1.0)
 
 
 def test_config5_moving_sphere_reduced_fp32_1_and_10_steps():
@@ -162,6 +167,24 @@ def test_config5_moving_sphere_reduced_fp32_1_and_10_steps():
     tu, tp = _calibrated(case)
     orc, sim, st = run_pair(case, 10, "f32")
     _compare(orc, sim, tu, tp)
+    # drag and lift (pressure force) of the oscillating sphere against the oracle's
+    F_or = oracle.forces(orc.g, orc.b, orc.t, orc.P)
+    F = sim.forces()
+    assert np.abs(F - F_or).max() < tp * max(np.abs(F_or).max(), 1.0)
+
+
+def test_moving_cylinder_benchmark_reduced_fp32_1_and_10_steps():
+    # the paper's moving-cylinder benchmark shape (9L x 6L x 2L, spanwise
+    # periodic, Re 1000 on D = L) at L = 8
+    case = synth.cylinder_benchmark(8)
+    orc, sim, st = run_pair(case, 1, "f32")
+    _compare(orc, sim, 1e-6, 1e-6)
+    tu, tp = _calibrated(case)
+    orc, sim, st = run_pair(case, 10, "f32")
+    _compare(orc, sim, tu, tp)
+    F_or = oracle.forces(orc.g, orc.b, orc.t, orc.P)
+    F = sim.forces()
+    assert np.abs(F - F_or).max() < tp * max(np.abs(F_or).max(), 1.0)
 
 
 def test_ragged_sizes_2d_and_3d():

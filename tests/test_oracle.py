@@ -204,6 +204,31 @@ def test_sphere_distance_normal_velocity():
         np.testing.assert_allclose(nrm, gd, atol=1e-7)
 
 
+def test_cylinder_distance_is_planar_and_its_normal_is_the_gradient():
+    # a z-axis cylinder: the distance to the axis minus the radius, the same
+    # in every z plane, normal = grad d (central differences) with no z part,
+    # velocity = d(centre)/dt of the heave map
+    B = synth.Body("cylinder", (20.3, 15.7, 0.0), 4.5, heave_amp=2.0, omega=0.3, phase=0.4, heave_axis=1)
+    bs = oracle.make_body(B)
+    for _ in range(20):
+        x = RNG.uniform(5, 35, size=3)
+        t = RNG.uniform(0, 10)
+        d, nrm, V = oracle.body_eval(bs, 3, x, t)
+        cy = 15.7 + 2.0 * np.sin(0.3 * t + 0.4)
+        assert d == pytest.approx(np.hypot(x[0] - 20.3, x[1] - cy) - 4.5, abs=1e-12)
+        for z in (0.0, 17.0):
+            assert oracle.body_eval(bs, 3, (x[0], x[1], z), t)[0] == pytest.approx(d, abs=1e-12)
+        gd = []
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = 1e-4
+            gd.append((oracle.body_eval(bs, 3, x + e, t)[0] - oracle.body_eval(bs, 3, x - e, t)[0]) / 2e-4)
+        assert np.allclose(nrm, gd, atol=1e-7) and nrm[2] == 0.0
+        h = 1e-5
+        vy = (2.0 * np.sin(0.3 * (t + h) + 0.4) - 2.0 * np.sin(0.3 * (t - h) + 0.4)) / (2 * h)
+        assert V[1] == pytest.approx(vy, abs=1e-8) and V[0] == 0.0 and V[2] == 0.0
+
+
 def test_ellipse_reduces_to_circle_and_normal_is_distance_gradient_on_surface():
     circ = oracle.make_body(synth.Body("ellipse", (10.0, 9.0, 0.0), 0.0, (4.0, 4.0), pitch_amp=0.4, omega=0.2))
     for _ in range(20):
