@@ -43,6 +43,7 @@ def workload(name):
         "circle": lambda: synth.config1_circle(),
         "ellipse": lambda: synth.config4_ellipse(),
         "cylinder64": lambda: synth.cylinder_benchmark(64),
+        "tgv_octant512": lambda: synth.tgv_octant(512),
     }
     return table[name]()
 

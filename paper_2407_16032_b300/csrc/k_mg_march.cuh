@@ -350,6 +350,10 @@ __global__ void __launch_bounds__(256) k_residm(LevelD<T> L, const T *__restrict
         const Col c = column(g, x0, y0);
         const int base = (c.in ? c.i : 0) + g.n[0] * (c.in ? c.j : 0);
         const int zb = NDIM == 3 ? z0 : 0, nz = NDIM == 3 ? min(TZ, g.n[2] - z0) : 1;
+        // uniform tile away from every non-periodic domain face
+        const bool plain = uni && (g.per[0] || (x0 > 0 && x0 + 32 < g.n[0])) &&
+                           (g.per[1] || (y0 > 0 && y0 + 8 < g.n[1])) &&
+                           (NDIM == 2 || pz || (zb > 0 && zb + nz < g.n[2]));
         T csum = T(0);
         for (int hb = 0; hb < nz; hb += HB) {
             // batch loads: z column (HB + 2), x/y neighbours, b pair
@@ -384,12 +388,29 @@ __global__ void __launch_bounds__(256) k_residm(LevelD<T> L, const T *__restrict
                 T res = T(0);
                 if (c.in && live) {
                     if (uni || L.invD[idx] != T(0)) {
-                        T cp[3], cm[3];
-                        coefs<T, NDIM>(L, uni, c.i, c.j, k, idx, cp, cm);
                         const T hc = hz[t + 1], lc = lz[t + 1];
                         const T hP[3] = {hx[1][t], hx[3][t], hz[t + 2]}, hM[3] = {hx[0][t], hx[2][t], hz[t]};
                         const T lP[3] = {lx[1][t], lx[3][t], lz[t + 2]}, lM[3] = {lx[0][t], lx[2][t], lz[t]};
                         T Ah = T(0), Al = T(0);
+                        if (plain) {
+                            // every face carries cu (a power of two: exact
+                            // scaling): A p = cu sum_a [(p+ - p) - (p - p-)], the
+                            // second differences formed and summed exactly
+#pragma unroll
+                            for (int a = 0; a < NDIM; ++a) {
+                                T d1, e1, d2, e2, s2, es, s, e;
+                                two_sum(hP[a], -hc, d1, e1);
+                                two_sum(hc, -hM[a], d2, e2);
+                                two_sum(d1, -d2, s2, es);
+                                two_sum(Ah, s2, s, e);
+                                Ah = s;
+                                Al += e + (((e1 - e2) + es) + ((lP[a] - lc) - (lc - lM[a])));
+                            }
+                            Ah *= L.cu;
+                            Al *= L.cu;
+                        } else {
+                        T cp[3], cm[3];
+                        coefs<T, NDIM>(L, uni, c.i, c.j, k, idx, cp, cm);
 #pragma unroll
                         for (int a = 0; a < NDIM; ++a) {
                             T th, tl, s, e;
@@ -415,6 +436,7 @@ __global__ void __launch_bounds__(256) k_residm(LevelD<T> L, const T *__restrict
                                 Ah = s;
                                 Al += e + tl;
                             }
+                        }
                         }
                         T r1, e1, r2, e2;
                         two_sum(bv[t], -bm, r1, e1);

@@ -187,6 +187,13 @@ def test_moving_cylinder_benchmark_reduced_fp32_1_and_10_steps():
     assert np.abs(F - F_or).max() < tp * max(np.abs(F_or).max(), 1.0)
 
 
+def test_tgv_symmetric_octant_fp32_10_steps():
+    # the TGV of period 64 on its octant (32^3, slip walls on the mirror planes)
+    case = synth.tgv_octant(64)
+    orc, sim, st = run_pair(case, 10, "f32")
+    _compare(orc, sim, 1e-5, 1e-5)
+
+
 def test_ragged_sizes_2d_and_3d():
     c2 = synth.Case("r2", 2, (70, 36, 1), (False, False, False), True, (1.0, 0, 0), 0.05,
                     synth.Body("sphere", (21.3, 17.9, 0), 5.4), init="noise", seed=3)

@@ -507,6 +507,18 @@ def test_tgv3d_keeps_reflection_symmetries():
     assert np.abs(w).max() > 1e-4
 
 
+def test_tgv_octant_start_is_the_full_field_on_its_mirror_planes():
+    # the octant start equals the full-period field on the first octant, and
+    # the normal velocity vanishes on every wall (the field's mirror planes)
+    N = 24
+    uo, _ = synth.initial_velocity(synth.tgv_octant(N))
+    uf, _ = synth.initial_velocity(synth.config2_tgv(N))
+    h = N // 2
+    assert np.abs(uo - uf[:, :h, :h, :h]).max() < 1e-14
+    assert np.abs(uo[0][:, :, 0]).max() == 0.0 and np.abs(uo[1][:, 0, :]).max() == 0.0
+    assert np.abs(uf[0][:h, :h, h]).max() < 1e-12 and np.abs(uf[1][:h, h, :h]).max() < 1e-12
+
+
 def test_tgv2d_decay_converges_at_second_order_or_better():
     # 2D Taylor-Green: exact Navier-Stokes solution whose kinetic energy decays
     # as exp(-4 nu k^2 t). The discrete decay rate error must fall by >= 4x per
