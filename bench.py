@@ -62,8 +62,11 @@ def describe(case, prec):
 # the body the Poisson coefficients are uniform and formed from the position,
 # so the multigrid kernels move no coefficient arrays there (body tiles, a
 # small fraction, also read them: not counted, so the figure is a lower bound).
-def algo_bytes(name, T, nd, has_body=False):
+def algo_bytes(name, T, nd, has_body=False, const_diag=False):
+    """const_diag: a body-free grid with every axis periodic, where every cell
+    has the same Jacobi diagonal and the kernels do not read 1/D."""
     m1 = nd * nd
+    d = 0 if const_diag else 1
     return {
         "flux_pred": 2 * nd * T, "flux_pred_f": 2 * nd * T,
         "flux_corr": 3 * nd * T, "flux_corr_f": 3 * nd * T,
@@ -71,10 +74,10 @@ def algo_bytes(name, T, nd, has_body=False):
         "div": (nd + 2) * T,                          # u -> b (pair)
         "resid": (4 + 1 + 1 / 2 ** nd) * T,           # ph, pl, b, bl -> r, coarse r
         "restrict": (2 ** nd + 1) * T,                # per coarse cell
-        "pcg_init": (1 / 2 ** nd + 1 + 1 + 2) * T,    # xc, r, 1/D -> x, s
+        "pcg_init": (1 / 2 ** nd + 1 + d + 2) * T,    # xc, r, (1/D) -> x, s
         "pcg_dq1": 3 * T,                             # s -> d, q (first iteration)
         "pcg_dq": 4 * T,                              # s, d_old -> d, q
-        "pcg_u": 7 * T,                               # x, d, s, q, 1/D -> x, s
+        "pcg_u": (6 + d) * T,                         # x, d, s, q, (1/D) -> x, s
         "pcg_u_last": 3 * T,                          # x, d -> x
         "pcg_u_last_fine": 6 * T,                     # x, d, ph, pl -> ph, pl
         "grad": (2 + 2 * nd) * T,                     # ph, pl, u -> u
@@ -280,12 +283,13 @@ def main():
             sim.mom_step()
         rows = sim.profile_report()
         sim.profile(False)
+        cdiag = case.body.kind == "none" and all(case.periodic[:case.ndim])
         tot = sum(r[3] for r in rows)
         by = {}
         for nm, lv, n, tms, cells in rows:
             by.setdefault(nm, [0.0, 0, 0.0])
             by[nm][0] += tms
-            b = algo_bytes(nm, 4 if prec == "f32" else 8, case.ndim, case.body.kind != "none")
+            b = algo_bytes(nm, 4 if prec == "f32" else 8, case.ndim, case.body.kind != "none", cdiag)
             if b is not None:
                 by[nm][2] += b * cells * n
             by[nm][1] += n
@@ -298,7 +302,7 @@ def main():
                 algo_bytes(nm, 4, case.ndim) is not None]
         top = max(fine, key=lambda r: r[3])
         nm, lv, n, tms, cells = top
-        bpl = algo_bytes(nm, 4 if prec == "f32" else 8, case.ndim, case.body.kind != "none") * cells
+        bpl = algo_bytes(nm, 4 if prec == "f32" else 8, case.ndim, case.body.kind != "none", cdiag) * cells
         ach = bpl / (tms / n / 1000) / 1e9
         roof = {"bound": "hbm", "kernel": f"{nm} (fine level)", "achieved": round(ach, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": src,

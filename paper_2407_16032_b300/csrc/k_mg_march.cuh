@@ -82,7 +82,11 @@ __device__ __forceinline__ void pcg_dq_run(const LevelD<T> &L, const T *__restri
     constexpr int TZ = MT<NDIM>::TZ;
     constexpr int PZ = NDIM == 3 ? TZ + 2 : 1;   // planes held (with the z ring)
     constexpr int Z0 = NDIM == 3 ? 1 : 0;        // smem plane of the tile's first plane
-    __shared__ T sd[PZ][10][34];
+    // two shared tiles, used by alternate tiles of the block: a tile's writes
+    // reuse a buffer last read two tiles ago, before the previous tile's
+    // barrier, so one barrier per tile suffices
+    __shared__ T sdb[2][PZ][10][34];
+    int tpar = 0;
     __shared__ T idtab[8];
     const GridD &g = L.g;
     const T beta = FIRST ? T(0) : (T)S->beta[lev];
@@ -151,7 +155,8 @@ __device__ __forceinline__ void pcg_dq_run(const LevelD<T> &L, const T *__restri
             }
         }
         const int NRP = NDIM == 3 ? 2 : 1;              // row planes per thread
-        __syncthreads();   // the previous tile's readers of sd are done
+        T(*sd)[10][34] = sdb[tpar];
+        tpar ^= 1;
         int kz[PZ];
 #pragma unroll
         for (int t = 0; t < PZ; ++t) kz[t] = NDIM == 3 ? edge_idx(zb - 1 + t, g.n[2], pz) : 0;
@@ -260,9 +265,11 @@ __device__ __forceinline__ void pcg_init_run(const LevelD<T> &L, const GridD &gc
         const int zb = NDIM == 3 ? z0 : 0, ze = NDIM == 3 ? min(z0 + MT<NDIM>::TZ, g.n[2]) : 1;
         constexpr int TZ = MT<NDIM>::TZ;
         constexpr int PZ = NDIM == 3 ? TZ + 2 : 1;
-        // uniform tile away from every non-periodic domain face
+        // uniform tile away from every non-periodic domain face: every cell
+        // has 2n faces of coefficient cu
         const bool plain = uni && (g.per[0] || (x0 > 0 && x0 + 32 < g.n[0])) &&
                            (g.per[1] || (y0 > 0 && y0 + 8 < g.n[1])) && (NDIM == 2 || pz || (zb > 0 && ze < g.n[2]));
+        const T idc = T(-1) / (T(2 * NDIM) * L.cu);
         const T *__restrict__ rr = L.r;
         const T *__restrict__ id = L.invD;
         const T *__restrict__ xcr = xc;
@@ -282,7 +289,7 @@ __device__ __forceinline__ void pcg_init_run(const LevelD<T> &L, const GridD &gc
             if (zb + t < ze) {
                 const int idx = c.i + g.n[0] * (c.j + g.n[1] * (zb + t));
                 rv[t] = rr[idx];
-                iv[t] = id[idx];
+                iv[t] = plain ? idc : id[idx];
                 const int cb = cbase + cplane * (NDIM == 3 ? ((zb + t) >> 1) : 0);
                 xn[t] = cxn ? xcr[cb + cxn] : T(0);
                 yn[t] = cyn ? xcr[cb + cyn] : T(0);

@@ -50,6 +50,7 @@ template <typename T> struct LevelD {
     T *d[2];
     const unsigned char *tflag;
     T cu;    // fluid face coefficient of this level
+    T iduni; // 1/D of every cell when the level has no body and only periodic axes, else 0
     Tiles tl;
 };
 
@@ -395,9 +396,18 @@ __device__ __forceinline__ void pcg_u_run(const LevelD<T> &L, const T *dcur, T *
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     const long long stride = (long long)gridDim.x * nthr;
     const long long t0 = blockIdx.x * (long long)nthr + tid;
+    const T idc = L.iduni;
     for (long long v = t0; v < nv; v += stride) {
         VT x = ((VT *)L.x)[v], d = ((const VT *)dcur)[v], s = ((VT *)L.s)[v], q = ((const VT *)L.q)[v];
-        VT iD = ((const VT *)L.invD)[v];
+        VT iD;
+        if (idc != T(0) || LAST) {
+            // (a constant diagonal; the last update does not use it)
+            T *ie = (T *)&iD;
+#pragma unroll
+            for (int e = 0; e < W; ++e) ie[e] = idc;
+        } else {
+            iD = ((const VT *)L.invD)[v];
+        }
         VT h, l;
         if (LAST && FINE) { h = ((VT *)ph)[v]; l = ((VT *)pl)[v]; }
         T *xe = (T *)&x, *se = (T *)&s, *he = (T *)&h, *le = (T *)&l;

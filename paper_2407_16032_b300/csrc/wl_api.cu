@@ -326,6 +326,10 @@ struct Sim : SimBase {
             tfl[l] = alloc_n<unsigned char>(L.tl.nt);
             L.tflag = tfl[l];
             L.cu = (T)std::pow(2.0, (double)l * (ND - 2));
+            // no body and every axis periodic: every cell has 2n faces of cu
+            bool allper = true;
+            for (int a = 0; a < g.ndim; ++a) allper = allper && g.per[a];
+            L.iduni = (!has_body && allper) ? (T)(-1.0 / (2.0 * ND * (double)L.cu)) : T(0);
         }
         cw = alloc_n<double>(4 * gl[nlev - 1].nc);
 
