@@ -11,6 +11,7 @@
 #include "k_body.cuh"
 #include "k_poisson.cuh"
 #include "k_mg_march.cuh"
+#include "k_resid.cuh"
 #include "k_misc.cuh"
 #include "k_net.cuh"
 #include "k_adjoint.cuh"
