@@ -181,6 +181,23 @@ def cpu_baseline(sample_n=96, steps=1):
                       f"FP64 single-threaded C, MG to 1e-6; {dt:.1f} s"}
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of one host number over all ranks (x itself on one
+    rank): the job takes as long as its slowest replica."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ncell, steps, world, seconds):
+    """Whole-job throughput of `world` replicas: the cell-steps all ranks made
+    over the slowest rank's time."""
+    return ncell * steps * world / seconds
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -199,7 +216,8 @@ def run_reference(args, rank, world):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (analytic Taylor-Green initial field)",
-           "config": describe(workload(args.workload), "fp32") | {
+           "config": describe(workload(args.workload),
+                              args.precision or ("f64" if args.workload == "circle" else "f32")) | {
                "reference_sample": "each step: one oracle step of TGV 64^3 (same Re), host cores"},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": "TGV 64^3 per step, FP64 single-threaded C oracle"},
@@ -269,11 +287,8 @@ def main():
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
     _, l1 = sim.info()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = case.ncell * args.steps * world / (ms / 1000.0)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = job_rate(case.ncell, args.steps, world, ms / 1000.0)
 
     # ---- roofline of the dominant kernel: per-kernel CUDA-event timing pass
     roof, kernels = None, []
@@ -413,12 +428,9 @@ def main():
             sim.get_velocity(hu, hue)       # D2H of the step's result field
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(el, dist, "cuda")
         nb = hu.numel() * hu.element_size() + (hue.numel() * hue.element_size() if case.exit_hi_x else 0)
-        e2e = {"value": case.ncell * n_e2e * world / el, "unit": UNIT, "h2d_bytes_per_step": nb,
+        e2e = {"value": job_rate(case.ncell, n_e2e, world, el), "unit": UNIT, "h2d_bytes_per_step": nb,
                "d2h_bytes_per_step": nb + 96}
 
     if rank == 0:

@@ -226,7 +226,8 @@ WL_API int wl_profile_report(wl_sim *sim, char *buf, size_t len, size_t *needed)
  * on multigrid level `level` (1/2^level of each axis): it maps the restricted
  * residual of the warm start to a coarse pressure correction, which is added to
  * the pressure by injection before the V-cycles; the V-cycles then converge to
- * the same tolerance (plain multigrid stays the judge of the error).
+ * the same tolerance (the guess only changes where they start, never when
+ * they stop).
  * Convolutions run on BF16 tensor cores (mma.sync) with FP32 accumulation;
  * weights are kept in FP32 (Adam) and copied to BF16.
  *   wl_guess_setup: allocate the network and room for `capacity` samples.
@@ -251,8 +252,8 @@ WL_API int wl_guess_info(wl_sim *sim, int *level, int *samples, double *gain);
  * H1, H2 the stage's last two converged pressures, Ho the other stage's latest
  * (w = (0, 1) is the plain warm start from the previous projection). It
  * replaces the warm start of each wl_mom_step projection once two steps of
- * history exist; the V-cycles then converge to the same tolerance (plain
- * multigrid stays the judge of the error). When both learned guesses are on,
+ * history exist; the V-cycles then converge to the same tolerance (the guess
+ * only changes where they start). When both learned guesses are on,
  * this one is applied first and the network's coarse correction after it.
  *   wl_tguess_mode: collect != 0 gathers, at every converged projection, the
  *     normal equations of the weights' least-squares fit in the residual norm

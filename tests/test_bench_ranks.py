@@ -1,0 +1,66 @@
+"""Host logic of the bench's multi-rank run, on CPU with the gloo backend.
+
+The time step does not shard without a halo exchange, so N GPUs run N
+independent replicas: each rank times its own steps, the job's time is the
+slowest rank's, and the reported value is the cell-steps of all ranks over that
+time. These tests run that reduction in two gloo processes (no GPU), and check
+that the reference arm does its work on rank 0 only.
+"""
+import argparse
+import os
+import socket
+
+import pytest
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _replica(rank, world, port, times_ms, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms = bench.max_over_ranks(times_ms[rank], dist, "cpu")
+        q.put((rank, ms, bench.job_rate(1000, 10, world, ms / 1000.0)))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("times_ms", [(12.5, 17.25), (30.0, 4.0)])
+def test_two_replicas_report_the_slowest_rank_and_the_whole_job(times_ms):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_replica, args=(r, 2, port, times_ms, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        got = sorted(q.get(timeout=120) for _ in range(2))
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+    assert [p.exitcode for p in procs] == [0, 0]
+    slowest = max(times_ms)
+    for rank, (r, ms, v) in enumerate(got):
+        assert r == rank
+        assert ms == slowest                       # every rank agrees on the job's time
+        assert v == pytest.approx(2 * 1000 * 10 / (slowest / 1000.0))   # cells of both replicas
+
+
+def test_single_rank_reduction_is_the_identity():
+    assert bench.max_over_ranks(3.25, None, "cpu") == 3.25
+    assert bench.job_rate(16, 4, 1, 2.0) == 32.0
+
+
+def test_reference_arm_runs_on_rank_zero_only(capsys):
+    args = argparse.Namespace(gpus=2, steps=1, warmup=0, workload="tgv256", precision=None)
+    assert bench.run_reference(args, rank=1, world=2) == 0
+    assert capsys.readouterr().out == ""
