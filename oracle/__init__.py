@@ -85,6 +85,7 @@ def lib():
             ("orc_project", [C.POINTER(Grid), _P, _P, _P, _P, C.c_double, C.c_double, C.POINTER(Solver), C.POINTER(Stats)], C.c_int),
             ("orc_cfl", [C.POINTER(Grid), _P, _P, C.c_double, C.c_double], C.c_double),
             ("orc_forces", [C.POINTER(Grid), C.POINTER(BodyS), C.c_double, _P, _P], None),
+            ("orc_forces_viscous", [C.POINTER(Grid), C.POINTER(BodyS), C.c_double, _P, _P, _P], None),
             ("orc_step", [C.POINTER(Grid), C.POINTER(BodyS), C.c_double, C.c_double, _P, _P, _P, C.POINTER(Solver), C.POINTER(Stats)], C.c_int),
             ("orc_diagnostics", [C.POINTER(Grid), _P, _P, _P, _P], None),
             ("orc_conv_diff_vjp", [C.POINTER(Grid), _P, _P, _P, _P, _P], None),
@@ -276,6 +277,13 @@ def cfl(g, u, ue, cfl=1.0, dt_max=1.0):
 def forces(g, body_s, t, p):
     F = np.zeros(3)
     lib().orc_forces(C.byref(g), C.byref(body_s), float(t), _p(_d(p)), _p(F))
+    return F
+
+
+def forces_viscous(g, body_s, t, u, ue):
+    """Viscous force nu sum_I K (grad u + grad u^T) . n at the cell centres."""
+    F = np.zeros(3)
+    lib().orc_forces_viscous(C.byref(g), C.byref(body_s), float(t), _p(_d(u)), _p(_d(ue)), _p(F))
     return F
 
 

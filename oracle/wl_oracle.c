@@ -743,6 +743,51 @@ void orc_forces(const orc_grid *g, const orc_body *B, double t, const double *p,
             }
 }
 
+/* Viscous force on the body (Sec. 5 reports drag; the paper prints no force
+ * formula). Reading: the viscous traction nu (grad u + grad u^T) . n of the
+ * stress on the body surface, n = grad d pointing into the fluid (the same
+ * orientation as the pressure part -p n), spread over the kernel band:
+ *   F_a = nu sum_I K_eps(d(x_I)) sum_b S_ab(x_I) n_b(x_I),  S = grad u + grad u^T,
+ * the velocity gradient at the cell centre x_I from the face samples:
+ *   d_a u_a = u_a[I+e_a] - u_a[I],
+ *   d_b u_a = (u_a[I+e_b] + u_a[I+e_a+e_b] - u_a[I-e_b] - u_a[I+e_a-e_b]) / 4  (b != a),
+ * samples beyond the stored range by the boundary rule of su. */
+static double centre_grad(const orc_grid *g, const double *u, const double *ue, int a, int b, int i, int j, int k)
+{
+    int A[3] = {0, 0, 0}, Bv[3] = {0, 0, 0};
+    A[a] = 1;
+    Bv[b] = 1;
+    if (a == b) return su(g, u, ue, a, i + A[0], j + A[1], k + A[2]) - su(g, u, ue, a, i, j, k);
+    double up = su(g, u, ue, a, i + Bv[0], j + Bv[1], k + Bv[2]) +
+                su(g, u, ue, a, i + A[0] + Bv[0], j + A[1] + Bv[1], k + A[2] + Bv[2]);
+    double dn = su(g, u, ue, a, i - Bv[0], j - Bv[1], k - Bv[2]) +
+                su(g, u, ue, a, i + A[0] - Bv[0], j + A[1] - Bv[1], k + A[2] - Bv[2]);
+    return 0.25 * (up - dn);
+}
+
+void orc_forces_viscous(const orc_grid *g, const orc_body *B, double t, const double *u, const double *ue, double *F)
+{
+    F[0] = F[1] = F[2] = 0.0;
+    if (B->kind == 0) return;
+    for (int k = 0; k < g->n[2]; ++k)
+        for (int j = 0; j < g->n[1]; ++j)
+            for (int i = 0; i < g->n[0]; ++i) {
+                double x[3] = {i + 0.5, j + 0.5, k + 0.5};
+                double d, nrm[3], v[3];
+                orc_body_eval(B, g->ndim, x, t, &d, nrm, v);
+                double K = orc_kernel(d, g->eps);
+                if (K == 0.0) continue;
+                double G[3][3] = {{0.0}};   /* G[a][b] = d_b u_a */
+                for (int a = 0; a < g->ndim; ++a)
+                    for (int b = 0; b < g->ndim; ++b) G[a][b] = centre_grad(g, u, ue, a, b, i, j, k);
+                for (int a = 0; a < g->ndim; ++a) {
+                    double tr = 0.0;
+                    for (int b = 0; b < g->ndim; ++b) tr += (G[a][b] + G[b][a]) * nrm[b];
+                    F[a] += g->nu * K * tr;
+                }
+            }
+}
+
 /* Derivative of the force component `axis` with respect to each cell's
  * pressure: the force is linear in p, dF_axis/dp_I = -n_axis(x_I) K_eps(d(x_I)). */
 void orc_force_dp(const orc_grid *g, const orc_body *B, double t, int axis, double *out)

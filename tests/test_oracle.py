@@ -436,6 +436,52 @@ def test_pressure_force_invariants():
     assert F3[2] == pytest.approx(-1.3 * 4 / 3 * math.pi * 8.0**3, rel=5e-3)
 
 
+def test_viscous_force_closed_forms():
+    # the viscous traction nu (grad u + grad u^T) . n over the body:
+    # * rigid motion (translation + rotation) has no strain: F = 0 to rounding;
+    # * a linear field u = M x has constant strain, so F = nu (M + M^T) sum K n,
+    #   and sum K n vanishes over a closed surface (O(h^2));
+    # * u_x = gam y^2 has strain 2 gam y in the xy pair, so by the divergence
+    #   theorem F_x = 2 nu gam * area (the body's volume in 3D), F_y ~ 0;
+    #   u_x = gam x^2 has normal strain 4 gam x, F_x = 4 nu gam * area.
+    nu, R = 0.05, 10.0
+    g = oracle.make_grid(2, (64, 64, 1), (False,) * 3, nu=nu)
+    bs = oracle.make_body(synth.Body("sphere", (31.3, 32.6, 0), R))
+    ue = np.zeros(64)
+    X = [face_coords(2, (64, 64), a) for a in range(2)]
+    om, x0, y0 = 0.37, 20.0, 41.0
+    u = np.stack([1.3 - om * (X[0][1] - y0), -0.4 + om * (X[1][0] - x0)])
+    assert np.abs(oracle.forces_viscous(g, bs, 0.0, u, ue)).max() < 1e-12
+    M = np.array([[0.2, 0.5], [-0.1, -0.2]])
+    u = np.stack([M[0, 0] * X[0][0] + M[0, 1] * X[0][1], M[1, 0] * X[1][0] + M[1, 1] * X[1][1]])
+    F = oracle.forces_viscous(g, bs, 0.0, u, ue)
+    assert np.abs(F).max() < 1e-3 * nu * np.abs(M + M.T).max() * 2 * math.pi * R
+    gam = 0.02
+    u = np.stack([gam * X[0][1] ** 2, np.zeros((64, 64))])
+    F = oracle.forces_viscous(g, bs, 0.0, u, ue)
+    assert F[0] == pytest.approx(2 * nu * gam * math.pi * R * R, rel=5e-3)
+    assert abs(F[1]) < 1e-2 * abs(F[0])
+    # u_x = gam x^2: the normal strain 2 d_x u_x = 4 gam x -> F_x = 4 nu gam * area
+    u = np.stack([gam * X[0][0] ** 2, np.zeros((64, 64))])
+    F = oracle.forces_viscous(g, bs, 0.0, u, ue)
+    assert F[0] == pytest.approx(4 * nu * gam * math.pi * R * R, rel=5e-3)
+    assert abs(F[1]) < 1e-2 * abs(F[0])
+    # 3D sphere: u_x = gam z^2 -> F_x = 2 nu gam (4/3) pi R^3; a rotation -> 0
+    n3 = (40, 40, 40)
+    g3 = oracle.make_grid(3, n3, (False,) * 3, nu=nu)
+    bs3 = oracle.make_body(synth.Body("sphere", (19.6, 20.3, 20.1), 8.0))
+    X3 = [face_coords(3, n3, a) for a in range(3)]
+    u3 = np.stack([gam * X3[0][2] ** 2, np.zeros(n3), np.zeros(n3)])
+    F3 = oracle.forces_viscous(g3, bs3, 0.0, u3, np.zeros(40 * 40))
+    assert F3[0] == pytest.approx(2 * nu * gam * 4 / 3 * math.pi * 8.0**3, rel=5e-3)
+    assert np.abs(F3[1:]).max() < 1e-2 * abs(F3[0])
+    w = np.array([0.1, -0.3, 0.2])   # u = w x (x - c)
+    c = np.array([15.0, 22.0, 18.0])
+    r = [[X3[a][b] - c[b] for b in range(3)] for a in range(3)]
+    u3 = np.stack([w[1] * r[0][2] - w[2] * r[0][1], w[2] * r[1][0] - w[0] * r[1][2], w[0] * r[2][1] - w[1] * r[2][0]])
+    assert np.abs(oracle.forces_viscous(g3, bs3, 0.0, u3, np.zeros(40 * 40))).max() < 1e-12
+
+
 def test_diagnostics_closed_form_on_2d_tgv():
     N = 24
     case = synth.Case("t", 2, (N, N, 1), (True, True, False), False, (0, 0, 0), 0.01, init="tgv2d")
