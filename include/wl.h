@@ -191,6 +191,18 @@ WL_API int wl_conv_diff(wl_sim *sim, const void *u, const void *ue, void *r);
  * was last measured. F: 3 doubles (host). */
 WL_API int wl_forces(wl_sim *sim, double *F);
 
+/* Viscous force on the body (the paper prints no force formula; Sec. 5 reports
+ * drag): the traction nu (grad u + grad u^T) . n of the viscous stress, spread
+ * over the kernel band like the pressure force,
+ *   F_a = nu sum_I K_eps(d(x_I)) sum_b S_ab(x_I) n_b(x_I),  S = grad u + grad u^T,
+ * with the gradient at the cell centre from the face samples (d_a u_a =
+ * u_a[I+e_a] - u_a[I]; d_b u_a the mean of the two central differences of the
+ * faces I and I+e_a, b != a). n = grad d points into the fluid, so the total
+ * force on the body is wl_forces + wl_forces_viscous. Uses the current velocity
+ * and the body at the time it was last measured. F: 3 doubles (host); 0 without
+ * a body. */
+WL_API int wl_forces_viscous(wl_sim *sim, double *F);
+
 /* Measure the body at time t onto the faces (mu0, mu1 n, V) and rebuild the
  * multigrid coefficients (Sec. 2 / Sec. 3 measure of AutoBody). */
 WL_API int wl_body_update(wl_sim *sim, double t);

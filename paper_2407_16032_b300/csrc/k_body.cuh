@@ -207,3 +207,68 @@ __global__ void k_forces(GridD g, BodyState B, const T *ph, const T *pl, const T
         if (threadIdx.x == 0) { S->red[0] = out[0]; S->red[1] = out[1]; S->red[2] = out[2]; }
     }
 }
+
+// Viscous force F_a = nu sum_I K_eps(d(x_I)) sum_b S_ab(x_I) n_b(x_I) over cell
+// centres: the viscous part of the stress traction on the body (n = grad d
+// points into the fluid, as in the pressure part), S = grad u + grad u^T at the
+// centre from the face samples,
+//   d_a u_a = u_a[I+e_a] - u_a[I],
+//   d_b u_a = ((u_a[I+e_b] + u_a[I+e_a+e_b]) - (u_a[I-e_b] + u_a[I+e_a-e_b])) / 4  (b != a),
+// samples beyond the stored range by the boundary rule of vel_sample.
+template <typename T>
+__global__ void k_forces_visc(GridD g, BodyState B, CVec3P<T> u, const T *ue, DevScalars *S, double *part) {
+    const T eps = (T)B.eps;
+    T acc[3] = {T(0), T(0), T(0)};
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nc;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        decode(g, idx, i, j, k);
+        T px[3] = {T(i) + T(0.5), T(j) + T(0.5), T(k) + T(0.5)};
+        T d, nrm[3], v[3];
+        body_eval<T>(B, g.ndim, px, d, nrm, v);
+        if (!(d > -eps - T(0.5) && d < eps + T(0.5))) continue;
+        double pd[3] = {i + 0.5, j + 0.5, k + 0.5}, dd, nd[3], vd[3];
+        body_eval<double>(B, g.ndim, pd, dd, nd, vd);
+        const double K = kkernel<double>(dd, B.eps);
+        if (K == 0.0) continue;
+        T G[3][3];   // G[a][b] = d_b u_a
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                G[a][b] = T(0);
+                if (a >= g.ndim || b >= g.ndim) continue;
+                const T *ua = u.p[a];
+                if (a == b) {
+                    int P[3] = {i, j, k};
+                    P[a] += 1;
+                    G[a][b] = vel_sample<T>(g, ua, ue, a, P[0], P[1], P[2]) - vel_sample<T>(g, ua, ue, a, i, j, k);
+                } else {
+                    int q1[3] = {i, j, k}, q2[3] = {i, j, k}, q3[3] = {i, j, k}, q4[3] = {i, j, k};
+                    q1[b] += 1;              // I + e_b
+                    q2[a] += 1; q2[b] += 1;  // I + e_a + e_b
+                    q3[b] -= 1;              // I - e_b
+                    q4[a] += 1; q4[b] -= 1;  // I + e_a - e_b
+                    const T up = vel_sample<T>(g, ua, ue, a, q1[0], q1[1], q1[2]) +
+                                 vel_sample<T>(g, ua, ue, a, q2[0], q2[1], q2[2]);
+                    const T dn = vel_sample<T>(g, ua, ue, a, q3[0], q3[1], q3[2]) +
+                                 vel_sample<T>(g, ua, ue, a, q4[0], q4[1], q4[2]);
+                    G[a][b] = T(0.25) * (up - dn);
+                }
+            }
+        const T nuK = (T)(g.nu * K);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (a >= g.ndim) continue;
+            T tr = T(0);
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                if (b < g.ndim) tr += (G[a][b] + G[b][a]) * (T)nd[b];
+            acc[a] += nuK * tr;
+        }
+    }
+    double out[3];
+    if (grid_reduce<3, false, T>(acc, part, &S->counters[RS_FORCE], out)) {
+        if (threadIdx.x == 0) { S->red[0] = out[0]; S->red[1] = out[1]; S->red[2] = out[2]; }
+    }
+}

@@ -64,6 +64,7 @@ struct SimBase {
     virtual int poisson_solve(const void *b, double *p, wl_solve_stats *st) = 0;
     virtual void conv_diff(const void *u, const void *ue, void *r) = 0;
     virtual void forces(double *F) = 0;
+    virtual void forces_viscous(double *F) = 0;
     virtual void body_update(double t) = 0;
     virtual void get_body_fields(void *c, void *mu1n, void *V) = 0;
     virtual void diagnostics(double *ke, double *ens, double *maxdiv) = 0;
@@ -938,6 +939,18 @@ struct Sim : SimBase {
         F[2] = hS->red[2];
     }
 
+    void forces_viscous(double *F) override {
+        F[0] = F[1] = F[2] = 0.0;
+        if (!has_body) return;
+        k_forces_visc<T><<<blocks(g.nc), 256, 0, st>>>(g, body_state(body_t), cv(cur), ueA, S, part);
+        WL_LAUNCH_CK();
+        ++launches;
+        read_scalars();
+        F[0] = hS->red[0];
+        F[1] = hS->red[1];
+        F[2] = hS->red[2];
+    }
+
     void diagnostics(double *ke, double *ens, double *maxdiv) override {
         k_diag<T><<<blocks(g.nc), 256, 0, st>>>(g, cv(cur), ueA, lv[0].invD, S, part);
         WL_LAUNCH_CK();
@@ -1793,6 +1806,10 @@ int wl_conv_diff(wl_sim *s, const void *u, const void *ue, void *r) {
 int wl_forces(wl_sim *s, double *F) {
     if (!F) return WL_ERR_ARG;
     return guard(s, [&] { s->impl->forces(F); return (int)WL_OK; });
+}
+int wl_forces_viscous(wl_sim *s, double *F) {
+    if (!F) return WL_ERR_ARG;
+    return guard(s, [&] { s->impl->forces_viscous(F); return (int)WL_OK; });
 }
 int wl_body_update(wl_sim *s, double t) {
     return guard(s, [&] { s->impl->body_update(t); return (int)WL_OK; });

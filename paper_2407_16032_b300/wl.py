@@ -24,7 +24,7 @@ BODY_KIND = {"none": 0, "sphere": 1, "ellipse": 2, "cylinder": 3}
 EXPORTS = (
     "wl_config_default", "wl_sim_create", "wl_sim_destroy", "wl_set_velocity", "wl_get_velocity",
     "wl_get_pressure", "wl_set_pressure", "wl_set_time", "wl_get_time", "wl_mom_step", "wl_project",
-    "wl_poisson_solve", "wl_conv_diff", "wl_forces", "wl_body_update", "wl_get_body_fields",
+    "wl_poisson_solve", "wl_conv_diff", "wl_forces", "wl_forces_viscous", "wl_body_update", "wl_get_body_fields",
     "wl_diagnostics", "wl_info", "wl_profile", "wl_profile_report", "wl_coarse_solve_static", "wl_guess_setup",
     "wl_guess_mode", "wl_guess_train", "wl_guess_weights", "wl_guess_info", "wl_net_eval", "wl_step_vjp",
     "wl_force_dp", "wl_window_forward", "wl_window_backward", "wl_set_body", "wl_tguess_mode", "wl_tguess_fit",
@@ -87,6 +87,7 @@ def lib() -> C.CDLL:
             "wl_poisson_solve": ([vp, vp, vp, C.POINTER(SolveStats)], ip),
             "wl_conv_diff": ([vp, vp, vp, vp], ip),
             "wl_forces": ([vp, dp], ip),
+            "wl_forces_viscous": ([vp, dp], ip),
             "wl_body_update": ([vp, C.c_double], ip),
             "wl_get_body_fields": ([vp, vp, vp, vp], ip),
             "wl_diagnostics": ([vp, dp, dp, dp], ip),
@@ -301,6 +302,12 @@ class Sim:
     def forces(self):
         F = (C.c_double * 3)()
         self._check(lib().wl_forces(self._h, F), "wl_forces")
+        return np.array(F[:])
+
+    def forces_viscous(self):
+        """Viscous force nu sum_I K (grad u + grad u^T) . n on the body."""
+        F = (C.c_double * 3)()
+        self._check(lib().wl_forces_viscous(self._h, F), "wl_forces_viscous")
         return np.array(F[:])
 
     def body_update(self, t):

@@ -173,6 +173,36 @@ def test_config5_moving_sphere_reduced_fp32_1_and_10_steps():
     assert np.abs(F - F_or).max() < tp * max(np.abs(F_or).max(), 1.0)
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("which", ["circle2d", "sphere3d", "ellipse_moving"])
+def test_viscous_force_matches_oracle(which, prec):
+    # the same velocity on both sides (the oracle's after 3 steps, rounded to
+    # the GPU's precision), the body at the same time: the viscous force of
+    # the kernel band against the oracle's. Bar: every cell's term is nu K S.n
+    # with S a sum of at most 2n differences of velocity samples, each off by
+    # at most 2 eps max|u|; summed over the band (sum K ~ the surface measure)
+    # that is 16 n eps nu max|u| * surface, eps the unit roundoff.
+    case = {"circle2d": synth.config1_circle((96, 48)).with_(body=synth.Body("sphere", (24.3, 23.6, 0.0), 6.0)),
+            "sphere3d": synth.config3_sphere((48, 24, 24), D=10.0, centre=(14.2, 12.3, 11.8)),
+            "ellipse_moving": synth.config4_ellipse((256, 128), chord=32.0, A=8.0, centre=(64.0, 64.0))}[which]
+    orc, sim, st = run_pair(case, 3, prec)
+    u, ue = orc.u.copy(), orc.ue.copy()
+    if prec == "f32":
+        u, ue = u.astype(np.float32).astype(np.float64), ue.astype(np.float32).astype(np.float64)
+    sim.set_velocity(_t(u, prec), _t(ue, prec))
+    F = sim.forces_viscous()
+    F_or = oracle.forces_viscous(orc.g, orc.b, orc.t, u, ue)
+    b = case.body
+    surf = {"circle2d": 2 * math.pi * b.radius, "sphere3d": 4 * math.pi * b.radius ** 2,
+            "ellipse_moving": 2 * math.pi * max(b.semi)}[which]
+    eps = 2.0 ** -24 if prec == "f32" else 2.0 ** -53
+    bar = 16 * case.ndim * eps * case.nu * np.abs(u).max() * surf
+    assert np.abs(F_or).max() > 100 * bar                     # a force well above the bar
+    assert np.abs(F - F_or).max() <= bar, (F, F_or, bar)
+    F_p = sim.forces()                                         # the pressure force is untouched
+    assert np.abs(F_p - oracle.forces(orc.g, orc.b, orc.t, orc.P)).max() < 1e-4 * max(np.abs(F_p).max(), 1.0)
+
+
 def test_moving_cylinder_benchmark_reduced_fp32_1_and_10_steps():
     # the paper's moving-cylinder benchmark shape (9L x 6L x 2L, spanwise
     # periodic, Re 1000 on D = L) at L = 8
