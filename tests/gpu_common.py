@@ -78,17 +78,25 @@ def flux_err(p, P, c, ndim):
     return e / ref
 
 
-def oracle_sensitivity(case, steps, amp=1e-7, seed=9):
-    """The oracle's own response to an absolute perturbation `amp` of the
-    initial velocity after `steps` steps (FP64 both runs): the amplification an
-    FP32 implementation's per-step rounding meets on this input."""
+def oracle_rounding_response(case, steps, amp=1e-7, seed=9):
+    """The oracle's own response after `steps` steps (FP64 throughout) to
+    (i) an absolute perturbation `amp` of the initial velocity, and (ii) its
+    velocity and exit plane rounded to FP32 after every step (the storage
+    rounding an FP32 implementation cannot avoid). Returns (u_start, p_start,
+    u_store, p_store): relative max-norm change of u and p_err change of p."""
     u, ue = start_fields(case, "f32")
     rng = np.random.default_rng(seed)
     a = oracle.Sim(case, tol=1e-11, u=u, ue=ue)
     b = oracle.Sim(case, tol=1e-11, u=u + amp * rng.uniform(-1, 1, size=u.shape), ue=ue)
+    r = oracle.Sim(case, tol=1e-11, u=u, ue=ue)
     for _ in range(steps):
         d = a.dt
         a.step(d)
         b.step(d)
+        r.step(d)
+        r.u[...] = r.u.astype(np.float32).astype(np.float64)
+        r.ue[...] = r.ue.astype(np.float32).astype(np.float64)
     c = oracle.coeffs(a.g, oracle.measure(a.g, a.b, a.t)[0] if case.body.kind != "none" else None)
-    return float(np.abs(a.u - b.u).max() / np.abs(a.u).max()), p_err(b.P, a.P, c, case.ndim)
+    un = np.abs(a.u).max()
+    return (float(np.abs(a.u - b.u).max() / un), p_err(b.P, a.P, c, case.ndim),
+            float(np.abs(a.u - r.u).max() / un), p_err(r.P, a.P, c, case.ndim))

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_common import flux_err, gpu_fields, gpu_sim, oracle_sensitivity, p_err, rel_max, run_pair
+from gpu_common import flux_err, gpu_fields, gpu_sim, oracle_rounding_response, p_err, rel_max, run_pair
 
 pytestmark = pytest.mark.gpu
 
@@ -115,11 +115,14 @@ def _compare(orc, sim, tol_u, tol_p):
 
 
 def _calibrated(case, steps=10):
-    """Parity bars (u, p) for inputs whose discrete step amplifies rounding:
-    five times the oracle's own response to a 1e-7 perturbation of the start
-    after the same number of steps, and at least 1e-5."""
-    su, sp = oracle_sensitivity(case, steps)
-    return max(1e-5, 5.0 * su), max(1e-5, 5.0 * sp)
+    """Parity bars (u, p) for inputs whose discrete step amplifies rounding,
+    from the oracle's own responses after the same number of steps: five
+    times its response to a 1e-7 perturbation of the start, three times its
+    response to storing the velocity in FP32 after every step (the FP32 path
+    rounds each stored value once plus a few times inside the step), and at
+    least 1e-5."""
+    su, sp, ru, rp = oracle_rounding_response(case, steps)
+    return max(1e-5, 5.0 * su, 3.0 * ru), max(1e-5, 5.0 * sp, 3.0 * rp)
 
 
 def test_config1_circle_fp64_full_size_10_steps():
