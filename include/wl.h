@@ -187,8 +187,9 @@ WL_API int wl_poisson_solve(wl_sim *sim, const void *b, double *p, wl_solve_stat
 WL_API int wl_conv_diff(wl_sim *sim, const void *u, const void *ue, void *r);
 
 /* Pressure force on the body, F = -sum_I p_I n(x_I) K_eps(d(x_I)) over cell
- * centres (the BDIM kernel-weighted surface integral), at the time the body
- * was last measured. F: 3 doubles (host). */
+ * centres (the BDIM kernel-weighted surface integral), p the pressure with its
+ * mean over active cells removed (as wl_get_pressure reports it), at the time
+ * the body was last measured. F: 3 doubles (host); 0 without a body. */
 WL_API int wl_forces(wl_sim *sim, double *F);
 
 /* Viscous force on the body (the paper prints no force formula; Sec. 5 reports
