@@ -71,3 +71,31 @@ def test_product_package_does_not_reach_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dp, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "liboracle" not in txt, f
+
+
+def test_every_call_on_a_null_simulation_is_rejected_without_a_device():
+    # each entry point that takes a simulation handle answers a NULL handle
+    # (and NULL buffers) with WL_ERR_ARG before any CUDA call; destroy accepts
+    # NULL as a no-op
+    from paper_2407_16032_b300 import build, wl
+    build.build()
+    src = open(os.path.join(ROOT, "include", "wl.h")).read()
+    L = C.CDLL(wl.LIB_PATH)
+    seen = 0
+    for name, params in re.findall(r"WL_API\s+int\s+(wl_\w+)\s*\(([^;]*?)\)\s*;", src, re.S):
+        ps = [p.strip() for p in params.replace("\n", " ").split(",") if p.strip()]
+        if not ps or not ps[0].startswith("wl_sim *"):
+            continue
+        types, args = [], []
+        for p in ps:
+            t = (C.c_void_p if "*" in p else C.c_double if p.startswith("double") else
+                 C.c_size_t if p.startswith("size_t") else C.c_longlong if p.startswith("long long") else
+                 C.c_uint if p.startswith("unsigned") else C.c_int)
+            types.append(t)
+            args.append(None if t is C.c_void_p else 0)
+        f = getattr(L, name)
+        f.argtypes, f.restype = types, C.c_int
+        want = 0 if name == "wl_sim_destroy" else 1     # WL_OK / WL_ERR_ARG
+        assert f(*args) == want, name
+        seen += 1
+    assert seen >= 30
