@@ -99,3 +99,15 @@ def test_every_call_on_a_null_simulation_is_rejected_without_a_device():
         assert f(*args) == want, name
         seen += 1
     assert seen >= 30
+
+
+def test_every_status_code_has_its_own_message():
+    from paper_2407_16032_b300 import wl
+    src = open(os.path.join(ROOT, "include", "wl.h")).read()
+    codes = {int(v) for v in re.findall(r"\bWL_(?:OK|ERR_\w+)\s*=\s*(\d+)", src)}
+    assert codes == set(range(len(codes)))
+    L = wl.lib()
+    msgs = [L.wl_status_string(c).decode() for c in sorted(codes)]
+    assert all(msgs) and len(set(msgs)) == len(msgs)
+    assert L.wl_status_string(max(codes) + 1).decode()          # unknown codes still get a message
+    assert L.wl_last_error(None) is not None
