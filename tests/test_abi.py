@@ -111,3 +111,69 @@ def test_every_status_code_has_its_own_message():
     assert all(msgs) and len(set(msgs)) == len(msgs)
     assert L.wl_status_string(max(codes) + 1).decode()          # unknown codes still get a message
     assert L.wl_last_error(None) is not None
+
+
+def _bad_cases():
+    def cfg(**kw):
+        def f(c, b):
+            for k, v in kw.items():
+                if k in ("n0", "n1", "n2"):
+                    c.n[int(k[1])] = v
+                elif k == "periodic_x":
+                    c.periodic[0] = v
+                else:
+                    setattr(c, k, v)
+        return f
+
+    def body(kind, **kw):
+        def f(c, b):
+            b.kind = kind
+            b.radius = kw.get("radius", 3.0)
+            b.semi[0], b.semi[1] = kw.get("semi", (4.0, 1.0))
+            b.heave_axis = kw.get("heave_axis", 1)
+            if "ndim" in kw:
+                c.ndim = kw["ndim"]
+                c.n[2] = 1 if kw["ndim"] == 2 else c.n[2]
+        return f
+
+    return {
+        "n below 2": cfg(n0=1), "n above 2^20": cfg(n1=(1 << 20) + 1),
+        "2^31 cells": cfg(n0=2048, n1=2048, n2=2048), "precision": cfg(precision=2),
+        "negative nu": cfg(nu=-1.0), "NaN nu": cfg(nu=float("nan")),
+        "exit on a periodic x": cfg(exit_hi_x=1, periodic_x=1), "tol 0": cfg(tol=0.0),
+        "itmax < 0": cfg(itmax=-1), "no smoothing": cfg(smooth_iters=0), "65 smoothing": cfg(smooth_iters=65),
+        "dt_init 0": cfg(dt_init=0.0), "cfl 0": cfg(cfl=0.0), "dt_max 0": cfg(dt_max=0.0),
+        "unknown body": body(4), "cylinder in 2D": body(3, ndim=2), "cylinder radius 0": body(3, radius=0.0),
+        "sphere radius 0": body(1, radius=0.0), "ellipse axis 0": body(2, ndim=2, semi=(4.0, 0.0)),
+        "heave axis 3": body(1, heave_axis=3), "heave axis z in 2D": body(1, ndim=2, heave_axis=2),
+    }
+
+
+@pytest.mark.parametrize("case", sorted(_bad_cases()))
+def test_create_rejects_each_invalid_setting_on_the_host(case):
+    from paper_2407_16032_b300 import wl
+    L = wl.lib()
+    c = wl.Config()
+    L.wl_config_default(C.byref(c), 3, (C.c_int * 3)(16, 12, 8))
+    b = wl.Body()
+    b.kind = 0
+    _bad_cases()[case](c, b)
+    h = C.c_void_p()
+    assert L.wl_sim_create(C.byref(c), C.byref(b), C.byref(h)) == wl.WL_ERR_ARG
+    assert not h.value
+
+
+def test_the_default_configuration_passes_validation():
+    # the control for the table above: without the bad setting, creation gets
+    # past validation (on a machine without a GPU it then fails in CUDA)
+    from paper_2407_16032_b300 import wl
+    L = wl.lib()
+    c = wl.Config()
+    L.wl_config_default(C.byref(c), 3, (C.c_int * 3)(16, 12, 8))
+    b = wl.Body()
+    b.kind = 0
+    h = C.c_void_p()
+    rc = L.wl_sim_create(C.byref(c), C.byref(b), C.byref(h))
+    if rc == wl.WL_OK:
+        L.wl_sim_destroy(h)
+    assert rc != wl.WL_ERR_ARG
