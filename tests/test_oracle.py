@@ -369,6 +369,23 @@ def test_multigrid_level_rule():
     assert oracle.mg_levels(oracle.make_grid(2, (40, 24, 1))) == 3           # 20x12, 10x6
 
 
+def test_multigrid_convergence_is_grid_independent():
+    # the textbook property of multigrid: the V-cycles needed for a fixed
+    # residual reduction do not grow with the grid (a single-level smoother
+    # would need O(N) times more), for periodic and walled boxes in 2D and 3D
+    counts = []
+    for nd, sizes in ((2, (32, 64, 128, 256)), (3, (16, 32, 64))):
+        for N in sizes:
+            n = (N, N, N if nd == 3 else 1)
+            for per in ((True,) * 3, (False,) * 3):
+                g = oracle.make_grid(nd, n, per)
+                p, rc, st = oracle.poisson_solve(g, oracle.coeffs(g, None), synth.random_scalar(5, nd, n),
+                                                 tol=1e-10, itmax=100)
+                assert rc == 0 and st.rel_resid <= 1e-10
+                counts.append(st.vcycles)
+    assert max(counts) <= 14 and max(counts) - min(counts) <= 2, counts
+
+
 def test_projection_leaves_discretely_divergence_free_field():
     case = synth.config1_circle((48, 32)).with_(body=synth.Body("sphere", (14.0, 15.5, 0.0), 5.0))
     g = oracle.grid_from_case(case)
@@ -385,6 +402,11 @@ def test_projection_leaves_discretely_divergence_free_field():
     div = oracle.divergence(g, u1, ue)
     assert np.abs(div).max() < 1e-10
     assert np.abs(oracle.divergence(g, u, ue)).max() > 0.1
+    # a projection is idempotent: projecting the result again changes nothing
+    u2, P2, rc, st = oracle.project(g, c, u1, ue, np.zeros((32, 48)), 1.0, 0.3, tol=1e-13)
+    assert rc == 0
+    assert np.abs(u2 - u1).max() < 1e-10 * np.abs(u1).max()
+    assert np.abs(P2).max() < 1e-8 * np.abs(P).max()
 
 
 # ----------------------------------------------------- exit, CFL, forces -----
