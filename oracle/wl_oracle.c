@@ -116,7 +116,7 @@ static double sc(const orc_grid *g, const double *f, int a, int i, int j, int k)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Flux-limited QUICK face value (Sec. 2: "flux-limited Quick scheme").      */
+/* Flux-limited QUICK face value (Sec. 2: QUICK with a flux limiter).          */
 /* Reading: upwind-biased third-order interpolation (5c + 2d - u)/6 limited  */
 /* by median(phi, c, median(10c - 9u, c, d)), u/c/d being the far-upstream,  */
 /* upstream and downstream samples.                                          */
@@ -345,7 +345,7 @@ static double boundary_outflux(const orc_grid *g, const double *u, const double 
     return q;
 }
 
-/* Convective exit on the upper x face (Sec. 4: "convective outlet").
+/* Convective exit on the upper x face (Sec. 4: convective outflow boundary).
  * Reading: the exit face value obeys du/dt + Ubar du/dx = 0 with a first-order
  * upwind difference against the last interior u_x face, Ubar = U_x, advanced
  * by the same Heun stages as the interior; afterwards a uniform correction
@@ -704,7 +704,7 @@ int orc_project(const orc_grid *g, const double *c, double *u, const double *ue,
     return rc;
 }
 
-/* CFL time step (Sec. 2: "time step adapted to ensure a stable CFL number").
+/* CFL time step (Sec. 2: the time step adapts to keep the CFL number stable).
  * Reading: dt = min(dt_max, cfl / (max_I sum_a [max(0,u_a[I+e_a]) - min(0,u_a[I])] + 5 nu)). */
 double orc_cfl(const orc_grid *g, const double *u, const double *ue, double cfl, double dt_max)
 {

@@ -3,7 +3,7 @@
 #include "wl_common.cuh"
 #include "k_poisson.cuh"
 
-// Convective outlet on the upper x face (Sec. 4: "convective outlet").
+// Convective outlet on the upper x face (Sec. 4: convective outflow boundary).
 // The exit face value follows du/dt + U du/dx = 0 with a first-order upwind
 // difference against the last interior u_x face, advanced by the same Heun
 // stages as the interior:
@@ -53,7 +53,7 @@ __global__ void k_fill(long long n, T v, T *x) {
         x[i] = v;
 }
 
-// CFL time step (Sec. 2: "time step adapted to ensure a stable CFL number"):
+// CFL time step (Sec. 2: the time step adapts to keep the CFL number stable):
 // dt = min(dt_max, cfl / (max_I sum_a [max(0,u_a[I+e_a]) - min(0,u_a[I])] + 5 nu)).
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(256) k_cfl(LevelD<T> L, CVec3P<T> u, const T *ue, double cfl, double dt_max,
