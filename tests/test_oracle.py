@@ -428,6 +428,27 @@ def test_exit_condition_zeroes_net_flux_and_keeps_uniform_flow():
     assert np.allclose(oracle.exit_bc(g, e1, uu, e1, 0.4, 0, None, uu, e1), 1.0, atol=1e-15)
 
 
+def test_exit_update_is_first_order_upwind_up_to_a_uniform_shift():
+    # du/dt + U du/dx = 0 on the exit plane, upwind against the last interior
+    # u_x face, one Heun stage at a time; the mass correction only adds the
+    # same constant to every exit face, so the mean-free part of the result is
+    # the closed form of the upwind update
+    n = (12, 7, 5)
+    Ux, dt = 1.3, 0.4
+    g = oracle.make_grid(3, n, (False,) * 3, True, (Ux, 0, 0), nu=0.01)
+    u = synth.random_field(4, 3, n, 0.3, (1.0, 0, 0))
+    last = u[0][:, :, n[0] - 1].ravel()          # plane index j + n1 k
+    ue0 = 1.0 + 0.1 * RNG.normal(size=n[1] * n[2])
+    ueG = 1.0 + 0.1 * RNG.normal(size=n[1] * n[2])
+    ue = oracle.exit_bc(g, ue0, u, ueG, dt, 0, None, u, ue0)
+    want = ue0 - dt * Ux * (ueG - last)
+    np.testing.assert_allclose(ue - ue.mean(), want - want.mean(), atol=1e-13)
+    us = 1.0 + 0.1 * RNG.normal(size=n[1] * n[2])  # predictor's exit plane
+    ue = oracle.exit_bc(g, ue0, u, ueG, dt, 1, us, u, ue0)
+    want = 0.5 * (us + ue0 - dt * Ux * (ueG - last))
+    np.testing.assert_allclose(ue - ue.mean(), want - want.mean(), atol=1e-13)
+
+
 def test_cfl_closed_form_on_uniform_field():
     n = (8, 7, 6)
     g = oracle.make_grid(3, n, (True,) * 3, False, (0, 0, 0), nu=0.05)
