@@ -608,6 +608,26 @@ def test_tgv_octant_start_is_the_full_field_on_its_mirror_planes():
     assert np.abs(uf[0][:h, :h, h]).max() < 1e-12 and np.abs(uf[1][:h, h, :h]).max() < 1e-12
 
 
+def test_heun_step_is_second_order_in_time():
+    # on a fixed grid, the step's error against a small-dt run falls 4x per
+    # halving of dt (Heun is second order; a forward-Euler slip, e.g. a lost
+    # corrector average, would give 2x)
+    N = 32
+    case = synth.Case("tgv2d", 2, (N, N, 1), (True, True, False), False, (0.0, 0.0, 0.0), 0.02,
+                      synth.Body("none", (0, 0, 0), 0.0), init="tgv2d")
+
+    def run(dt, T=2.0):
+        u, ue = synth.initial_velocity(case)
+        s = oracle.Sim(case, tol=1e-13, u=u, ue=ue)
+        for _ in range(int(round(T / dt))):
+            s.step(dt)
+        return s.u.copy()
+
+    ref = run(0.0125)
+    e = [np.abs(run(dt) - ref).max() for dt in (0.2, 0.1, 0.05)]
+    assert e[0] / e[1] > 3.5 and e[1] / e[2] > 3.5, e
+
+
 def test_tgv2d_decay_converges_at_second_order_or_better():
     # 2D Taylor-Green: exact Navier-Stokes solution whose kinetic energy decays
     # as exp(-4 nu k^2 t). The discrete decay rate error must fall by >= 4x per
