@@ -47,7 +47,7 @@ __device__ __forceinline__ int tap_nb(const NetGrid &g, int x, int y, int z, int
 // Y = conv(X, W) (FP32 pre-activation) and optionally A = relu(Y) in BF16.
 // Wt: [27][16 out][16 in] BF16. Each warp computes 16 voxels x 16 channels as
 // two m16n8 tiles, K = 16 input channels per tap, 27 taps.
-__global__ void __launch_bounds__(128) k_conv_fwd(NetGrid g, const __nv_bfloat16 *__restrict__ X,
+static __global__ void __launch_bounds__(128) k_conv_fwd(NetGrid g, const __nv_bfloat16 *__restrict__ X,
                                                   const __nv_bfloat16 *__restrict__ Wt, float *__restrict__ Y,
                                                   __nv_bfloat16 *__restrict__ A) {
     __shared__ uint32_t sW[NET_TAPS * NET_C * NET_C / 2];
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(128) k_conv_fwd(NetGrid g, const __nv_bfloat16
 // blockIdx.y; each warp reduces chunks of 16 voxels with the MMA (M = 16 input
 // channels, N = 16 output channels, K = 16 voxels), staging the transposed
 // operands through shared memory.
-__global__ void __launch_bounds__(128) k_conv_dw(NetGrid g, const __nv_bfloat16 *__restrict__ X,
+static __global__ void __launch_bounds__(128) k_conv_dw(NetGrid g, const __nv_bfloat16 *__restrict__ X,
                                                  const __nv_bfloat16 *__restrict__ dZ, float *__restrict__ dW) {
     __shared__ __nv_bfloat16 sx[4][16][18], sd[4][16][18];
     const int t = blockIdx.y;
@@ -152,13 +152,13 @@ __global__ void __launch_bounds__(128) k_conv_dw(NetGrid g, const __nv_bfloat16 
 }
 
 // dZ = dA * (Z > 0) in BF16 (ReLU backward), dA and Z FP32.
-__global__ void k_relu_bwd(int n, const float *__restrict__ dA, const float *__restrict__ Z, __nv_bfloat16 *dZ) {
+static __global__ void k_relu_bwd(int n, const float *__restrict__ dA, const float *__restrict__ Z, __nv_bfloat16 *dZ) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
         dZ[e] = __float2bfloat16(Z[e] > 0.f ? dA[e] : 0.f);
 }
 
 // Network input: channel 0 = x (BF16), other channels 0.
-__global__ void k_net_input(int V, const float *__restrict__ x, __nv_bfloat16 *X) {
+static __global__ void k_net_input(int V, const float *__restrict__ x, __nv_bfloat16 *X) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x)
 #pragma unroll
         for (int c = 0; c < NET_C; ++c) X[v * NET_C + c] = __float2bfloat16(c == 0 ? x[v] : 0.f);
@@ -167,7 +167,7 @@ __global__ void k_net_input(int V, const float *__restrict__ x, __nv_bfloat16 *X
 // Loss sum (y - t)^2 / tn2 of one sample (y = channel 0 of Y) and its gradient
 // dY[v][0] = 2 (y - t)/tn2 in BF16 (other channels 0); loss accumulated into
 // *loss (FP64 atomics, one per block).
-__global__ void k_net_loss(int V, const float *__restrict__ Y, const float *__restrict__ t, const double *tn2,
+static __global__ void k_net_loss(int V, const float *__restrict__ Y, const float *__restrict__ t, const double *tn2,
                            __nv_bfloat16 *dY, double *loss) {
     __shared__ double sh[64];
     const double den = *tn2 > 0 ? *tn2 : 1.0;
@@ -184,7 +184,7 @@ __global__ void k_net_loss(int V, const float *__restrict__ Y, const float *__re
 }
 
 // Sum of squares of a sample (its loss normaliser), into *out.
-__global__ void k_sumsq(int V, const float *__restrict__ t, double *out) {
+static __global__ void k_sumsq(int V, const float *__restrict__ t, double *out) {
     __shared__ double sh[64];
     float acc[1] = {0.f};
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) acc[0] += t[v] * t[v];
@@ -196,7 +196,7 @@ __global__ void k_sumsq(int V, const float *__restrict__ t, double *out) {
 // BF16 working copies of the FP32 weights W[l][t][i][o]:
 // fwd[l][t][o][i] (forward) and bwd[l][t][i][o] = W[l][26 - t][i][o] viewed
 // as [t][out = i][in = o] (the transposed, flipped kernel of the dX pass).
-__global__ void k_net_weights(const float *__restrict__ W, __nv_bfloat16 *fwd, __nv_bfloat16 *bwd) {
+static __global__ void k_net_weights(const float *__restrict__ W, __nv_bfloat16 *fwd, __nv_bfloat16 *bwd) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 3 * NET_WL; e += gridDim.x * blockDim.x) {
         const int l = e / NET_WL, r = e % NET_WL;
         const int t = r / (NET_C * NET_C), i = (r / NET_C) % NET_C, o = r % NET_C;
@@ -208,7 +208,7 @@ __global__ void k_net_weights(const float *__restrict__ W, __nv_bfloat16 *fwd, _
 
 // Adam step on the FP32 weights (gradients averaged over `nb` samples); the
 // padded entries (layer 1 inputs > 0, layer 3 outputs > 0) stay zero.
-__global__ void k_adam(float *W, const float *G, float *m, float *v, int step, float lr, float nb) {
+static __global__ void k_adam(float *W, const float *G, float *m, float *v, int step, float lr, float nb) {
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 3 * NET_WL; e += gridDim.x * blockDim.x) {
@@ -245,7 +245,7 @@ __global__ void k_guess_target(GridD gf, int shift, NetGrid gc, const T *ph1, co
 }
 
 // Subtract the mean of a coarse field (one block).
-__global__ void k_demean(int V, float *a) {
+static __global__ void k_demean(int V, float *a) {
     __shared__ double sh[64];
     __shared__ float mean;
     float acc[1] = {0.f};
@@ -312,13 +312,13 @@ __global__ void k_to_float(long long n, const T *__restrict__ a, float *b) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
         b[e] = (float)a[e];
 }
-__global__ void k_scale_copy(int n, float s, const float *__restrict__ a, float *b) {
+static __global__ void k_scale_copy(int n, float s, const float *__restrict__ a, float *b) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) b[e] = s * a[e];
 }
-__global__ void k_scale_ch0(int V, float s, float *Y) {
+static __global__ void k_scale_ch0(int V, float s, float *Y) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) Y[v * NET_C] *= s;
 }
-__global__ void k_channel0(int V, const float *__restrict__ Y, float *y) {
+static __global__ void k_channel0(int V, const float *__restrict__ Y, float *y) {
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) y[v] = Y[v * NET_C];
 }
 

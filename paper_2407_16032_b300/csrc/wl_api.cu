@@ -1,1662 +1,21 @@
-// wl_api.cu -- host driver of the BDIM time step and the C ABI of include/wl.h.
-//
-// One simulation owns every device array of the step; the step enqueues its
-// kernels on the caller's stream and reads back one small block of scalars per
-// multigrid V-cycle (convergence test) and per step (time step, status).
-// The V-cycle (restrictions, coarsest solve, prolongation + PCG smoothing on
-// every level, and the next refinement residual) is one CUDA graph.
+// wl_api.cu -- the C ABI of include/wl.h: argument checks, status codes and
+// error strings around the simulation objects (wl_sim.cuh), plus the
+// stand-alone network check entry point.
 #include "../../include/wl.h"
+#include "wl_sim_base.h"
 #include "wl_common.cuh"
-#include "k_flux.cuh"
-#include "k_body.cuh"
-#include "k_poisson.cuh"
-#include "k_mg_march.cuh"
-#include "k_resid.cuh"
-#include "k_misc.cuh"
 #include "k_net.cuh"
-#include "k_adjoint.cuh"
 
-#include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <algorithm>
-#include <map>
-#include <random>
 #include <new>
 #include <string>
-#include <utility>
 #include <vector>
 
+using wl::Err;
+using wl::SimBase;
+
 namespace {
-
-const double PI = 3.14159265358979323846;
-
-struct Err {
-    int code;
-    std::string msg;
-};
-
-#define WL_CK(call)                                                                         \
-    do {                                                                                    \
-        cudaError_t e_ = (call);                                                            \
-        if (e_ != cudaSuccess) {                                                            \
-            throw Err{WL_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};     \
-        }                                                                                   \
-    } while (0)
-
-#define WL_LAUNCH_CK()                                                                      \
-    do {                                                                                    \
-        cudaError_t e_ = cudaGetLastError();                                                \
-        if (e_ != cudaSuccess) throw Err{WL_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e_)}; \
-    } while (0)
-
-struct SimBase {
-    wl_config cfg{};
-    wl_body body{};
-    std::string err;
-    virtual ~SimBase() {}
-    virtual void set_velocity(const void *u, const void *ue) = 0;
-    virtual void get_velocity(void *u, void *ue) = 0;
-    virtual void get_pressure(double *p) = 0;
-    virtual void set_pressure(const double *p) = 0;
-    virtual int mom_step(double dt_fixed, wl_step_stats *st) = 0;
-    virtual int project(double w, double dt, wl_solve_stats *st) = 0;
-    virtual int poisson_solve(const void *b, double *p, wl_solve_stats *st) = 0;
-    virtual void conv_diff(const void *u, const void *ue, void *r) = 0;
-    virtual void forces(double *F) = 0;
-    virtual void forces_viscous(double *F) = 0;
-    virtual void body_update(double t) = 0;
-    virtual void get_body_fields(void *c, void *mu1n, void *V) = 0;
-    virtual void diagnostics(double *ke, double *ens, double *maxdiv) = 0;
-    virtual void info(int *levels, long long *launches) = 0;
-    virtual void profile(int on) = 0;
-    virtual void guess_setup(int level, int capacity) = 0;
-    virtual void guess_mode(int collect, int use) = 0;
-    virtual void guess_train(int iters, double lr, int batch, unsigned seed, double *l0, double *l1) = 0;
-    virtual void guess_weights(const float *in, float *out) = 0;
-    virtual void guess_info(int *level, int *samples, double *gain) = 0;
-    virtual std::string profile_report() = 0;
-    virtual int step_vjp(double t0, double dt, const void *u0, const void *ue0, const double *P0, const void *lu,
-                         const void *le, const double *lP, double tol, void *ub, void *ueb, wl_solve_stats *st) = 0;
-    virtual void force_dp(int axis, double scale, double *g) = 0;
-    virtual int window_forward(int nsteps, int ckpt, const double *dts, const double *w, double *J, double *dts_out) = 0;
-    virtual int window_backward(double gJ, const void *lu, const void *le, double tol, void *du0, void *due0,
-                                double *dparams) = 0;
-    virtual void set_body(const wl_body *bd) = 0;
-    virtual void tguess_mode(int collect, int use) = 0;
-    virtual void tguess_fit(double *w, double *ratio) = 0;
-    virtual void tguess_weights(const double *in, double *out) = 0;
-    double t = 0.0, dt_next = 0.25;
-};
-
-// Per-kernel timing with CUDA events on the sim's stream (profiling mode only:
-// the V-cycle then runs as direct launches instead of its graph).
-struct Prof {
-    struct Rec { const char *name; int level; long long cells; cudaEvent_t a, b; };
-    bool on = false;
-    std::vector<Rec> pending;
-    std::vector<cudaEvent_t> pool;
-    std::map<std::pair<std::string, int>, std::pair<long long, std::pair<double, long long>>> acc;
-    cudaEvent_t get() {
-        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
-        cudaEvent_t e;
-        WL_CK(cudaEventCreate(&e));
-        return e;
-    }
-    void beg(cudaStream_t s, const char *name, int level, long long cells) {
-        if (!on) return;
-        Rec r{name, level, cells, get(), get()};
-        WL_CK(cudaEventRecord(r.a, s));
-        pending.push_back(r);
-    }
-    void end(cudaStream_t s) {
-        if (!on || pending.empty()) return;
-        WL_CK(cudaEventRecord(pending.back().b, s));
-    }
-    void flush() {
-        for (auto &r : pending) {
-            WL_CK(cudaEventSynchronize(r.b));
-            float ms = 0.f;
-            WL_CK(cudaEventElapsedTime(&ms, r.a, r.b));
-            auto &v = acc[{std::string(r.name), r.level}];
-            v.first += 1;
-            v.second.first += ms;
-            v.second.second = r.cells;
-            pool.push_back(r.a);
-            pool.push_back(r.b);
-        }
-        pending.clear();
-    }
-    ~Prof() {
-        for (auto &r : pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
-        for (auto e : pool) cudaEventDestroy(e);
-    }
-};
-
-template <typename T, int ND>
-struct Sim : SimBase {
-    cudaStream_t st = nullptr;
-    cudaStream_t cap = nullptr;
-    int nsm = 148, maxb = 1184;
-    GridD g{};
-    int nlev = 1;
-    GridD gl[WL_MAXLEV];
-    std::vector<void *> allocs;
-    // fields
-    T *vel[4][3] = {};
-    int cur = 0;
-    T *ueA = nullptr, *ueB = nullptr, *ueC = nullptr;
-    T *mu1n = nullptr;
-    T *Vb[3] = {};
-    // refinement pressure (ph + pl), the warm start of every solve
-    T *b = nullptr, *bl = nullptr, *ph = nullptr, *pl = nullptr;
-    LevelD<T> lv[WL_MAXLEV];
-    T *lc[WL_MAXLEV][3] = {};
-    unsigned char *tfl[WL_MAXLEV] = {};
-    double *cw = nullptr;   // coarsest scratch
-    double *cM = nullptr;   // dense solution operator of the coarsest level (static coefficients)
-    bool cdense = false;
-    double *pout = nullptr; // reported pressure scratch
-    DevScalars *S = nullptr, *hS = nullptr;
-    double *part = nullptr;
-    cudaGraphExec_t vexec = nullptr;
-    long long vnodes = 0;
-    long long launches = 0;
-    bool has_body = false, moving = false;
-    double body_t = -1.0;
-    int np = 1;
-    // learned initial guess (network on multigrid level gq.lev)
-    struct GuessState {
-        int lev = -1, shift = 0, cap = 0, count = 0, next = 0, step = 0;
-        bool collect = false, use = false, ready = false;
-        double gain = 1.0;
-        NetGrid ng{};
-        float *dx = nullptr, *dt = nullptr;  // samples: inputs, targets (cap x V)
-        double *dn = nullptr;                 // per-sample sums of squares (x, t)
-        float *W = nullptr, *G = nullptr, *m = nullptr, *v = nullptr, *Y = nullptr, *Z1 = nullptr, *Z2 = nullptr;
-        float *fx = nullptr, *tt = nullptr;   // network input and scaled target (one sample)
-        __nv_bfloat16 *Wf = nullptr, *Wb = nullptr, *A0 = nullptr, *A1 = nullptr, *A2 = nullptr, *dY = nullptr;
-        double *loss = nullptr;
-        T *ph0 = nullptr, *pl0 = nullptr;
-    } gq;
-    // adjoint of one step: forward copies, cotangents, and a backup of the state
-    struct AdjState {
-        bool ready = false, pready = false;
-        T *u0[3] = {}, *us[3] = {}, *lu[3] = {}, *x[3] = {}, *usb[3] = {}, *fb[3] = {}, *ub[3] = {}, *bku[3] = {};
-        T *ue0 = nullptr, *ues = nullptr, *le = nullptr, *xe = nullptr, *uesb = nullptr, *ueb = nullptr, *bkue = nullptr;
-        T *bkph = nullptr, *bkpl = nullptr;
-        double *lP = nullptr;
-        // parameter mode: blend inputs and pressures of both stages, gradient
-        T *f1[3] = {}, *f2[3] = {}, *P1h = nullptr, *P1l = nullptr, *P2h = nullptr, *P2l = nullptr;
-        double *dpar = nullptr;
-        // warm starts of the adjoint solves over a window (per stage: the
-        // previous reverse step's solution)
-        T *qh[2] = {}, *ql[2] = {};
-        bool qwarm = false, qvalid[2] = {false, false};
-    } ad;
-    // learned temporal guess: per projection stage (0 predictor, 1 corrector)
-    // its last two converged pressures (hi, lo), the fitted weights and the
-    // gathered normal equations
-    struct TGuess {
-        bool collect = false, use = false, ready = false;
-        T *H[2][2][2] = {};       // [stage][age][hi / lo]
-        int count[2] = {0, 0};
-        double w[2][2] = {{0.0, 1.0}, {0.0, 1.0}};
-        double *stats = nullptr;  // 2 x 6 doubles on the device
-    } tg;
-    // checkpointed time window (forward run kept for the reverse sweep)
-    struct Snap { T *u[3]; T *ue; T *ph; T *pl; double t; };
-    struct Window {
-        bool active = false;
-        int n = 0, k = 0;
-        double w[3] = {0, 0, 0};
-        std::vector<double> dts, t0s;
-        std::vector<Snap> ck, seg;
-        Snap fin{};
-        double fin_dt_next = 0.0;
-    } win;
-    Prof prof;
-    void P0(const char *name, int level, long long cells) { prof.beg(st, name, level, cells); }
-    void P1() { prof.end(st); }
-
-    void *dalloc(size_t bytes) {
-        void *p = nullptr;
-        bytes = (bytes + 255) & ~size_t(255);
-        if (cfg.allocator.alloc) {
-            p = cfg.allocator.alloc(cfg.allocator.ctx, bytes);
-            if (!p) throw Err{WL_ERR_ALLOC, "allocator callback returned NULL"};
-        } else {
-            cudaError_t e = cudaMalloc(&p, bytes);
-            if (e != cudaSuccess) throw Err{WL_ERR_ALLOC, std::string("cudaMalloc: ") + cudaGetErrorString(e)};
-        }
-        allocs.push_back(p);
-        WL_CK(cudaMemsetAsync(p, 0, bytes, st));
-        return p;
-    }
-    template <typename Q> Q *alloc_n(size_t n) { return (Q *)dalloc(n * sizeof(Q)); }
-
-    int blocks(long long n) const {
-        long long b = (n + 255) / 256;
-        return (int)(b < maxb ? (b < 1 ? 1 : b) : maxb);
-    }
-    // tiled kernels: one 32x8 block per tile, grid-stride over tiles
-    int tgrid(int l) const { return lv[l].tl.nt < maxb ? lv[l].tl.nt : maxb; }
-    dim3 tblk() const { return dim3(32, 8, 1); }
-
-    ~Sim() override {
-        if (vexec) cudaGraphExecDestroy(vexec);
-        if (cap) cudaStreamDestroy(cap);
-        if (hS) cudaFreeHost(hS);
-        for (void *p : allocs) {
-            if (cfg.allocator.alloc) {
-                if (cfg.allocator.free) cfg.allocator.free(cfg.allocator.ctx, p);
-            } else {
-                cudaFree(p);
-            }
-        }
-    }
-
-    void init(const wl_config &c, const wl_body *bd) {
-        cfg = c;
-        st = (cudaStream_t)c.stream;
-        if (bd) body = *bd; else { std::memset(&body, 0, sizeof(body)); body.kind = WL_BODY_NONE; }
-        int dev = 0;
-        WL_CK(cudaGetDevice(&dev));
-        WL_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        maxb = nsm * 8;
-        if (maxb > WL_MAXPART) maxb = WL_MAXPART;
-        WL_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-        WL_CK(cudaMallocHost(&hS, sizeof(DevScalars)));
-        g.ndim = c.ndim;
-        for (int a = 0; a < 3; ++a) {
-            g.n[a] = (a < c.ndim) ? c.n[a] : 1;
-            g.per[a] = (a < c.ndim) ? (c.periodic[a] != 0) : 0;
-            g.U[a] = (a < c.ndim) ? c.U[a] : 0.0;
-        }
-        g.exit_x = c.exit_hi_x != 0;
-        g.nu = c.nu;
-        g.nc = (long long)g.n[0] * g.n[1] * g.n[2];
-        np = g.n[1] * g.n[2];
-        has_body = body.kind != WL_BODY_NONE;
-        moving = has_body && (body.heave_amp != 0.0 || body.pitch_amp != 0.0);
-        const long long nc = g.nc;
-        for (int q = 0; q < 4; ++q)
-            for (int a = 0; a < g.ndim; ++a) vel[q][a] = alloc_n<T>(nc);
-        ueA = alloc_n<T>(np);
-        ueB = alloc_n<T>(np);
-        ueC = alloc_n<T>(np);
-        if (has_body) {
-            mu1n = alloc_n<T>((size_t)9 * nc);
-            for (int a = 0; a < g.ndim; ++a) Vb[a] = alloc_n<T>(nc);
-        }
-        b = alloc_n<T>(nc);
-        bl = alloc_n<T>(nc);
-        ph = alloc_n<T>(nc);
-        pl = alloc_n<T>(nc);
-        S = alloc_n<DevScalars>(1);
-        part = alloc_n<double>(8 * WL_MAXPART);
-        // multigrid hierarchy: halve every axis while all are even and >= 8
-        gl[0] = g;
-        nlev = 1;
-        while (nlev < WL_MAXLEV) {
-            const GridD &f = gl[nlev - 1];
-            bool ok = true;
-            for (int a = 0; a < g.ndim; ++a)
-                if ((f.n[a] % 2) != 0 || f.n[a] / 2 < 4) ok = false;
-            if (!ok) break;
-            GridD cg = f;
-            for (int a = 0; a < g.ndim; ++a) cg.n[a] = f.n[a] / 2;
-            cg.nc = (long long)cg.n[0] * cg.n[1] * cg.n[2];
-            gl[nlev++] = cg;
-        }
-        for (int l = 0; l < nlev; ++l) {
-            const long long m = gl[l].nc;
-            LevelD<T> &L = lv[l];
-            L.g = gl[l];
-            for (int a = 0; a < 3; ++a) {
-                lc[l][a] = (a < g.ndim) ? alloc_n<T>(m) : nullptr;
-                L.c[a] = lc[l][a];
-            }
-            L.invD = alloc_n<T>(m);
-            L.x = alloc_n<T>(m);
-            L.r = alloc_n<T>(m);
-            L.s = alloc_n<T>(m);
-            L.q = alloc_n<T>(m);
-            L.d[0] = alloc_n<T>(m);
-            L.d[1] = alloc_n<T>(m);
-            L.tl = tiles_of(gl[l], MT<ND>::TZ);
-            tfl[l] = alloc_n<unsigned char>(L.tl.nt);
-            L.tflag = tfl[l];
-            L.cu = (T)std::pow(2.0, (double)l * (ND - 2));
-            // no body and every axis periodic: every cell has 2n faces of cu
-            bool allper = true;
-            for (int a = 0; a < g.ndim; ++a) allper = allper && g.per[a];
-            L.iduni = (!has_body && allper) ? (T)(-1.0 / (2.0 * ND * (double)L.cu)) : T(0);
-        }
-        cw = alloc_n<double>(4 * gl[nlev - 1].nc);
-
-        // initial state: u = 0 with U on boundary normal faces, exit plane U_x
-        t = 0.0;
-        dt_next = c.dt_init;
-        set_velocity_fill();
-        body_update(0.0);
-        // a small coarsest level with coefficients that never change (no body
-        // or a fixed one) is solved by a precomputed dense operator
-        cdense = gl[nlev - 1].nc <= 256 && !moving && coarse_dense_build();
-        build_vcycle_graph();
-        WL_CK(cudaStreamSynchronize(st));
-    }
-
-    // ------------------------------------------------------------ helpers
-    CVec3P<T> cv(int q) const { CVec3P<T> r{}; for (int a = 0; a < 3; ++a) r.p[a] = vel[q][a]; return r; }
-    Vec3P<T> vv(int q) const { Vec3P<T> r{}; for (int a = 0; a < 3; ++a) r.p[a] = vel[q][a]; return r; }
-    CVec3P<T> cc0() const { CVec3P<T> r{}; for (int a = 0; a < 3; ++a) r.p[a] = lc[0][a]; return r; }
-
-    void fill_boundary(int q) {
-        k_bc_lower<T><<<blocks(g.nc), 256, 0, st>>>(g, vv(q));
-        WL_LAUNCH_CK();
-        ++launches;
-    }
-
-    void set_velocity_fill() {
-        for (int a = 0; a < g.ndim; ++a) WL_CK(cudaMemsetAsync(vel[cur][a], 0, g.nc * sizeof(T), st));
-        fill_boundary(cur);
-        k_fill<T><<<blocks(np), 256, 0, st>>>((long long)np, (T)g.U[0], ueA);
-        WL_LAUNCH_CK();
-        ++launches;
-    }
-
-    BodyState body_state(double tt) const {
-        BodyState B{};
-        B.kind = body.kind;
-        B.eps = cfg.eps;
-        double c[3] = {body.centre[0], body.centre[1], body.centre[2]};
-        double vc[3] = {0, 0, 0};
-        const int ax = body.heave_axis;
-        if (ax >= 0 && ax < 3) {
-            c[ax] += body.heave_amp * std::sin(body.omega * tt + body.phase);
-            vc[ax] = body.heave_amp * body.omega * std::cos(body.omega * tt + body.phase);
-        }
-        for (int a = 0; a < 3; ++a) {
-            B.chi[a] = std::floor(c[a]);
-            B.clo[a] = c[a] - B.chi[a];
-            B.vc[a] = vc[a];
-        }
-        B.radius = body.radius;
-        B.sa = body.semi[0];
-        B.sb = body.semi[1];
-        const double th = body.pitch_amp * std::sin(body.omega * tt + body.phase + 0.5 * PI);
-        B.thd = body.pitch_amp * body.omega * std::cos(body.omega * tt + body.phase + 0.5 * PI);
-        B.cth = std::cos(th);
-        B.sth = std::sin(th);
-        return B;
-    }
-
-    void read_scalars() {
-        WL_CK(cudaMemcpyAsync(hS, S, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
-        WL_CK(cudaStreamSynchronize(st));
-    }
-
-    // ------------------------------------------------------------ body
-    void body_update(double tt) override {
-        BodyState B = body_state(tt);
-        Vec3P<T> c{}, V{};
-        for (int a = 0; a < 3; ++a) { c.p[a] = lc[0][a]; V.p[a] = Vb[a]; }
-        P0("measure", 0, g.nc);
-        k_measure<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], B, c, mu1n, (long long)g.nc, V, has_body);
-        P1();
-        WL_LAUNCH_CK();
-        ++launches;
-        for (int l = 1; l < nlev; ++l) {
-            CVec3P<T> cf{};
-            Vec3P<T> cc{};
-            for (int a = 0; a < 3; ++a) { cf.p[a] = lc[l - 1][a]; cc.p[a] = lc[l][a]; }
-            k_coarsen_c<T, ND><<<tgrid(l), tblk(), 0, st>>>(gl[l - 1], cf, lv[l], cc);
-            WL_LAUNCH_CK();
-            ++launches;
-        }
-        for (int l = 0; l < nlev; ++l) {
-            if (l == 0) k_invd<T, ND, true><<<tgrid(l), tblk(), 0, st>>>(lv[l], S, part);
-            else k_invd<T, ND, false><<<tgrid(l), tblk(), 0, st>>>(lv[l], S, part);
-            WL_LAUNCH_CK();
-            WL_CK(cudaMemsetAsync(tfl[l], 1, lv[l].tl.nt, st));
-            k_tileflags<T, ND><<<tgrid(l), tblk(), 0, st>>>(lv[l], tfl[l]);
-            WL_LAUNCH_CK();
-            launches += 2;
-        }
-        body_t = tt;
-    }
-
-    void get_body_fields(void *c, void *m1, void *V) override {
-        const size_t bytes = g.nc * sizeof(T);
-        for (int a = 0; a < g.ndim; ++a) {
-            if (c) WL_CK(cudaMemcpyAsync((char *)c + a * bytes, lc[0][a], bytes, cudaMemcpyDefault, st));
-            if (V && has_body) WL_CK(cudaMemcpyAsync((char *)V + a * bytes, Vb[a], bytes, cudaMemcpyDefault, st));
-        }
-        if (m1 && has_body) WL_CK(cudaMemcpyAsync(m1, mu1n, 9 * bytes, cudaMemcpyDefault, st));
-        WL_CK(cudaStreamSynchronize(st));
-    }
-
-    // ------------------------------------------------------------ multigrid
-    void enqueue_vcycle(cudaStream_t s, long long &nodes) {
-        const int k = cfg.smooth_iters;
-        const bool tm = prof.on && s == st;
-        auto B = [&](const char *nm, int l) { if (tm) P0(nm, l, gl[l].nc); };
-        auto E = [&]() { if (tm) P1(); ++nodes; };
-        // level 0 -> 1 restriction is fused into the refinement residual
-        for (int l = 1; l + 1 < nlev; ++l) {
-            B("restrict", l + 1);
-            k_restrict<T, ND><<<tgrid(l + 1), tblk(), 0, s>>>(gl[l], lv[l].r, lv[l + 1]);
-            E();
-        }
-        const int L = nlev - 1;
-        long long ncl = gl[L].nc;
-        int maxit = (int)(2 * ncl + 200);
-        if (maxit > 2000) maxit = 2000;
-        B("coarsest", L);
-        if (cdense) k_coarsest_dense<T><<<1, 256, 0, s>>>(lv[L], cM);
-        else k_coarsest<T><<<1, ncl >= 512 ? 512 : 256, 0, s>>>(lv[L], cw, maxit);
-        E();
-        for (int l = nlev - 2; l >= 0; --l) {
-            B("pcg_init", l);
-            k_pcg_initm<T, ND><<<tgrid(l), tblk(), 0, s>>>(lv[l], gl[l + 1], lv[l + 1].x, S, part, l);
-            E();
-            for (int it = 0; it < k; ++it) {
-                // d alternates between the two buffers (the next pass reads the
-                // previous direction of neighbouring tiles while writing its own)
-                T *dnew = lv[l].d[it & 1], *dold = lv[l].d[(it + 1) & 1];
-                B(it == 0 ? "pcg_dq1" : "pcg_dq", l);
-                if (it == 0) k_pcg_dq<T, ND, true><<<tgrid(l), tblk(), 0, s>>>(lv[l], dold, dnew, S, part, l);
-                else k_pcg_dq<T, ND, false><<<tgrid(l), tblk(), 0, s>>>(lv[l], dold, dnew, S, part, l);
-                E();
-                const bool last = it == k - 1;
-                B(last ? (l == 0 ? "pcg_u_last_fine" : "pcg_u_last") : "pcg_u", l);
-                const int vb = blocks((gl[l].nc + 3) / 4);
-                if (!last) k_pcg_u<T, false, false><<<vb, 256, 0, s>>>(lv[l], dnew, ph, pl, S, part, l, it);
-                else if (l > 0) k_pcg_u<T, true, false><<<vb, 256, 0, s>>>(lv[l], dnew, ph, pl, S, part, l, it);
-                else k_pcg_u<T, true, true><<<vb, 256, 0, s>>>(lv[l], dnew, ph, pl, S, part, l, it);
-                E();
-            }
-        }
-        if (nlev == 1) {
-            B("padd", 0);
-            k_padd<T><<<blocks(g.nc), 256, 0, s>>>(g, lv[0].x, ph, pl);
-            E();
-        }
-        B("resid", 0);
-        resid_launch(s);
-        E();
-    }
-
-    // refinement residual on level 0, restricted into level 1 when there is one
-    void resid_launch(cudaStream_t s) {
-        if (nlev > 1) k_residm<T, ND, true><<<tgrid(0), tblk(), 0, s>>>(lv[0], b, bl, ph, pl, lv[1], S, part);
-        else k_residm<T, ND, false><<<tgrid(0), tblk(), 0, s>>>(lv[0], b, bl, ph, pl, lv[0], S, part);
-    }
-
-    // Dense solution operator of the coarsest level: the inverse of the active
-    // operator bordered by the mean constraint, [A 1; 1^T 0], by Gauss-Jordan
-    // elimination with partial pivoting in double on the host. Returns false
-    // (PCG stays) if the bordered matrix is singular (a disconnected active set).
-    bool coarse_dense_build() {
-        const int L = nlev - 1;
-        const GridD &cg = gl[L];
-        const int n = (int)cg.nc;
-        std::vector<T> hc[3], hinv(n);
-        for (int a = 0; a < g.ndim; ++a) {
-            hc[a].resize(n);
-            WL_CK(cudaMemcpyAsync(hc[a].data(), lc[L][a], n * sizeof(T), cudaMemcpyDeviceToHost, st));
-        }
-        WL_CK(cudaMemcpyAsync(hinv.data(), lv[L].invD, n * sizeof(T), cudaMemcpyDeviceToHost, st));
-        WL_CK(cudaStreamSynchronize(st));
-        std::vector<int> act;
-        std::vector<int> pos(n, -1);
-        for (int e = 0; e < n; ++e)
-            if (hinv[e] != T(0)) { pos[e] = (int)act.size(); act.push_back(e); }
-        const int m = (int)act.size();
-        if (m == 0) return false;
-        const int K = m + 1;
-        std::vector<double> A((size_t)K * K, 0.0), X((size_t)K * K, 0.0);
-        const int st3[3] = {1, cg.n[0], cg.n[0] * cg.n[1]};
-        double amax = 0.0;
-        for (int r = 0; r < m; ++r) {
-            const int e = act[r];
-            const int I[3] = {e % cg.n[0], (e / cg.n[0]) % cg.n[1], e / (cg.n[0] * cg.n[1])};
-            for (int a = 0; a < g.ndim; ++a) {
-                const int N = cg.n[a];
-                const bool per = cg.per[a] != 0;
-                const int ep = I[a] == N - 1 ? (per ? e - (N - 1) * st3[a] : -1) : e + st3[a];
-                const int em = I[a] == 0 ? (per ? e + (N - 1) * st3[a] : -1) : e - st3[a];
-                const double cp = ep >= 0 ? (double)hc[a][ep] : 0.0, cm = (double)hc[a][e];
-                A[(size_t)r * K + r] -= cp + cm;
-                if (ep >= 0 && pos[ep] >= 0) A[(size_t)r * K + pos[ep]] += cp;
-                if (em >= 0 && pos[em] >= 0) A[(size_t)r * K + pos[em]] += cm;
-            }
-            amax = std::max(amax, std::fabs(A[(size_t)r * K + r]));
-            A[(size_t)r * K + m] = 1.0;
-            A[(size_t)m * K + r] = 1.0;
-        }
-        for (int r = 0; r < K; ++r) X[(size_t)r * K + r] = 1.0;
-        for (int c = 0; c < K; ++c) {
-            int piv = c;
-            for (int r = c + 1; r < K; ++r)
-                if (std::fabs(A[(size_t)r * K + c]) > std::fabs(A[(size_t)piv * K + c])) piv = r;
-            if (!(std::fabs(A[(size_t)piv * K + c]) > 1e-10 * std::max(amax, 1.0))) return false;
-            if (piv != c)
-                for (int q = 0; q < K; ++q) {
-                    std::swap(A[(size_t)c * K + q], A[(size_t)piv * K + q]);
-                    std::swap(X[(size_t)c * K + q], X[(size_t)piv * K + q]);
-                }
-            const double inv = 1.0 / A[(size_t)c * K + c];
-            for (int q = 0; q < K; ++q) { A[(size_t)c * K + q] *= inv; X[(size_t)c * K + q] *= inv; }
-            for (int r = 0; r < K; ++r) {
-                if (r == c) continue;
-                const double f = A[(size_t)r * K + c];
-                if (f == 0.0) continue;
-                for (int q = 0; q < K; ++q) {
-                    A[(size_t)r * K + q] -= f * A[(size_t)c * K + q];
-                    X[(size_t)r * K + q] -= f * X[(size_t)c * K + q];
-                }
-            }
-        }
-        std::vector<double> Mh((size_t)n * n, 0.0);
-        for (int r = 0; r < m; ++r)
-            for (int q = 0; q < m; ++q) Mh[(size_t)act[r] * n + act[q]] = X[(size_t)r * K + q];
-        if (!cM) cM = alloc_n<double>((size_t)256 * 256);
-        WL_CK(cudaMemcpyAsync(cM, Mh.data(), Mh.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-        WL_CK(cudaStreamSynchronize(st));
-        return true;
-    }
-
-    void build_vcycle_graph() {
-        if (vexec) {
-            WL_CK(cudaGraphExecDestroy(vexec));
-            vexec = nullptr;
-        }
-        cudaGraph_t graph;
-        long long nodes = 0;
-        WL_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-        enqueue_vcycle(cap, nodes);
-        cudaError_t e = cudaStreamEndCapture(cap, &graph);
-        if (e != cudaSuccess) throw Err{WL_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e)};
-        WL_CK(cudaGraphInstantiate(&vexec, graph, 0));
-        WL_CK(cudaGraphDestroy(graph));
-        vnodes = nodes;
-    }
-
-    // b is in place; solve A (ph+pl) = b - mean with warm start; fills stats.
-    int solve(wl_solve_stats *sts) {
-        P0("resid", 0, g.nc);
-        resid_launch(st);
-        P1();
-        WL_LAUNCH_CK();
-        ++launches;
-        const bool collecting = gq.collect && gq.cap > 0;
-        if (collecting || (gq.use && gq.ready)) guess_begin(collecting);
-        read_scalars();
-        const double rel0 = hS->rel;
-        int it = 0;
-        while (hS->rel > cfg.tol && it < cfg.itmax && !(hS->status & 1)) {
-            if (prof.on) {
-                long long nodes = 0;
-                enqueue_vcycle(st, nodes);
-                WL_LAUNCH_CK();
-                launches += nodes;
-            } else {
-                WL_CK(cudaGraphLaunch(vexec, st));
-                launches += vnodes;
-            }
-            read_scalars();
-            ++it;
-        }
-        if (sts) { sts->vcycles = it; sts->rel_resid = hS->rel; sts->bnorm = hS->bnorm; sts->rel_initial = rel0; }
-        if (collecting && !(hS->status & 1) && hS->rel <= cfg.tol) guess_end();
-        if (hS->status & 1) return WL_ERR_NONFINITE;
-        if (hS->rel > cfg.tol) return WL_ERR_NOT_CONVERGED;
-        return WL_OK;
-    }
-
-    int project_buf(int q, const T *ue, double w, double dt, wl_solve_stats *sts, int stage = -1) {
-        P0("div", 0, g.nc);
-        k_div<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], cv(q), ue, (T)(1.0 / (w * dt)), b, bl, S, part);
-        P1();
-        WL_LAUNCH_CK();
-        ++launches;
-        const bool tgs = stage >= 0 && tg.ready;
-        if (tgs && tg.use && tg.count[stage] >= 2 && tg.count[1 - stage] >= 1) tguess_apply(stage);
-        int rc = solve(sts);
-        if (tgs && rc == WL_OK) tguess_push(stage);
-        P0("grad", 0, g.nc);
-        k_grad<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], ph, pl, (T)(w * dt), vv(q));
-        P1();
-        WL_LAUNCH_CK();
-        ++launches;
-        return rc;
-    }
-
-    // ---------------------------------------------- learned temporal guess
-    void tguess_alloc() {
-        if (tg.ready) return;
-        for (int sg = 0; sg < 2; ++sg)
-            for (int a = 0; a < 2; ++a)
-                for (int h = 0; h < 2; ++h) tg.H[sg][a][h] = alloc_n<T>(g.nc);
-        tg.stats = alloc_n<double>(12);
-        tg.ready = true;
-    }
-    void tguess_apply(int sg) {
-        const int o = 1 - sg;
-        P0("tguess_apply", 0, g.nc);
-        k_tguess_apply<T><<<blocks(g.nc), 256, 0, st>>>(g.nc, tg.H[sg][0][0], tg.H[sg][0][1], tg.H[sg][1][0],
-                                                        tg.H[sg][1][1], tg.H[o][0][0], tg.H[o][0][1],
-                                                        (T)tg.w[sg][0], (T)tg.w[sg][1], ph, pl);
-        P1();
-        WL_LAUNCH_CK();
-        ++launches;
-        // the first residual is of the guess
-        P0("resid", 0, g.nc);
-        resid_launch(st);
-        P1();
-        WL_LAUNCH_CK();
-        ++launches;
-    }
-    // after a converged projection of stage sg: gather the fit's normal
-    // equations (collecting) and push the solution into the stage's history
-    void tguess_push(int sg) {
-        const int o = 1 - sg;
-        if (tg.collect && tg.count[sg] >= 2 && tg.count[o] >= 1) {
-            k_tguess_stats<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], ph, pl, tg.H[sg][0][0], tg.H[sg][0][1],
-                                                               tg.H[sg][1][0], tg.H[sg][1][1], tg.H[o][0][0],
-                                                               tg.H[o][0][1], S, part, tg.stats + 6 * sg);
-            WL_LAUNCH_CK();
-            ++launches;
-        }
-        std::swap(tg.H[sg][0][0], tg.H[sg][1][0]);
-        std::swap(tg.H[sg][0][1], tg.H[sg][1][1]);
-        WL_CK(cudaMemcpyAsync(tg.H[sg][0][0], ph, g.nc * sizeof(T), cudaMemcpyDeviceToDevice, st));
-        WL_CK(cudaMemcpyAsync(tg.H[sg][0][1], pl, g.nc * sizeof(T), cudaMemcpyDeviceToDevice, st));
-        if (tg.count[sg] < 2) ++tg.count[sg];
-    }
-    void tguess_mode(int collect, int use) override {
-        tguess_alloc();
-        if (collect && !tg.collect) WL_CK(cudaMemsetAsync(tg.stats, 0, 12 * sizeof(double), st));
-        tg.collect = collect != 0;
-        tg.use = use != 0;
-        WL_CK(cudaStreamSynchronize(st));
-    }
-    // least-squares weights per stage from the gathered normal equations;
-    // ratio[sg]: predicted initial-residual norm of the fitted guess over the
-    // plain warm start's on the collected projections
-    void tguess_fit(double *w, double *ratio) override {
-        tguess_alloc();
-        double h[12];
-        WL_CK(cudaMemcpyAsync(h, tg.stats, sizeof(h), cudaMemcpyDeviceToHost, st));
-        WL_CK(cudaStreamSynchronize(st));
-        for (int sg = 0; sg < 2; ++sg) {
-            const double *m = h + 6 * sg;
-            const double G11 = m[0], G12 = m[1], G22 = m[2], c1 = m[3], c2 = m[4], dd = m[5];
-            const double ridge = 1e-12 * (G11 + G22);
-            const double a = G11 + ridge, d = G22 + ridge, det = a * d - G12 * G12;
-            double w1 = 0.0, w2 = 1.0;
-            if (det > 0 && G11 > 0 && G22 > 0) {
-                w1 = (d * c1 - G12 * c2) / det;
-                w2 = (a * c2 - G12 * c1) / det;
-            }
-            tg.w[sg][0] = w1;
-            tg.w[sg][1] = w2;
-            auto loss = [&](double x1, double x2) {
-                return dd - 2 * (x1 * c1 + x2 * c2) + x1 * x1 * G11 + 2 * x1 * x2 * G12 + x2 * x2 * G22;
-            };
-            const double lp = loss(0.0, 1.0), lf = loss(w1, w2);
-            if (w) { w[2 * sg] = w1; w[2 * sg + 1] = w2; }
-            if (ratio) ratio[sg] = lp > 0 ? std::sqrt(std::max(lf, 0.0) / lp) : 1.0;
-        }
-    }
-    void tguess_weights(const double *in, double *out) override {
-        tguess_alloc();
-        for (int q = 0; q < 4; ++q) {
-            if (in) tg.w[q / 2][q % 2] = in[q];
-            if (out) out[q] = tg.w[q / 2][q % 2];
-        }
-    }
-    void tguess_reset() { tg.count[0] = tg.count[1] = 0; }
-
-    // ------------------------------------------------------------ stages
-    template <int NDIM, int MODE>
-    void flux_launch(const FluxArgs<T> &A) {
-        using TL = FluxTile<NDIM>;
-        const size_t smem = (size_t)NDIM * TL::SN * sizeof(T);
-        static bool attr = false;
-        if (!attr) {
-            WL_CK(cudaFuncSetAttribute(k_flux<T, NDIM, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr = true;
-        }
-        const long long ntiles = (long long)((g.n[0] + TL::TX - 1) / TL::TX) * ((g.n[1] + TL::TY - 1) / TL::TY) *
-                                 ((g.n[2] + TL::TZ - 1) / TL::TZ);
-        int occ = 0;
-        WL_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_flux<T, NDIM, MODE>, TL::NT, smem));
-        if (occ < 1) occ = 1;
-        long long grid = (long long)nsm * occ;
-        if (grid > ntiles) grid = ntiles;
-        dim3 blk(TL::TX, TL::TY, TL::TZ);
-        static const char *names[5] = {"flux_raw", "flux_pred_f", "flux_pred", "flux_corr_f", "flux_corr"};
-        P0(names[MODE], 0, g.nc);
-        k_flux<T, NDIM, MODE><<<(int)grid, blk, smem, st>>>(g, A);
-        P1();
-        WL_LAUNCH_CK();
-        ++launches;
-    }
-    template <int MODE>
-    void flux(const FluxArgs<T> &A) {
-        flux_launch<ND, MODE>(A);
-    }
-
-    FluxArgs<T> fargs(int qu, const T *ue, int qu0, int qout, double dt) {
-        FluxArgs<T> A{};
-        for (int a = 0; a < 3; ++a) {
-            A.u[a] = vel[qu][a];
-            A.u0[a] = qu0 >= 0 ? vel[qu0][a] : nullptr;
-            A.out[a] = vel[qout][a];
-        }
-        A.ue = ue;
-        A.dt = (T)dt;
-        return A;
-    }
-
-    void exit_stage(bool corr, int quG, double dt) {
-        if (!g.exit_x) return;
-        // ueB: start-of-step plane; ueC: star plane (corrector); result into ueA
-        if (!corr) {
-            P0("exit", 0, np);
-            k_exit<T, false><<<1, 1024, 0, st>>>(g, ueB, vel[quG][0], ueB, nullptr, (T)dt, ueA);
-            P1();
-        } else {
-            WL_CK(cudaMemcpyAsync(ueC, ueA, np * sizeof(T), cudaMemcpyDeviceToDevice, st));
-            P0("exit", 0, np);
-            k_exit<T, true><<<1, 1024, 0, st>>>(g, ueB, vel[quG][0], ueC, ueC, (T)dt, ueA);
-            P1();
-        }
-        WL_LAUNCH_CK();
-        ++launches;
-    }
-
-    void blend(bool corr, int qf, int qstar, int qout) {
-        CVec3P<T> f = cv(qf), V{}, us{};
-        for (int a = 0; a < 3; ++a) { V.p[a] = Vb[a]; us.p[a] = qstar >= 0 ? vel[qstar][a] : nullptr; }
-        P0("blend", 0, g.nc);
-        if (corr) k_blend<T, ND, true><<<tgrid(0), tblk(), 0, st>>>(lv[0], f, mu1n, (long long)g.nc, V, us, vv(qout));
-        else k_blend<T, ND, false><<<tgrid(0), tblk(), 0, st>>>(lv[0], f, mu1n, (long long)g.nc, V, us, vv(qout));
-        P1();
-        WL_LAUNCH_CK();
-        ++launches;
-    }
-
-    int mom_step(double dt_fixed, wl_step_stats *sts) override {
-        const double dt = dt_fixed > 0 ? dt_fixed : dt_next;
-        if (!(dt > cfg.dt_min)) throw Err{WL_ERR_UNSTABLE, "time step below dt_min"};
-        if (moving) body_update(t + dt);
-        const int A0 = cur, B1 = (cur + 1) & 3, C2 = (cur + 2) & 3, D3 = (cur + 3) & 3;
-        if (g.exit_x) WL_CK(cudaMemcpyAsync(ueB, ueA, np * sizeof(T), cudaMemcpyDeviceToDevice, st));
-        wl_solve_stats s0{}, s1{};
-        int rc0, rc1;
-        int ustar, unew;
-        if (!has_body) {
-            flux<FM_PRED_U>(fargs(A0, ueB, -1, B1, dt));
-            ustar = B1;
-        } else {
-            flux<FM_PRED_F>(fargs(A0, ueB, -1, B1, dt));
-            blend(false, B1, -1, C2);
-            ustar = C2;
-        }
-        exit_stage(false, A0, dt);
-        rc0 = project_buf(ustar, ueA, 1.0, dt, &s0, 0);
-        if (rc0 == WL_ERR_NONFINITE) return fail_restore(rc0, "non-finite values in the predictor projection");
-        if (!has_body) {
-            flux<FM_CORR_U>(fargs(ustar, ueA, A0, C2, dt));
-            unew = C2;
-        } else {
-            flux<FM_CORR_F>(fargs(ustar, ueA, A0, B1, dt));
-            blend(true, B1, ustar, D3);
-            unew = D3;
-        }
-        exit_stage(true, ustar, dt);
-        rc1 = project_buf(unew, ueA, 0.5, dt, &s1, 1);
-        if (rc1 == WL_ERR_NONFINITE) return fail_restore(rc1, "non-finite values in the corrector projection");
-        // CFL for the next step
-        P0("cfl", 0, g.nc);
-        k_cfl<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], cv(unew), ueA, cfg.cfl, cfg.dt_max, S, part);
-        P1();
-        WL_LAUNCH_CK();
-        ++launches;
-        read_scalars();
-        prof.flush();
-        cur = unew;
-        t += dt;
-        dt_next = hS->dt_next;
-        if (sts) {
-            sts->proj[0] = s0;
-            sts->proj[1] = s1;
-            sts->dt = dt;
-            sts->t = t;
-            sts->dt_next = dt_next;
-        }
-        if (!(dt_next == dt_next)) { err = "non-finite CFL time step"; return WL_ERR_NONFINITE; }
-        if (rc0 != WL_OK || rc1 != WL_OK) { err = "Poisson solve did not reach tol within itmax"; return WL_ERR_NOT_CONVERGED; }
-        if (dt_next < cfg.dt_min) { err = "CFL time step below dt_min"; return WL_ERR_UNSTABLE; }
-        return WL_OK;
-    }
-
-    int fail_restore(int rc, const char *msg) {
-        if (g.exit_x) WL_CK(cudaMemcpyAsync(ueA, ueB, np * sizeof(T), cudaMemcpyDeviceToDevice, st));
-        WL_CK(cudaStreamSynchronize(st));
-        err = msg;
-        return rc;
-    }
-
-    int project(double w, double dt, wl_solve_stats *sts) override {
-        if (!(w > 0 && dt > 0)) throw Err{WL_ERR_ARG, "project: w and dt must be positive"};
-        int rc = project_buf(cur, ueA, w, dt, sts);
-        WL_CK(cudaStreamSynchronize(st));
-        return rc;
-    }
-
-    int poisson_solve(const void *bin, double *p, wl_solve_stats *sts) override {
-        WL_CK(cudaMemcpyAsync(b, bin, g.nc * sizeof(T), cudaMemcpyDefault, st));
-        WL_CK(cudaMemsetAsync(bl, 0, g.nc * sizeof(T), st));
-        if (!pout) pout = alloc_n<double>(g.nc);
-        WL_CK(cudaMemcpyAsync(pout, p, g.nc * sizeof(double), cudaMemcpyDefault, st));
-        k_pin<T><<<blocks(g.nc), 256, 0, st>>>(g, pout, ph, pl);
-        ++launches;
-        k_bstats<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], b, S, part);
-        WL_LAUNCH_CK();
-        ++launches;
-        int rc = solve(sts);
-        get_pressure(p);
-        return rc;
-    }
-
-    void conv_diff(const void *u, const void *ue, void *r) override {
-        const int qi = (cur + 1) & 3, qo = (cur + 2) & 3;
-        const size_t bytes = g.nc * sizeof(T);
-        for (int a = 0; a < g.ndim; ++a) WL_CK(cudaMemcpyAsync(vel[qi][a], (const char *)u + a * bytes, bytes, cudaMemcpyDefault, st));
-        if (ue && g.exit_x) WL_CK(cudaMemcpyAsync(ueC, ue, np * sizeof(T), cudaMemcpyDefault, st));
-        flux<FM_RAW>(fargs(qi, ueC, -1, qo, 1.0));
-        for (int a = 0; a < g.ndim; ++a) WL_CK(cudaMemcpyAsync((char *)r + a * bytes, vel[qo][a], bytes, cudaMemcpyDefault, st));
-        WL_CK(cudaStreamSynchronize(st));
-    }
-
-    void set_velocity(const void *u, const void *ue) override {
-        tguess_reset();
-        const size_t bytes = g.nc * sizeof(T);
-        for (int a = 0; a < g.ndim; ++a) WL_CK(cudaMemcpyAsync(vel[cur][a], (const char *)u + a * bytes, bytes, cudaMemcpyDefault, st));
-        fill_boundary(cur);
-        if (ue && g.exit_x) WL_CK(cudaMemcpyAsync(ueA, ue, np * sizeof(T), cudaMemcpyDefault, st));
-        WL_CK(cudaStreamSynchronize(st));
-    }
-
-    void get_velocity(void *u, void *ue) override {
-        const size_t bytes = g.nc * sizeof(T);
-        for (int a = 0; a < g.ndim; ++a) WL_CK(cudaMemcpyAsync((char *)u + a * bytes, vel[cur][a], bytes, cudaMemcpyDefault, st));
-        if (ue && g.exit_x) WL_CK(cudaMemcpyAsync(ue, ueA, np * sizeof(T), cudaMemcpyDefault, st));
-        WL_CK(cudaStreamSynchronize(st));
-    }
-
-    void pmean() {
-        k_pmean<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], ph, pl, S, part);
-        WL_LAUNCH_CK();
-        ++launches;
-    }
-
-    void get_pressure(double *p) override {
-        if (!pout) pout = alloc_n<double>(g.nc);
-        pmean();
-        k_pout<T><<<blocks(g.nc), 256, 0, st>>>(g, ph, pl, lv[0].invD, S, pout);
-        WL_LAUNCH_CK();
-        ++launches;
-        WL_CK(cudaMemcpyAsync(p, pout, g.nc * sizeof(double), cudaMemcpyDefault, st));
-        WL_CK(cudaStreamSynchronize(st));
-    }
-
-    void set_pressure(const double *p) override {
-        tguess_reset();
-        if (!pout) pout = alloc_n<double>(g.nc);
-        WL_CK(cudaMemcpyAsync(pout, p, g.nc * sizeof(double), cudaMemcpyDefault, st));
-        k_pin<T><<<blocks(g.nc), 256, 0, st>>>(g, pout, ph, pl);
-        WL_LAUNCH_CK();
-        ++launches;
-        WL_CK(cudaStreamSynchronize(st));
-    }
-
-    void forces(double *F) override {
-        F[0] = F[1] = F[2] = 0.0;
-        if (!has_body) return;
-        pmean();
-        k_forces<T><<<blocks(g.nc), 256, 0, st>>>(g, body_state(body_t), ph, pl, lv[0].invD, S, part);
-        WL_LAUNCH_CK();
-        ++launches;
-        read_scalars();
-        F[0] = hS->red[0];
-        F[1] = hS->red[1];
-        F[2] = hS->red[2];
-    }
-
-    void forces_viscous(double *F) override {
-        F[0] = F[1] = F[2] = 0.0;
-        if (!has_body) return;
-        k_forces_visc<T><<<blocks(g.nc), 256, 0, st>>>(g, body_state(body_t), cv(cur), ueA, S, part);
-        WL_LAUNCH_CK();
-        ++launches;
-        read_scalars();
-        F[0] = hS->red[0];
-        F[1] = hS->red[1];
-        F[2] = hS->red[2];
-    }
-
-    void diagnostics(double *ke, double *ens, double *maxdiv) override {
-        k_diag<T><<<blocks(g.nc), 256, 0, st>>>(g, cv(cur), ueA, lv[0].invD, S, part);
-        WL_LAUNCH_CK();
-        ++launches;
-        read_scalars();
-        if (ke) *ke = hS->red[0];
-        if (ens) *ens = hS->red[1];
-        if (maxdiv) *maxdiv = hS->red[2];
-    }
-
-    void profile(int on) override {
-        prof.flush();
-        prof.on = on != 0;
-        if (on) prof.acc.clear();
-    }
-
-    std::string profile_report() override {
-        WL_CK(cudaStreamSynchronize(st));
-        prof.flush();
-        std::string out;
-        char line[256];
-        for (auto &kv : prof.acc) {
-            std::snprintf(line, sizeof(line), "%s %d %lld %.6f %lld\n", kv.first.first.c_str(), kv.first.second,
-                          kv.second.first, kv.second.second.first, kv.second.second.second);
-            out += line;
-        }
-        return out;
-    }
-
-    // ---------------------------------------------------------- learned guess
-    void guess_setup(int level, int capacity) override {
-        if (level < 1 || level >= nlev) throw Err{WL_ERR_ARG, "guess level must be a coarse multigrid level"};
-        if (capacity < 0 || capacity > 100000) throw Err{WL_ERR_ARG, "bad sample capacity"};
-        if (gq.lev >= 0) throw Err{WL_ERR_STATE, "learned guess already set up"};
-        gq.lev = level;
-        gq.shift = level;
-        gq.ng.nx = gl[level].n[0];
-        gq.ng.ny = gl[level].n[1];
-        gq.ng.nz = gl[level].n[2];
-        gq.ng.V = (int)gl[level].nc;
-        const size_t V = gq.ng.V;
-        gq.cap = capacity;
-        if (capacity > 0) {
-            gq.dx = alloc_n<float>((size_t)capacity * V);
-            gq.dt = alloc_n<float>((size_t)capacity * V);
-            gq.dn = alloc_n<double>(2 * (size_t)capacity);
-            gq.ph0 = alloc_n<T>(g.nc);
-            gq.pl0 = alloc_n<T>(g.nc);
-        }
-        gq.W = alloc_n<float>(3 * NET_WL);
-        gq.G = alloc_n<float>(3 * NET_WL);
-        gq.m = alloc_n<float>(3 * NET_WL);
-        gq.v = alloc_n<float>(3 * NET_WL);
-        gq.Wf = alloc_n<__nv_bfloat16>(3 * NET_WL);
-        gq.Wb = alloc_n<__nv_bfloat16>(3 * NET_WL);
-        gq.fx = alloc_n<float>(V);
-        gq.tt = alloc_n<float>(V);
-        gq.Y = alloc_n<float>(V * NET_C);
-        gq.Z1 = alloc_n<float>(V * NET_C);
-        gq.Z2 = alloc_n<float>(V * NET_C);
-        gq.A0 = alloc_n<__nv_bfloat16>(V * NET_C);
-        gq.A1 = alloc_n<__nv_bfloat16>(V * NET_C);
-        gq.A2 = alloc_n<__nv_bfloat16>(V * NET_C);
-        gq.dY = alloc_n<__nv_bfloat16>(V * NET_C);
-        gq.loss = alloc_n<double>(1);
-        WL_CK(cudaStreamSynchronize(st));
-    }
-
-    void guess_mode(int collect, int use) override {
-        if (gq.lev < 0) throw Err{WL_ERR_STATE, "learned guess not set up"};
-        if (use && !gq.ready) throw Err{WL_ERR_STATE, "learned guess has no trained weights"};
-        gq.collect = collect != 0;
-        gq.use = use != 0;
-    }
-
-    void guess_weights(const float *in, float *out) override {
-        if (gq.lev < 0) throw Err{WL_ERR_STATE, "learned guess not set up"};
-        if (in) {
-            WL_CK(cudaMemcpyAsync(gq.W, in, 3 * NET_WL * sizeof(float), cudaMemcpyDefault, st));
-            k_net_weights<<<blocks(3 * NET_WL), 256, 0, st>>>(gq.W, gq.Wf, gq.Wb);
-            WL_LAUNCH_CK();
-            gq.ready = true;
-        }
-        if (out) WL_CK(cudaMemcpyAsync(out, gq.W, 3 * NET_WL * sizeof(float), cudaMemcpyDefault, st));
-        WL_CK(cudaStreamSynchronize(st));
-    }
-
-    void guess_info(int *level, int *samples, double *gain) override {
-        if (level) *level = gq.lev;
-        if (samples) *samples = gq.count;
-        if (gain) *gain = gq.gain;
-    }
-
-    // restrict the current fine residual (already on level 1) down to the net level
-    void restrict_to_guess_level() {
-        for (int l = 1; l < gq.lev; ++l) {
-            k_restrict<T, ND><<<tgrid(l + 1), tblk(), 0, st>>>(gl[l], lv[l].r, lv[l + 1]);
-            WL_LAUNCH_CK();
-            ++launches;
-        }
-    }
-
-    // network forward on fx (FP32 input) -> Y (channel 0 = output)
-    void net_forward(const float *x) {
-        const NetGrid &ng = gq.ng;
-        const int nb = (ng.V + 63) / 64, cb = nb < 2048 ? nb : 2048;
-        k_net_input<<<blocks(ng.V), 256, 0, st>>>(ng.V, x, gq.A0);
-        k_conv_fwd<<<cb, 128, 0, st>>>(ng, gq.A0, gq.Wf, gq.Z1, gq.A1);
-        k_conv_fwd<<<cb, 128, 0, st>>>(ng, gq.A1, gq.Wf + NET_WL, gq.Z2, gq.A2);
-        k_conv_fwd<<<cb, 128, 0, st>>>(ng, gq.A2, gq.Wf + 2 * NET_WL, gq.Y, nullptr);
-        WL_LAUNCH_CK();
-        launches += 4;
-    }
-
-    // At the start of a solve (after the first residual): record the sample
-    // input and the warm start (collecting), or apply the network's correction
-    // and recompute the residual (using).
-    void guess_begin(bool collecting) {
-        restrict_to_guess_level();
-        const size_t V = gq.ng.V;
-        if (collecting) {
-            float *xs = gq.dx + (size_t)gq.next * V;
-            if (sizeof(T) == sizeof(float)) WL_CK(cudaMemcpyAsync(xs, lv[gq.lev].r, V * sizeof(float), cudaMemcpyDeviceToDevice, st));
-            else k_to_float<T><<<blocks(V), 256, 0, st>>>((long long)V, lv[gq.lev].r, xs);
-            WL_CK(cudaMemcpyAsync(gq.ph0, ph, g.nc * sizeof(T), cudaMemcpyDeviceToDevice, st));
-            WL_CK(cudaMemcpyAsync(gq.pl0, pl, g.nc * sizeof(T), cudaMemcpyDeviceToDevice, st));
-        } else {
-            if (sizeof(T) == sizeof(float)) WL_CK(cudaMemcpyAsync(gq.fx, lv[gq.lev].r, V * sizeof(float), cudaMemcpyDeviceToDevice, st));
-            else k_to_float<T><<<blocks(V), 256, 0, st>>>((long long)V, lv[gq.lev].r, gq.fx);
-            P0("guess_net", gq.lev, (long long)V);
-            net_forward(gq.fx);
-            P1();
-            P0("guess_apply", 0, g.nc);
-            k_guess_apply<T><<<blocks(g.nc), 256, 0, st>>>(g, gq.shift, gq.ng, (float)gq.gain, gq.Y, ph, pl);
-            P1();
-            P0("resid", 0, g.nc);
-            resid_launch(st);
-            P1();
-            WL_LAUNCH_CK();
-            launches += 3;
-        }
-    }
-
-    // After a converged solve: the target (coarse mean of p_converged - p_warm),
-    // mean-free, and the sample's norms.
-    void guess_end() {
-        const size_t V = gq.ng.V;
-        float *ts = gq.dt + (size_t)gq.next * V;
-        k_guess_target<T><<<blocks(V), 256, 0, st>>>(g, gq.shift, gq.ng, ph, pl, gq.ph0, gq.pl0, ts);
-        k_demean<<<1, 1024, 0, st>>>(gq.ng.V, ts);
-        WL_CK(cudaMemsetAsync(gq.dn + 2 * gq.next, 0, 2 * sizeof(double), st));
-        k_sumsq<<<blocks(V), 256, 0, st>>>(gq.ng.V, gq.dx + (size_t)gq.next * V, gq.dn + 2 * gq.next);
-        k_sumsq<<<blocks(V), 256, 0, st>>>(gq.ng.V, ts, gq.dn + 2 * gq.next + 1);
-        WL_LAUNCH_CK();
-        launches += 4;
-        gq.next = (gq.next + 1) % gq.cap;
-        if (gq.count < gq.cap) ++gq.count;
-    }
-
-    // Adam on the collected samples (inputs scaled to unit RMS, targets by the
-    // same factor and by the dataset gain; the bias-free ReLU network is
-    // positively homogeneous, so at inference y = gain * net(r)).
-    void guess_train(int iters, double lr, int batch, unsigned seed, double *l0, double *l1) override {
-        if (gq.lev < 0 || gq.count < 1) throw Err{WL_ERR_STATE, "no collected samples to train on"};
-        const size_t V = gq.ng.V;
-        const int n = gq.count;
-        std::vector<double> hn(2 * n);
-        WL_CK(cudaMemcpyAsync(hn.data(), gq.dn, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
-        WL_CK(cudaStreamSynchronize(st));
-        std::vector<double> ratio, sx(n);
-        for (int i = 0; i < n; ++i) {
-            sx[i] = std::sqrt(hn[2 * i] / V);
-            if (hn[2 * i] > 0 && hn[2 * i + 1] > 0) ratio.push_back(std::sqrt(hn[2 * i + 1] / hn[2 * i]));
-        }
-        if (ratio.empty()) throw Err{WL_ERR_STATE, "collected samples are all zero"};
-        std::nth_element(ratio.begin(), ratio.begin() + ratio.size() / 2, ratio.end());
-        const double gain = ratio[ratio.size() / 2];
-        std::vector<double> tn2(n);
-        if (!gq.ready) {
-            // He-style initial weights, seeded
-            std::mt19937 rng(seed);
-            std::normal_distribution<float> nd(0.f, 1.f);
-            std::vector<float> w(3 * NET_WL, 0.f);
-            for (int l = 0; l < 3; ++l)
-                for (int t = 0; t < NET_TAPS; ++t)
-                    for (int i = 0; i < NET_C; ++i)
-                        for (int o = 0; o < NET_C; ++o) {
-                            if ((l == 0 && i > 0) || (l == 2 && o > 0)) continue;
-                            const float fan = (float)(NET_TAPS * (l == 0 ? 1 : NET_C));
-                            w[(l * NET_TAPS + t) * NET_C * NET_C + i * NET_C + o] = nd(rng) * std::sqrt(2.f / fan);
-                        }
-            WL_CK(cudaMemcpyAsync(gq.W, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-            WL_CK(cudaMemsetAsync(gq.m, 0, 3 * NET_WL * sizeof(float), st));
-            WL_CK(cudaMemsetAsync(gq.v, 0, 3 * NET_WL * sizeof(float), st));
-            gq.step = 0;
-        }
-        k_net_weights<<<blocks(3 * NET_WL), 256, 0, st>>>(gq.W, gq.Wf, gq.Wb);
-        std::mt19937 pick(seed + 1);
-        std::uniform_int_distribution<int> ud(0, n - 1);
-        float *tt = gq.tt;
-        double *dtn = gq.loss;
-        std::vector<double> hl(1);
-        double *tnorm = nullptr;
-        tnorm = alloc_n<double>(1);
-        const NetGrid &ng = gq.ng;
-        const int nbk = (ng.V + 63) / 64, cb = nbk < 2048 ? nbk : 2048;
-        const int wb = (ng.V + 16 * 4 * 16 - 1) / (16 * 4 * 16);
-        const dim3 dwg(wb < 1 ? 1 : (wb > 512 ? 512 : wb), NET_TAPS);
-        for (int itn = 0; itn < iters; ++itn) {
-            WL_CK(cudaMemsetAsync(gq.G, 0, 3 * NET_WL * sizeof(float), st));
-            WL_CK(cudaMemsetAsync(dtn, 0, sizeof(double), st));
-            for (int bi = 0; bi < batch; ++bi) {
-                const int sm = ud(pick);
-                const float sxi = sx[sm] > 0 ? (float)(1.0 / sx[sm]) : 1.f;
-                // input x / s, target t / (s gain)
-                k_scale_copy<<<blocks(V), 256, 0, st>>>(ng.V, sxi, gq.dx + (size_t)sm * V, gq.fx);
-                k_scale_copy<<<blocks(V), 256, 0, st>>>(ng.V, (float)(sxi / gain), gq.dt + (size_t)sm * V, tt);
-                WL_CK(cudaMemsetAsync(tnorm, 0, sizeof(double), st));
-                k_sumsq<<<blocks(V), 256, 0, st>>>(ng.V, tt, tnorm);
-                net_forward(gq.fx);
-                k_net_loss<<<blocks(V), 256, 0, st>>>(ng.V, gq.Y, tt, tnorm, gq.dY, dtn);
-                // layer 3
-                k_conv_dw<<<dwg, 128, 0, st>>>(ng, gq.A2, gq.dY, gq.G + 2 * NET_WL);
-                k_conv_fwd<<<cb, 128, 0, st>>>(ng, gq.dY, gq.Wb + 2 * NET_WL, gq.Y, nullptr);
-                k_relu_bwd<<<blocks(V * NET_C), 256, 0, st>>>((int)(V * NET_C), gq.Y, gq.Z2, gq.A2);
-                // layer 2 (A2 now holds dZ2)
-                k_conv_dw<<<dwg, 128, 0, st>>>(ng, gq.A1, gq.A2, gq.G + NET_WL);
-                k_conv_fwd<<<cb, 128, 0, st>>>(ng, gq.A2, gq.Wb + NET_WL, gq.Y, nullptr);
-                k_relu_bwd<<<blocks(V * NET_C), 256, 0, st>>>((int)(V * NET_C), gq.Y, gq.Z1, gq.A1);
-                // layer 1 (A1 now holds dZ1)
-                k_conv_dw<<<dwg, 128, 0, st>>>(ng, gq.A0, gq.A1, gq.G);
-                WL_LAUNCH_CK();
-                launches += 14;
-            }
-            ++gq.step;
-            k_adam<<<blocks(3 * NET_WL), 256, 0, st>>>(gq.W, gq.G, gq.m, gq.v, gq.step, (float)lr, (float)batch);
-            k_net_weights<<<blocks(3 * NET_WL), 256, 0, st>>>(gq.W, gq.Wf, gq.Wb);
-            WL_LAUNCH_CK();
-            launches += 2;
-            if (itn == 0 || itn == iters - 1) {
-                WL_CK(cudaMemcpyAsync(hl.data(), dtn, sizeof(double), cudaMemcpyDeviceToHost, st));
-                WL_CK(cudaStreamSynchronize(st));
-                if (itn == 0 && l0) *l0 = hl[0] / batch;
-                if (itn == iters - 1 && l1) *l1 = hl[0] / batch;
-            }
-        }
-        gq.gain = gain;
-        gq.ready = true;
-        WL_CK(cudaStreamSynchronize(st));
-    }
-
-    // ------------------------------------------------------------ adjoint
-    void adj_alloc() {
-        if (ad.ready) return;
-        const long long nc = g.nc;
-        for (int a = 0; a < g.ndim; ++a) {
-            ad.u0[a] = alloc_n<T>(nc); ad.us[a] = alloc_n<T>(nc); ad.lu[a] = alloc_n<T>(nc);
-            ad.x[a] = alloc_n<T>(nc); ad.usb[a] = alloc_n<T>(nc); ad.fb[a] = alloc_n<T>(nc);
-            ad.ub[a] = alloc_n<T>(nc); ad.bku[a] = alloc_n<T>(nc);
-        }
-        ad.ue0 = alloc_n<T>(np); ad.ues = alloc_n<T>(np); ad.le = alloc_n<T>(np); ad.xe = alloc_n<T>(np);
-        ad.uesb = alloc_n<T>(np); ad.ueb = alloc_n<T>(np); ad.bkue = alloc_n<T>(np);
-        ad.bkph = alloc_n<T>(nc); ad.bkpl = alloc_n<T>(nc);
-        ad.lP = alloc_n<double>(nc);
-        ad.dpar = alloc_n<double>(2);
-        for (int q = 0; q < 2; ++q) { ad.qh[q] = alloc_n<T>(nc); ad.ql[q] = alloc_n<T>(nc); }
-        if (!pout) pout = alloc_n<double>(nc);
-        ad.ready = true;
-    }
-    void adj_alloc_params() {
-        adj_alloc();
-        if (ad.pready) return;
-        for (int a = 0; a < g.ndim; ++a) { ad.f1[a] = alloc_n<T>(g.nc); ad.f2[a] = alloc_n<T>(g.nc); }
-        ad.P1h = alloc_n<T>(g.nc); ad.P1l = alloc_n<T>(g.nc); ad.P2h = alloc_n<T>(g.nc); ad.P2l = alloc_n<T>(g.nc);
-        ad.pready = true;
-    }
-    static CVec3P<T> cvp(T *const (&p)[3]) { CVec3P<T> r{}; for (int a = 0; a < 3; ++a) r.p[a] = p[a]; return r; }
-    static Vec3P<T> vvp(T *const (&p)[3]) { Vec3P<T> r{}; for (int a = 0; a < 3; ++a) r.p[a] = p[a]; return r; }
-    void zero_vec(T *const (&p)[3]) {
-        for (int a = 0; a < g.ndim; ++a) WL_CK(cudaMemsetAsync(p[a], 0, g.nc * sizeof(T), st));
-    }
-    void copy_vec(T *const (&dst)[3], T *const (&src)[3]) {
-        for (int a = 0; a < g.ndim; ++a)
-            WL_CK(cudaMemcpyAsync(dst[a], src[a], g.nc * sizeof(T), cudaMemcpyDeviceToDevice, st));
-    }
-    void dcopy(T *dst, const T *src, size_t n) {
-        WL_CK(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
-    }
-
-    // Tangents of the body state at time tt along the heave and pitch amplitudes.
-    void param_tangents(double tt, BodyTangent &h, BodyTangent &p) const {
-        std::memset(&h, 0, sizeof(h));
-        std::memset(&p, 0, sizeof(p));
-        const int ax = body.heave_axis;
-        if (ax >= 0 && ax < 3) {
-            h.dc[ax] = std::sin(body.omega * tt + body.phase);
-            h.dvc[ax] = body.omega * std::cos(body.omega * tt + body.phase);
-        }
-        if (body.kind == WL_BODY_ELLIPSE) {
-            p.dth = std::sin(body.omega * tt + body.phase + 0.5 * PI);
-            p.dthd = body.omega * std::cos(body.omega * tt + body.phase + 0.5 * PI);
-        }
-    }
-
-    // Projection transposed: (out, oute) = (lam, le) + D^T A^+ (div(c lam) + lP/(w dt)).
-    // With the stage's forward pressure (Ph, Pl) and params, also the
-    // coefficient part of the parameter gradient.
-    int proj_vjp(T *const (&lam)[3], const T *le, const double *lP, double w, double dt, T *const (&out)[3], T *oute,
-                 wl_solve_stats *sts, const T *Ph = nullptr, const T *Pl = nullptr, const BodyTangent *dB = nullptr,
-                 double tt = 0.0, int stage = -1) {
-        P0("adj_rhs", 0, g.nc);
-        k_adj_rhs<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], cvp(lam), lP, 1.0 / (w * dt), b, bl);
-        P1();
-        k_bstats<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], b, S, part);
-        WL_LAUNCH_CK();
-        launches += 2;
-        // warm start: the same stage's solution of the previous reverse step
-        // over a window (any start converges to the same solution), else 0
-        const bool warm = stage >= 0 && ad.qwarm && ad.qvalid[stage];
-        if (warm) {
-            dcopy(ph, ad.qh[stage], g.nc);
-            dcopy(pl, ad.ql[stage], g.nc);
-        } else {
-            WL_CK(cudaMemsetAsync(ph, 0, g.nc * sizeof(T), st));
-            WL_CK(cudaMemsetAsync(pl, 0, g.nc * sizeof(T), st));
-        }
-        const int rc = solve(sts);
-        if (stage >= 0 && ad.qwarm) {
-            dcopy(ad.qh[stage], ph, g.nc);
-            dcopy(ad.ql[stage], pl, g.nc);
-            ad.qvalid[stage] = true;
-        }
-        if (Ph && dB) {
-            P0("adj_param_coef", 0, g.nc);
-            k_adj_param_coef<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], Ph, Pl, ph, pl, cvp(lam), w * dt,
-                                                                 body_state(tt), dB[0], dB[1], S, part, ad.dpar);
-            P1();
-            WL_LAUNCH_CK();
-            ++launches;
-        }
-        pmean();
-        P0("adj_grad", 0, g.nc);
-        k_adj_grad<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], ph, pl, S, cvp(lam), le, vvp(out), oute);
-        P1();
-        WL_LAUNCH_CK();
-        ++launches;
-        return rc;
-    }
-
-    void adj_flux(T *const (&u)[3], const T *ue, T *const (&lam)[3], T *const (&ub)[3], T *ueb) {
-        P0("adj_flux", 0, g.nc);
-        k_adj_flux<T, ND><<<blocks(g.nc), 256, 0, st>>>(g, cvp(u), ue, cvp(lam), vvp(ub), ueb);
-        P1();
-        WL_LAUNCH_CK();
-        ++launches;
-    }
-
-    void adj_blend(T *const (&gin)[3], double s, T *const *ustar_b, T *const (&ub)[3], T *const (&fb)[3], double dt) {
-        Vec3P<T> sb{};
-        for (int a = 0; a < 3; ++a) sb.p[a] = ustar_b ? ustar_b[a] : nullptr;
-        P0("adj_blend", 0, g.nc);
-        k_adj_blend<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], cvp(gin), (T)s, mu1n, (long long)g.nc, has_body, sb,
-                                                        vvp(ub), vvp(fb), (T)dt);
-        P1();
-        WL_LAUNCH_CK();
-        ++launches;
-    }
-
-    void adj_param_blend(T *const (&gin)[3], double s, T *const (&f)[3], const BodyTangent *dB, double tt) {
-        CVec3P<T> V{};
-        for (int a = 0; a < 3; ++a) V.p[a] = Vb[a];
-        P0("adj_param_blend", 0, g.nc);
-        k_adj_param_blend<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], cvp(gin), (T)s, cvp(f), V, body_state(tt),
-                                                              dB[0], dB[1], S, part, ad.dpar);
-        P1();
-        WL_LAUNCH_CK();
-        ++launches;
-    }
-
-    // Core of the step's adjoint on device buffers. In: ad.u0 / ad.ue0 (start
-    // state), ph / pl (warm start), ad.lu / ad.le (cotangents of the step's
-    // velocity and exit plane), ad.lP when haveP (of its pressure). Out:
-    // ad.ub / ad.ueb. With params, the heave / pitch amplitude derivative of
-    // the step (and of wF . F of its pressure, wF may be null) is added into
-    // ad.dpar. Leaves the velocity slots, exit planes and ph / pl changed.
-    int vjp_core(double t0, double dt, bool haveP, double tol, bool params, const double *wF, wl_solve_stats *sts) {
-        const size_t pb = (size_t)np * sizeof(T);
-        const double t1 = t0 + dt;
-        const double tol0 = cfg.tol;
-        const bool gc = gq.collect, gu = gq.use;
-        gq.collect = gq.use = false;
-        cfg.tol = tol;
-        if (has_body && (moving || body_t != t1)) body_update(t1);
-        params = params && has_body;
-        BodyTangent dB[2];
-        if (params) { adj_alloc_params(); param_tangents(t1, dB[0], dB[1]); }
-        wl_solve_stats s[2] = {};
-        // forward predictor: u*, u_e* (and its blend input and pressure)
-        copy_vec(vel[cur], ad.u0);
-        if (g.exit_x) {
-            dcopy(ueA, ad.ue0, np);
-            dcopy(ueB, ad.ue0, np);
-        }
-        const int A0 = cur, B1 = (cur + 1) & 3, C2 = (cur + 2) & 3, D3 = (cur + 3) & 3;
-        int ustar;
-        if (!has_body) {
-            flux<FM_PRED_U>(fargs(A0, ueB, -1, B1, dt));
-            ustar = B1;
-        } else {
-            flux<FM_PRED_F>(fargs(A0, ueB, -1, B1, dt));
-            if (params) copy_vec(ad.f1, vel[B1]);
-            blend(false, B1, -1, C2);
-            ustar = C2;
-        }
-        exit_stage(false, A0, dt);
-        int r0 = project_buf(ustar, ueA, 1.0, dt, nullptr);
-        copy_vec(ad.us, vel[ustar]);
-        if (g.exit_x) dcopy(ad.ues, ueA, np);
-        int r0c = WL_OK;
-        if (params) {
-            // forward corrector: its blend input and pressure
-            dcopy(ad.P1h, ph, g.nc);
-            dcopy(ad.P1l, pl, g.nc);
-            flux<FM_CORR_F>(fargs(ustar, ueA, A0, B1, dt));
-            copy_vec(ad.f2, vel[B1]);
-            blend(true, B1, ustar, D3);
-            exit_stage(true, ustar, dt);
-            r0c = project_buf(D3, ueA, 0.5, dt, nullptr);
-            dcopy(ad.P2h, ph, g.nc);
-            dcopy(ad.P2l, pl, g.nc);
-            if (wF) {
-                // direct dependence of wF . F on the body at fixed pressure
-                pmean();
-                P0("force_dparam", 0, g.nc);
-                k_force_dparam<T><<<blocks(g.nc), 256, 0, st>>>(g, body_state(t1), dB[0], dB[1], ph, pl, lv[0].invD,
-                                                                wF[0], wF[1], wF[2], S, part, ad.dpar);
-                P1();
-                WL_LAUNCH_CK();
-                ++launches;
-            }
-        }
-        // reverse: corrector projection, exit, blend, flux at u*
-        int r1 = proj_vjp(ad.lu, g.exit_x ? ad.le : nullptr, haveP ? ad.lP : nullptr, 0.5, dt, ad.x, ad.xe, &s[1],
-                          params ? ad.P2h : nullptr, params ? ad.P2l : nullptr, params ? dB : nullptr, t1, 1);
-        zero_vec(ad.ub);
-        zero_vec(ad.usb);
-        if (g.exit_x) {
-            WL_CK(cudaMemsetAsync(ad.ueb, 0, pb, st));
-            WL_CK(cudaMemsetAsync(ad.uesb, 0, pb, st));
-            k_adj_exit<T, true><<<1, 1024, 0, st>>>(g, ad.xe, (T)dt, ad.ueb, ad.uesb, ad.usb[0]);
-            WL_LAUNCH_CK();
-            ++launches;
-        }
-        if (params) adj_param_blend(ad.x, 0.5, ad.f2, dB, t1);
-        adj_blend(ad.x, 0.5, ad.usb, ad.ub, ad.fb, dt);
-        adj_flux(ad.us, ad.ues, ad.fb, ad.usb, ad.uesb);
-        // predictor projection, exit, blend, flux at u0
-        int r2 = proj_vjp(ad.usb, g.exit_x ? ad.uesb : nullptr, nullptr, 1.0, dt, ad.x, ad.xe, &s[0],
-                          params ? ad.P1h : nullptr, params ? ad.P1l : nullptr, params ? dB : nullptr, t1, 0);
-        if (g.exit_x) {
-            k_adj_exit<T, false><<<1, 1024, 0, st>>>(g, ad.xe, (T)dt, ad.ueb, ad.ueb, ad.ub[0]);
-            WL_LAUNCH_CK();
-            ++launches;
-        }
-        if (params) adj_param_blend(ad.x, 1.0, ad.f1, dB, t1);
-        adj_blend(ad.x, 1.0, nullptr, ad.ub, ad.fb, dt);
-        adj_flux(ad.u0, ad.ue0, ad.fb, ad.ub, ad.ueb);
-        cfg.tol = tol0;
-        gq.collect = gc;
-        gq.use = gu;
-        if (sts) { sts[0] = s[0]; sts[1] = s[1]; }
-        int rc = WL_OK;
-        for (int r : {r0, r0c, r1, r2})
-            if (r != WL_OK && rc == WL_OK) rc = r;
-        if (rc == WL_ERR_NONFINITE) err = "non-finite values in the adjoint step";
-        else if (rc == WL_ERR_NOT_CONVERGED) err = "a Poisson solve of the adjoint step did not reach tol";
-        return rc;
-    }
-
-    void backup_state() {
-        copy_vec(ad.bku, vel[cur]);
-        dcopy(ad.bkue, ueA, np);
-        dcopy(ad.bkph, ph, g.nc);
-        dcopy(ad.bkpl, pl, g.nc);
-    }
-    void restore_state(double body_t0) {
-        copy_vec(vel[cur], ad.bku);
-        dcopy(ueA, ad.bkue, np);
-        dcopy(ph, ad.bkph, g.nc);
-        dcopy(pl, ad.bkpl, g.nc);
-        if (has_body && body_t != body_t0 && body_t0 >= 0) body_update(body_t0);
-    }
-
-    // Vector-Jacobian product of one step (mom_step with a fixed dt, body
-    // measured at t0 + dt) at the start state (u0, ue0), warm start P0: given
-    // the cotangents (lu, le) of the step's velocity and exit plane and lP of
-    // its reported pressure, returns (ub, ueb) for (u0, ue0). The sim's state
-    // (velocity, exit plane, pressure, time, body) is left as it was.
-    int step_vjp(double t0, double dt, const void *u0, const void *ue0, const double *P0in, const void *lu,
-                 const void *le, const double *lP, double tol, void *ub, void *ueb, wl_solve_stats *sts) override {
-        if (!(dt > 0)) throw Err{WL_ERR_ARG, "step_vjp: dt must be positive"};
-        adj_alloc();
-        const size_t vb = g.nc * sizeof(T), pb = (size_t)np * sizeof(T);
-        const double body_t0 = body_t;
-        backup_state();
-        for (int a = 0; a < g.ndim; ++a) {
-            WL_CK(cudaMemcpyAsync(ad.u0[a], (const char *)u0 + a * vb, vb, cudaMemcpyDefault, st));
-            WL_CK(cudaMemcpyAsync(ad.lu[a], (const char *)lu + a * vb, vb, cudaMemcpyDefault, st));
-        }
-        if (g.exit_x) {
-            if (ue0) WL_CK(cudaMemcpyAsync(ad.ue0, ue0, pb, cudaMemcpyDefault, st));
-            else k_fill<T><<<blocks(np), 256, 0, st>>>((long long)np, (T)g.U[0], ad.ue0);
-            if (le) WL_CK(cudaMemcpyAsync(ad.le, le, pb, cudaMemcpyDefault, st));
-            else WL_CK(cudaMemsetAsync(ad.le, 0, pb, st));
-        }
-        if (lP) WL_CK(cudaMemcpyAsync(ad.lP, lP, g.nc * sizeof(double), cudaMemcpyDefault, st));
-        if (P0in) {
-            WL_CK(cudaMemcpyAsync(pout, P0in, g.nc * sizeof(double), cudaMemcpyDefault, st));
-            k_pin<T><<<blocks(g.nc), 256, 0, st>>>(g, pout, ph, pl);
-            WL_LAUNCH_CK();
-            ++launches;
-        } else {
-            WL_CK(cudaMemsetAsync(ph, 0, vb, st));
-            WL_CK(cudaMemsetAsync(pl, 0, vb, st));
-        }
-        const int rc = vjp_core(t0, dt, lP != nullptr, tol, false, nullptr, sts);
-        for (int a = 0; a < g.ndim; ++a) WL_CK(cudaMemcpyAsync((char *)ub + a * vb, ad.ub[a], vb, cudaMemcpyDefault, st));
-        if (ueb && g.exit_x) WL_CK(cudaMemcpyAsync(ueb, ad.ueb, pb, cudaMemcpyDefault, st));
-        restore_state(body_t0);
-        WL_CK(cudaStreamSynchronize(st));
-        prof.flush();
-        return rc;
-    }
-
-    // Weighted pressure derivative of the force into ad.lP: scale * sum_a w_a dF_a/dp.
-    void force_dp_w(double tt, const double *w, double scale) {
-        adj_alloc();
-        if (!has_body) {
-            WL_CK(cudaMemsetAsync(ad.lP, 0, g.nc * sizeof(double), st));
-            return;
-        }
-        k_force_dp<T><<<blocks(g.nc), 256, 0, st>>>(g, body_state(tt), lv[0].invD, w[0] * scale, w[1] * scale,
-                                                    w[2] * scale, ad.lP);
-        WL_LAUNCH_CK();
-        ++launches;
-    }
-
-    void force_dp(int axis, double scale, double *gout) override {
-        if (axis < 0 || axis >= g.ndim) throw Err{WL_ERR_ARG, "force_dp: axis out of range"};
-        double w[3] = {0, 0, 0};
-        w[axis] = 1.0;
-        force_dp_w(body_t, w, scale);
-        WL_CK(cudaMemcpyAsync(gout, ad.lP, g.nc * sizeof(double), cudaMemcpyDefault, st));
-        WL_CK(cudaStreamSynchronize(st));
-    }
-
-    // ------------------------------------------------- checkpointed window
-    Snap snap_alloc() {
-        Snap s{};
-        for (int a = 0; a < g.ndim; ++a) s.u[a] = alloc_n<T>(g.nc);
-        s.ue = alloc_n<T>(np);
-        s.ph = alloc_n<T>(g.nc);
-        s.pl = alloc_n<T>(g.nc);
-        return s;
-    }
-    void snap_take(Snap &s) {
-        copy_vec(s.u, vel[cur]);
-        dcopy(s.ue, ueA, np);
-        dcopy(s.ph, ph, g.nc);
-        dcopy(s.pl, pl, g.nc);
-        s.t = t;
-    }
-    void snap_put(const Snap &s) {
-        copy_vec(vel[cur], s.u);
-        dcopy(ueA, s.ue, np);
-        dcopy(ph, s.ph, g.nc);
-        dcopy(pl, s.pl, g.nc);
-        t = s.t;
-    }
-
-    int window_forward(int nsteps, int ckpt, const double *dts, const double *w, double *J, double *dts_out) override {
-        if (nsteps < 1 || ckpt < 1) throw Err{WL_ERR_ARG, "window: nsteps and ckpt_every must be >= 1"};
-        adj_alloc();
-        const int nck = (nsteps + ckpt - 1) / ckpt;
-        if ((int)win.ck.size() < nck) while ((int)win.ck.size() < nck) win.ck.push_back(snap_alloc());
-        if ((int)win.seg.size() < ckpt) while ((int)win.seg.size() < ckpt) win.seg.push_back(snap_alloc());
-        if (!win.fin.ue) win.fin = snap_alloc();
-        win.active = false;
-        // the learned guesses change the converged fields only within the
-        // solver tolerance, but the backward sweep's recomputation must repeat
-        // this forward run exactly: both stay off over the window
-        const bool tgu = tg.use, gqu = gq.use;
-        tg.use = gq.use = false;
-        struct Restore { bool &a, &b; bool va, vb; ~Restore() { a = va; b = vb; } } rs{tg.use, gq.use, tgu, gqu};
-        win.n = nsteps;
-        win.k = ckpt;
-        for (int a = 0; a < 3; ++a) win.w[a] = w ? w[a] : 0.0;
-        win.dts.assign(nsteps, 0.0);
-        double Jv = 0.0;
-        for (int n = 0; n < nsteps; ++n) {
-            if (n % ckpt == 0) snap_take(win.ck[n / ckpt]);
-            const double dt = dts ? dts[n] : dt_next;
-            win.dts[n] = dt;
-            const int rc = mom_step(dt, nullptr);
-            if (rc != WL_OK) return rc;
-            if (w && has_body) {
-                double F[3];
-                forces(F);
-                Jv += w[0] * F[0] + w[1] * F[1] + w[2] * F[2];
-            }
-        }
-        snap_take(win.fin);
-        win.fin_dt_next = dt_next;
-        WL_CK(cudaStreamSynchronize(st));
-        if (J) *J = Jv;
-        if (dts_out) for (int n = 0; n < nsteps; ++n) dts_out[n] = win.dts[n];
-        win.active = true;
-        return WL_OK;
-    }
-
-    int window_backward(double gJ, const void *luf, const void *lef, double tol, void *du0, void *due0,
-                        double *dparams) override {
-        if (!win.active) throw Err{WL_ERR_STATE, "window_backward: no forward window is held"};
-        adj_alloc();
-        const size_t vb = g.nc * sizeof(T), pb = (size_t)np * sizeof(T);
-        const bool params = dparams != nullptr && has_body;
-        const bool force = has_body && (win.w[0] != 0 || win.w[1] != 0 || win.w[2] != 0) && gJ != 0.0;
-        double wF[3] = {gJ * win.w[0], gJ * win.w[1], gJ * win.w[2]};
-        // final cotangents
-        for (int a = 0; a < g.ndim; ++a) {
-            if (luf) WL_CK(cudaMemcpyAsync(ad.lu[a], (const char *)luf + a * vb, vb, cudaMemcpyDefault, st));
-            else WL_CK(cudaMemsetAsync(ad.lu[a], 0, vb, st));
-        }
-        if (g.exit_x) {
-            if (lef) WL_CK(cudaMemcpyAsync(ad.le, lef, pb, cudaMemcpyDefault, st));
-            else WL_CK(cudaMemsetAsync(ad.le, 0, pb, st));
-        }
-        WL_CK(cudaMemsetAsync(ad.dpar, 0, 2 * sizeof(double), st));
-        const bool tgu = tg.use, gqu = gq.use;
-        tg.use = gq.use = false;
-        struct Restore { bool &a, &b; bool va, vb; ~Restore() { a = va; b = vb; } } rs{tg.use, gq.use, tgu, gqu};
-        ad.qwarm = true;
-        ad.qvalid[0] = ad.qvalid[1] = false;
-        struct QOff { bool &q; ~QOff() { q = false; } } qoff{ad.qwarm};
-        int rc = WL_OK;
-        const int nseg = (win.n + win.k - 1) / win.k;
-        for (int sgi = nseg - 1; sgi >= 0 && rc == WL_OK; --sgi) {
-            const int n0 = sgi * win.k, n1 = std::min(win.n, n0 + win.k);
-            // recompute the segment's start states from its checkpoint
-            snap_put(win.ck[sgi]);
-            for (int n = n0; n < n1; ++n) {
-                snap_take(win.seg[n - n0]);
-                if (n + 1 < n1) {
-                    const int r = mom_step(win.dts[n], nullptr);
-                    if (r != WL_OK && r != WL_ERR_NOT_CONVERGED) { rc = r; break; }
-                }
-            }
-            for (int n = n1 - 1; n >= n0 && rc == WL_OK; --n) {
-                const Snap &s = win.seg[n - n0];
-                const double dt = win.dts[n];
-                copy_vec(ad.u0, s.u);
-                dcopy(ad.ue0, s.ue, np);
-                dcopy(ph, s.ph, g.nc);
-                dcopy(pl, s.pl, g.nc);
-                if (has_body && (moving || body_t != s.t + dt)) body_update(s.t + dt);
-                if (force) force_dp_w(s.t + dt, win.w, gJ);
-                const int r = vjp_core(s.t, dt, force, tol, params, force ? wF : nullptr, nullptr);
-                if (r == WL_ERR_NONFINITE) rc = r;
-                for (int a = 0; a < 3; ++a) std::swap(ad.lu[a], ad.ub[a]);
-                std::swap(ad.le, ad.ueb);
-            }
-        }
-        if (rc == WL_OK) {
-            for (int a = 0; a < g.ndim; ++a)
-                if (du0) WL_CK(cudaMemcpyAsync((char *)du0 + a * vb, ad.lu[a], vb, cudaMemcpyDefault, st));
-            if (due0 && g.exit_x) WL_CK(cudaMemcpyAsync(due0, ad.le, pb, cudaMemcpyDefault, st));
-            if (dparams) WL_CK(cudaMemcpyAsync(dparams, ad.dpar, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
-        }
-        // back to the state after the window
-        snap_put(win.fin);
-        dt_next = win.fin_dt_next;
-        if (has_body && (moving || body_t != t)) body_update(t);
-        WL_CK(cudaStreamSynchronize(st));
-        prof.flush();
-        return rc;
-    }
-
-    void set_body(const wl_body *bd) override {
-        if (!bd || bd->kind != body.kind) throw Err{WL_ERR_ARG, "set_body: the body kind cannot change"};
-        body = *bd;
-        moving = has_body && (body.heave_amp != 0.0 || body.pitch_amp != 0.0);
-        win.active = false;
-        if (has_body) body_update(body_t >= 0 ? body_t : t);
-        // the coarsest level's dense operator follows the new coefficients
-        const bool want = gl[nlev - 1].nc <= 256 && !moving;
-        const bool was = cdense;
-        cdense = want && coarse_dense_build();
-        if (cdense != was) build_vcycle_graph();
-        WL_CK(cudaStreamSynchronize(st));
-    }
-
-    void info(int *levels, long long *nl) override {
-        if (levels) *levels = nlev;
-        if (nl) *nl = launches;
-    }
-};
 
 int validate(const wl_config *c, const wl_body *bd, std::string &msg) {
     if (!c) { msg = "cfg is NULL"; return WL_ERR_ARG; }
@@ -1734,13 +93,9 @@ int wl_sim_create(const wl_config *cfg, const wl_body *body, wl_sim **out) {
     wl_sim *s = new (std::nothrow) wl_sim();
     if (!s) return WL_ERR_ALLOC;
     try {
-        if (cfg->precision == WL_F64) {
-            if (cfg->ndim == 3) { auto *p = new Sim<double, 3>(); s->impl = p; p->init(*cfg, body); }
-            else { auto *p = new Sim<double, 2>(); s->impl = p; p->init(*cfg, body); }
-        } else {
-            if (cfg->ndim == 3) { auto *p = new Sim<float, 3>(); s->impl = p; p->init(*cfg, body); }
-            else { auto *p = new Sim<float, 2>(); s->impl = p; p->init(*cfg, body); }
-        }
+        if (cfg->precision == WL_F64) s->impl = cfg->ndim == 3 ? wl::new_sim_f64_3d() : wl::new_sim_f64_2d();
+        else s->impl = cfg->ndim == 3 ? wl::new_sim_f32_3d() : wl::new_sim_f32_2d();
+        s->impl->init(*cfg, body);
     } catch (const Err &e) {
         std::fprintf(stderr, "wl_sim_create: %s\n", e.msg.c_str());
         delete s->impl;

@@ -14,7 +14,7 @@ NOT_STREAMING = {"coarsest", "padd", "exit", "tguess_apply", "guess_net", "guess
 
 
 def _named_launches():
-    src = open(os.path.join(ROOT, "paper_2407_16032_b300", "csrc", "wl_api.cu")).read()
+    src = open(os.path.join(ROOT, "paper_2407_16032_b300", "csrc", "wl_sim.cuh")).read()
     names = set()
     for args in re.findall(r'\b(?:B|P0)\(([^;]*);', src):   # every quoted name in the call's arguments
         names |= set(re.findall(r'"([a-z_0-9]+)"', args))
