@@ -27,9 +27,10 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so (plain gcc, no fast-math, no FMA contraction)."""
+    """Compile liboracle.so (plain gcc, no fast-math, no FMA contraction; OpenMP
+    over cells with results independent of the thread count)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off", "-fopenmp",
                "-o", _LIB + ".tmp", _SRC, "-lm"]
         subprocess.check_call(cmd)
         os.replace(_LIB + ".tmp", _LIB)
@@ -66,6 +67,8 @@ def lib():
         _lib = C.CDLL(build())
         L = _lib
         for name, args, res in [
+            ("orc_set_threads", [C.c_int], None),
+            ("orc_get_threads", [], C.c_int),
             ("orc_quick", [C.c_double] * 3, C.c_double),
             ("orc_mu0", [C.c_double, C.c_double], C.c_double),
             ("orc_mu1", [C.c_double, C.c_double], C.c_double),
@@ -101,6 +104,23 @@ def lib():
             f.argtypes = args
             f.restype = res
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's per-cell loops (results do not depend on it)."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+def host_cores() -> int:
+    """Cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def _p(a):

@@ -24,6 +24,12 @@
  * kernel moments, the exit condition, multigrid details, CFL formula).
  *
  * Layout: every field is component-major, x fastest: u[a*nc + i + n0*(j + n1*k)].
+ *
+ * Threads: the per-cell loops carry OpenMP pragmas (compiled with -fopenmp;
+ * without it they are ignored). Every cell's value is computed by the same
+ * expression whatever thread runs it, and every sum over cells uses a fixed
+ * blocked order (fixed_sum), so results are bitwise identical for any number
+ * of threads. The adjoint routines, whose loops scatter, stay serial.
  * 2D uses n[2] = 1 and ndim = 2.
  */
 #include <math.h>
@@ -31,7 +37,30 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #define OR_PI 3.14159265358979323846
+
+/* Number of OpenMP threads of the per-cell loops (1 without OpenMP). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 typedef struct {
     int ndim;
@@ -155,6 +184,7 @@ void orc_conv_diff(const orc_grid *g, const double *u, const double *ue, double 
 {
     size_t nc = ncell(g);
     for (int a = 0; a < g->ndim; ++a)
+        #pragma omp parallel for collapse(2) schedule(static)
         for (int k = 0; k < g->n[2]; ++k)
             for (int j = 0; j < g->n[1]; ++j)
                 for (int i = 0; i < g->n[0]; ++i) {
@@ -254,6 +284,7 @@ void orc_measure(const orc_grid *g, const orc_body *B, double t, double *mu0, do
 {
     size_t nc = ncell(g);
     for (int a = 0; a < g->ndim; ++a)
+        #pragma omp parallel for collapse(2) schedule(static)
         for (int k = 0; k < g->n[2]; ++k)
             for (int j = 0; j < g->n[1]; ++j)
                 for (int i = 0; i < g->n[0]; ++i) {
@@ -275,6 +306,7 @@ void orc_coeffs(const orc_grid *g, const double *mu0, double *c)
 {
     size_t nc = ncell(g);
     for (int a = 0; a < g->ndim; ++a)
+        #pragma omp parallel for collapse(2) schedule(static)
         for (int k = 0; k < g->n[2]; ++k)
             for (int j = 0; j < g->n[1]; ++j)
                 for (int i = 0; i < g->n[0]; ++i) {
@@ -299,6 +331,7 @@ void orc_bdim(const orc_grid *g, const double *u0, const double *r, double dt,
     double *f = (double *)malloc(sizeof(double) * g->ndim * nc);
     for (size_t q = 0; q < (size_t)g->ndim * nc; ++q) f[q] = u0[q] + dt * r[q];
     for (int a = 0; a < g->ndim; ++a)
+        #pragma omp parallel for collapse(2) schedule(static)
         for (int k = 0; k < g->n[2]; ++k)
             for (int j = 0; j < g->n[1]; ++j)
                 for (int i = 0; i < g->n[0]; ++i) {
@@ -374,6 +407,7 @@ void orc_exit_bc(const orc_grid *g, const double *ue0, const double *uG, const d
 /* Discrete divergence sum_a (u_a[I+e_a] - u_a[I]). */
 void orc_divergence(const orc_grid *g, const double *u, const double *ue, double *div)
 {
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < g->n[2]; ++k)
         for (int j = 0; j < g->n[1]; ++j)
             for (int i = 0; i < g->n[0]; ++i) {
@@ -446,6 +480,7 @@ static double lv_diag(const orc_level *L, int i, int j, int k)
 
 static void lv_apply(const orc_level *L, const double *p, double *Ap)
 {
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < L->n[2]; ++k)
         for (int j = 0; j < L->n[1]; ++j)
             for (int i = 0; i < L->n[0]; ++i) Ap[lv_lin(L, i, j, k)] = lv_apply_row(L, p, i, j, k);
@@ -469,6 +504,7 @@ void orc_poisson_apply(const orc_grid *g, const double *c, const double *p, doub
 void orc_poisson_diag(const orc_grid *g, const double *c, double *D)
 {
     orc_level L = fine_level(g, (double *)c);
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < L.n[2]; ++k)
         for (int j = 0; j < L.n[1]; ++j)
             for (int i = 0; i < L.n[0]; ++i) D[lv_lin(&L, i, j, k)] = lv_diag(&L, i, j, k);
@@ -500,6 +536,7 @@ static void coarsen(const orc_level *F, orc_level *C)
     C->c = (double *)calloc((size_t)C->ndim * ncc, sizeof(double));
     int kz = F->ndim == 3 ? 2 : 1;
     for (int a = 0; a < C->ndim; ++a)
+        #pragma omp parallel for collapse(2) schedule(static)
         for (int k = 0; k < C->n[2]; ++k)
             for (int j = 0; j < C->n[1]; ++j)
                 for (int i = 0; i < C->n[0]; ++i) {
@@ -518,6 +555,7 @@ static void coarsen(const orc_level *F, orc_level *C)
 static void restrict_sum(const orc_level *F, const orc_level *C, const double *rf, double *rc)
 {
     int kz = F->ndim == 3 ? 2 : 1;
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < C->n[2]; ++k)
         for (int j = 0; j < C->n[1]; ++j)
             for (int i = 0; i < C->n[0]; ++i) {
@@ -531,18 +569,46 @@ static void restrict_sum(const orc_level *F, const orc_level *C, const double *r
 
 static void prolong_inject(const orc_level *F, const orc_level *C, const double *ec, double *ef)
 {
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < F->n[2]; ++k)
         for (int j = 0; j < F->n[1]; ++j)
             for (int i = 0; i < F->n[0]; ++i)
                 ef[lv_lin(F, i, j, k)] = ec[lv_lin(C, i / 2, j / 2, F->ndim == 3 ? k / 2 : 0)];
 }
 
-static double dot(const double *a, const double *b, size_t n)
+/* Sums over a level in a fixed order that does not depend on the number of
+ * threads: consecutive blocks of OR_RBLOCK terms are summed left to right
+ * (blocks in parallel), then the block sums left to right. Below one block
+ * this is the plain left-to-right sum. */
+#define OR_RBLOCK 4096
+
+/* sum_q w[q] a[q] b[q], with a NULL w counting every term once and a NULL b
+ * taking b[q] = 1; w is a 0/1 mask (active rows) */
+static double fixed_sum(const double *a, const double *b, const char *w, size_t n)
 {
+    size_t nb = (n + OR_RBLOCK - 1) / OR_RBLOCK;
+    if (nb <= 1) {
+        double s = 0.0;
+        for (size_t q = 0; q < n; ++q)
+            if (!w || w[q]) s += b ? a[q] * b[q] : a[q];
+        return s;
+    }
+    double *part = malloc(nb * sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (size_t blk = 0; blk < nb; ++blk) {
+        size_t q1 = (blk + 1) * OR_RBLOCK < n ? (blk + 1) * OR_RBLOCK : n;
+        double s = 0.0;
+        for (size_t q = blk * OR_RBLOCK; q < q1; ++q)
+            if (!w || w[q]) s += b ? a[q] * b[q] : a[q];
+        part[blk] = s;
+    }
     double s = 0.0;
-    for (size_t q = 0; q < n; ++q) s += a[q] * b[q];
+    for (size_t blk = 0; blk < nb; ++blk) s += part[blk];
+    free(part);
     return s;
 }
+
+static double dot(const double *a, const double *b, size_t n) { return fixed_sum(a, b, NULL, n); }
 
 /* Jacobi-preconditioned CG on A x = r from the given x, for `iters` iterations
  * or until the residual norm falls to rtol * |r|. Rows with zero diagonal are
@@ -553,6 +619,7 @@ static void pcg(const orc_level *L, const double *r, double *x, int iters, doubl
     double *s = malloc(n * sizeof(double)), *z = malloc(n * sizeof(double));
     double *d = malloc(n * sizeof(double)), *q = malloc(n * sizeof(double));
     double *iD = malloc(n * sizeof(double));
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < L->n[2]; ++k)
         for (int j = 0; j < L->n[1]; ++j)
             for (int i = 0; i < L->n[0]; ++i) {
@@ -560,6 +627,7 @@ static void pcg(const orc_level *L, const double *r, double *x, int iters, doubl
                 iD[lv_lin(L, i, j, k)] = D != 0.0 ? 1.0 / D : 0.0;
             }
     lv_apply(L, x, q);
+#pragma omp parallel for schedule(static)
     for (size_t e = 0; e < n; ++e) { s[e] = iD[e] != 0.0 ? r[e] - q[e] : 0.0; z[e] = iD[e] * s[e]; d[e] = z[e]; }
     double rho = dot(s, z, n);
     double r0 = sqrt(dot(r, r, n));
@@ -570,10 +638,12 @@ static void pcg(const orc_level *L, const double *r, double *x, int iters, doubl
         double dq = dot(d, q, n);
         if (dq == 0.0) break;
         double alpha = rho / dq;
+#pragma omp parallel for schedule(static)
         for (size_t e = 0; e < n; ++e) { x[e] += alpha * d[e]; s[e] -= alpha * q[e]; z[e] = iD[e] * s[e]; }
         double rho2 = dot(s, z, n);
         double beta = rho2 / rho;
         rho = rho2;
+#pragma omp parallel for schedule(static)
         for (size_t e = 0; e < n; ++e) d[e] = z[e] + beta * d[e];
     }
     free(s); free(z); free(d); free(q); free(iD);
@@ -643,8 +713,10 @@ int orc_poisson_solve(const orc_grid *g, const double *c, const double *b_in, do
     double *D = malloc(n * sizeof(double)), *b = malloc(n * sizeof(double));
     double *r = malloc(n * sizeof(double)), *e = malloc(n * sizeof(double));
     orc_poisson_diag(g, c, D);
-    double sb = 0.0, na = 0.0;
-    for (size_t q = 0; q < n; ++q) if (D[q] != 0.0) { sb += b_in[q]; na += 1.0; }
+    char *act = malloc(n);
+    double na = 0.0;
+    for (size_t q = 0; q < n; ++q) { act[q] = D[q] != 0.0; na += act[q] ? 1.0 : 0.0; }
+    double sb = fixed_sum(b_in, NULL, act, n);
     double mean = na > 0 ? sb / na : 0.0;
     for (size_t q = 0; q < n; ++q) b[q] = D[q] != 0.0 ? b_in[q] - mean : 0.0;
     double bn = sqrt(dot(b, b, n));
@@ -652,22 +724,23 @@ int orc_poisson_solve(const orc_grid *g, const double *c, const double *b_in, do
     double rel = 0.0;
     for (;;) {
         lv_apply(&lev[0], p, r);
+#pragma omp parallel for schedule(static)
         for (size_t q = 0; q < n; ++q) r[q] = D[q] != 0.0 ? b[q] - r[q] : 0.0;
         double rn = sqrt(dot(r, r, n));
         rel = bn > 0.0 ? rn / bn : 0.0;
         if (rel <= S->tol) break;
         if (it >= S->itmax) { rc = 1; break; }
         vcycle(lev, 0, nlev, r, e, S->smooth_iters);
+#pragma omp parallel for schedule(static)
         for (size_t q = 0; q < n; ++q) p[q] += e[q];
         ++it;
     }
-    double sp = 0.0;
-    for (size_t q = 0; q < n; ++q) if (D[q] != 0.0) sp += p[q];
+    double sp = fixed_sum(p, NULL, act, n);
     double pm = na > 0 ? sp / na : 0.0;
     for (size_t q = 0; q < n; ++q) p[q] = D[q] != 0.0 ? p[q] - pm : 0.0;
     if (st) { st->vcycles = it; st->rel_resid = rel; st->bnorm = bn; }
     for (int l = 1; l < nlev; ++l) free(lev[l].c);
-    free(D); free(b); free(r); free(e);
+    free(D); free(b); free(r); free(e); free(act);
     return rc;
 }
 
@@ -677,6 +750,7 @@ void orc_grad_update(const orc_grid *g, const double *c, const double *p, double
     size_t nc = ncell(g);
     orc_level L = fine_level(g, (double *)c);
     for (int a = 0; a < g->ndim; ++a)
+        #pragma omp parallel for collapse(2) schedule(static)
         for (int k = 0; k < g->n[2]; ++k)
             for (int j = 0; j < g->n[1]; ++j)
                 for (int i = 0; i < g->n[0]; ++i) {
@@ -709,6 +783,7 @@ int orc_project(const orc_grid *g, const double *c, double *u, const double *ue,
 double orc_cfl(const orc_grid *g, const double *u, const double *ue, double cfl, double dt_max)
 {
     double m = 0.0;
+#pragma omp parallel for collapse(2) schedule(static) reduction(max : m)
     for (int k = 0; k < g->n[2]; ++k)
         for (int j = 0; j < g->n[1]; ++j)
             for (int i = 0; i < g->n[0]; ++i) {
@@ -792,6 +867,7 @@ void orc_forces_viscous(const orc_grid *g, const orc_body *B, double t, const do
  * pressure: the force is linear in p, dF_axis/dp_I = -n_axis(x_I) K_eps(d(x_I)). */
 void orc_force_dp(const orc_grid *g, const orc_body *B, double t, int axis, double *out)
 {
+    #pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < g->n[2]; ++k)
         for (int j = 0; j < g->n[1]; ++j)
             for (int i = 0; i < g->n[0]; ++i) {
