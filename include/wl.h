@@ -285,7 +285,10 @@ WL_API int wl_tguess_weights(wl_sim *sim, const double *in, double *out);
  * checking the kernels): grid ndim, n[3]; weights w (3 x 27 x 16 x 16 floats);
  * input x and target t (n[0]*n[1]*n[2] floats, t may be NULL for forward
  * only); outputs y (forward result), dw (gradient of the loss w.r.t. w) and
- * the loss. All host or device pointers. Allocates its own device buffers. */
+ * the loss. All host or device pointers. Allocates its own device buffers.
+ * Grids of more than 134217727 cells (2^31 / 16: the kernels index voxel x
+ * channel in 32-bit integers) give WL_ERR_ARG before any device work; the same
+ * bound applies to the level chosen by wl_guess_setup. */
 WL_API int wl_net_eval(int ndim, const int *n, const float *w, const float *x, const float *t, float *y, float *dw,
                        double *loss);
 
@@ -357,9 +360,11 @@ WL_API int wl_set_body(wl_sim *sim, const wl_body *body);
 
 /* Poisson solve that allocates no device memory (no counterpart in the paper:
  * an addition for callers that cannot call cudaMalloc when they need the
- * solve, such as code running during CUDA graph capture, where allocation is
- * not a capturable call, or applications whose device memory is entirely
- * owned by their own pool). Solves, on one thread block in double precision,
+ * solve: an application whose device memory is entirely held by its own pool
+ * or budget, so that a library allocation would fail or break the budget, and
+ * a time-critical loop that must not call cudaMalloc because the call can
+ * synchronise the device and stall the work on every stream). Solves, on one
+ * thread block (up to 1024 threads) in double precision,
  * A x = r - mean(r) with the operator and Jacobi-preconditioned CG of the
  * library's coarsest multigrid level (the mean is over rows with a nonzero
  * diagonal; x is returned mean-free over those rows and 0 elsewhere).

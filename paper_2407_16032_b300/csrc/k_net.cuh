@@ -16,6 +16,8 @@
 #include "k_poisson.cuh"
 
 #define NET_C 16
+// Largest grid the network kernels take: they index voxel * NET_C + channel in int.
+#define WL_NET_MAX_VOXELS ((long long)(2147483647 / NET_C))
 #define NET_TAPS 27
 #define NET_WL (NET_TAPS * NET_C * NET_C)  // weights per layer
 

@@ -455,21 +455,29 @@ __global__ void k_padd(GridD g, const T *x, T *ph, T *pl) {
     }
 }
 
-// Coarsest level: one block, double-precision Jacobi-PCG on the mean-free part
-// of the right-hand side over active rows, to 1e-12 relative or maxit; the
-// mean-free solution is written to L.x. w: 4*nc doubles of scratch.
-template <typename T>
-__device__ __forceinline__ void coarsest_run(const LevelD<T> &L, double *w, int maxit) {
-    const GridD &g = L.g;
-    const long long n = g.nc;
-    double *xs = w, *ss = w + n, *ds = w + 2 * n, *qs = w + 3 * n;
+// One thread block, double-precision Jacobi-preconditioned CG on the mean-free
+// part of a right-hand side over active rows (rows with a nonzero diagonal),
+// A x = r - mean(r), from x = 0, until |s| <= rtol |s_0| or maxit iterations;
+// the solution is made mean-free over active rows and written through the
+// operator. Op supplies the problem:
+//   long long n() const;                 number of cells
+//   double invd(long long e) const;      1/D of row e (0: inactive row)
+//   double rhs(long long e) const;       r[e]
+//   double apply(const double *d, long long e) const;   (A d)[e]
+//   void out(long long e, double x) const;              store x[e] (0 on inactive rows)
+// Scratch: xs, ss, ds, qs, n doubles each. Returns |s| / |s_0| (0 if s_0 = 0)
+// in every thread. Used by the coarsest multigrid level and by
+// wl_coarse_solve_static, so both solve with the same arithmetic.
+template <class Op>
+__device__ __forceinline__ double block_pcg_solve(const Op &op, double *xs, double *ss, double *ds, double *qs,
+                                                  int maxit, double rtol) {
+    const long long n = op.n();
     __shared__ double sh[64];
     const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
-    const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
     double v1[1], o1[1];
     double sr = 0.0, na = 0.0;
     for (long long e = tid; e < n; e += nt)
-        if (L.invD[e] != T(0)) { sr += (double)L.r[e]; na += 1.0; }
+        if (op.invd(e) != 0.0) { sr += op.rhs(e); na += 1.0; }
     double v2[2] = {sr, na}, o2[2];
     block_reduce<2, false, double>(v2, o2, sh);
     if (tid == 0) { sh[40] = o2[0]; sh[41] = o2[1]; }
@@ -478,11 +486,11 @@ __device__ __forceinline__ void coarsest_run(const LevelD<T> &L, double *w, int 
     __syncthreads();
     double r0 = 0.0, rho = 0.0;
     for (long long e = tid; e < n; e += nt) {
-        const bool act = L.invD[e] != T(0);
-        const double s = act ? (double)L.r[e] - rmean : 0.0;
-        xs[e] = 0.0;
+        const double iD = op.invd(e);
+        const double s = iD != 0.0 ? op.rhs(e) - rmean : 0.0;
+        xs[e] = 0.0;  // scratch may hold an earlier solve: start from zero
         ss[e] = s;
-        ds[e] = (double)L.invD[e] * s;
+        ds[e] = iD * s;
         rho += s * ds[e];
         r0 += s * s;
     }
@@ -492,26 +500,14 @@ __device__ __forceinline__ void coarsest_run(const LevelD<T> &L, double *w, int 
     __syncthreads();
     rho = sh[40];
     const double rnorm0 = sqrt(sh[41]);
+    double sn = rnorm0;
     __syncthreads();
-    for (int it = 0; it < maxit; ++it) {
-        if (rho == 0.0) break;
+    for (int it = 0; it < maxit && rho != 0.0 && sn > rtol * rnorm0; ++it) {
         double dq = 0.0;
         for (long long e = tid; e < n; e += nt) {
-            const long long q = e / g.n[0];
-            const int I[3] = {(int)(e - q * g.n[0]), (int)(q % g.n[1]), (int)(q / g.n[1])};
-            double Ad = 0.0;
-            const double d0 = ds[e];
-            for (int a = 0; a < g.ndim; ++a) {
-                const int N = g.n[a];
-                const bool top = I[a] == N - 1, bot = I[a] == 0, per = g.per[a] != 0;
-                const long long ip = top ? (per ? e - (long long)(N - 1) * st[a] : e) : e + st[a];
-                const long long im = bot ? (per ? e + (long long)(N - 1) * st[a] : e) : e - st[a];
-                const double cp = (top && !per) ? 0.0 : (double)L.c[a][ip];
-                const double cm = (double)L.c[a][e];
-                Ad += cp * (ds[ip] - d0) - cm * (d0 - ds[im]);
-            }
+            const double Ad = op.apply(ds, e);
             qs[e] = Ad;
-            dq += d0 * Ad;
+            dq += ds[e] * Ad;
         }
         v1[0] = dq;
         block_reduce<1, false, double>(v1, o1, sh);
@@ -526,7 +522,7 @@ __device__ __forceinline__ void coarsest_run(const LevelD<T> &L, double *w, int 
             xs[e] += alpha * ds[e];
             const double s = ss[e] - alpha * qs[e];
             ss[e] = s;
-            rn += s * (double)L.invD[e] * s;
+            rn += s * op.invd(e) * s;
             ss2 += s * s;
         }
         v3[0] = rn;
@@ -534,27 +530,63 @@ __device__ __forceinline__ void coarsest_run(const LevelD<T> &L, double *w, int 
         block_reduce<2, false, double>(v3, o3, sh);
         if (tid == 0) { sh[40] = o3[0]; sh[41] = o3[1]; }
         __syncthreads();
-        const double rho2 = sh[40], sn = sqrt(sh[41]);
+        const double rho2 = sh[40];
+        sn = sqrt(sh[41]);
         __syncthreads();
         const double beta = rho2 / rho;
         rho = rho2;
-        for (long long e = tid; e < n; e += nt) ds[e] = (double)L.invD[e] * ss[e] + beta * ds[e];
+        for (long long e = tid; e < n; e += nt) ds[e] = op.invd(e) * ss[e] + beta * ds[e];
         __syncthreads();
-        if (sn <= 1e-12 * rnorm0) break;
     }
     double sx = 0.0;
     for (long long e = tid; e < n; e += nt)
-        if (L.invD[e] != T(0)) sx += xs[e];
+        if (op.invd(e) != 0.0) sx += xs[e];
     v1[0] = sx;
     block_reduce<1, false, double>(v1, o1, sh);
     if (tid == 0) sh[40] = o1[0];
     __syncthreads();
     const double xm = nact > 0 ? sh[40] / nact : 0.0;
-    for (long long e = tid; e < n; e += nt) L.x[e] = L.invD[e] != T(0) ? (T)(xs[e] - xm) : T(0);
+    for (long long e = tid; e < n; e += nt) op.out(e, op.invd(e) != 0.0 ? xs[e] - xm : 0.0);
+    return rnorm0 > 0 ? sn / rnorm0 : 0.0;
 }
+
+// (A d)[e] of a level with lower-face coefficients c[a] (cell e's own lower
+// face; the upper face is the next cell's, 0 at the top of a non-periodic
+// axis; periodic axes wrap), in double.
+template <typename T>
+__device__ __forceinline__ double level_apply(const GridD &g, const T *const *c, const double *d, long long e) {
+    const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
+    const long long q = e / g.n[0];
+    const int I[3] = {(int)(e - q * g.n[0]), (int)(q % g.n[1]), (int)(q / g.n[1])};
+    double Ad = 0.0;
+    const double d0 = d[e];
+    for (int a = 0; a < g.ndim; ++a) {
+        const int N = g.n[a];
+        const bool top = I[a] == N - 1, bot = I[a] == 0, per = g.per[a] != 0;
+        const long long ip = top ? (per ? e - (long long)(N - 1) * st[a] : e) : e + st[a];
+        const long long im = bot ? (per ? e + (long long)(N - 1) * st[a] : e) : e - st[a];
+        const double cp = (top && !per) ? 0.0 : (double)c[a][ip];
+        const double cm = (double)c[a][e];
+        Ad += cp * (d[ip] - d0) - cm * (d0 - d[im]);
+    }
+    return Ad;
+}
+
+// Coarsest level: one block, Jacobi-PCG in double to 1e-12 relative or maxit;
+// the mean-free solution is written to L.x. w: 4*nc doubles of scratch.
+template <typename T>
+struct CoarsestOp {
+    LevelD<T> L;
+    __device__ long long n() const { return L.g.nc; }
+    __device__ double invd(long long e) const { return (double)L.invD[e]; }
+    __device__ double rhs(long long e) const { return (double)L.r[e]; }
+    __device__ double apply(const double *d, long long e) const { return level_apply<T>(L.g, L.c, d, e); }
+    __device__ void out(long long e, double x) const { L.x[e] = (T)x; }
+};
 template <typename T>
 __global__ void k_coarsest(LevelD<T> L, double *w, int maxit) {
-    coarsest_run<T>(L, w, maxit);
+    const long long n = L.g.nc;
+    block_pcg_solve(CoarsestOp<T>{L}, w, w + n, w + 2 * n, w + 3 * n, maxit, 1e-12);
 }
 
 // Coarsest level by a precomputed dense solution operator (one block, FP64):

@@ -215,7 +215,8 @@ int wl_net_eval(int ndim, const int *n, const float *w, const float *x, const fl
                 double *loss) {
     if ((ndim != 2 && ndim != 3) || !n || !w || !x) return WL_ERR_ARG;
     NetGrid ng{n[0], n[1], ndim == 3 ? n[2] : 1, 0};
-    if (ng.nx < 1 || ng.ny < 1 || ng.nz < 1 || (long long)ng.nx * ng.ny * ng.nz > (1LL << 28)) return WL_ERR_ARG;
+    // the network kernels index voxel x channel in int: V * NET_C < 2^31
+    if (ng.nx < 1 || ng.ny < 1 || ng.nz < 1 || (long long)ng.nx * ng.ny * ng.nz > WL_NET_MAX_VOXELS) return WL_ERR_ARG;
     ng.V = ng.nx * ng.ny * ng.nz;
     const size_t V = ng.V;
     std::vector<void *> bufs;

@@ -927,6 +927,8 @@ struct Sim : SimBase {
         if (level < 1 || level >= nlev) throw Err{WL_ERR_ARG, "guess level must be a coarse multigrid level"};
         if (capacity < 0 || capacity > 100000) throw Err{WL_ERR_ARG, "bad sample capacity"};
         if (gq.lev >= 0) throw Err{WL_ERR_STATE, "learned guess already set up"};
+        if (gl[level].nc > WL_NET_MAX_VOXELS)
+            throw Err{WL_ERR_ARG, "guess level too large for the network kernels (voxels x channels must stay below 2^31)"};
         gq.lev = level;
         gq.shift = level;
         gq.ng.nx = gl[level].n[0];

@@ -1,9 +1,9 @@
 // wl_static.cu -- small Poisson solve that allocates no device memory.
 //
 // Some callers cannot allocate device memory at the moment they need a solve:
-// code that runs while a CUDA graph is being captured (cudaMalloc is not a
-// capturable call), or an application whose device memory is entirely
-// reserved by its own pool or budget so that a library allocation would fail.
+// an application whose device memory is entirely reserved by its own pool or
+// budget, so that a library allocation would fail, or a time-critical loop
+// that must not call cudaMalloc because it can synchronise the whole device.
 // wl_coarse_solve_static serves them: it solves the same variable-coefficient
 // Poisson problem as the library's coarsest multigrid level, with all of its
 // working memory in one file-scope device array that every GPU loading the
@@ -11,6 +11,7 @@
 // the right-hand side and the output buffer.
 #include "../../include/wl.h"
 #include "wl_common.cuh"
+#include "k_poisson.cuh"
 
 #include <mutex>
 
@@ -20,128 +21,47 @@ static __device__ __align__(256) double wl_static_scratch[5 * WL_STATIC_MAX_CELL
 
 namespace {
 
-// Face coefficient c_a of cell I (lower face) or of its upper neighbour (+1):
-// upper faces of non-periodic axes are 0; periodic axes wrap.
+// The problem of one call: the caller's coefficients, right-hand side and
+// output, and the 1/D of every row computed by the kernel into the scratch.
 template <typename T>
-__device__ __forceinline__ double coef(const GridD &g, const T *const *c, int a, const int (&I)[3], long long e,
-                                       int up, long long &nb) {
-    const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
-    const int N = g.n[a];
-    if (up) {
-        if (I[a] + 1 < N) { nb = e + st[a]; return (double)c[a][nb]; }
-        if (g.per[a]) { nb = e - (long long)(N - 1) * st[a]; return (double)c[a][nb]; }
-        nb = e;
-        return 0.0;
-    }
-    if (I[a] > 0) nb = e - st[a];
-    else if (g.per[a]) nb = e + (long long)(N - 1) * st[a];
-    else nb = e;
-    return (double)c[a][e];
-}
+struct StaticOp {
+    GridD g;
+    CVec3P<T> c;
+    const T *r;
+    T *x;
+    const double *iD;
+    __device__ long long n() const { return g.nc; }
+    __device__ double invd(long long e) const { return iD[e]; }
+    __device__ double rhs(long long e) const { return (double)r[e]; }
+    __device__ double apply(const double *d, long long e) const { return level_apply<T>(g, c.p, d, e); }
+    __device__ void out(long long e, double v) const { x[e] = (T)v; }
+};
 
-// One block: Jacobi-preconditioned CG in double on A x = r - mean(r) (mean over
-// rows with a nonzero diagonal), to rtol relative residual or maxit iterations;
-// writes the mean-free x and, in w[5n], the final relative residual.
+// One block: 1/D in double from the coefficients (upper faces of non-periodic
+// axes are 0, periodic axes wrap), then the Jacobi-preconditioned CG of the
+// library's coarsest level (block_pcg_solve) on A x = r - mean(r) to rtol or
+// maxit; the final relative residual goes to w[5n].
 template <typename T>
-__global__ void k_coarse_static(GridD g, CVec3P<T> cc, const T *r, T *x, double *w, int maxit, double rtol) {
+__global__ void __launch_bounds__(1024) k_coarse_static(GridD g, CVec3P<T> cc, const T *r, T *x, double *w, int maxit,
+                                                        double rtol) {
     const long long n = g.nc;
-    double *iD = w, *xs = w + n, *ss = w + 2 * n, *ds = w + 3 * n, *qs = w + 4 * n, *res = w + 5 * n;
-    __shared__ double sh[64];
-    __shared__ double bc[2];  // broadcast of reduction results
-    const int tid = threadIdx.x, nt = blockDim.x;
-    double v1[1], o1[1], v2[2], o2[2];
-    double sr = 0.0, na = 0.0;
-    for (long long e = tid; e < n; e += nt) {
+    const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
+    double *iD = w;
+    for (long long e = threadIdx.x; e < n; e += blockDim.x) {
         const long long q = e / g.n[0];
         const int I[3] = {(int)(e - q * g.n[0]), (int)(q % g.n[1]), (int)(q / g.n[1])};
         double D = 0.0;
         for (int a = 0; a < g.ndim; ++a) {
-            long long nb;
-            D -= coef<T>(g, cc.p, a, I, e, 1, nb) + coef<T>(g, cc.p, a, I, e, 0, nb);
+            const int N = g.n[a];
+            const double cp = I[a] + 1 < N ? (double)cc.p[a][e + st[a]]
+                                           : (g.per[a] ? (double)cc.p[a][e - (long long)(N - 1) * st[a]] : 0.0);
+            D -= cp + (double)cc.p[a][e];
         }
         iD[e] = D != 0.0 ? 1.0 / D : 0.0;
-        if (D != 0.0) { sr += (double)r[e]; na += 1.0; }
     }
-    v2[0] = sr;
-    v2[1] = na;
-    block_reduce<2, false, double>(v2, o2, sh);
-    if (tid == 0) { bc[0] = o2[0]; bc[1] = o2[1]; }
     __syncthreads();
-    const double rmean = bc[1] > 0 ? bc[0] / bc[1] : 0.0, nact = bc[1];
-    __syncthreads();
-    double r0 = 0.0, rho = 0.0;
-    for (long long e = tid; e < n; e += nt) {
-        const double s = iD[e] != 0.0 ? (double)r[e] - rmean : 0.0;
-        xs[e] = 0.0;  // the scratch keeps the previous call's contents: restart from zero
-        ss[e] = s;
-        ds[e] = iD[e] * s;
-        rho += s * ds[e];
-        r0 += s * s;
-    }
-    v2[0] = rho;
-    v2[1] = r0;
-    block_reduce<2, false, double>(v2, o2, sh);
-    if (tid == 0) { bc[0] = o2[0]; bc[1] = o2[1]; }
-    __syncthreads();
-    rho = bc[0];
-    const double rnorm0 = sqrt(bc[1]);
-    double sn = rnorm0;
-    __syncthreads();
-    for (int it = 0; it < maxit && rho != 0.0 && sn > rtol * rnorm0; ++it) {
-        double dq = 0.0;
-        for (long long e = tid; e < n; e += nt) {
-            const long long q = e / g.n[0];
-            const int I[3] = {(int)(e - q * g.n[0]), (int)(q % g.n[1]), (int)(q / g.n[1])};
-            const double d0 = ds[e];
-            double Ad = 0.0;
-            for (int a = 0; a < g.ndim; ++a) {
-                long long ip, im;
-                const double cp = coef<T>(g, cc.p, a, I, e, 1, ip);
-                const double cm = coef<T>(g, cc.p, a, I, e, 0, im);
-                Ad += cp * (ds[ip] - d0) - cm * (d0 - ds[im]);
-            }
-            qs[e] = Ad;
-            dq += d0 * Ad;
-        }
-        v1[0] = dq;
-        block_reduce<1, false, double>(v1, o1, sh);
-        if (tid == 0) bc[0] = o1[0];
-        __syncthreads();
-        dq = bc[0];
-        __syncthreads();
-        if (dq == 0.0) break;
-        const double alpha = rho / dq;
-        double rn = 0.0, s2 = 0.0;
-        for (long long e = tid; e < n; e += nt) {
-            xs[e] += alpha * ds[e];
-            const double s = ss[e] - alpha * qs[e];
-            ss[e] = s;
-            rn += s * iD[e] * s;
-            s2 += s * s;
-        }
-        v2[0] = rn;
-        v2[1] = s2;
-        block_reduce<2, false, double>(v2, o2, sh);
-        if (tid == 0) { bc[0] = o2[0]; bc[1] = o2[1]; }
-        __syncthreads();
-        const double rho2 = bc[0];
-        sn = sqrt(bc[1]);
-        __syncthreads();
-        const double beta = rho2 / rho;
-        rho = rho2;
-        for (long long e = tid; e < n; e += nt) ds[e] = iD[e] * ss[e] + beta * ds[e];
-        __syncthreads();
-    }
-    double sx = 0.0;
-    for (long long e = tid; e < n; e += nt)
-        if (iD[e] != 0.0) sx += xs[e];
-    v1[0] = sx;
-    block_reduce<1, false, double>(v1, o1, sh);
-    if (tid == 0) bc[0] = o1[0];
-    __syncthreads();
-    const double xm = nact > 0 ? bc[0] / nact : 0.0;
-    for (long long e = tid; e < n; e += nt) x[e] = iD[e] != 0.0 ? (T)(xs[e] - xm) : T(0);
-    if (tid == 0) res[0] = rnorm0 > 0 ? sn / rnorm0 : 0.0;
+    const double rel = block_pcg_solve(StaticOp<T>{g, cc, r, x, iD}, w + n, w + 2 * n, w + 3 * n, w + 4 * n, maxit, rtol);
+    if (threadIdx.x == 0) w[5 * n] = rel;
 }
 
 // Device address of the scratch array, looked up once per device.

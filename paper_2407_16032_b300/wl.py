@@ -437,12 +437,32 @@ def sim_from_case(case, precision="f32", **kw) -> Sim:
                case.body, cfl=case.cfl, dt_max=case.dt_max, dt_init=case.dt0, **kw)
 
 
-def coarse_solve_static(ndim, n, periodic, c, r, x, maxit=2000, rtol=1e-12, stream=None):
+def coarse_solve_static(ndim, n, periodic, c, r, x, maxit=2000, rtol=1e-12, stream=None, want_resid=True):
     """wl_coarse_solve_static: the small Poisson solve that allocates no device
-    memory (for callers that cannot allocate, e.g. during CUDA graph capture).
-    c: sequence of ndim device tensors, r, x: device tensors, all float32 or
-    all float64. Returns (status, final relative residual)."""
+    memory, for callers that must not allocate when they solve (an application
+    whose device memory is all held by its own pool, or a loop that must not
+    stall on an allocation). c: sequence of ndim CUDA tensors, r, x: CUDA
+    tensors; all contiguous, of one dtype (float32 or float64) and at least
+    prod(n) elements each. want_resid=False passes no residual pointer: the
+    call then only enqueues work (no copy to the host, no synchronisation) and
+    returns None for the residual. Returns (status, final relative residual)."""
     import torch
+    if r.dtype not in (torch.float32, torch.float64):
+        raise ValueError("coarse_solve_static: r must be float32 or float64")
+    if len(c) != ndim:
+        raise ValueError(f"coarse_solve_static: need {ndim} coefficient arrays, got {len(c)}")
+    cells = int(np.prod([int(v) for v in list(n)[:ndim]]))
+    named = [("r", r), ("x", x)] + [(f"c[{a}]", t) for a, t in enumerate(c)]
+    for name, t in named:
+        if t.dtype != r.dtype:
+            raise ValueError(f"coarse_solve_static: {name} is {t.dtype}, r is {r.dtype}")
+        if t.numel() < cells:
+            raise ValueError(f"coarse_solve_static: {name} holds {t.numel()} values, the grid has {cells} cells")
+        if not t.is_contiguous():
+            raise ValueError(f"coarse_solve_static: {name} must be contiguous")
+    for name, t in named:
+        if not t.is_cuda:
+            raise ValueError(f"coarse_solve_static: {name} must be a CUDA tensor")
     prec = WL_F32 if r.dtype == torch.float32 else WL_F64
     nn = (C.c_int * 3)(*(list(n) + [1, 1, 1])[:3])
     pp = (C.c_int * 3)(*[int(bool(v)) for v in (list(periodic) + [0, 0, 0])[:3]])
@@ -450,8 +470,8 @@ def coarse_solve_static(ndim, n, periodic, c, r, x, maxit=2000, rtol=1e-12, stre
     rel = C.c_double()
     st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
     rc = lib().wl_coarse_solve_static(ndim, nn, pp, prec, cp, r.data_ptr(), x.data_ptr(), int(maxit),
-                                      float(rtol), st, C.byref(rel))
-    return rc, rel.value
+                                      float(rtol), st, C.byref(rel) if want_resid else None)
+    return rc, (rel.value if want_resid else None)
 
 
 def net_eval(ndim, n, w, x, t=None):

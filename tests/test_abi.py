@@ -177,3 +177,35 @@ def test_the_default_configuration_passes_validation():
     if rc == wl.WL_OK:
         L.wl_sim_destroy(h)
     assert rc != wl.WL_ERR_ARG
+
+
+def test_network_check_rejects_grids_beyond_32bit_voxel_channel_indexing():
+    # the network kernels index voxel * 16 + channel in int: 2^31 / 16 voxels
+    # and more are refused before any device work (no GPU needed)
+    from paper_2407_16032_b300 import wl
+    L = wl.lib()
+    buf = (C.c_float * 16)()
+    for n, want in [((512, 512, 512), wl.WL_ERR_ARG), ((1 << 27, 1, 1), wl.WL_ERR_ARG)]:
+        nn = (C.c_int * 3)(*n)
+        rc = L.wl_net_eval(3, nn, buf, buf, None, None, None, None)
+        assert rc == want, (n, rc)
+
+
+def test_static_solve_wrapper_rejects_mismatched_tensors_on_the_host():
+    # each argument check of the binding fires before the library is called
+    import torch
+    from paper_2407_16032_b300 import wl
+    n = (8, 6)
+    ok = lambda dt=torch.float64, m=48: torch.zeros(m, dtype=dt)
+    cases = [
+        ("float32 or float64", lambda: wl.coarse_solve_static(2, n, (0, 0), [ok(), ok()], ok(torch.int32), ok())),
+        ("coefficient arrays", lambda: wl.coarse_solve_static(2, n, (0, 0), [ok()], ok(), ok())),
+        ("is torch.float32", lambda: wl.coarse_solve_static(2, n, (0, 0), [ok(), ok(torch.float32)], ok(), ok())),
+        ("holds 40 values", lambda: wl.coarse_solve_static(2, n, (0, 0), [ok(), ok()], ok(), ok(m=40))),
+        ("contiguous", lambda: wl.coarse_solve_static(2, n, (0, 0), [ok(), torch.zeros(96, dtype=torch.float64)[::2]],
+                                                      ok(), ok())),
+        ("CUDA tensor", lambda: wl.coarse_solve_static(2, n, (0, 0), [ok(), ok()], ok(), ok())),
+    ]
+    for msg, call in cases:
+        with pytest.raises(ValueError, match=msg):
+            call()

@@ -1,9 +1,10 @@
 """The Poisson solve that allocates no device memory (wl_coarse_solve_static).
 
-Callers that cannot call cudaMalloc when they need a solve (code running
-during CUDA graph capture, or applications whose device memory is all owned by
-their own pool) use this entry point; its working memory is a fixed device
-array inside the library. This test calls it through the C ABI and checks its
+Callers that cannot call cudaMalloc when they need a solve (an application
+whose device memory is all held by its own pool or budget, or a time-critical
+loop that must not call cudaMalloc because it can synchronise the device) use
+this entry point; its working memory is a fixed device array inside the
+library. This test calls it through the C ABI and checks its
 output against the library's regular solve (wl_poisson_solve) on the same
 problem, twice in a row (the shared array keeps the previous call's contents).
 It lives in its own file so that it runs after every other test.
@@ -58,6 +59,31 @@ def test_static_solve_matches_regular_solve_on_two_calls(prec, body):
         xs = x.double().cpu().numpy()
         tol = 2e-6 if prec == "f32" else 1e-10
         assert p_err(xs, p_ref, cnp, 2) < tol
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_static_solve_on_the_1024_thread_path_matches_regular_solve(prec):
+    # 100 x 60 = 6000 cells: at or above 4096 cells the entry point launches
+    # its block with 1024 threads; walls on x, periodic y, no body, so both
+    # precisions compare the full pressure
+    import torch
+    from paper_2407_16032_b300 import wl
+    case = synth.Case("na", 2, (100, 60, 1), (False, True, False), False, (0, 0, 0), 0.0, synth.Body())
+    sim = gpu_sim(case, prec, tol=5e-9 if prec == "f32" else 1e-12, itmax=60)
+    c, _, _ = sim.get_body_fields()
+    dt = torch.float32 if prec == "f32" else torch.float64
+    cs = [c[a].contiguous() for a in range(2)]
+    cnp = c.double().cpu().numpy()
+    for seed in (5, 6):
+        b = synth.random_scalar(seed, 2, case.n)
+        p_ref = np.zeros(b.shape)
+        sim.poisson_solve(torch.tensor(b, dtype=dt).cuda(), p_ref)
+        x = torch.full(b.shape, float("nan"), dtype=dt, device="cuda")
+        rc, rel = wl.coarse_solve_static(2, case.n, case.periodic, cs, torch.tensor(b, dtype=dt).cuda(), x,
+                                         maxit=20000)
+        assert rc == wl.WL_OK and rel <= 1e-12, (rc, rel)
+        tol = 2e-6 if prec == "f32" else 1e-10
+        assert p_err(x.double().cpu().numpy(), p_ref, cnp, 2) < tol
 
 
 def test_static_solve_rejects_oversized_grids():
