@@ -5,7 +5,7 @@ One step = one Heun predictor-corrector step of the solver (two convection-
 diffusion + BDIM stages, two projections each converged to a 1e-6 relative
 Poisson residual, CFL update) through the C ABI of libwl.so.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload tgv256]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload msphere]
     python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 
 Multi-GPU: the time step does not shard without a halo exchange, so N > 1 runs
@@ -24,6 +24,8 @@ import subprocess
 import sys
 import tempfile
 import time
+
+import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -101,16 +103,19 @@ def source_hash(files):
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the kernel's current source files (else None)."""
+def traffic_for(kernel, case):
+    """DRAM bytes per launch of `kernel` on `case` from the committed ncu
+    summary (profiles/traffic.json), if it was taken on the kernel's current
+    source files and on the same flow: either the same grid, or the same flow
+    on a smaller grid whose traffic is scaled by the cells a launch processes
+    (the entry then says "scaled_from"). Else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    e = json.load(open(p)).get(kernel)
+    e = json.load(open(p)).get(f"{kernel}@{case.name}")
     if not e or e.get("source_hash") != source_hash(e.get("source_files", [])):
         return None
-    return e.get("dram_bytes_per_launch")
+    return int(round(e["dram_bytes_per_cell"] * case.ncell))
 
 
 class Clocks:
@@ -162,23 +167,61 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(sample_n=96, steps=1):
-    """The FP64 oracle, as it stands, on a bounded sample of the same workload:
-    the Taylor-Green vortex at the same Reynolds number on a sample_n^3 grid,
-    one untimed step then `steps` timed steps; per-cell cost is size-independent
-    for the oracle, so cell-steps/s carries over."""
-    import oracle
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_sample(name):
+    """The bounded workload the FP64 oracle is timed on for a bench workload:
+    the same flow at its oracle size (the moving sphere at 128x64x64, the
+    fixed sphere at 128x64x64, the Taylor-Green vortex at 96^3, ...); the
+    oracle's cost per cell-step does not depend on the size."""
     import synth
-    case = synth.config2_tgv(sample_n)
+    case = workload(name)
+    if case.ncell <= 600_000:
+        return case
+    if name.startswith("tgv") and "octant" not in name:
+        return synth.config2_tgv(96)
+    f = (524288 / case.ncell) ** (1.0 / case.ndim)
+    f = 2.0 ** round(np.log2(f)) if case.ndim == 3 else 0.25
+    return synth.scaled(case, f)
+
+
+def time_oracle(case, steps, threads):
+    """Oracle steps of `case` from its start (one untimed step first) with
+    `threads` OpenMP threads: (cell-steps/s, seconds)."""
+    import oracle
+    oracle.set_threads(threads)
     s = oracle.Sim(case, tol=1e-6)
-    s.step(0.4)
+    s.step()
     t0 = time.perf_counter()
     for _ in range(steps):
         s.step()
     dt = time.perf_counter() - t0
-    return {"value": case.ncell * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"TGV {sample_n}^3 (Re 1600 on 1/k), {steps} warm step(s) after 1 untimed step, "
-                      f"FP64 single-threaded C, MG to 1e-6; {dt:.1f} s"}
+    return case.ncell * steps / dt, dt
+
+
+def cpu_baseline(name, steps=4):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload
+    (oracle_sample), on all host cores; a single-thread step alongside."""
+    import oracle
+    case = oracle_sample(name)
+    cores = oracle.host_cores()
+    v, dt = time_oracle(case, steps, cores)
+    v1, dt1 = time_oracle(case, 1, 1)
+    oracle.set_threads(cores)
+    dims = "x".join(str(v) for v in case.n[:case.ndim])
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{case.name} {dims} ({case.ncell} cells), {steps} timed steps after 1 untimed, "
+                      f"FP64 C oracle, OpenMP over all {cores} host cores, MG to 1e-6; {dt:.1f} s",
+            "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "single_thread": {"value": v1, "cores": 1, "sample": f"1 timed step, {dt1:.1f} s"}}
 
 
 def max_over_ranks(x, dist, device):
@@ -199,11 +242,14 @@ def job_rate(ncell, steps, world, seconds):
 
 
 def run_reference(args, rank, world):
+    """The oracle on the host cores: each step one oracle step of the bench
+    workload's bounded sample (oracle_sample); rank 0 only."""
     if rank != 0:
         return 0
     import oracle
-    import synth
-    case = synth.config2_tgv(64)
+    case = oracle_sample(args.workload)
+    cores = oracle.host_cores()
+    oracle.set_threads(cores)
     s = oracle.Sim(case, tol=1e-6)
     for _ in range(args.warmup):
         s.step()
@@ -212,18 +258,45 @@ def run_reference(args, rank, world):
         s.step()
     dt = time.perf_counter() - t0
     v = case.ncell * args.steps / dt
+    prec = args.precision or ("f64" if args.workload == "circle" else "f32")
+    dims = "x".join(str(x) for x in case.n[:case.ndim])
+    sample = f"each step: one FP64 oracle step of {case.name} {dims}, OpenMP over all {cores} host cores"
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic (analytic Taylor-Green initial field)",
-           "config": describe(workload(args.workload),
-                              args.precision or ("f64" if args.workload == "circle" else "f32")) | {
-               "reference_sample": "each step: one oracle step of TGV 64^3 (same Re), host cores"},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": "TGV 64^3 per step, FP64 single-threaded C oracle"},
+           "data": "synthetic (analytic fields, seeded noise)",
+           "config": describe(workload(args.workload), prec) | {"reference_sample": sample},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                            "cpu_model": cpu_model()},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
+
+
+def tgv256_rate(steps, warmup):
+    """The body-free Taylor-Green vortex 256^3 (FP32, plain multigrid to 1e-6):
+    cell-steps/s over `steps` steps by CUDA events, for comparison with the
+    moving-sphere headline."""
+    import torch
+    import synth
+    from paper_2407_16032_b300 import sim_from_case
+    case = synth.config2_tgv(256)
+    sim = sim_from_case(case, "f32", tol=1e-6, itmax=32)
+    u, ue = synth.initial_velocity(case)
+    sim.set_velocity(torch.tensor(u, dtype=torch.float32, device="cuda"))
+    for _ in range(max(warmup, 3)):
+        sim.mom_step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(sim.stream)
+    for _ in range(steps):
+        sim.mom_step()
+    b.record(sim.stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    sim.close()
+    return {"workload": "tgv256 256x256x256", "value": case.ncell * steps / (ms / 1000.0), "unit": UNIT,
+            "ms_per_step": ms / steps, "steps": steps}
 
 
 def main():
@@ -232,7 +305,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="tgv256")
+    ap.add_argument("--workload", default="msphere")
+    ap.add_argument("--no-tgv", action="store_true")
     ap.add_argument("--precision", default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
@@ -321,7 +395,7 @@ def main():
         ach = bpl / (tms / n / 1000) / 1e9
         roof = {"bound": "hbm", "kernel": f"{nm} (fine level)", "achieved": round(ach, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": src,
-                "algorithmic_bytes_per_launch": int(bpl), "traffic": traffic_for(nm)}
+                "algorithmic_bytes_per_launch": int(bpl), "traffic": traffic_for(nm, case)}
 
     # ---- learned Poisson guess vs plain multigrid on the same workload. Both
     # learned parts are fitted on the solver's own converged projections: the
@@ -434,14 +508,16 @@ def main():
                "d2h_bytes_per_step": nb + 96}
 
     if rank == 0:
-        cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline()
+        cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(args.workload)
+        tgv = None if (args.no_tgv or args.workload == "tgv256") else tgv256_rate(args.steps, args.warmup)
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic (analytic fields, seeded noise)",
                "config": describe(case, prec) | {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                                                  "vcycles_per_step_mean": statistics.mean(vcyc)},
                "hbm_GBps_dominant_kernel": roof["achieved"] if roof else None,
-               "roofline": roof, "kernels": kernels[:10], "learned_guess": learned, "adjoint": adjoint, "cpu_baseline": cpu, "e2e": e2e,
+               "roofline": roof, "kernels": kernels[:16], "learned_guess": learned, "adjoint": adjoint,
+               "cpu_baseline": cpu, "e2e": e2e, "tgv256": tgv,
                "gpu_launches": l1 - l0, "clocks": clocks,
                "paper_context": {"ns_per_cell_step": 1.57, "cell_steps_per_s": 6.4e8,
                                  "hw": "NVIDIA H100, FP32, TGV 134M cells (Sec. 4.1)"}}

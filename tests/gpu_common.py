@@ -19,9 +19,10 @@ def start_fields(case, precision):
     return u, ue
 
 
-def run_pair(case, steps, precision="f32", dt=None, gpu_tol=5e-9, oracle_tol=1e-11, smooth_iters=4):
+def run_pair(case, steps, precision="f32", dt=None, gpu_tol=5e-9, oracle_tol=1e-11, smooth_iters=4, on_step=None):
     """Advance the oracle and the GPU path `steps` steps with the oracle's
-    time steps; returns (oracle Sim, gpu Sim, per-step GPU stats)."""
+    time steps; returns (oracle Sim, gpu Sim, per-step GPU stats). on_step(k,
+    orc, sim), if given, runs after step k (1-based) of both."""
     import torch
     u, ue = start_fields(case, precision)
     orc = oracle.Sim(case, tol=oracle_tol, u=u, ue=ue)
@@ -29,11 +30,15 @@ def run_pair(case, steps, precision="f32", dt=None, gpu_tol=5e-9, oracle_tol=1e-
     tdt = torch.float32 if precision == "f32" else torch.float64
     sim.set_velocity(torch.tensor(orc.u, dtype=tdt).cuda(), torch.tensor(orc.ue, dtype=tdt).cuda())
     stats = []
+    orc.dts = []
     for _ in range(steps):
         d = orc.dt if dt is None else dt
+        orc.dts.append(d)
         orc.step(d)
         st, rc = sim.mom_step(d, allow_unconverged=True)
         stats.append((st.proj[0].vcycles, st.proj[0].rel_resid, st.proj[1].vcycles, st.proj[1].rel_resid, rc))
+        if on_step:
+            on_step(len(stats), orc, sim)
     return orc, sim, stats
 
 
@@ -66,6 +71,23 @@ def p_err(p, P, c, ndim):
     return float(np.abs(pm - Pm)[m].max() / np.abs(Pm[m]).max())
 
 
+def near_body_p_err(p, P, c, ndim):
+    """Relative max error of the mean-free pressure on the cells that p_err
+    leaves out: active cells (a face with c > 0) with a face of c < 1/2, the
+    band where the pressure force is integrated. Means and scale are those of
+    the well-determined cells, as in p_err."""
+    m = well_determined(c, ndim)
+    act = np.zeros(c.shape[1:], bool)
+    for a in range(ndim):
+        ax = ndim - 1 - a
+        act |= (c[a] > 0) | (np.roll(c[a], -1, axis=ax) > 0)
+    band = act & ~m
+    if not band.any():
+        return 0.0
+    pm, Pm = p - p[m].mean(), P - P[m].mean()
+    return float(np.abs(pm - Pm)[band].max() / np.abs(Pm[m]).max())
+
+
 def flux_err(p, P, c, ndim):
     """Relative max error of the projection face fluxes c_a (p[I] - p[I - e_a])."""
     e, ref = 0.0, 0.0
@@ -78,25 +100,38 @@ def flux_err(p, P, c, ndim):
     return e / ref
 
 
-def oracle_rounding_response(case, steps, amp=1e-7, seed=9):
-    """The oracle's own response after `steps` steps (FP64 throughout) to
-    (i) an absolute perturbation `amp` of the initial velocity, and (ii) its
-    velocity and exit plane rounded to FP32 after every step (the storage
-    rounding an FP32 implementation cannot avoid). Returns (u_start, p_start,
-    u_store, p_store): relative max-norm change of u and p_err change of p."""
+def oracle_start_response(case, ref, amp=1e-7, seed=9):
+    """The oracle's own response to an absolute perturbation `amp` of the
+    initial velocity (FP64 both runs): a second oracle run from the perturbed
+    start, with the time steps and tolerance of the reference run `ref` (an
+    oracle Sim that ran from the unperturbed start), compared after the same
+    number of steps. This is the amplification that an FP32 implementation's
+    rounding meets on this input. Returns (u change, p change): relative
+    max-norm of u and p_err of p."""
     u, ue = start_fields(case, "f32")
     rng = np.random.default_rng(seed)
-    a = oracle.Sim(case, tol=1e-11, u=u, ue=ue)
-    b = oracle.Sim(case, tol=1e-11, u=u + amp * rng.uniform(-1, 1, size=u.shape), ue=ue)
-    r = oracle.Sim(case, tol=1e-11, u=u, ue=ue)
-    for _ in range(steps):
-        d = a.dt
-        a.step(d)
+    b = oracle.Sim(case, tol=ref.S.tol, u=u + amp * rng.uniform(-1, 1, size=u.shape), ue=ue)
+    for d in ref.dts:
         b.step(d)
-        r.step(d)
-        r.u[...] = r.u.astype(np.float32).astype(np.float64)
-        r.ue[...] = r.ue.astype(np.float32).astype(np.float64)
-    c = oracle.coeffs(a.g, oracle.measure(a.g, a.b, a.t)[0] if case.body.kind != "none" else None)
-    un = np.abs(a.u).max()
-    return (float(np.abs(a.u - b.u).max() / un), p_err(b.P, a.P, c, case.ndim),
-            float(np.abs(a.u - r.u).max() / un), p_err(r.P, a.P, c, case.ndim))
+    c = oracle.coeffs(ref.g, oracle.measure(ref.g, ref.b, ref.t)[0] if case.body.kind != "none" else None)
+    return float(np.abs(ref.u - b.u).max() / np.abs(ref.u).max()), p_err(b.P, ref.P, c, case.ndim)
+
+
+def calibrated_bars(case, ref, floor=1e-5):
+    """Parity bars (u, p) for inputs whose discrete step amplifies rounding:
+    five times the oracle's own response to a 1e-7 perturbation of the start
+    (oracle_start_response), and at least `floor`. Computed from the oracle
+    only."""
+    su, sp = oracle_start_response(case, ref)
+    return max(floor, 5.0 * su), max(floor, 5.0 * sp)
+
+
+def report(name, **vals):
+    """Append the measured errors of a parity case to the JSON-lines file named
+    by WL_PARITY_REPORT (nothing when it is unset)."""
+    import json
+    import os
+    path = os.environ.get("WL_PARITY_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"case": name, **{k: float(v) for k, v in vals.items()}}) + "\n")
