@@ -75,6 +75,9 @@ __device__ __forceinline__ T face_sample(const GridD &g, const T *__restrict__ f
     return f[lin3(g, I[0], I[1], I[2])];
 }
 
+// Shared-memory address of a generic pointer to shared memory (for PTX).
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
 // ---------------------------------------------------------------- reductions
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

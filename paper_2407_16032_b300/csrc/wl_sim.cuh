@@ -15,6 +15,7 @@
 #include "k_poisson.cuh"
 #include "k_mg_march.cuh"
 #include "k_resid.cuh"
+#include "k_march4.cuh"
 #include "k_misc.cuh"
 #include "k_net.cuh"
 #include "k_adjoint.cuh"
@@ -26,6 +27,7 @@
 #include <random>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -408,8 +410,7 @@ struct Sim : SimBase {
                 // previous direction of neighbouring tiles while writing its own)
                 T *dnew = lv[l].d[it & 1], *dold = lv[l].d[(it + 1) & 1];
                 B(it == 0 ? "pcg_dq1" : "pcg_dq", l);
-                if (it == 0) k_pcg_dq<T, ND, true><<<tgrid(l), tblk(), 0, s>>>(lv[l], dold, dnew, S, part, l);
-                else k_pcg_dq<T, ND, false><<<tgrid(l), tblk(), 0, s>>>(lv[l], dold, dnew, S, part, l);
+                dq_launch(l, it == 0, dold, dnew, s);
                 E();
                 const bool last = it == k - 1;
                 B(last ? (l == 0 ? "pcg_u_last_fine" : "pcg_u_last") : "pcg_u", l);
@@ -430,8 +431,53 @@ struct Sim : SimBase {
         E();
     }
 
+    // the fine level of FP32 3D grids whose rows split into 16-byte groups
+    // marches planes (k_march4.cuh); coarser levels (too few tiles to fill
+    // the GPU) and other grids run the column kernels
+    bool march4(int l) const {
+        return std::is_same<T, float>::value && ND == 3 && l == 0 && gl[l].n[0] % 4 == 0 && gl[l].n[0] >= 64;
+    }
+    int m4grid(int l, int per_sm = M4_MINB) const {
+        const GridD &q = gl[l];
+        const long long nt = (long long)((q.n[0] + m4::TX - 1) / m4::TX) * ((q.n[1] + m4::TY - 1) / m4::TY) *
+                             ((q.n[2] + m4::KZ - 1) / m4::KZ);
+        return (int)std::min<long long>(nt, (long long)nsm * per_sm);
+    }
+    void dq_launch(int l, bool first, const T *dold, T *dnew, cudaStream_t s) {
+        if constexpr (std::is_same<T, float>::value && ND == 3) {
+            if (march4(l)) {
+                static bool attr = false;
+                if (!attr) {
+                    WL_CK(cudaFuncSetAttribute(k_pcg_dq4<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)pcg_dq4_smem<false>()));
+                    attr = true;
+                }
+                if (first) k_pcg_dq4<true><<<m4grid(l), 256, pcg_dq4_smem<true>(), s>>>(lv[l], dold, dnew, S, part, l);
+                else k_pcg_dq4<false><<<m4grid(l), 256, pcg_dq4_smem<false>(), s>>>(lv[l], dold, dnew, S, part, l);
+                return;
+            }
+        }
+        if (first) k_pcg_dq<T, ND, true><<<tgrid(l), tblk(), 0, s>>>(lv[l], dold, dnew, S, part, l);
+        else k_pcg_dq<T, ND, false><<<tgrid(l), tblk(), 0, s>>>(lv[l], dold, dnew, S, part, l);
+    }
+
     // refinement residual on level 0, restricted into level 1 when there is one
     void resid_launch(cudaStream_t s) {
+        if constexpr (std::is_same<T, float>::value && ND == 3) {
+            if (march4(0)) {
+                static bool attr = false;
+                if (!attr) {
+                    WL_CK(cudaFuncSetAttribute(k_resid4<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)resid4_smem<true>()));
+                    WL_CK(cudaFuncSetAttribute(k_resid4<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)resid4_smem<false>()));
+                    attr = true;
+                }
+                if (nlev > 1) k_resid4<true><<<m4grid(0, 2), 256, resid4_smem<true>(), s>>>(lv[0], b, bl, ph, pl, lv[1], S, part);
+                else k_resid4<false><<<m4grid(0, 2), 256, resid4_smem<false>(), s>>>(lv[0], b, bl, ph, pl, lv[0], S, part);
+                return;
+            }
+        }
         if (nlev > 1) k_residm<T, ND, true><<<tgrid(0), tblk(), 0, s>>>(lv[0], b, bl, ph, pl, lv[1], S, part);
         else k_residm<T, ND, false><<<tgrid(0), tblk(), 0, s>>>(lv[0], b, bl, ph, pl, lv[0], S, part);
     }
@@ -558,7 +604,11 @@ struct Sim : SimBase {
         return WL_OK;
     }
 
+    // status flags are per solve: clear them before its right-hand side is formed
+    void clear_status() { WL_CK(cudaMemsetAsync(&S->status, 0, sizeof(int), st)); }
+
     int project_buf(int q, const T *ue, double w, double dt, wl_solve_stats *sts, int stage = -1) {
+        clear_status();
         P0("div", 0, g.nc);
         k_div<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], cv(q), ue, (T)(1.0 / (w * dt)), b, bl, S, part);
         P1();
@@ -808,6 +858,7 @@ struct Sim : SimBase {
         WL_CK(cudaMemcpyAsync(pout, p, g.nc * sizeof(double), cudaMemcpyDefault, st));
         k_pin<T><<<blocks(g.nc), 256, 0, st>>>(g, pout, ph, pl);
         ++launches;
+        clear_status();
         k_bstats<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], b, S, part);
         WL_LAUNCH_CK();
         ++launches;
@@ -1208,6 +1259,7 @@ struct Sim : SimBase {
         P0("adj_rhs", 0, g.nc);
         k_adj_rhs<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], cvp(lam), lP, 1.0 / (w * dt), b, bl);
         P1();
+        clear_status();
         k_bstats<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], b, S, part);
         WL_LAUNCH_CK();
         launches += 2;
