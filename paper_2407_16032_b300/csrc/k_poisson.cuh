@@ -589,6 +589,31 @@ __global__ void k_coarsest(LevelD<T> L, double *w, int maxit) {
     block_pcg_solve(CoarsestOp<T>{L}, w, w + n, w + 2 * n, w + 3 * n, maxit, 1e-12);
 }
 
+// Dense solution operator of the coarsest level, built on the device: block j
+// solves A x = e_j - mean(e_j) (mean over active rows) by block_pcg_solve to
+// 1e-13 and writes the mean-free x as column j of M (M[e * n + j]); columns of
+// inactive rows come out zero. M is the active block of the inverse of the
+// operator bordered by the mean constraint, as k_coarsest_dense expects. One
+// block per column: the solves run side by side on the SMs. w: 4 n doubles of
+// scratch per block.
+template <typename T>
+struct UnitColumnOp {
+    LevelD<T> L;
+    int j;
+    double *M;
+    __device__ long long n() const { return L.g.nc; }
+    __device__ double invd(long long e) const { return (double)L.invD[e]; }
+    __device__ double rhs(long long e) const { return e == j ? 1.0 : 0.0; }
+    __device__ double apply(const double *d, long long e) const { return level_apply<T>(L.g, L.c, d, e); }
+    __device__ void out(long long e, double x) const { M[e * L.g.nc + j] = x; }
+};
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_operator(LevelD<T> L, double *M, double *w, int maxit) {
+    const long long n = L.g.nc;
+    double *wb = w + 4 * n * blockIdx.x;
+    block_pcg_solve(UnitColumnOp<T>{L, (int)blockIdx.x, M}, wb, wb + n, wb + 2 * n, wb + 3 * n, maxit, 1e-13);
+}
+
 // Coarsest level by a precomputed dense solution operator (one block, FP64):
 // x = M (r - mean r) over active rows, M the active block of the inverse of
 // the operator bordered by the mean constraint, [A 1; 1^T 0]; x is made

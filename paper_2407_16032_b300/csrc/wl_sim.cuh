@@ -98,8 +98,9 @@ struct Sim : SimBase {
     T *lc[WL_MAXLEV][3] = {};
     unsigned char *tfl[WL_MAXLEV] = {};
     double *cw = nullptr;   // coarsest scratch
-    double *cM = nullptr;   // dense solution operator of the coarsest level (static coefficients)
+    double *cM = nullptr;   // dense solution operator of the coarsest level
     bool cdense = false;
+    double *cMw = nullptr;  // scratch of its device build (moving bodies)
     double *pout = nullptr; // reported pressure scratch
     DevScalars *S = nullptr, *hS = nullptr;
     double *part = nullptr;
@@ -286,7 +287,10 @@ struct Sim : SimBase {
         body_update(0.0);
         // a small coarsest level with coefficients that never change (no body
         // or a fixed one) is solved by a precomputed dense operator
-        cdense = gl[nlev - 1].nc <= 256 && !moving && coarse_dense_build();
+        // the coarsest level (at most 256 cells) is solved by a dense solution
+        // operator: built on the host once for fixed coefficients, on the
+        // device after every measure of a moving body
+        cdense = gl[nlev - 1].nc <= 256 && (moving ? coarse_dense_device() : coarse_dense_build());
         build_vcycle_graph();
         WL_CK(cudaStreamSynchronize(st));
     }
@@ -369,6 +373,7 @@ struct Sim : SimBase {
             launches += 2;
         }
         body_t = tt;
+        if (cdense && moving) coarse_dense_device();
     }
 
     void get_body_fields(void *c, void *m1, void *V) override {
@@ -553,6 +558,24 @@ struct Sim : SimBase {
         if (!cM) cM = alloc_n<double>((size_t)256 * 256);
         WL_CK(cudaMemcpyAsync(cM, Mh.data(), Mh.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         WL_CK(cudaStreamSynchronize(st));
+        return true;
+    }
+
+    // Dense solution operator of the coarsest level from its current
+    // coefficients, on the device (one PCG solve per column, all columns side
+    // by side); enqueued on the sim's stream, so it follows the measure.
+    bool coarse_dense_device() {
+        const int L = nlev - 1;
+        const long long n = gl[L].nc;
+        if (n > 256) return false;
+        if (!cM) cM = alloc_n<double>((size_t)256 * 256);
+        if (!cMw) cMw = alloc_n<double>((size_t)4 * n * n);
+        int maxit = (int)(2 * n + 200);
+        P0("coarse_operator", L, n);
+        k_coarse_operator<T><<<(int)n, n >= 128 ? 128 : 64, 0, st>>>(lv[L], cM, cMw, maxit);
+        P1();
+        WL_LAUNCH_CK();
+        ++launches;
         return true;
     }
 
@@ -1641,9 +1664,9 @@ struct Sim : SimBase {
         win.active = false;
         if (has_body) body_update(body_t >= 0 ? body_t : t);
         // the coarsest level's dense operator follows the new coefficients
-        const bool want = gl[nlev - 1].nc <= 256 && !moving;
+        const bool want = gl[nlev - 1].nc <= 256;
         const bool was = cdense;
-        cdense = want && coarse_dense_build();
+        cdense = want && (moving ? coarse_dense_device() : coarse_dense_build());
         if (cdense != was) build_vcycle_graph();
         WL_CK(cudaStreamSynchronize(st));
     }
