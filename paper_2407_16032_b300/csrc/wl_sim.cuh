@@ -16,6 +16,7 @@
 #include "k_mg_march.cuh"
 #include "k_resid.cuh"
 #include "k_march4.cuh"
+#include "k_flux4.cuh"
 #include "k_misc.cuh"
 #include "k_net.cuh"
 #include "k_adjoint.cuh"
@@ -738,6 +739,31 @@ struct Sim : SimBase {
     // ------------------------------------------------------------ stages
     template <int NDIM, int MODE>
     void flux_launch(const FluxArgs<T> &A) {
+        if constexpr (std::is_same<T, float>::value && NDIM == 3) {
+            if (g.n[0] % 4 == 0 && g.n[0] >= 64) {
+                static bool attr4 = false;
+                if (!attr4) {
+                    WL_CK(cudaFuncSetAttribute(k_flux4<MODE, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)f4::SMEM));
+                    WL_CK(cudaFuncSetAttribute(k_flux4<MODE, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)f4::SMEM));
+                    attr4 = true;
+                }
+                // 16-plane marches when they give every block a few tiles, else 8
+                const long long nxy = (long long)((g.n[0] + f4::TX - 1) / f4::TX) * ((g.n[1] + f4::TY - 1) / f4::TY);
+                const bool deep = nxy * ((g.n[2] + 15) / 16) >= 4LL * nsm * 2;
+                const long long nt = nxy * (deep ? (g.n[2] + 15) / 16 : (g.n[2] + 7) / 8);
+                const int grid = (int)std::min<long long>(nt, (long long)nsm * 2);
+                static const char *names4[5] = {"flux_raw", "flux_pred_f", "flux_pred", "flux_corr_f", "flux_corr"};
+                P0(names4[MODE], 0, g.nc);
+                if (deep) k_flux4<MODE, 16><<<grid, 256, f4::SMEM, st>>>(g, A);
+                else k_flux4<MODE, 8><<<grid, 256, f4::SMEM, st>>>(g, A);
+                P1();
+                WL_LAUNCH_CK();
+                ++launches;
+                return;
+            }
+        }
         using TL = FluxTile<NDIM>;
         const size_t smem = (size_t)NDIM * TL::SN * sizeof(T);
         static bool attr = false;
