@@ -70,8 +70,8 @@ def algo_bytes(name, T, nd, has_body=False, const_diag=False):
     m1 = nd * nd
     d = 0 if const_diag else 1
     return {
-        "flux_pred": 2 * nd * T, "flux_pred_f": 2 * nd * T,
-        "flux_corr": 3 * nd * T, "flux_corr_f": 3 * nd * T,
+        "flux_pred": 2 * nd * T, "flux_pred_f": 2 * nd * T, "flux_pred_m": 2 * nd * T,
+        "flux_corr": 3 * nd * T, "flux_corr_f": 3 * nd * T, "flux_corr_m": 3 * nd * T,
         "blend": (nd + nd + m1 + nd + nd) * T,
         "div": (nd + 2) * T,                          # u -> b (pair)
         "resid": (4 + 1 + 1 / 2 ** nd) * T,           # ph, pl, b, bl -> r, coarse r

@@ -177,6 +177,85 @@ __global__ void __launch_bounds__(256) k_blend(LevelD<T> L, CVec3P<T> f, const T
     });
 }
 
+// The blend on the tiles flagged non-uniform only (the tiles within a cell of
+// a body face; elsewhere the blend is the identity and the flux kernel wrote
+// the stage's final value, FM_PRED_M / FM_CORR_M): the blend of k_blend into
+// `out` at those tiles' cells. The blend's neighbour samples of f lie in
+// flagged tiles too (mu1 != 0 only within the kernel band).
+template <typename T, int NDIM, bool CORR>
+__global__ void __launch_bounds__(256) k_blend_band(LevelD<T> L, CVec3P<T> f, const T *mu1n0, long long mstride,
+                                                    CVec3P<T> V, CVec3P<T> ustar, Vec3P<T> out, const int *tlist,
+                                                    const unsigned *tcount) {
+    const GridD &g = L.g;
+    // work items: (listed tile, plane of the tile)
+    const int nb = (int)*tcount * MT<NDIM>::TZ;
+    for (int q = blockIdx.x; q < nb; q += gridDim.x) {
+        const int t = tlist[q / MT<NDIM>::TZ];
+        const int bx = t % L.tl.ntx, rr = t / L.tl.ntx;
+        const int by = rr % L.tl.nty, bz = rr / L.tl.nty;
+        const int i = bx * 32 + threadIdx.x, j = by * 8 + threadIdx.y;
+        if (i >= g.n[0] || j >= g.n[1]) continue;
+        {
+            const int k = bz * MT<NDIM>::TZ + q % MT<NDIM>::TZ;
+            if (k >= g.n[2]) continue;
+            const long long idx = (long long)i + (long long)g.n[0] * ((long long)j + (long long)g.n[1] * k);
+            const int I[3] = {i, j, k};
+#pragma unroll
+            for (int a = 0; a < NDIM; ++a) {
+                const T fa = f.p[a][idx];
+                const T Va = V.p[a][idx];
+                T grad = T(0);
+#pragma unroll
+                for (int b = 0; b < NDIM; ++b) {
+                    const T m = mu1n0[(a * 3 + b) * mstride + idx];
+                    if (m != T(0)) {
+                        int Pp[3] = {i, j, k}, M[3] = {i, j, k};
+                        Pp[b] += 1;
+                        M[b] -= 1;
+                        const T up = face_sample<T>(g, f.p[a], Pp[0], Pp[1], Pp[2]) - face_sample<T>(g, V.p[a], Pp[0], Pp[1], Pp[2]);
+                        const T dn = face_sample<T>(g, f.p[a], M[0], M[1], M[2]) - face_sample<T>(g, V.p[a], M[0], M[1], M[2]);
+                        grad += m * T(0.5) * (up - dn);
+                    }
+                }
+                T val = Va + L.c[a][idx] * (fa - Va) + grad;
+                if (CORR) val = T(0.5) * (ustar.p[a][idx] + val);
+                if (!g.per[a] && I[a] == 0) val = (T)g.U[a];
+                out.p[a][idx] = val;
+            }
+        }
+    }
+}
+
+// Copy the cells of the tiles flagged non-uniform (the list) from src to dst.
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_band_copy(LevelD<T> L, CVec3P<T> src, Vec3P<T> dst, const int *tlist,
+                                                   const unsigned *tcount) {
+    const GridD &g = L.g;
+    // work items: (listed tile, plane of the tile)
+    const int nb = (int)*tcount * MT<NDIM>::TZ;
+    for (int q = blockIdx.x; q < nb; q += gridDim.x) {
+        const int t = tlist[q / MT<NDIM>::TZ];
+        const int bx = t % L.tl.ntx, rr = t / L.tl.ntx;
+        const int by = rr % L.tl.nty, bz = rr / L.tl.nty;
+        const int i = bx * 32 + threadIdx.x, j = by * 8 + threadIdx.y;
+        if (i >= g.n[0] || j >= g.n[1]) continue;
+        {
+            const int k = bz * MT<NDIM>::TZ + q % MT<NDIM>::TZ;
+            if (k >= g.n[2]) continue;
+            const long long idx = (long long)i + (long long)g.n[0] * ((long long)j + (long long)g.n[1] * k);
+#pragma unroll
+            for (int a = 0; a < NDIM; ++a) dst.p[a][idx] = src.p[a][idx];
+        }
+    }
+}
+
+// The tiles flagged non-uniform, appended to tlist (in no particular order;
+// each tile's blend is independent of the others'); *tcount starts at 0.
+static __global__ void __launch_bounds__(256) k_tile_list(const unsigned char *tflag, int nt, int *tlist, unsigned *tcount) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x)
+        if (!tflag[t]) tlist[atomicAdd(tcount, 1u)] = t;
+}
+
 // Pressure force F = -sum_I (p_I - pmean) n(x_I) K_eps(d(x_I)) over active cells.
 template <typename T>
 __global__ void k_forces(GridD g, BodyState B, const T *ph, const T *pl, const T *invD, DevScalars *S, double *part) {

@@ -31,7 +31,12 @@ enum FluxMode {
     FM_PRED_F = 1,     // out = u0 + dt r                       (u evaluated = u0)
     FM_PRED_U = 2,     // out = BC(u0 + dt r)                   (no body)
     FM_CORR_F = 3,     // out = u0 + dt r(u*)                   (u evaluated = u*)
-    FM_CORR_U = 4      // out = BC((u* + u0 + dt r(u*)) / 2)    (no body)
+    FM_CORR_U = 4,     // out = BC((u* + u0 + dt r(u*)) / 2)    (no body)
+    // with a body, k_flux4 only: cells of tiles flagged uniform (no body face
+    // within a cell of the tile) get the stage's final value, as FM_PRED_U /
+    // FM_CORR_U; the others get the blend input, as FM_PRED_F / FM_CORR_F
+    FM_PRED_M = 5,
+    FM_CORR_M = 6
 };
 
 template <typename T> struct FluxArgs {
@@ -40,6 +45,8 @@ template <typename T> struct FluxArgs {
     const T *u0[3];  // start-of-step velocity (corrector modes)
     T *out[3];
     T dt;
+    const unsigned char *tflag;   // uniform flags of the 32 x 8 x 8 tiles (mixed modes)
+    int tntx, tnty;               // tiles along x and y
 };
 
 template <typename T>

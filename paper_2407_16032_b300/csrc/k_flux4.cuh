@@ -232,12 +232,15 @@ __global__ void __launch_bounds__(256, 2) k_flux4(GridD g, FluxArgs<float> A) {
             if (in) {
                 const int id = xb + n0 * y + plane * k;
                 const int I[3] = {xb, y, k};
+                // mixed modes: the final value in uniform tiles, the blend input elsewhere
+                const bool fin = (MODE == FM_PRED_M || MODE == FM_CORR_M) &&
+                                 A.tflag[(xb >> 5) + A.tntx * ((y >> 3) + A.tnty * (k >> 3))] != 0;
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     const float4 c4 = row4(s0, a, ry);
                     const float sv[4] = {c4.x, c4.y, c4.z, c4.w};
                     float4 u0v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (MODE == FM_CORR_F || MODE == FM_CORR_U) u0v = *(const float4 *)(A.u0[a] + id);
+                    if (MODE == FM_CORR_F || MODE == FM_CORR_U || MODE == FM_CORR_M) u0v = *(const float4 *)(A.u0[a] + id);
                     const float u0a[4] = {u0v.x, u0v.y, u0v.z, u0v.w};
                     float o[4];
 #pragma unroll
@@ -247,12 +250,12 @@ __global__ void __launch_bounds__(256, 2) k_flux4(GridD g, FluxArgs<float> A) {
                         float outv;
                         if (MODE == FM_RAW) {
                             outv = r;
-                        } else if (MODE == FM_PRED_F || MODE == FM_PRED_U) {
+                        } else if (MODE == FM_PRED_F || MODE == FM_PRED_U || MODE == FM_PRED_M) {
                             outv = sv[e] + dt * r;
-                            if (MODE == FM_PRED_U && bface) outv = (float)g.U[a];
+                            if ((MODE == FM_PRED_U || (MODE == FM_PRED_M && fin)) && bface) outv = (float)g.U[a];
                         } else {
                             const float f = u0a[e] + dt * r;
-                            if (MODE == FM_CORR_F) outv = f;
+                            if (MODE == FM_CORR_F || (MODE == FM_CORR_M && !fin)) outv = f;
                             else outv = bface ? (float)g.U[a] : 0.5f * (sv[e] + f);
                         }
                         o[e] = outv;

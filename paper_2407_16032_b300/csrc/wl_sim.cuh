@@ -102,6 +102,8 @@ struct Sim : SimBase {
     double *cM = nullptr;   // dense solution operator of the coarsest level
     bool cdense = false;
     double *cMw = nullptr;  // scratch of its device build (moving bodies)
+    int *tlist = nullptr;   // level-0 tiles flagged non-uniform (band blend)
+    unsigned *tcount = nullptr;
     double *pout = nullptr; // reported pressure scratch
     DevScalars *S = nullptr, *hS = nullptr;
     double *part = nullptr;
@@ -375,6 +377,16 @@ struct Sim : SimBase {
         }
         body_t = tt;
         if (cdense && moving) coarse_dense_device();
+        if (band_blend()) {
+            if (!tlist) {
+                tlist = alloc_n<int>(lv[0].tl.nt);
+                tcount = alloc_n<unsigned>(1);
+            }
+            WL_CK(cudaMemsetAsync(tcount, 0, sizeof(unsigned), st));
+            k_tile_list<<<blocks(lv[0].tl.nt), 256, 0, st>>>(tfl[0], lv[0].tl.nt, tlist, tcount);
+            WL_LAUNCH_CK();
+            ++launches;
+        }
     }
 
     void get_body_fields(void *c, void *m1, void *V) override {
@@ -754,7 +766,8 @@ struct Sim : SimBase {
                 const bool deep = nxy * ((g.n[2] + 15) / 16) >= 4LL * nsm * 2;
                 const long long nt = nxy * (deep ? (g.n[2] + 15) / 16 : (g.n[2] + 7) / 8);
                 const int grid = (int)std::min<long long>(nt, (long long)nsm * 2);
-                static const char *names4[5] = {"flux_raw", "flux_pred_f", "flux_pred", "flux_corr_f", "flux_corr"};
+                static const char *names4[7] = {"flux_raw", "flux_pred_f", "flux_pred", "flux_corr_f", "flux_corr",
+                                                "flux_pred_m", "flux_corr_m"};
                 P0(names4[MODE], 0, g.nc);
                 if (deep) k_flux4<MODE, 16><<<grid, 256, f4::SMEM, st>>>(g, A);
                 else k_flux4<MODE, 8><<<grid, 256, f4::SMEM, st>>>(g, A);
@@ -764,6 +777,7 @@ struct Sim : SimBase {
                 return;
             }
         }
+        if (MODE == FM_PRED_M || MODE == FM_CORR_M) throw Err{WL_ERR_CUDA, "mixed flux modes need the plane-marching kernel"};
         using TL = FluxTile<NDIM>;
         const size_t smem = (size_t)NDIM * TL::SN * sizeof(T);
         static bool attr = false;
@@ -779,7 +793,8 @@ struct Sim : SimBase {
         long long grid = (long long)nsm * occ;
         if (grid > ntiles) grid = ntiles;
         dim3 blk(TL::TX, TL::TY, TL::TZ);
-        static const char *names[5] = {"flux_raw", "flux_pred_f", "flux_pred", "flux_corr_f", "flux_corr"};
+        static const char *names[7] = {"flux_raw", "flux_pred_f", "flux_pred", "flux_corr_f", "flux_corr",
+                                       "flux_pred_m", "flux_corr_m"};
         P0(names[MODE], 0, g.nc);
         k_flux<T, NDIM, MODE><<<(int)grid, blk, smem, st>>>(g, A);
         P1();
@@ -800,7 +815,32 @@ struct Sim : SimBase {
         }
         A.ue = ue;
         A.dt = (T)dt;
+        A.tflag = tfl[0];
+        A.tntx = lv[0].tl.ntx;
+        A.tnty = lv[0].tl.nty;
         return A;
+    }
+
+    // the flux kernel writes the stage's final value in tiles without a body
+    // face and the blend runs on the other tiles only (FP32 3D grids of the
+    // plane-marching flux kernel)
+    bool band_blend() const {
+        return std::is_same<T, float>::value && ND == 3 && has_body && g.n[0] % 4 == 0 && g.n[0] >= 64;
+    }
+    void blend_band(bool corr, int qf, int qstar, int qout) {
+        CVec3P<T> f = cv(qf), V{}, us{};
+        for (int a = 0; a < 3; ++a) { V.p[a] = Vb[a]; us.p[a] = qstar >= 0 ? vel[qstar][a] : nullptr; }
+        P0("blend_band", 0, g.nc);
+        const int gb = nsm * 4;
+        if (corr) k_blend_band<T, ND, true><<<gb, tblk(), 0, st>>>(lv[0], f, mu1n, (long long)g.nc, V, us, vv(qout), tlist, tcount);
+        else k_blend_band<T, ND, false><<<gb, tblk(), 0, st>>>(lv[0], f, mu1n, (long long)g.nc, V, us, vv(qout), tlist, tcount);
+        P1();
+        WL_LAUNCH_CK();
+        P0("band_copy", 0, g.nc);
+        k_band_copy<T, ND><<<gb, tblk(), 0, st>>>(lv[0], cv(qout), vv(qf), tlist, tcount);
+        P1();
+        WL_LAUNCH_CK();
+        launches += 2;
     }
 
     void exit_stage(bool corr, int quG, double dt) {
@@ -840,8 +880,13 @@ struct Sim : SimBase {
         wl_solve_stats s0{}, s1{};
         int rc0, rc1;
         int ustar, unew;
+        const bool band = band_blend();
         if (!has_body) {
             flux<FM_PRED_U>(fargs(A0, ueB, -1, B1, dt));
+            ustar = B1;
+        } else if (band) {
+            flux<FM_PRED_M>(fargs(A0, ueB, -1, B1, dt));
+            blend_band(false, B1, -1, C2);   // the body's tiles, blended through C2 back into B1
             ustar = B1;
         } else {
             flux<FM_PRED_F>(fargs(A0, ueB, -1, B1, dt));
@@ -853,6 +898,10 @@ struct Sim : SimBase {
         if (rc0 == WL_ERR_NONFINITE) return fail_restore(rc0, "non-finite values in the predictor projection");
         if (!has_body) {
             flux<FM_CORR_U>(fargs(ustar, ueA, A0, C2, dt));
+            unew = C2;
+        } else if (band) {
+            flux<FM_CORR_M>(fargs(ustar, ueA, A0, C2, dt));
+            blend_band(true, C2, ustar, D3);   // through D3 back into C2
             unew = C2;
         } else {
             flux<FM_CORR_F>(fargs(ustar, ueA, A0, B1, dt));

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 # named launches that are not fine-grid streaming passes of the forward step:
 # latency-bound or plane-sized work, the learned guess and the adjoint
-NOT_STREAMING = {"coarsest", "coarse_operator", "padd", "exit", "tguess_apply", "guess_net", "guess_apply", "force_dparam", "flux_raw"}
+NOT_STREAMING = {"coarsest", "coarse_operator", "blend_band", "band_copy", "padd", "exit", "tguess_apply", "guess_net", "guess_apply", "force_dparam", "flux_raw"}
 
 
 def _named_launches():
@@ -18,7 +18,7 @@ def _named_launches():
     names = set()
     for args in re.findall(r'\b(?:B|P0)\(([^;]*);', src):   # every quoted name in the call's arguments
         names |= set(re.findall(r'"([a-z_0-9]+)"', args))
-    flux = re.search(r'names\[5\] = \{([^}]*)\}', src).group(1)
+    flux = re.search(r'names\[7\] = \{([^}]*)\}', src).group(1)
     names |= set(re.findall(r'"([a-z_0-9]+)"', flux))
     return {n for n in names if not n.startswith("adj_")}
 
