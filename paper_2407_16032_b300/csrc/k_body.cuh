@@ -102,12 +102,13 @@ __device__ __forceinline__ void body_eval(const BodyState &B, int ndim, const T 
 
 // Measure every stored face: c_a = mu0 (0 on lower faces of non-periodic axes),
 // mu1n[a*3+b] = mu1 n_b, V[a] = body velocity component a.
+// On the cells of box b only.
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(256) k_measure(LevelD<T> L, BodyState B, Vec3P<T> c, T *mu1n0, long long mstride,
-                                                 Vec3P<T> V, bool full) {
+                                                 Vec3P<T> V, bool full, CellBox box) {
     const T eps = (T)B.eps;
     const GridD &g = L.g;
-    for_cells<NDIM>(g, L.tl, nullptr, [&](int i, int j, int k, long long idx, bool) {
+    for_box_cells<NDIM>(g, box, [&](int i, int j, int k, long long idx) {
         const int I[3] = {i, j, k};
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {
@@ -140,7 +141,8 @@ __global__ void __launch_bounds__(256) k_measure(LevelD<T> L, BodyState B, Vec3P
 // BDIM blend of the stage value f (Sec. 2): u = V + mu0 (f - V) + mu1 n.grad(f - V);
 // corrector stage averages with u*: u = (u* + blend)/2; lower boundary faces of
 // non-periodic axes take U_a. Tiles flagged uniform (no body face in the tile
-// or its halo) have mu0 = 1, mu1 = 0 and skip the body arrays.
+// or its halo) have mu0 = 1, mu1 = 0 and skip the body arrays, and so do fluid
+// faces outside the kernel band (mu0 = 1, mu1 = 0): there u = f.
 template <typename T, int NDIM, bool CORR>
 __global__ void __launch_bounds__(256) k_blend(LevelD<T> L, CVec3P<T> f, const T *mu1n0, long long mstride,
                                                CVec3P<T> V, CVec3P<T> ustar, Vec3P<T> out) {
@@ -151,7 +153,13 @@ __global__ void __launch_bounds__(256) k_blend(LevelD<T> L, CVec3P<T> f, const T
         for (int a = 0; a < NDIM; ++a) {
             const T fa = f.p[a][idx];
             T val;
-            if (uni) {
+            bool plain = uni || L.c[a][idx] == L.cu;
+            if (!uni)
+#pragma unroll
+                for (int b = 0; b < NDIM; ++b) plain = plain && mu1n0[(a * 3 + b) * mstride + idx] == T(0);
+            if (plain) {
+                // no body face within a cell, or a fluid face outside the
+                // kernel band: the blend is f itself (no body velocity read)
                 val = fa;
             } else {
                 const T Va = V.p[a][idx];
@@ -180,8 +188,9 @@ __global__ void __launch_bounds__(256) k_blend(LevelD<T> L, CVec3P<T> f, const T
 // The blend on the tiles flagged non-uniform only (the tiles within a cell of
 // a body face; elsewhere the blend is the identity and the flux kernel wrote
 // the stage's final value, FM_PRED_M / FM_CORR_M): the blend of k_blend into
-// `out` at those tiles' cells. The blend's neighbour samples of f lie in
-// flagged tiles too (mu1 != 0 only within the kernel band).
+// `out` at those tiles' cells; fluid faces outside the kernel band (c = cu,
+// mu1 = 0) take f itself and read no body velocity. The blend's neighbour
+// samples of f lie in flagged tiles too (mu1 != 0 only within the kernel band).
 template <typename T, int NDIM, bool CORR>
 __global__ void __launch_bounds__(256) k_blend_band(LevelD<T> L, CVec3P<T> f, const T *mu1n0, long long mstride,
                                                     CVec3P<T> V, CVec3P<T> ustar, Vec3P<T> out, const int *tlist,
@@ -203,6 +212,18 @@ __global__ void __launch_bounds__(256) k_blend_band(LevelD<T> L, CVec3P<T> f, co
 #pragma unroll
             for (int a = 0; a < NDIM; ++a) {
                 const T fa = f.p[a][idx];
+                const T ca = L.c[a][idx];
+                bool plain = ca == L.cu;
+#pragma unroll
+                for (int b = 0; b < NDIM; ++b) plain = plain && mu1n0[(a * 3 + b) * mstride + idx] == T(0);
+                if (plain) {
+                    // a fluid face outside the kernel band: the blend is f itself
+                    T val = fa;
+                    if (CORR) val = T(0.5) * (ustar.p[a][idx] + val);
+                    if (!g.per[a] && I[a] == 0) val = (T)g.U[a];
+                    out.p[a][idx] = val;
+                    continue;
+                }
                 const T Va = V.p[a][idx];
                 T grad = T(0);
 #pragma unroll
@@ -217,7 +238,7 @@ __global__ void __launch_bounds__(256) k_blend_band(LevelD<T> L, CVec3P<T> f, co
                         grad += m * T(0.5) * (up - dn);
                     }
                 }
-                T val = Va + L.c[a][idx] * (fa - Va) + grad;
+                T val = Va + ca * (fa - Va) + grad;
                 if (CORR) val = T(0.5) * (ustar.p[a][idx] + val);
                 if (!g.per[a] && I[a] == 0) val = (T)g.U[a];
                 out.p[a][idx] = val;

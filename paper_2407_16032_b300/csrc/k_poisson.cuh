@@ -73,6 +73,32 @@ __device__ __forceinline__ void for_cells(const GridD &g, const Tiles &tl, const
     }
 }
 
+// A half-open box of cells of a level (lo <= index < hi on every axis).
+struct CellBox {
+    int lo[3], hi[3];
+};
+
+// Sweep the cells of a box, by the tiles of the level that meet it;
+// f(i, j, k, idx).
+template <int NDIM, typename F>
+__device__ __forceinline__ void for_box_cells(const GridD &g, const CellBox &b, F &&f) {
+    constexpr int TZ = MT<NDIM>::TZ;
+    const int t0x = b.lo[0] / 32, t0y = b.lo[1] / 8, t0z = b.lo[2] / TZ;
+    const int nx = (b.hi[0] + 31) / 32 - t0x, ny = (b.hi[1] + 7) / 8 - t0y, nz = (b.hi[2] + TZ - 1) / TZ - t0z;
+    for (int q = blockIdx.x; q < nx * ny * nz; q += gridDim.x) {
+        const int bx = t0x + q % nx, rr = q / nx;
+        const int by = t0y + rr % ny, bz = t0z + rr / ny;
+        const int i = bx * 32 + threadIdx.x, j = by * 8 + threadIdx.y;
+        if (i < b.lo[0] || i >= b.hi[0] || j < b.lo[1] || j >= b.hi[1]) continue;
+        for (int kk = 0; kk < TZ; ++kk) {
+            const int k = bz * TZ + kk;
+            if (k < b.lo[2]) continue;
+            if (k >= b.hi[2]) break;
+            f(i, j, k, (long long)i + (long long)g.n[0] * ((long long)j + (long long)g.n[1] * k));
+        }
+    }
+}
+
 // Walk the tiles of a level: body(x0, y0, z0, uniform) for each tile.
 template <int NDIM, typename F>
 __device__ __forceinline__ void for_tiles(const Tiles &tl, const unsigned char *tflag, F &&body) {
@@ -128,10 +154,12 @@ __device__ __forceinline__ T invd_at(const LevelD<T> &L, bool uni, int i, int j,
 // ------------------------------------------------------------------ set-up
 // Inverse Jacobi diagonal 1/D, D = -sum of the 2n face coefficients (0 -> 0);
 // counts active rows (D != 0) into S->nact when COUNT.
+// On the cells of box b only; with COUNT, S->nact = active rows of the box +
+// `outside` (every cell outside the box being active).
 template <typename T, int NDIM, bool COUNT>
-__global__ void __launch_bounds__(256) k_invd(LevelD<T> L, DevScalars *S, double *part) {
+__global__ void __launch_bounds__(256) k_invd(LevelD<T> L, CellBox b, double outside, DevScalars *S, double *part) {
     T cnt[1] = {T(0)};
-    for_cells<NDIM>(L.g, L.tl, nullptr, [&](int i, int j, int k, long long idx, bool) {
+    for_box_cells<NDIM>(L.g, b, [&](int i, int j, int k, long long idx) {
         long long ip[3], im[3];
         T cp[3], cm[3];
         nb_setup<T, NDIM>(L, false, i, j, k, idx, ip, im, cp, cm);
@@ -144,15 +172,28 @@ __global__ void __launch_bounds__(256) k_invd(LevelD<T> L, DevScalars *S, double
     if (COUNT) {
         double out[1];
         if (grid_reduce<1, false, T>(cnt, part, &S->counters[RS_INVD], out))
-            if (threadIdx.x == 0 && threadIdx.y == 0) S->nact = out[0];
+            if (threadIdx.x == 0 && threadIdx.y == 0) S->nact = out[0] + outside;
+    }
+}
+
+// Set the flags of the tiles that meet box b to 1 (uniform, before k_tileflags).
+template <int NDIM>
+__global__ void k_tileflag_reset(Tiles tl, CellBox b, unsigned char *flags) {
+    constexpr int TZ = MT<NDIM>::TZ;
+    const int t0x = b.lo[0] / 32, t0y = b.lo[1] / 8, t0z = b.lo[2] / TZ;
+    const int nx = (b.hi[0] + 31) / 32 - t0x, ny = (b.hi[1] + 7) / 8 - t0y, nz = (b.hi[2] + TZ - 1) / TZ - t0z;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nx * ny * nz; q += gridDim.x * blockDim.x) {
+        const int bx = t0x + q % nx, rr = q / nx;
+        flags[bx + tl.ntx * ((t0y + rr % ny) + tl.nty * (t0z + rr / ny))] = 1;
     }
 }
 
 // Tile flags: clear the flag of every tile whose cells or one-cell halo have a
 // face coefficient different from the uniform pattern (flags preset to 1).
+// Scans the cells of box b (the other cells being uniform).
 template <typename T, int NDIM>
-__global__ void __launch_bounds__(256) k_tileflags(LevelD<T> L, unsigned char *flags) {
-    for_cells<NDIM>(L.g, L.tl, nullptr, [&](int i, int j, int k, long long idx, bool) {
+__global__ void __launch_bounds__(256) k_tileflags(LevelD<T> L, CellBox b, unsigned char *flags) {
+    for_box_cells<NDIM>(L.g, b, [&](int i, int j, int k, long long idx) {
         long long ip[3], im[3];
         T cp[3], cm[3], up[3], um[3];
         nb_setup<T, NDIM>(L, false, i, j, k, idx, ip, im, cp, cm);
@@ -182,9 +223,10 @@ __global__ void __launch_bounds__(256) k_tileflags(LevelD<T> L, unsigned char *f
 }
 
 // Coarse coefficients: half the sum of the 2^(n-1) fine faces on each coarse face.
+// On the coarse cells of box b.
 template <typename T, int NDIM>
-__global__ void __launch_bounds__(256) k_coarsen_c(GridD gf, CVec3P<T> cf, LevelD<T> C, Vec3P<T> cc) {
-    for_cells<NDIM>(C.g, C.tl, nullptr, [&](int i, int j, int k, long long idx, bool) {
+__global__ void __launch_bounds__(256) k_coarsen_c(GridD gf, CVec3P<T> cf, LevelD<T> C, CellBox b, Vec3P<T> cc) {
+    for_box_cells<NDIM>(C.g, b, [&](int i, int j, int k, long long idx) {
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {
             T s = T(0);

@@ -112,6 +112,7 @@ struct Sim : SimBase {
     long long launches = 0;
     bool has_body = false, moving = false;
     double body_t = -1.0;
+    bool measure_partial = false;   // the last measure updated a box only
     int np = 1;
     // learned initial guess (network on multigrid level gq.lev)
     struct GuessState {
@@ -349,12 +350,72 @@ struct Sim : SimBase {
     }
 
     // ------------------------------------------------------------ body
-    void body_update(double tt) override {
+    // Box of level-0 cells whose measured fields can differ between the body
+    // at time ta and at time tb: both positions' kernel bands and interiors
+    // (the body's extent + eps + 3 cells around its centre; the band blend
+    // reads the body velocity only there). False (measure everything) if the
+    // box would wrap around a periodic axis.
+    bool body_box(double ta, double tb, CellBox &b) const {
+        double r;
+        if (body.kind == WL_BODY_SPHERE || body.kind == WL_BODY_CYLINDER) r = body.radius;
+        else if (body.kind == WL_BODY_ELLIPSE) r = std::max(body.semi[0], body.semi[1]);
+        else return false;
+        r += cfg.eps + 3.0;
+        for (int a = 0; a < 3; ++a) {
+            b.lo[a] = 0;
+            b.hi[a] = g.n[a];
+            if (a >= ND || (body.kind == WL_BODY_CYLINDER && a == 2)) continue;
+            double ca = body.centre[a], cb = body.centre[a];
+            if (a == body.heave_axis) {
+                ca += body.heave_amp * std::sin(body.omega * ta + body.phase);
+                cb += body.heave_amp * std::sin(body.omega * tb + body.phase);
+            }
+            long long lo = (long long)std::floor(std::min(ca, cb) - r), hi = (long long)std::ceil(std::max(ca, cb) + r) + 1;
+            if (lo < 0 || hi > g.n[a]) {
+                if (g.per[a]) return false;
+                lo = std::max(lo, 0LL);
+                hi = std::min(hi, (long long)g.n[a]);
+            }
+            b.lo[a] = (int)lo;
+            b.hi[a] = (int)hi;
+        }
+        return true;
+    }
+    // the level-0 box on level l, with a margin of one cell
+    CellBox level_box(const CellBox &b0, int l) const {
+        CellBox b{};
+        for (int a = 0; a < 3; ++a) {
+            if (a >= ND) { b.lo[a] = 0; b.hi[a] = 1; continue; }
+            b.lo[a] = std::max(0, (b0.lo[a] >> l) - 1);
+            b.hi[a] = std::min(gl[l].n[a], ((b0.hi[a] + (1 << l) - 1) >> l) + 1);
+        }
+        return b;
+    }
+
+    void body_update(double tt) override { measure_body(tt, false); }
+
+    // Measure the body at time tt onto the faces and rebuild the coefficients,
+    // 1/D and tile flags of every level. partial: only inside the box where
+    // the fields can differ from the last measure (at body_t, same body), the
+    // per-step update of a moving body; the body velocity outside that box is
+    // then left at its previous value (the step reads it only inside).
+    void measure_body(double tt, bool partial) {
+        CellBox b0{};
+        const bool box = partial && has_body && body_t >= 0 && body_box(body_t, tt, b0);
+        if (!box)
+            for (int a = 0; a < 3; ++a) { b0.lo[a] = 0; b0.hi[a] = a < ND ? g.n[a] : 1; }
+        const long long bcells = (long long)(b0.hi[0] - b0.lo[0]) * (b0.hi[1] - b0.lo[1]) * (b0.hi[2] - b0.lo[2]);
+        auto bgrid = [&](const CellBox &b, int l) {
+            const long long nt = (long long)((b.hi[0] + 31) / 32 - b.lo[0] / 32) * ((b.hi[1] + 7) / 8 - b.lo[1] / 8) *
+                                 ((b.hi[2] + MT<ND>::TZ - 1) / MT<ND>::TZ - b.lo[2] / MT<ND>::TZ);
+            return (int)std::max(1LL, std::min(nt, (long long)maxb));
+            (void)l;
+        };
         BodyState B = body_state(tt);
         Vec3P<T> c{}, V{};
         for (int a = 0; a < 3; ++a) { c.p[a] = lc[0][a]; V.p[a] = Vb[a]; }
-        P0("measure", 0, g.nc);
-        k_measure<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], B, c, mu1n, (long long)g.nc, V, has_body);
+        P0("measure", 0, bcells);
+        k_measure<T, ND><<<bgrid(b0, 0), tblk(), 0, st>>>(lv[0], B, c, mu1n, (long long)g.nc, V, has_body, b0);
         P1();
         WL_LAUNCH_CK();
         ++launches;
@@ -362,20 +423,25 @@ struct Sim : SimBase {
             CVec3P<T> cf{};
             Vec3P<T> cc{};
             for (int a = 0; a < 3; ++a) { cf.p[a] = lc[l - 1][a]; cc.p[a] = lc[l][a]; }
-            k_coarsen_c<T, ND><<<tgrid(l), tblk(), 0, st>>>(gl[l - 1], cf, lv[l], cc);
+            const CellBox bl = box ? level_box(b0, l) : CellBox{{0, 0, 0}, {gl[l].n[0], gl[l].n[1], gl[l].n[2]}};
+            k_coarsen_c<T, ND><<<bgrid(bl, l), tblk(), 0, st>>>(gl[l - 1], cf, lv[l], bl, cc);
             WL_LAUNCH_CK();
             ++launches;
         }
         for (int l = 0; l < nlev; ++l) {
-            if (l == 0) k_invd<T, ND, true><<<tgrid(l), tblk(), 0, st>>>(lv[l], S, part);
-            else k_invd<T, ND, false><<<tgrid(l), tblk(), 0, st>>>(lv[l], S, part);
+            const CellBox bl = l == 0 ? b0 : (box ? level_box(b0, l) : CellBox{{0, 0, 0}, {gl[l].n[0], gl[l].n[1], gl[l].n[2]}});
+            const long long cells = (long long)(bl.hi[0] - bl.lo[0]) * (bl.hi[1] - bl.lo[1]) * (bl.hi[2] - bl.lo[2]);
+            if (l == 0) k_invd<T, ND, true><<<bgrid(bl, l), tblk(), 0, st>>>(lv[l], bl, (double)(g.nc - cells), S, part);
+            else k_invd<T, ND, false><<<bgrid(bl, l), tblk(), 0, st>>>(lv[l], bl, 0.0, S, part);
             WL_LAUNCH_CK();
-            WL_CK(cudaMemsetAsync(tfl[l], 1, lv[l].tl.nt, st));
-            k_tileflags<T, ND><<<tgrid(l), tblk(), 0, st>>>(lv[l], tfl[l]);
+            k_tileflag_reset<ND><<<blocks(lv[l].tl.nt), 256, 0, st>>>(lv[l].tl, bl, tfl[l]);
             WL_LAUNCH_CK();
-            launches += 2;
+            k_tileflags<T, ND><<<bgrid(bl, l), tblk(), 0, st>>>(lv[l], bl, tfl[l]);
+            WL_LAUNCH_CK();
+            launches += 3;
         }
         body_t = tt;
+        measure_partial = box;
         if (cdense && moving) coarse_dense_device();
         if (band_blend()) {
             if (!tlist) {
@@ -390,6 +456,7 @@ struct Sim : SimBase {
     }
 
     void get_body_fields(void *c, void *m1, void *V) override {
+        if (measure_partial) measure_body(body_t, false);   // the body velocity everywhere
         const size_t bytes = g.nc * sizeof(T);
         for (int a = 0; a < g.ndim; ++a) {
             if (c) WL_CK(cudaMemcpyAsync((char *)c + a * bytes, lc[0][a], bytes, cudaMemcpyDefault, st));
@@ -874,7 +941,7 @@ struct Sim : SimBase {
     int mom_step(double dt_fixed, wl_step_stats *sts) override {
         const double dt = dt_fixed > 0 ? dt_fixed : dt_next;
         if (!(dt > cfg.dt_min)) throw Err{WL_ERR_UNSTABLE, "time step below dt_min"};
-        if (moving) body_update(t + dt);
+        if (moving) measure_body(t + dt, true);
         const int A0 = cur, B1 = (cur + 1) & 3, C2 = (cur + 2) & 3, D3 = (cur + 3) & 3;
         if (g.exit_x) WL_CK(cudaMemcpyAsync(ueB, ueA, np * sizeof(T), cudaMemcpyDeviceToDevice, st));
         wl_solve_stats s0{}, s1{};
