@@ -85,6 +85,7 @@ def algo_bytes(name, T, nd, has_body=False, const_diag=False):
         "grad": (2 + 2 * nd) * T,                     # ph, pl, u -> u
         "cfl": nd * T,
         "measure": ((nd + m1 + nd) if has_body else nd) * T,
+        "measure_sampled": (nd + m1 + nd + 3 * nd) * T,   # d, n -> c, mu1 n (in place)
     }.get(name)
 
 

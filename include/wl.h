@@ -67,7 +67,16 @@ typedef enum {
 
 typedef enum { WL_F32 = 0, WL_F64 = 1 } wl_precision;
 
-typedef enum { WL_BODY_NONE = 0, WL_BODY_SPHERE = 1, WL_BODY_ELLIPSE = 2, WL_BODY_CYLINDER = 3 } wl_body_kind;
+/* USER_FACE_FIELDS: a body of any shape and motion whose distance, normal and
+ * velocity the caller samples on the grid (wl_set_body_fields); the other
+ * wl_body members are ignored for it. */
+typedef enum {
+    WL_BODY_NONE = 0,
+    WL_BODY_SPHERE = 1,
+    WL_BODY_ELLIPSE = 2,
+    WL_BODY_CYLINDER = 3,
+    WL_BODY_USER_FACE_FIELDS = 4
+} wl_body_kind;
 
 /* Optional device allocator (e.g. a framework's caching allocator).
  * alloc returns a device pointer of at least `bytes` (256-byte aligned) or
@@ -205,8 +214,40 @@ WL_API int wl_forces(wl_sim *sim, double *F);
 WL_API int wl_forces_viscous(wl_sim *sim, double *F);
 
 /* Measure the body at time t onto the faces (mu0, mu1 n, V) and rebuild the
- * multigrid coefficients (Sec. 2 / Sec. 3 measure of AutoBody). */
+ * multigrid coefficients (Sec. 2 / Sec. 3 measure of AutoBody). For a
+ * WL_BODY_USER_FACE_FIELDS body the fields stay as last set and only the time
+ * they stand for moves to t. */
 WL_API int wl_body_update(wl_sim *sim, double t);
+
+/* Set the body of a WL_BODY_USER_FACE_FIELDS sim from samples of its signed
+ * distance function and motion map (Sec. 3 AutoBody: the caller evaluates the
+ * distance, its gradient and the body velocity; Sec. 2 forms the kernel
+ * moments). All arrays are in cfg.precision, host or device, x fastest
+ * (layout of wl_set_velocity), nc = n0 n1 (n2) cells; face a of cell I sits at
+ * I + 1/2 - e_a/2 (unit cells), the centre of cell I at I + 1/2:
+ *   d_face: ndim arrays, signed distance at face a (> 0 in the fluid);
+ *   n_face: ndim*ndim arrays, array a*ndim + b = component b of the unit normal
+ *           (grad d, into the fluid) at face a;
+ *   V_face: ndim arrays, component a of the body velocity at face a;
+ *   d_cell: 1 array, signed distance at the cell centres (forces);
+ *   n_cell: ndim arrays, unit normal at the cell centres (forces).
+ * The library copies them, forms mu0(d) and mu1(d) n on every face in double
+ * precision (rounded once to cfg.precision), zeroes the lower boundary faces
+ * of non-periodic axes, and rebuilds every multigrid level's coefficients,
+ * 1/D, tile flags and coarsest operator. The fields hold until the next call
+ * (steps do not re-measure such a body: set the fields for t + dt before a
+ * step to move it); until the first call the grid is all fluid. Drops a held
+ * window. Errors: WL_ERR_ARG (another body kind, a NULL array), WL_ERR_CUDA. */
+WL_API int wl_set_body_fields(wl_sim *sim, const void *d_face, const void *n_face, const void *V_face,
+                              const void *d_cell, const void *n_cell);
+
+/* Tangent of a WL_BODY_USER_FACE_FIELDS body's face velocity along one scalar
+ * parameter theta (layout of V_face; cfg.precision, host or device), for a body
+ * whose geometry does not depend on theta (e.g. the spin rate of a circular
+ * cylinder). wl_window_backward's dparams[0] is then dJ/dtheta through the
+ * BDIM blend's body velocity (dparams[1] = 0). NULL clears it (dparams = 0).
+ * Errors: WL_ERR_ARG (another body kind), WL_ERR_CUDA. */
+WL_API int wl_set_body_velocity_tangent(wl_sim *sim, const void *dV_face);
 
 /* Copy the measured face fields out (host or device, cfg.precision type):
  * c = Poisson coefficients (mu0 with non-periodic lower boundary faces zeroed,
@@ -338,14 +379,20 @@ WL_API int wl_force_dp(wl_sim *sim, int axis, double scale, double *g);
  *     of J), lu / le (cotangents of the final velocity and exit plane, may be
  *     NULL = 0). Outputs (each may be NULL): du0, due0 (gradient with respect
  *     to the window's start velocity and exit plane, layout of wl_set_velocity)
- *     and dparams = (dJ/d heave_amp, dJ/d pitch_amp) of the body (host, 2
- *     doubles), through the measured face fields, the Poisson coefficients and
- *     the force's own dependence on the body. The sim is left in the state
+ *     and dparams (host, 2 doubles): (dJ/d heave_amp, dJ/d pitch_amp) of an
+ *     analytic body, through the measured face fields, the Poisson
+ *     coefficients and the force's own dependence on the body; (dJ/d theta, 0)
+ *     of a sampled body along its velocity tangent. The sim is left in the state
  *     after the window. Errors: WL_ERR_STATE (no forward window held),
  *     WL_ERR_NONFINITE, WL_ERR_ARG, WL_ERR_CUDA; a forward step that fails
  *     returns its status from wl_window_forward. */
 WL_API int wl_window_forward(wl_sim *sim, int nsteps, int ckpt_every, const double *dts, const double *w, double *J,
                              double *dts_out);
+/* wl_window_forward with per-step weights: J = sum_n step_w[n] w . F_n
+ * (step_w: nsteps doubles, host; NULL = all 1), e.g. the force at the final
+ * step alone. wl_window_backward then pulls back this J. */
+WL_API int wl_window_forward_weighted(wl_sim *sim, int nsteps, int ckpt_every, const double *dts, const double *w,
+                                      const double *step_w, double *J, double *dts_out);
 WL_API int wl_window_backward(wl_sim *sim, double gJ, const void *lu, const void *le, double tol, void *du0,
                               void *due0, double *dparams);
 

@@ -77,6 +77,10 @@ def lib():
             ("orc_body_eval", [C.POINTER(BodyS), C.c_int, _P, C.c_double, _P, _P, _P], None),
             ("orc_measure", [C.POINTER(Grid), C.POINTER(BodyS), C.c_double, _P, _P, _P], None),
             ("orc_coeffs", [C.POINTER(Grid), _P, _P], None),
+            ("orc_measure_sampled", [C.POINTER(Grid), _P, _P, _P, _P, _P, _P], None),
+            ("orc_forces_sampled", [C.POINTER(Grid), _P, _P, _P, _P], None),
+            ("orc_forces_viscous_sampled", [C.POINTER(Grid), _P, _P, _P, _P, _P], None),
+            ("orc_force_dp_sampled", [C.POINTER(Grid), _P, _P, C.c_int, _P], None),
             ("orc_bdim", [C.POINTER(Grid), _P, _P, C.c_double, _P, _P, _P, _P, _P], None),
             ("orc_exit_bc", [C.POINTER(Grid), _P, _P, _P, C.c_double, C.c_int, _P, _P, _P], None),
             ("orc_divergence", [C.POINTER(Grid), _P, _P, _P], None),
@@ -221,6 +225,42 @@ def measure(g, body_s, t):
     V = np.zeros((g.ndim,) + sh)
     lib().orc_measure(C.byref(g), C.byref(body_s), float(t), _p(mu0a), _p(mu1n), _p(V))
     return mu0a, mu1n, V
+
+
+def measure_sampled(g, d, n, V):
+    """Face moments of a body given by samples: d (ndim, *grid) signed distance
+    at the faces, n (ndim, ndim, *grid) unit normal (n[a, b]: component b at
+    face a), V (ndim, *grid) body velocity. Returns (mu0, mu1n, V) in the
+    layout of measure()."""
+    sh = _shape(g)
+    mu0a = np.zeros((g.ndim,) + sh)
+    mu1n = np.zeros((g.ndim, 3) + sh)
+    Vo = np.zeros((g.ndim,) + sh)
+    lib().orc_measure_sampled(C.byref(g), _p(_d(d)), _p(_d(n)), _p(_d(V)), _p(mu0a), _p(mu1n), _p(Vo))
+    return mu0a, mu1n, Vo
+
+
+def forces_sampled(g, dc, ncen, p):
+    """Pressure force of a sampled body from the distance dc (grid) and normal
+    ncen (ndim, *grid) at the cell centres."""
+    F = np.zeros(3)
+    lib().orc_forces_sampled(C.byref(g), _p(_d(dc)), _p(_d(ncen)), _p(_d(p)), _p(F))
+    return F
+
+
+def forces_viscous_sampled(g, dc, ncen, u, ue):
+    """Viscous force of a sampled body from centre samples dc, ncen."""
+    F = np.zeros(3)
+    ue = _d(ue) if ue is not None else np.zeros(max(plane_size(g), 1))
+    lib().orc_forces_viscous_sampled(C.byref(g), _p(_d(dc)), _p(_d(ncen)), _p(_d(u)), _p(ue), _p(F))
+    return F
+
+
+def force_dp_sampled(g, dc, ncen, axis):
+    """dF_axis/dp per cell of a sampled body."""
+    out = np.zeros(_shape(g))
+    lib().orc_force_dp_sampled(C.byref(g), _p(_d(dc)), _p(_d(ncen)), int(axis), _p(out))
+    return out
 
 
 def coeffs(g, mu0a=None):

@@ -96,3 +96,42 @@ def window_gradient(case, u0, ue0, P0, t0, dts, w, params=(), body=None, lu=None
             grads[p] += float(np.dot(w, dforce_dparam(g, body, t1, Pn, p)[: len(w)]))
         lam, lame = ub, ueb
     return J, lam, lame, grads
+
+
+# ------------------------------------------------------------- sampled bodies
+def window_forward_sampled(case, fields, centre, u0, ue0, P0, dts, w, step_w=None, tol=1e-13):
+    """window_forward for a body given by samples: fixed face fields (mu0,
+    mu1n, V) of orc_measure_sampled and centre samples (d_cell, n_cell) for
+    the force; J = sum_n step_w[n] w . F_n (step_w None = all 1)."""
+    from . import forces_sampled
+    g = grid_from_case(case)
+    u, ue, P = np.array(u0, float), np.array(ue0, float), np.array(P0, float)
+    states = [(u, ue, P)]
+    J = 0.0
+    for n, dt in enumerate(dts):
+        u, ue, P = step_fields_fn(g, fields, dt, u, ue, P, tol=tol)
+        sw = 1.0 if step_w is None else float(step_w[n])
+        J += sw * float(np.dot(w, forces_sampled(g, centre[0], centre[1], P)[: len(w)]))
+        states.append((u, ue, P))
+    return J, states
+
+
+def window_gradient_sampled(case, fields, centre, dV, u0, ue0, P0, dts, w, step_w=None):
+    """Discrete adjoint of window_forward_sampled: returns (J, dJ/du0, dJ/due0,
+    dJ/dtheta) for a parameter theta that moves the body velocity only, along
+    the face tangent dV (layout of V): dJ/dtheta = sum_n <Vbar_n, dV>, Vbar_n
+    the cotangent of the face velocity from step n's vector-Jacobian product."""
+    from . import force_dp_sampled
+    g = grid_from_case(case)
+    J, states = window_forward_sampled(case, fields, centre, u0, ue0, P0, dts, w, step_w)
+    lam = np.zeros_like(states[0][0])
+    lame = np.zeros_like(states[0][1])
+    dtheta = 0.0
+    for n in range(len(dts) - 1, -1, -1):
+        u, ue, P = states[n]
+        sw = 1.0 if step_w is None else float(step_w[n])
+        lP = sw * sum(w[a] * force_dp_sampled(g, centre[0], centre[1], a) for a in range(len(w)))
+        ub, ueb, mu0b, mu1nb, Vb = step_vjp_fields(g, fields, dts[n], u, ue, P, lam, lame, lP)
+        dtheta += float(np.sum(Vb * dV))
+        lam, lame = ub, ueb
+    return J, lam, lame, dtheta

@@ -300,6 +300,43 @@ void orc_measure(const orc_grid *g, const orc_body *B, double t, double *mu0, do
                 }
 }
 
+/* Measure a body given by samples instead of a formula (Sec. 3: a body is a
+ * distance function plus a map; here the caller evaluates them): on every face
+ * a of every cell the signed distance d[a] (> 0 in the fluid), the unit normal
+ * n[a*ndim + b] (component b, into the fluid) and the body velocity V[a]
+ * (component a). The kernel moments are those of the analytic bodies:
+ * mu0 = mu0(d), mu1n = mu1(d) n, V = V (layouts of orc_measure). */
+void orc_measure_sampled(const orc_grid *g, const double *d, const double *n, const double *Vin, double *mu0,
+                         double *mu1n, double *V)
+{
+    size_t nc = ncell(g);
+    int nd = g->ndim;
+    for (int a = 0; a < nd; ++a)
+        for (size_t L = 0; L < nc; ++L) {
+            double da = d[(size_t)a * nc + L];
+            double m1 = orc_mu1(da, g->eps);
+            mu0[(size_t)a * nc + L] = orc_mu0(da, g->eps);
+            for (int b = 0; b < 3; ++b)
+                mu1n[(size_t)(a * 3 + b) * nc + L] = b < nd ? m1 * n[(size_t)(a * nd + b) * nc + L] : 0.0;
+            V[(size_t)a * nc + L] = Vin[(size_t)a * nc + L];
+        }
+}
+
+/* Pressure force of a sampled body (the reading of orc_forces): F = -sum_I p_I
+ * n(x_I) K_eps(d(x_I)) with the distance dc and normal ncen (component b at
+ * b*nc) sampled at the cell centres. */
+void orc_forces_sampled(const orc_grid *g, const double *dc, const double *ncen, const double *p, double *F)
+{
+    size_t nc = ncell(g);
+    F[0] = F[1] = F[2] = 0.0;
+    for (size_t L = 0; L < nc; ++L) {
+        double K = orc_kernel(dc[L], g->eps);
+        if (K == 0.0) continue;
+        double pk = p[L] * K;
+        for (int a = 0; a < g->ndim; ++a) F[a] -= pk * ncen[(size_t)a * nc + L];
+    }
+}
+
 /* Poisson coefficients c_a = mu0 on face a, zero on non-periodic boundary faces
  * (Neumann condition at the domain boundary). */
 void orc_coeffs(const orc_grid *g, const double *mu0, double *c)
@@ -878,6 +915,39 @@ void orc_force_dp(const orc_grid *g, const orc_body *B, double t, int axis, doub
                 orc_body_eval(B, g->ndim, x, t, &d, nrm, v);
                 out[lin(g, i, j, k)] = -nrm[axis] * orc_kernel(d, g->eps);
             }
+}
+
+/* Viscous force of a sampled body (the reading of orc_forces_viscous) with the
+ * distance dc and normal ncen (component b at b*nc) sampled at the cell
+ * centres. */
+void orc_forces_viscous_sampled(const orc_grid *g, const double *dc, const double *ncen, const double *u,
+                                const double *ue, double *F)
+{
+    size_t nc = ncell(g);
+    F[0] = F[1] = F[2] = 0.0;
+    for (int k = 0; k < g->n[2]; ++k)
+        for (int j = 0; j < g->n[1]; ++j)
+            for (int i = 0; i < g->n[0]; ++i) {
+                size_t L = lin(g, i, j, k);
+                double K = orc_kernel(dc[L], g->eps);
+                if (K == 0.0) continue;
+                double G[3][3] = {{0.0}};   /* G[a][b] = d_b u_a */
+                for (int a = 0; a < g->ndim; ++a)
+                    for (int b = 0; b < g->ndim; ++b) G[a][b] = centre_grad(g, u, ue, a, b, i, j, k);
+                for (int a = 0; a < g->ndim; ++a) {
+                    double tr = 0.0;
+                    for (int b = 0; b < g->ndim; ++b) tr += (G[a][b] + G[b][a]) * ncen[(size_t)b * nc + L];
+                    F[a] += g->nu * K * tr;
+                }
+            }
+}
+
+/* dF_axis/dp_I of the sampled body's pressure force: -n_axis K(d) at each
+ * cell centre. */
+void orc_force_dp_sampled(const orc_grid *g, const double *dc, const double *ncen, int axis, double *out)
+{
+    size_t nc = ncell(g);
+    for (size_t L = 0; L < nc; ++L) out[L] = -ncen[(size_t)axis * nc + L] * orc_kernel(dc[L], g->eps);
 }
 
 /* One Heun predictor-corrector step with projections (Sec. 2), with the body

@@ -308,18 +308,15 @@ __global__ void k_adj_exit(GridD g, const T *ein, T dt, T *ue0b, T *ueGb, T *uGx
 // F = -sum_I (p_I - mean) n(x_I) K_eps(d(x_I)) over active cells, so
 // d(w.F)/dp_I = -(w . n) K on active cells of the kernel band (the mean's share
 // is removed by the adjoint solve, whose right-hand side is made mean-free).
-template <typename T>
-__global__ void k_force_dp(GridD g, BodyState B, const T *invD, double w0, double w1, double w2, double *out) {
+template <typename T, typename CS>
+__global__ void k_force_dp(GridD g, CS cs, const T *invD, double w0, double w1, double w2, double *out) {
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nc;
          idx += (long long)gridDim.x * blockDim.x) {
         int i, j, k;
         decode(g, idx, i, j, k);
-        double v = 0.0;
-        if (invD[idx] != T(0)) {
-            double pd[3] = {i + 0.5, j + 0.5, k + 0.5}, dd, nd[3], vd[3];
-            body_eval<double>(B, g.ndim, pd, dd, nd, vd);
-            v = -(w0 * nd[0] + w1 * nd[1] + w2 * nd[2]) * kkernel<double>(dd, B.eps);
-        }
+        double v = 0.0, K, nd[3];
+        if (invD[idx] != T(0) && cs.template eval<T>(g, i, j, k, idx, K, nd))
+            v = -(w0 * nd[0] + w1 * nd[1] + w2 * nd[2]) * K;
         out[idx] = v;
     }
 }
@@ -476,6 +473,51 @@ __global__ void __launch_bounds__(256) k_adj_param_blend(LevelD<T> L, CVec3P<T> 
     double red[2];
     if (grid_reduce<2, false, double>(acc, part, &S->counters[RS_MISC], red))
         if (threadIdx.x == 0 && threadIdx.y == 0) { out[0] += red[0]; out[1] += red[1]; }
+}
+
+// Tangent of the blended velocity along a body-velocity field dV at fixed
+// geometry (a sampled body whose velocity depends on one parameter), contracted
+// with the blend's cotangent: acc += sum_faces s gin du on the faces k_blend
+// treats as body faces, with
+//   du = dV - mu0 dV - sum_b mu1 n_b (dV(P_b) - dV(M_b)) / 2,
+// neighbours sampled as k_blend samples f and V. Adds into out[0].
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_adj_vtan_blend(LevelD<T> L, CVec3P<T> gin, T s, const T *mu1n0,
+                                                        long long mstride, CVec3P<T> dV, DevScalars *S, double *part,
+                                                        double *out) {
+    const GridD &g = L.g;
+    double acc[1] = {0.0};
+    for_cells<NDIM>(g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
+        if (uni) return;
+        const int J[3] = {i, j, k};
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            if (!g.per[a] && J[a] == 0) continue;
+            const T ca = L.c[a][idx];
+            bool plain = ca == L.cu;
+#pragma unroll
+            for (int b = 0; b < NDIM; ++b) plain = plain && mu1n0[(a * 3 + b) * mstride + idx] == T(0);
+            if (plain) continue;
+            const double gv = (double)s * (double)gin.p[a][idx];
+            if (gv == 0.0) continue;
+            const double dv = (double)dV.p[a][idx];
+            double du = dv - (double)ca * dv;
+#pragma unroll
+            for (int b = 0; b < NDIM; ++b) {
+                const T m = mu1n0[(a * 3 + b) * mstride + idx];
+                if (m == T(0)) continue;
+                int P[3] = {i, j, k}, M[3] = {i, j, k};
+                P[b] += 1;
+                M[b] -= 1;
+                du -= (double)m * 0.5 *
+                      ((double)face_sample<T>(g, dV.p[a], P[0], P[1], P[2]) - (double)face_sample<T>(g, dV.p[a], M[0], M[1], M[2]));
+            }
+            acc[0] += gv * du;
+        }
+    });
+    double red[1];
+    if (grid_reduce<1, false, double>(acc, part, &S->counters[RS_MISC], red))
+        if (threadIdx.x == 0 && threadIdx.y == 0) out[0] += red[0];
 }
 
 // Coefficient part of the projection's parameter derivative: with the forward

@@ -138,6 +138,70 @@ __global__ void __launch_bounds__(256) k_measure(LevelD<T> L, BodyState B, Vec3P
     });
 }
 
+// Moments of a body given by samples (Sec. 3 states a body as a distance
+// function and a map; here the caller evaluates them): on entry c.p[a] holds
+// the signed distance at face a and mu1n slot a*NDIM+b the normal component b
+// there; on return c.p[a] = mu0(d) (0 on lower faces of non-periodic axes) and
+// slot a*3+b = mu1(d) n_b (0 for b >= NDIM), both formed in double from the
+// stored samples and rounded once to T. Every cell is read before it is
+// written, by the thread that owns it.
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_measure_sampled(GridD g, Vec3P<T> c, T *mu1n0, long long mstride, double eps) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nc;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        decode(g, idx, i, j, k);
+        const int I[3] = {i, j, k};
+        double d[NDIM], n[NDIM][NDIM];
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            d[a] = (double)c.p[a][idx];
+#pragma unroll
+            for (int b = 0; b < NDIM; ++b) n[a][b] = (double)mu1n0[(a * NDIM + b) * mstride + idx];
+        }
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            const double m1 = kmu1<double>(d[a], eps);
+            c.p[a][idx] = (!g.per[a] && I[a] == 0) ? T(0) : (T)kmu0<double>(d[a], eps);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) mu1n0[(a * 3 + b) * mstride + idx] = b < NDIM ? (T)(m1 * n[a][b]) : T(0);
+        }
+    }
+}
+
+// Kernel weight K_eps(d) and unit normal at the centre of cell (i, j, k):
+// false where K is zero. Analytic bodies evaluate the distance in T first
+// and only inside the band (with half a cell of margin) again in double;
+// sampled bodies read the caller's centre samples.
+struct CentreAnalytic {
+    BodyState B;
+    template <typename T>
+    __device__ __forceinline__ bool eval(const GridD &g, int i, int j, int k, long long, double &K, double (&n)[3]) const {
+        const T eps = (T)B.eps;
+        T px[3] = {T(i) + T(0.5), T(j) + T(0.5), T(k) + T(0.5)};
+        T d, nrm[3], v[3];
+        body_eval<T>(B, g.ndim, px, d, nrm, v);
+        if (!(d > -eps - T(0.5) && d < eps + T(0.5))) return false;
+        double pd[3] = {i + 0.5, j + 0.5, k + 0.5}, dd, vd[3];
+        body_eval<double>(B, g.ndim, pd, dd, n, vd);
+        K = kkernel<double>(dd, B.eps);
+        return K != 0.0;
+    }
+};
+template <typename TS> struct CentreSampled {
+    const TS *d;       // signed distance at the cell centres
+    const TS *n[3];    // unit normal components at the cell centres
+    double eps;
+    template <typename T>
+    __device__ __forceinline__ bool eval(const GridD &g, int, int, int, long long idx, double &K, double (&nv)[3]) const {
+        K = kkernel<double>((double)d[idx], eps);
+        if (K == 0.0) return false;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) nv[a] = a < g.ndim ? (double)n[a][idx] : 0.0;
+        return true;
+    }
+};
+
 // BDIM blend of the stage value f (Sec. 2): u = V + mu0 (f - V) + mu1 n.grad(f - V);
 // corrector stage averages with u*: u = (u* + blend)/2; lower boundary faces of
 // non-periodic axes take U_a. Tiles flagged uniform (no body face in the tile
@@ -278,9 +342,8 @@ static __global__ void __launch_bounds__(256) k_tile_list(const unsigned char *t
 }
 
 // Pressure force F = -sum_I (p_I - pmean) n(x_I) K_eps(d(x_I)) over active cells.
-template <typename T>
-__global__ void k_forces(GridD g, BodyState B, const T *ph, const T *pl, const T *invD, DevScalars *S, double *part) {
-    const T eps = (T)B.eps;
+template <typename T, typename CS>
+__global__ void k_forces(GridD g, CS cs, const T *ph, const T *pl, const T *invD, DevScalars *S, double *part) {
     const T pm = (T)S->pmean;
     T acc[3] = {T(0), T(0), T(0)};
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nc;
@@ -288,14 +351,11 @@ __global__ void k_forces(GridD g, BodyState B, const T *ph, const T *pl, const T
         int i, j, k;
         decode(g, idx, i, j, k);
         if (invD[idx] == T(0)) continue;
-        T px[3] = {T(i) + T(0.5), T(j) + T(0.5), T(k) + T(0.5)};
-        T d, nrm[3], v[3];
-        body_eval<T>(B, g.ndim, px, d, nrm, v);
-        if (!(d > -eps - T(0.5) && d < eps + T(0.5))) continue;
-        double pd[3] = {i + 0.5, j + 0.5, k + 0.5}, dd, nd[3], vd[3];
-        body_eval<double>(B, g.ndim, pd, dd, nd, vd);
-        const T K = (T)kkernel<double>(dd, B.eps);
+        double Kd, nd[3];
+        if (!cs.template eval<T>(g, i, j, k, idx, Kd, nd)) continue;
+        const T K = (T)Kd;
         if (K == T(0)) continue;
+        T nrm[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) nrm[a] = (T)nd[a];
         const T p = (ph[idx] - pm) + pl[idx];
@@ -315,22 +375,15 @@ __global__ void k_forces(GridD g, BodyState B, const T *ph, const T *pl, const T
 //   d_a u_a = u_a[I+e_a] - u_a[I],
 //   d_b u_a = ((u_a[I+e_b] + u_a[I+e_a+e_b]) - (u_a[I-e_b] + u_a[I+e_a-e_b])) / 4  (b != a),
 // samples beyond the stored range by the boundary rule of vel_sample.
-template <typename T>
-__global__ void k_forces_visc(GridD g, BodyState B, CVec3P<T> u, const T *ue, DevScalars *S, double *part) {
-    const T eps = (T)B.eps;
+template <typename T, typename CS>
+__global__ void k_forces_visc(GridD g, CS cs, CVec3P<T> u, const T *ue, DevScalars *S, double *part) {
     T acc[3] = {T(0), T(0), T(0)};
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nc;
          idx += (long long)gridDim.x * blockDim.x) {
         int i, j, k;
         decode(g, idx, i, j, k);
-        T px[3] = {T(i) + T(0.5), T(j) + T(0.5), T(k) + T(0.5)};
-        T d, nrm[3], v[3];
-        body_eval<T>(B, g.ndim, px, d, nrm, v);
-        if (!(d > -eps - T(0.5) && d < eps + T(0.5))) continue;
-        double pd[3] = {i + 0.5, j + 0.5, k + 0.5}, dd, nd[3], vd[3];
-        body_eval<double>(B, g.ndim, pd, dd, nd, vd);
-        const double K = kkernel<double>(dd, B.eps);
-        if (K == 0.0) continue;
+        double K, nd[3];
+        if (!cs.template eval<T>(g, i, j, k, idx, K, nd)) continue;
         T G[3][3];   // G[a][b] = d_b u_a
 #pragma unroll
         for (int a = 0; a < 3; ++a)

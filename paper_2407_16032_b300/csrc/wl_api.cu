@@ -32,7 +32,7 @@ int validate(const wl_config *c, const wl_body *bd, std::string &msg) {
     if (!(c->tol > 0) || c->itmax < 0 || c->smooth_iters < 1 || c->smooth_iters > 64) { msg = "bad solver settings"; return WL_ERR_ARG; }
     if (!(c->dt_init > 0) || !(c->dt_max > 0) || !(c->cfl > 0)) { msg = "bad time-step settings"; return WL_ERR_ARG; }
     if (bd) {
-        if (bd->kind < 0 || bd->kind > 3) { msg = "unknown body kind"; return WL_ERR_ARG; }
+        if (bd->kind < 0 || bd->kind > 4) { msg = "unknown body kind"; return WL_ERR_ARG; }
         if (bd->kind == WL_BODY_CYLINDER && c->ndim != 3) { msg = "cylinder body is 3D only (use a sphere in 2D)"; return WL_ERR_ARG; }
         if (bd->kind == WL_BODY_CYLINDER && !(bd->radius > 0)) { msg = "cylinder radius must be positive"; return WL_ERR_ARG; }
         if (bd->kind == WL_BODY_ELLIPSE && c->ndim != 2) { msg = "ellipse body is 2D only"; return WL_ERR_ARG; }
@@ -280,7 +280,11 @@ int wl_step_vjp(wl_sim *s, double t, double dt, const void *u0, const void *ue0,
 }
 int wl_window_forward(wl_sim *s, int nsteps, int ckpt_every, const double *dts, const double *w, double *J,
                       double *dts_out) {
-    return guard(s, [&] { return s->impl->window_forward(nsteps, ckpt_every, dts, w, J, dts_out); });
+    return guard(s, [&] { return s->impl->window_forward(nsteps, ckpt_every, dts, w, nullptr, J, dts_out); });
+}
+int wl_window_forward_weighted(wl_sim *s, int nsteps, int ckpt_every, const double *dts, const double *w,
+                               const double *step_w, double *J, double *dts_out) {
+    return guard(s, [&] { return s->impl->window_forward(nsteps, ckpt_every, dts, w, step_w, J, dts_out); });
 }
 int wl_window_backward(wl_sim *s, double gJ, const void *lu, const void *le, double tol, void *du0, void *due0,
                        double *dparams) {
@@ -298,6 +302,14 @@ int wl_tguess_weights(wl_sim *s, const double *in, double *out) {
 }
 int wl_set_body(wl_sim *s, const wl_body *body) {
     return guard(s, [&] { s->impl->set_body(body); return (int)WL_OK; });
+}
+int wl_set_body_fields(wl_sim *s, const void *d_face, const void *n_face, const void *V_face, const void *d_cell,
+                       const void *n_cell) {
+    if (!d_face || !n_face || !V_face || !d_cell || !n_cell) return WL_ERR_ARG;
+    return guard(s, [&] { s->impl->set_body_fields(d_face, n_face, V_face, d_cell, n_cell); return (int)WL_OK; });
+}
+int wl_set_body_velocity_tangent(wl_sim *s, const void *dV_face) {
+    return guard(s, [&] { s->impl->set_body_velocity_tangent(dV_face); return (int)WL_OK; });
 }
 int wl_force_dp(wl_sim *s, int axis, double scale, double *g) {
     if (!g) return WL_ERR_ARG;

@@ -111,6 +111,10 @@ struct Sim : SimBase {
     long long vnodes = 0;
     long long launches = 0;
     bool has_body = false, moving = false;
+    // body given by caller samples (WL_BODY_USER_FACE_FIELDS): its cell-centre
+    // distance and normal (forces), and an optional body-velocity tangent
+    bool user = false, fields_set = false, vtan = false;
+    T *dcell = nullptr, *ncell[3] = {}, *dVt[3] = {};
     double body_t = -1.0;
     bool measure_partial = false;   // the last measure updated a box only
     int np = 1;
@@ -159,7 +163,7 @@ struct Sim : SimBase {
         bool active = false;
         int n = 0, k = 0;
         double w[3] = {0, 0, 0};
-        std::vector<double> dts, t0s;
+        std::vector<double> dts, t0s, ws;   // steps, start times, per-step weights
         std::vector<Snap> ck, seg;
         Snap fin{};
         double fin_dt_next = 0.0;
@@ -227,7 +231,8 @@ struct Sim : SimBase {
         g.nc = (long long)g.n[0] * g.n[1] * g.n[2];
         np = g.n[1] * g.n[2];
         has_body = body.kind != WL_BODY_NONE;
-        moving = has_body && (body.heave_amp != 0.0 || body.pitch_amp != 0.0);
+        user = body.kind == WL_BODY_USER_FACE_FIELDS;
+        moving = has_body && !user && (body.heave_amp != 0.0 || body.pitch_amp != 0.0);
         const long long nc = g.nc;
         for (int q = 0; q < 4; ++q)
             for (int a = 0; a < g.ndim; ++a) vel[q][a] = alloc_n<T>(nc);
@@ -237,6 +242,10 @@ struct Sim : SimBase {
         if (has_body) {
             mu1n = alloc_n<T>((size_t)9 * nc);
             for (int a = 0; a < g.ndim; ++a) Vb[a] = alloc_n<T>(nc);
+        }
+        if (user) {
+            dcell = alloc_n<T>(nc);
+            for (int a = 0; a < g.ndim; ++a) ncell[a] = alloc_n<T>(nc);
         }
         b = alloc_n<T>(nc);
         bl = alloc_n<T>(nc);
@@ -294,7 +303,7 @@ struct Sim : SimBase {
         // the coarsest level (at most 256 cells) is solved by a dense solution
         // operator: built on the host once for fixed coefficients, on the
         // device after every measure of a moving body
-        cdense = gl[nlev - 1].nc <= 256 && (moving ? coarse_dense_device() : coarse_dense_build());
+        cdense = gl[nlev - 1].nc <= 256 && coarse_dense();
         build_vcycle_graph();
         WL_CK(cudaStreamSynchronize(st));
     }
@@ -392,7 +401,74 @@ struct Sim : SimBase {
         return b;
     }
 
-    void body_update(double tt) override { measure_body(tt, false); }
+    // A sampled body keeps its fields until the caller sets new ones: its
+    // update only moves the time the fields stand for.
+    void body_update(double tt) override {
+        if (user && fields_set) { body_t = tt; return; }
+        measure_body(tt, false);
+    }
+
+    // The coarsest level's dense solution operator for the current
+    // coefficients: on the device where they change during a run (a moving or
+    // sampled body), else on the host.
+    bool coarse_dense() { return (moving || user) ? coarse_dense_device() : coarse_dense_build(); }
+
+    // A body given by samples (Sec. 3: distance function and map evaluated by
+    // the caller): face distances d, face normals n (component b of face a at
+    // slot a*ndim+b), face body velocities V, and the distance and normal at
+    // the cell centres (forces). The moments, coefficients, 1/D and tile flags
+    // of every level are formed on the device.
+    void set_body_fields(const void *d, const void *n, const void *V, const void *dc, const void *ncen) override {
+        if (!user) throw Err{WL_ERR_ARG, "set_body_fields: the body kind is not WL_BODY_USER_FACE_FIELDS"};
+        if (!d || !n || !V || !dc || !ncen) throw Err{WL_ERR_ARG, "set_body_fields: a field pointer is NULL"};
+        const size_t bytes = g.nc * sizeof(T);
+        for (int a = 0; a < ND; ++a) {
+            WL_CK(cudaMemcpyAsync(lc[0][a], (const char *)d + a * bytes, bytes, cudaMemcpyDefault, st));
+            WL_CK(cudaMemcpyAsync(Vb[a], (const char *)V + a * bytes, bytes, cudaMemcpyDefault, st));
+            WL_CK(cudaMemcpyAsync(ncell[a], (const char *)ncen + a * bytes, bytes, cudaMemcpyDefault, st));
+        }
+        WL_CK(cudaMemcpyAsync(mu1n, n, (size_t)ND * ND * bytes, cudaMemcpyDefault, st));
+        WL_CK(cudaMemcpyAsync(dcell, dc, bytes, cudaMemcpyDefault, st));
+        Vec3P<T> c{};
+        for (int a = 0; a < 3; ++a) c.p[a] = lc[0][a];
+        P0("measure_sampled", 0, g.nc);
+        k_measure_sampled<T, ND><<<blocks(g.nc), 256, 0, st>>>(g, c, mu1n, (long long)g.nc, cfg.eps);
+        P1();
+        WL_LAUNCH_CK();
+        ++launches;
+        CellBox all{{0, 0, 0}, {g.n[0], g.n[1], g.n[2]}};
+        levels_from_fine(all, false);
+        body_t = t;
+        measure_partial = false;
+        fields_set = true;
+        win.active = false;
+        WL_CK(cudaStreamSynchronize(st));
+    }
+
+    // Tangent dV of the sampled body's face velocity along one parameter
+    // (layout of V in set_body_fields); NULL clears it. The window gradient's
+    // first parameter is then dJ/dtheta along it.
+    void set_body_velocity_tangent(const void *dV) override {
+        if (!user) throw Err{WL_ERR_ARG, "set_body_velocity_tangent: the body kind is not WL_BODY_USER_FACE_FIELDS"};
+        vtan = dV != nullptr;
+        if (!vtan) return;
+        const size_t bytes = g.nc * sizeof(T);
+        for (int a = 0; a < ND; ++a) {
+            if (!dVt[a]) dVt[a] = alloc_n<T>(g.nc);
+            WL_CK(cudaMemcpyAsync(dVt[a], (const char *)dV + a * bytes, bytes, cudaMemcpyDefault, st));
+        }
+        WL_CK(cudaStreamSynchronize(st));
+    }
+
+    // Launch f with the cell-centre sampler of the body at time tt.
+    template <typename F> void with_centre(double tt, F &&f) {
+        if (user) {
+            CentreSampled<T> cs{dcell, {ncell[0], ncell[1], ncell[2]}, cfg.eps};
+            f(cs);
+        } else {
+            f(CentreAnalytic{body_state(tt)});
+        }
+    }
 
     // Measure the body at time tt onto the faces and rebuild the coefficients,
     // 1/D and tile flags of every level. partial: only inside the box where
@@ -419,6 +495,21 @@ struct Sim : SimBase {
         P1();
         WL_LAUNCH_CK();
         ++launches;
+        levels_from_fine(b0, box);
+        body_t = tt;
+        measure_partial = box;
+    }
+
+    // After the fine level's coefficients changed inside box b0 (everywhere
+    // unless box): the coarse coefficients, 1/D and tile flags of every level,
+    // the coarsest level's dense operator and the band blend's tile list.
+    void levels_from_fine(const CellBox &b0, bool box) {
+        auto bgrid = [&](const CellBox &b, int l) {
+            const long long nt = (long long)((b.hi[0] + 31) / 32 - b.lo[0] / 32) * ((b.hi[1] + 7) / 8 - b.lo[1] / 8) *
+                                 ((b.hi[2] + MT<ND>::TZ - 1) / MT<ND>::TZ - b.lo[2] / MT<ND>::TZ);
+            return (int)std::max(1LL, std::min(nt, (long long)maxb));
+            (void)l;
+        };
         for (int l = 1; l < nlev; ++l) {
             CVec3P<T> cf{};
             Vec3P<T> cc{};
@@ -440,9 +531,7 @@ struct Sim : SimBase {
             WL_LAUNCH_CK();
             launches += 3;
         }
-        body_t = tt;
-        measure_partial = box;
-        if (cdense && moving) coarse_dense_device();
+        if (cdense && (moving || user)) coarse_dense_device();
         if (band_blend()) {
             if (!tlist) {
                 tlist = alloc_n<int>(lv[0].tl.nt);
@@ -1088,7 +1177,9 @@ struct Sim : SimBase {
         F[0] = F[1] = F[2] = 0.0;
         if (!has_body) return;
         pmean();
-        k_forces<T><<<blocks(g.nc), 256, 0, st>>>(g, body_state(body_t), ph, pl, lv[0].invD, S, part);
+        with_centre(body_t, [&](auto cs) {
+            k_forces<T, decltype(cs)><<<blocks(g.nc), 256, 0, st>>>(g, cs, ph, pl, lv[0].invD, S, part);
+        });
         WL_LAUNCH_CK();
         ++launches;
         read_scalars();
@@ -1100,7 +1191,9 @@ struct Sim : SimBase {
     void forces_viscous(double *F) override {
         F[0] = F[1] = F[2] = 0.0;
         if (!has_body) return;
-        k_forces_visc<T><<<blocks(g.nc), 256, 0, st>>>(g, body_state(body_t), cv(cur), ueA, S, part);
+        with_centre(body_t, [&](auto cs) {
+            k_forces_visc<T, decltype(cs)><<<blocks(g.nc), 256, 0, st>>>(g, cs, cv(cur), ueA, S, part);
+        });
         WL_LAUNCH_CK();
         ++launches;
         read_scalars();
@@ -1481,6 +1574,16 @@ struct Sim : SimBase {
     }
 
     void adj_param_blend(T *const (&gin)[3], double s, T *const (&f)[3], const BodyTangent *dB, double tt) {
+        if (user) {
+            if (!vtan) return;
+            P0("adj_vtan_blend", 0, g.nc);
+            k_adj_vtan_blend<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], cvp(gin), (T)s, mu1n, (long long)g.nc, cvp(dVt),
+                                                                 S, part, ad.dpar);
+            P1();
+            WL_LAUNCH_CK();
+            ++launches;
+            return;
+        }
         CVec3P<T> V{};
         for (int a = 0; a < 3; ++a) V.p[a] = Vb[a];
         P0("adj_param_blend", 0, g.nc);
@@ -1508,6 +1611,9 @@ struct Sim : SimBase {
         params = params && has_body;
         BodyTangent dB[2];
         if (params) { adj_alloc_params(); param_tangents(t1, dB[0], dB[1]); }
+        // a sampled body's only parameter moves its velocity, not its geometry:
+        // no coefficient or direct force term
+        const bool geo = params && !user;
         wl_solve_stats s[2] = {};
         // forward predictor: u*, u_e* (and its blend input and pressure)
         copy_vec(vel[cur], ad.u0);
@@ -1542,7 +1648,7 @@ struct Sim : SimBase {
             r0c = project_buf(D3, ueA, 0.5, dt, nullptr);
             dcopy(ad.P2h, ph, g.nc);
             dcopy(ad.P2l, pl, g.nc);
-            if (wF) {
+            if (wF && geo) {
                 // direct dependence of wF . F on the body at fixed pressure
                 pmean();
                 P0("force_dparam", 0, g.nc);
@@ -1555,7 +1661,7 @@ struct Sim : SimBase {
         }
         // reverse: corrector projection, exit, blend, flux at u*
         int r1 = proj_vjp(ad.lu, g.exit_x ? ad.le : nullptr, haveP ? ad.lP : nullptr, 0.5, dt, ad.x, ad.xe, &s[1],
-                          params ? ad.P2h : nullptr, params ? ad.P2l : nullptr, params ? dB : nullptr, t1, 1);
+                          geo ? ad.P2h : nullptr, geo ? ad.P2l : nullptr, geo ? dB : nullptr, t1, 1);
         zero_vec(ad.ub);
         zero_vec(ad.usb);
         if (g.exit_x) {
@@ -1570,7 +1676,7 @@ struct Sim : SimBase {
         adj_flux(ad.us, ad.ues, ad.fb, ad.usb, ad.uesb);
         // predictor projection, exit, blend, flux at u0
         int r2 = proj_vjp(ad.usb, g.exit_x ? ad.uesb : nullptr, nullptr, 1.0, dt, ad.x, ad.xe, &s[0],
-                          params ? ad.P1h : nullptr, params ? ad.P1l : nullptr, params ? dB : nullptr, t1, 0);
+                          geo ? ad.P1h : nullptr, geo ? ad.P1l : nullptr, geo ? dB : nullptr, t1, 0);
         if (g.exit_x) {
             k_adj_exit<T, false><<<1, 1024, 0, st>>>(g, ad.xe, (T)dt, ad.ueb, ad.ueb, ad.ub[0]);
             WL_LAUNCH_CK();
@@ -1653,8 +1759,10 @@ struct Sim : SimBase {
             WL_CK(cudaMemsetAsync(ad.lP, 0, g.nc * sizeof(double), st));
             return;
         }
-        k_force_dp<T><<<blocks(g.nc), 256, 0, st>>>(g, body_state(tt), lv[0].invD, w[0] * scale, w[1] * scale,
-                                                    w[2] * scale, ad.lP);
+        with_centre(tt, [&](auto cs) {
+            k_force_dp<T, decltype(cs)><<<blocks(g.nc), 256, 0, st>>>(g, cs, lv[0].invD, w[0] * scale, w[1] * scale,
+                                                                      w[2] * scale, ad.lP);
+        });
         WL_LAUNCH_CK();
         ++launches;
     }
@@ -1692,7 +1800,8 @@ struct Sim : SimBase {
         t = s.t;
     }
 
-    int window_forward(int nsteps, int ckpt, const double *dts, const double *w, double *J, double *dts_out) override {
+    int window_forward(int nsteps, int ckpt, const double *dts, const double *w, const double *step_w, double *J,
+                       double *dts_out) override {
         if (nsteps < 1 || ckpt < 1) throw Err{WL_ERR_ARG, "window: nsteps and ckpt_every must be >= 1"};
         adj_alloc();
         const int nck = (nsteps + ckpt - 1) / ckpt;
@@ -1710,6 +1819,8 @@ struct Sim : SimBase {
         win.k = ckpt;
         for (int a = 0; a < 3; ++a) win.w[a] = w ? w[a] : 0.0;
         win.dts.assign(nsteps, 0.0);
+        win.ws.assign(nsteps, 1.0);
+        if (step_w) for (int n = 0; n < nsteps; ++n) win.ws[n] = step_w[n];
         double Jv = 0.0;
         for (int n = 0; n < nsteps; ++n) {
             if (n % ckpt == 0) snap_take(win.ck[n / ckpt]);
@@ -1717,10 +1828,10 @@ struct Sim : SimBase {
             win.dts[n] = dt;
             const int rc = mom_step(dt, nullptr);
             if (rc != WL_OK) return rc;
-            if (w && has_body) {
+            if (w && has_body && win.ws[n] != 0.0) {
                 double F[3];
                 forces(F);
-                Jv += w[0] * F[0] + w[1] * F[1] + w[2] * F[2];
+                Jv += win.ws[n] * (w[0] * F[0] + w[1] * F[1] + w[2] * F[2]);
             }
         }
         snap_take(win.fin);
@@ -1739,7 +1850,7 @@ struct Sim : SimBase {
         const size_t vb = g.nc * sizeof(T), pb = (size_t)np * sizeof(T);
         const bool params = dparams != nullptr && has_body;
         const bool force = has_body && (win.w[0] != 0 || win.w[1] != 0 || win.w[2] != 0) && gJ != 0.0;
-        double wF[3] = {gJ * win.w[0], gJ * win.w[1], gJ * win.w[2]};
+
         // final cotangents
         for (int a = 0; a < g.ndim; ++a) {
             if (luf) WL_CK(cudaMemcpyAsync(ad.lu[a], (const char *)luf + a * vb, vb, cudaMemcpyDefault, st));
@@ -1777,8 +1888,11 @@ struct Sim : SimBase {
                 dcopy(ph, s.ph, g.nc);
                 dcopy(pl, s.pl, g.nc);
                 if (has_body && (moving || body_t != s.t + dt)) body_update(s.t + dt);
-                if (force) force_dp_w(s.t + dt, win.w, gJ);
-                const int r = vjp_core(s.t, dt, force, tol, params, force ? wF : nullptr, nullptr);
+                const double gn = gJ * win.ws[n];
+                const bool fn = force && gn != 0.0;
+                const double wF[3] = {gn * win.w[0], gn * win.w[1], gn * win.w[2]};
+                if (fn) force_dp_w(s.t + dt, win.w, gn);
+                const int r = vjp_core(s.t, dt, fn, tol, params, fn ? wF : nullptr, nullptr);
                 if (r == WL_ERR_NONFINITE) rc = r;
                 for (int a = 0; a < 3; ++a) std::swap(ad.lu[a], ad.ub[a]);
                 std::swap(ad.le, ad.ueb);
@@ -1802,13 +1916,13 @@ struct Sim : SimBase {
     void set_body(const wl_body *bd) override {
         if (!bd || bd->kind != body.kind) throw Err{WL_ERR_ARG, "set_body: the body kind cannot change"};
         body = *bd;
-        moving = has_body && (body.heave_amp != 0.0 || body.pitch_amp != 0.0);
+        moving = has_body && !user && (body.heave_amp != 0.0 || body.pitch_amp != 0.0);
         win.active = false;
         if (has_body) body_update(body_t >= 0 ? body_t : t);
         // the coarsest level's dense operator follows the new coefficients
         const bool want = gl[nlev - 1].nc <= 256;
         const bool was = cdense;
-        cdense = want && (moving ? coarse_dense_device() : coarse_dense_build());
+        cdense = want && coarse_dense();
         if (cdense != was) build_vcycle_graph();
         WL_CK(cudaStreamSynchronize(st));
     }

@@ -59,10 +59,13 @@ struct SimBase {
     virtual int step_vjp(double t0, double dt, const void *u0, const void *ue0, const double *P0, const void *lu,
                          const void *le, const double *lP, double tol, void *ub, void *ueb, wl_solve_stats *st) = 0;
     virtual void force_dp(int axis, double scale, double *g) = 0;
-    virtual int window_forward(int nsteps, int ckpt, const double *dts, const double *w, double *J, double *dts_out) = 0;
+    virtual int window_forward(int nsteps, int ckpt, const double *dts, const double *w, const double *step_w,
+                               double *J, double *dts_out) = 0;
     virtual int window_backward(double gJ, const void *lu, const void *le, double tol, void *du0, void *due0,
                                 double *dparams) = 0;
     virtual void set_body(const wl_body *bd) = 0;
+    virtual void set_body_fields(const void *d, const void *n, const void *V, const void *dc, const void *ncen) = 0;
+    virtual void set_body_velocity_tangent(const void *dV) = 0;
     virtual void tguess_mode(int collect, int use) = 0;
     virtual void tguess_fit(double *w, double *ratio) = 0;
     virtual void tguess_weights(const double *in, double *out) = 0;

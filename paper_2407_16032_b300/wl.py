@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libwl.so")
 
 WL_OK, WL_ERR_ARG, WL_ERR_CUDA, WL_ERR_ALLOC, WL_ERR_NOT_CONVERGED, WL_ERR_NONFINITE, WL_ERR_UNSTABLE, WL_ERR_STATE = range(8)
 WL_F32, WL_F64 = 0, 1
-BODY_KIND = {"none": 0, "sphere": 1, "ellipse": 2, "cylinder": 3}
+BODY_KIND = {"none": 0, "sphere": 1, "ellipse": 2, "cylinder": 3, "user": 4}
 
 EXPORTS = (
     "wl_config_default", "wl_sim_create", "wl_sim_destroy", "wl_set_velocity", "wl_get_velocity",
@@ -28,7 +28,8 @@ EXPORTS = (
     "wl_diagnostics", "wl_info", "wl_profile", "wl_profile_report", "wl_coarse_solve_static", "wl_guess_setup",
     "wl_guess_mode", "wl_guess_train", "wl_guess_weights", "wl_guess_info", "wl_net_eval", "wl_step_vjp",
     "wl_force_dp", "wl_window_forward", "wl_window_backward", "wl_set_body", "wl_tguess_mode", "wl_tguess_fit",
-    "wl_tguess_weights", "wl_last_error", "wl_status_string",
+    "wl_tguess_weights", "wl_last_error", "wl_status_string", "wl_set_body_fields", "wl_set_body_velocity_tangent",
+    "wl_window_forward_weighted",
 )
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t)
@@ -108,6 +109,9 @@ def lib() -> C.CDLL:
             "wl_window_forward": ([vp, ip, ip, vp, vp, dp, vp], ip),
             "wl_window_backward": ([vp, C.c_double, vp, vp, C.c_double, vp, vp, vp], ip),
             "wl_set_body": ([vp, C.POINTER(Body)], ip),
+            "wl_set_body_fields": ([vp, vp, vp, vp, vp, vp], ip),
+            "wl_set_body_velocity_tangent": ([vp, vp], ip),
+            "wl_window_forward_weighted": ([vp, ip, ip, vp, vp, vp, dp, vp], ip),
             "wl_tguess_mode": ([vp, ip, ip], ip),
             "wl_tguess_fit": ([vp, vp, vp], ip),
             "wl_tguess_weights": ([vp, vp, vp], ip),
@@ -384,14 +388,23 @@ class Sim:
         self._check(lib().wl_force_dp(self._h, int(axis), float(scale), _ptr(out)), "wl_force_dp")
         return out
 
-    def window_forward(self, nsteps, ckpt_every=20, dts=None, w=(0.0, 0.0, 0.0)):
-        """wl_window_forward: returns (J, dts taken)."""
+    def window_forward(self, nsteps, ckpt_every=20, dts=None, w=(0.0, 0.0, 0.0), step_w=None):
+        """wl_window_forward (wl_window_forward_weighted with per-step weights
+        step_w): returns (J, dts taken)."""
         J = C.c_double()
         out = np.zeros(int(nsteps))
         d = None if dts is None else np.ascontiguousarray(dts, dtype=np.float64)
         ww = np.ascontiguousarray((list(w) + [0.0, 0.0, 0.0])[:3], dtype=np.float64)
-        self._check(lib().wl_window_forward(self._h, int(nsteps), int(ckpt_every), _ptr(d), _ptr(ww), C.byref(J),
-                                            _ptr(out)), "wl_window_forward")
+        if step_w is None:
+            self._check(lib().wl_window_forward(self._h, int(nsteps), int(ckpt_every), _ptr(d), _ptr(ww),
+                                                C.byref(J), _ptr(out)), "wl_window_forward")
+        else:
+            sw = np.ascontiguousarray(step_w, dtype=np.float64)
+            if sw.shape != (int(nsteps),):
+                raise ValueError("step_w needs one weight per step")
+            self._check(lib().wl_window_forward_weighted(self._h, int(nsteps), int(ckpt_every), _ptr(d), _ptr(ww),
+                                                         _ptr(sw), C.byref(J), _ptr(out)),
+                        "wl_window_forward_weighted")
         return J.value, out
 
     def window_backward(self, gJ=1.0, lu=None, le=None, tol=1e-7, params=True):
@@ -402,6 +415,31 @@ class Sim:
         self._check(lib().wl_window_backward(self._h, float(gJ), _ptr(lu), _ptr(le), float(tol), _ptr(du0),
                                              _ptr(due0), _ptr(dp)), "wl_window_backward")
         return du0, due0, dp
+
+    def _field(self, x, comps, what):
+        """A (comps, *grid) array of the sim's dtype, contiguous, as given or
+        converted (host arrays stay on the host: the library copies them)."""
+        T = self.torch
+        if isinstance(x, np.ndarray):
+            x = T.from_numpy(np.ascontiguousarray(x))
+        x = x.to(self.dtype).contiguous()
+        if x.numel() != comps * self.ncell:
+            raise ValueError(f"{what}: expected {comps} x {self.ncell} values, got {x.numel()}")
+        return x
+
+    def set_body_fields(self, d_face, n_face, V_face, d_cell, n_cell):
+        """wl_set_body_fields: a "user" body from its samples (layouts of
+        include/wl.h: d_face (ndim, *grid), n_face (ndim, ndim, *grid),
+        V_face (ndim, *grid), d_cell (*grid), n_cell (ndim, *grid))."""
+        nd = self.ndim
+        f = [self._field(d_face, nd, "d_face"), self._field(n_face, nd * nd, "n_face"),
+             self._field(V_face, nd, "V_face"), self._field(d_cell, 1, "d_cell"), self._field(n_cell, nd, "n_cell")]
+        self._check(lib().wl_set_body_fields(self._h, *[_ptr(x) for x in f]), "wl_set_body_fields")
+
+    def set_body_velocity_tangent(self, dV_face=None):
+        """wl_set_body_velocity_tangent (None clears it)."""
+        x = None if dV_face is None else self._field(dV_face, self.ndim, "dV_face")
+        self._check(lib().wl_set_body_velocity_tangent(self._h, _ptr(x)), "wl_set_body_velocity_tangent")
 
     def set_body(self, body):
         """wl_set_body with a body description (kind unchanged)."""

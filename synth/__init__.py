@@ -46,8 +46,9 @@ def uniform01(seed: int, comp: int, count: int) -> np.ndarray:
 class Body:
     """Analytic immersed body (Sec. 3: AutoBody = signed distance + motion map).
 
-    kind: "none", "sphere" (a circle when ndim == 2), "ellipse" (2D only) or
-    "cylinder" (3D, axis along z through the centre's x and y).
+    kind: "none", "sphere" (a circle when ndim == 2), "ellipse" (2D only),
+    "cylinder" (3D, axis along z through the centre's x and y) or "user" (a
+    body given by grid samples, see ``sample_body``; the other members unused).
     Motion: centre moves along ``heave_axis`` as
     ``centre + heave_amp * sin(omega * t + phase)``; the ellipse pitches about
     its centre by ``pitch_amp * sin(omega * t + phase + pi/2)``.
@@ -64,7 +65,7 @@ class Body:
 
     @property
     def kind_id(self) -> int:
-        return {"none": 0, "sphere": 1, "ellipse": 2, "cylinder": 3}[self.kind]
+        return {"none": 0, "sphere": 1, "ellipse": 2, "cylinder": 3, "user": 4}[self.kind]
 
 
 @dataclass
@@ -244,3 +245,137 @@ def scaled(case: Case, factor: float) -> Case:
                    semi=tuple(s * factor for s in b.semi), heave_amp=b.heave_amp * factor,
                    omega=b.omega / factor)
     return replace(case, n=n, nu=case.nu * factor, body=body)
+
+
+# ------------------------------------------------------------- sampled bodies
+# A body of any shape is a signed distance function plus a velocity field (the
+# paper's distance function and coordinate map, Sec. 3); a user evaluates them
+# at the grid's faces and cell centres and hands the samples to
+# wl_set_body_fields. The shapes below play that user: each evaluates its
+# distance d (> 0 in the fluid), unit normal grad d and body velocity at given
+# points; union and difference combine them the way the paper's body
+# arithmetic does (Sec. 5: `big + small`, a sphere minus a plane).
+
+class SDF:
+    def eval(self, x):
+        """x: list of ndim coordinate arrays -> (d, [n_b], [V_b])."""
+        raise NotImplementedError
+
+    def __add__(self, other):
+        return Union(self, other)
+
+    def __sub__(self, other):
+        return Difference(self, other)
+
+
+@dataclass
+class Circle(SDF):
+    """Sphere (a circle when ndim == 2) of radius ``radius`` about ``centre``,
+    translating with ``velocity`` and, in 2D, spinning at rate ``spin``: the
+    map rot(spin t)(x - c) gives the body velocity spin (y - c_y, -(x - c_x))
+    (clockwise for spin > 0)."""
+    centre: tuple
+    radius: float
+    velocity: tuple = (0.0, 0.0, 0.0)
+    spin: float = 0.0
+
+    def eval(self, x):
+        nd = len(x)
+        r = [x[a] - self.centre[a] for a in range(nd)]
+        rr = np.sqrt(sum(ra * ra for ra in r))
+        safe = np.where(rr > 0.0, rr, 1.0)
+        n = [np.where(rr > 0.0, ra / safe, 1.0 if a == 0 else 0.0) for a, ra in enumerate(r)]
+        V = [np.full_like(rr, float(self.velocity[a])) for a in range(nd)]
+        if self.spin != 0.0:
+            V[0] = V[0] + self.spin * r[1]
+            V[1] = V[1] - self.spin * r[0]
+        return rr - self.radius, n, V
+
+
+@dataclass
+class HalfSpace(SDF):
+    """The solid half-space behind a plane: d = (x - point) . normal, so the
+    fluid lies on the side the unit ``normal`` points to."""
+    point: tuple
+    normal: tuple
+
+    def eval(self, x):
+        nd = len(x)
+        nv = np.asarray(self.normal[:nd], dtype=np.float64)
+        nv = nv / np.linalg.norm(nv)
+        d = sum((x[a] - self.point[a]) * nv[a] for a in range(nd))
+        return d, [np.full_like(d, nv[a]) for a in range(nd)], [np.zeros_like(d) for _ in range(nd)]
+
+
+@dataclass
+class Union(SDF):
+    """Solid where either body is: d = min(d_a, d_b); normal and velocity of
+    the body with the smaller distance (the first on ties)."""
+    a: SDF
+    b: SDF
+
+    def eval(self, x):
+        da, na, Va = self.a.eval(x)
+        db, nb, Vb = self.b.eval(x)
+        pick = db < da
+        return (np.where(pick, db, da), [np.where(pick, q, p) for p, q in zip(na, nb)],
+                [np.where(pick, q, p) for p, q in zip(Va, Vb)])
+
+
+@dataclass
+class Difference(SDF):
+    """Solid where body a is and body b is not: d = max(d_a, -d_b); normal and
+    velocity of the side that sets d (b's normal reversed)."""
+    a: SDF
+    b: SDF
+
+    def eval(self, x):
+        da, na, Va = self.a.eval(x)
+        db, nb, Vb = self.b.eval(x)
+        pick = -db > da
+        return (np.where(pick, -db, da), [np.where(pick, -q, p) for p, q in zip(na, nb)],
+                [np.where(pick, q, p) for p, q in zip(Va, Vb)])
+
+
+def cell_coords(ndim: int, n: tuple):
+    """Coordinates of every cell centre (I + 1/2), x fastest in memory."""
+    axes = [np.arange(n[d], dtype=np.float64) + 0.5 for d in range(ndim)]
+    return np.meshgrid(*axes[::-1], indexing="ij")[::-1]
+
+
+def sample_body(shape: SDF, ndim: int, n: tuple, dtype=np.float64):
+    """Samples of a body for wl_set_body_fields, in ``dtype``:
+    d_face (ndim, *grid), n_face (ndim, ndim, *grid), V_face (ndim, *grid) at
+    the lower a-face of every cell (component a of the velocity on face a),
+    d_cell (*grid) and n_cell (ndim, *grid) at the cell centres."""
+    d_face, n_face, V_face = [], [], []
+    for a in range(ndim):
+        d, nv, V = shape.eval(face_coords(ndim, n, a))
+        d_face.append(d)
+        n_face.append(np.stack(nv))
+        V_face.append(V[a])
+    dc, nc, _ = shape.eval(cell_coords(ndim, n))
+    cast = lambda v: np.ascontiguousarray(np.asarray(v), dtype=dtype)
+    return cast(np.stack(d_face)), cast(np.stack(n_face)), cast(np.stack(V_face)), cast(dc), cast(np.stack(nc))
+
+
+def spinning_cylinders(D=96, Re=500.0, d_D=0.15, g_D=0.05, xi=1.0, U=1.0):
+    """The controlled-cylinder flow of Sec. 5: a fixed circle of diameter D at
+    (2D, 0) on the symmetry plane y = 0 (a slip wall) of a 6D x 2D domain (the
+    upper half of the full flow; uniform inflow U, convective exit), and a small circle of radius r = d_D D / 2 centred at
+    distance D/2 + r + g_D D from it, 60 degrees above the downstream axis,
+    spinning with surface speed xi U (rate xi U / r). Returns (case, shape,
+    spin tangent shape): the last is the small circle's velocity per unit xi
+    on the union's geometry, i.e. d(shape velocity)/d xi."""
+    R = D / 2.0
+    r = d_D * R
+    C = (2.0 * D, 0.0)
+    c = (C[0] + (R + r + g_D * D) * 0.5, C[1] + (R + r + g_D * D) * math.sqrt(3.0) / 2.0)
+    big = Circle(C, R)
+    case = Case(f"spin{D}", 2, (6 * D, 2 * D, 1), (False, False, False), True, (U, 0.0, 0.0), U * D / Re,
+                Body("user"), init="uniform+noise", steps=0)
+    shape = big + Circle(c, r, spin=xi * U / r)
+    tangent = Circle(C, R) + Circle(c, r, spin=U / r)
+    # the tangent's distance and normal equal the shape's; its velocity is the
+    # small circle's at unit xi (the big circle is at rest)
+    return case, shape, tangent

@@ -143,7 +143,7 @@ def _bad_cases():
         "exit on a periodic x": cfg(exit_hi_x=1, periodic_x=1), "tol 0": cfg(tol=0.0),
         "itmax < 0": cfg(itmax=-1), "no smoothing": cfg(smooth_iters=0), "65 smoothing": cfg(smooth_iters=65),
         "dt_init 0": cfg(dt_init=0.0), "cfl 0": cfg(cfl=0.0), "dt_max 0": cfg(dt_max=0.0),
-        "unknown body": body(4), "cylinder in 2D": body(3, ndim=2), "cylinder radius 0": body(3, radius=0.0),
+        "unknown body": body(5), "cylinder in 2D": body(3, ndim=2), "cylinder radius 0": body(3, radius=0.0),
         "sphere radius 0": body(1, radius=0.0), "ellipse axis 0": body(2, ndim=2, semi=(4.0, 0.0)),
         "heave axis 3": body(1, heave_axis=3), "heave axis z in 2D": body(1, ndim=2, heave_axis=2),
     }

@@ -229,3 +229,32 @@ def test_window_parameter_gradient_matches_central_differences():
         Jm, _ = adjoint.window_forward(case, u0 - h * v, ue0, P0, 0.5, dts, w)
         fds.append((Jp - Jm) / (2 * h))
     assert _close_to_one(_dot(du0, v), fds, 1e-5, 1e-9), (_dot(du0, v), fds)
+
+
+def test_sampled_body_velocity_gradient_matches_central_differences():
+    # a spinning control cylinder beside a fixed one (Sec. 5's controlled
+    # flow, coarse): the window gradient of the final step's thrust along the
+    # spin rate's velocity tangent against central differences of complete
+    # forward windows with the face velocity moved by +-h dV
+    from oracle import adjoint as oadj
+    case, shape, tangent = synth.spinning_cylinders(D=12, Re=100.0, xi=3.0)
+    g = oracle.grid_from_case(case)
+    d, nf, V, dc, nc = synth.sample_body(shape, 2, case.n)
+    dV = synth.sample_body(tangent, 2, case.n)[2]
+    fields = oracle.measure_sampled(g, d, nf, V)
+    u0 = synth.random_field(31, 2, case.n, amp=0.05, offset=(1.0, 0.0))
+    u0[0][:, 0] = 1.0
+    u0[1][0, :] = 0.0
+    ue0 = np.ones(case.n[1])
+    P0 = np.zeros(u0.shape[1:])
+    dts = [0.2, 0.22, 0.2, 0.21]
+    w, sw = (-1.0, 0.0), [0.0, 0.0, 0.5, 1.0]
+    J, du, due, dth = oadj.window_gradient_sampled(case, fields, (dc, nc), dV, u0, ue0, P0, dts, w, sw)
+    assert abs(dth) > 1e-3
+    for h in (1e-4, 1e-5):
+        Jp = oadj.window_forward_sampled(case, (fields[0], fields[1], fields[2] + h * dV), (dc, nc), u0, ue0, P0,
+                                         dts, w, sw)[0]
+        Jm = oadj.window_forward_sampled(case, (fields[0], fields[1], fields[2] - h * dV), (dc, nc), u0, ue0, P0,
+                                         dts, w, sw)[0]
+        fd = (Jp - Jm) / (2 * h)
+        assert abs(fd - dth) <= 1e-5 * abs(dth), (fd, dth, h)
