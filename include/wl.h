@@ -388,11 +388,15 @@ WL_API int wl_force_dp(wl_sim *sim, int axis, double scale, double *g);
  *     returns its status from wl_window_forward. */
 WL_API int wl_window_forward(wl_sim *sim, int nsteps, int ckpt_every, const double *dts, const double *w, double *J,
                              double *dts_out);
-/* wl_window_forward with per-step weights: J = sum_n step_w[n] w . F_n
- * (step_w: nsteps doubles, host; NULL = all 1), e.g. the force at the final
- * step alone. wl_window_backward then pulls back this J. */
+/* wl_window_forward with per-step weights and an optional viscous part:
+ * J = sum_n step_w[n] w . F_n (step_w: nsteps doubles, host; NULL = all 1),
+ * e.g. the force at the final step alone, with F_n = wl_forces, plus
+ * wl_forces_viscous when viscous != 0 (the total force on the body).
+ * wl_window_backward then pulls back this J; the viscous force is linear in
+ * the velocity, so its part adds a fixed field to each weighted step's
+ * velocity cotangent. */
 WL_API int wl_window_forward_weighted(wl_sim *sim, int nsteps, int ckpt_every, const double *dts, const double *w,
-                                      const double *step_w, double *J, double *dts_out);
+                                      const double *step_w, int viscous, double *J, double *dts_out);
 WL_API int wl_window_backward(wl_sim *sim, double gJ, const void *lu, const void *le, double tol, void *du0,
                               void *due0, double *dparams);
 

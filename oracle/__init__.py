@@ -81,6 +81,7 @@ def lib():
             ("orc_forces_sampled", [C.POINTER(Grid), _P, _P, _P, _P], None),
             ("orc_forces_viscous_sampled", [C.POINTER(Grid), _P, _P, _P, _P, _P], None),
             ("orc_force_dp_sampled", [C.POINTER(Grid), _P, _P, C.c_int, _P], None),
+            ("orc_forces_viscous_sampled_vjp", [C.POINTER(Grid), _P, _P, _P, _P, _P], None),
             ("orc_bdim", [C.POINTER(Grid), _P, _P, C.c_double, _P, _P, _P, _P, _P], None),
             ("orc_exit_bc", [C.POINTER(Grid), _P, _P, _P, C.c_double, C.c_int, _P, _P, _P], None),
             ("orc_divergence", [C.POINTER(Grid), _P, _P, _P], None),
@@ -254,6 +255,16 @@ def forces_viscous_sampled(g, dc, ncen, u, ue):
     ue = _d(ue) if ue is not None else np.zeros(max(plane_size(g), 1))
     lib().orc_forces_viscous_sampled(C.byref(g), _p(_d(dc)), _p(_d(ncen)), _p(_d(u)), _p(ue), _p(F))
     return F
+
+
+def forces_viscous_sampled_vjp(g, dc, ncen, w):
+    """d(w . F_v)/d(u, ue) of the sampled body's viscous force: (ub, ueb)."""
+    ub = np.zeros((g.ndim,) + _shape(g))
+    ueb = np.zeros(max(plane_size(g), 1))
+    ww = np.zeros(3)
+    ww[: len(w)] = w
+    lib().orc_forces_viscous_sampled_vjp(C.byref(g), _p(_d(dc)), _p(_d(ncen)), _p(ww), _p(ub), _p(ueb))
+    return ub, ueb
 
 
 def force_dp_sampled(g, dc, ncen, axis):

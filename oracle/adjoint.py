@@ -99,11 +99,12 @@ def window_gradient(case, u0, ue0, P0, t0, dts, w, params=(), body=None, lu=None
 
 
 # ------------------------------------------------------------- sampled bodies
-def window_forward_sampled(case, fields, centre, u0, ue0, P0, dts, w, step_w=None, tol=1e-13):
+def window_forward_sampled(case, fields, centre, u0, ue0, P0, dts, w, step_w=None, tol=1e-13, viscous=False):
     """window_forward for a body given by samples: fixed face fields (mu0,
     mu1n, V) of orc_measure_sampled and centre samples (d_cell, n_cell) for
-    the force; J = sum_n step_w[n] w . F_n (step_w None = all 1)."""
-    from . import forces_sampled
+    the force; J = sum_n step_w[n] w . F_n (step_w None = all 1), F_n the
+    pressure force plus, with viscous, the viscous force."""
+    from . import forces_sampled, forces_viscous_sampled
     g = grid_from_case(case)
     u, ue, P = np.array(u0, float), np.array(ue0, float), np.array(P0, float)
     states = [(u, ue, P)]
@@ -111,25 +112,35 @@ def window_forward_sampled(case, fields, centre, u0, ue0, P0, dts, w, step_w=Non
     for n, dt in enumerate(dts):
         u, ue, P = step_fields_fn(g, fields, dt, u, ue, P, tol=tol)
         sw = 1.0 if step_w is None else float(step_w[n])
-        J += sw * float(np.dot(w, forces_sampled(g, centre[0], centre[1], P)[: len(w)]))
+        F = forces_sampled(g, centre[0], centre[1], P)
+        if viscous:
+            F = F + forces_viscous_sampled(g, centre[0], centre[1], u, ue)
+        J += sw * float(np.dot(w, F[: len(w)]))
         states.append((u, ue, P))
     return J, states
 
 
-def window_gradient_sampled(case, fields, centre, dV, u0, ue0, P0, dts, w, step_w=None):
-    """Discrete adjoint of window_forward_sampled: returns (J, dJ/du0, dJ/due0,
+def window_gradient_sampled(case, fields, centre, dV, u0, ue0, P0, dts, w, step_w=None, viscous=False):
+    """Discrete adjoint of window_forward_sampled (viscous: J includes the
+    viscous force, linear in the state after each step): returns (J, dJ/du0, dJ/due0,
     dJ/dtheta) for a parameter theta that moves the body velocity only, along
     the face tangent dV (layout of V): dJ/dtheta = sum_n <Vbar_n, dV>, Vbar_n
     the cotangent of the face velocity from step n's vector-Jacobian product."""
-    from . import force_dp_sampled
+    from . import force_dp_sampled, forces_viscous_sampled_vjp
     g = grid_from_case(case)
-    J, states = window_forward_sampled(case, fields, centre, u0, ue0, P0, dts, w, step_w)
+    J, states = window_forward_sampled(case, fields, centre, u0, ue0, P0, dts, w, step_w, viscous=viscous)
+    if viscous:
+        gv, gve = forces_viscous_sampled_vjp(g, centre[0], centre[1], w)
     lam = np.zeros_like(states[0][0])
     lame = np.zeros_like(states[0][1])
     dtheta = 0.0
     for n in range(len(dts) - 1, -1, -1):
         u, ue, P = states[n]
         sw = 1.0 if step_w is None else float(step_w[n])
+        if viscous:
+            # the viscous force of step n reads the state after it
+            lam = lam + sw * gv
+            lame = lame + sw * gve[: lame.size]
         lP = sw * sum(w[a] * force_dp_sampled(g, centre[0], centre[1], a) for a in range(len(w)))
         ub, ueb, mu0b, mu1nb, Vb = step_vjp_fields(g, fields, dts[n], u, ue, P, lam, lame, lP)
         dtheta += float(np.sum(Vb * dV))

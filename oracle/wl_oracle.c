@@ -1079,6 +1079,47 @@ static void scatter(int kind, size_t index, double v, double *ub, double *ueb)
     else if (kind == 1) ueb[index] += v;
 }
 
+/* Transpose of the sampled body's viscous force (orc_forces_viscous_sampled)
+ * contracted with w: the force is linear in the velocity samples, so
+ * (ub, ueb) += d(w . F_v)/d(u, ue), each centre difference of centre_grad
+ * passing its weight nu K (w_a n_b + w_b n_a) to the samples it reads. */
+void orc_forces_viscous_sampled_vjp(const orc_grid *g, const double *dc, const double *ncen, const double *w,
+                                    double *ub, double *ueb)
+{
+    size_t nc = ncell(g);
+    for (int k = 0; k < g->n[2]; ++k)
+        for (int j = 0; j < g->n[1]; ++j)
+            for (int i = 0; i < g->n[0]; ++i) {
+                size_t L = lin(g, i, j, k);
+                double K = orc_kernel(dc[L], g->eps);
+                if (K == 0.0) continue;
+                for (int a = 0; a < g->ndim; ++a)
+                    for (int b = 0; b < g->ndim; ++b) {
+                        double M = g->nu * K * (w[a] * ncen[(size_t)b * nc + L] + w[b] * ncen[(size_t)a * nc + L]);
+                        int A[3] = {0, 0, 0}, Bv[3] = {0, 0, 0}, kind;
+                        size_t at;
+                        A[a] = 1;
+                        Bv[b] = 1;
+                        if (a == b) {
+                            su_loc(g, a, i + A[0], j + A[1], k + A[2], &kind, &at);
+                            scatter(kind, at, M, ub, ueb);
+                            su_loc(g, a, i, j, k, &kind, &at);
+                            scatter(kind, at, -M, ub, ueb);
+                        } else {
+                            double q = 0.25 * M;
+                            su_loc(g, a, i + Bv[0], j + Bv[1], k + Bv[2], &kind, &at);
+                            scatter(kind, at, q, ub, ueb);
+                            su_loc(g, a, i + A[0] + Bv[0], j + A[1] + Bv[1], k + A[2] + Bv[2], &kind, &at);
+                            scatter(kind, at, q, ub, ueb);
+                            su_loc(g, a, i - Bv[0], j - Bv[1], k - Bv[2], &kind, &at);
+                            scatter(kind, at, -q, ub, ueb);
+                            su_loc(g, a, i + A[0] - Bv[0], j + A[1] - Bv[1], k + A[2] - Bv[2], &kind, &at);
+                            scatter(kind, at, -q, ub, ueb);
+                        }
+                    }
+            }
+}
+
 /* median3 with the index (0, 1, 2) of the argument it returns */
 static double median3_w(double a, double b, double c, int *w)
 {

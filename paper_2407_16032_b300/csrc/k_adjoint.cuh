@@ -321,6 +321,48 @@ __global__ void k_force_dp(GridD g, CS cs, const T *invD, double w0, double w1, 
     }
 }
 
+// Velocity derivative of the weighted viscous force w . F_v of k_forces_visc.
+// F_v is linear in the velocity samples:
+//   w . F_v = sum_I sum_ab M_ab(I) G_ab(I),  M_ab = nu K(d_I) (w_a n_b + w_b n_a),
+// with G_ab = d_b u_a the centre differences of k_forces_visc, so each sample
+// that a difference reads gets M_ab times its coefficient there (1 and -1 for
+// a == b, +-1/4 otherwise). Adds scale times that into (ub, ueb) through
+// vel_slot (constant samples get nothing).
+template <typename T, typename CS>
+__global__ void k_force_visc_du(GridD g, CS cs, double w0, double w1, double w2, double scale, Vec3P<T> ub, T *ueb) {
+    const double w[3] = {w0, w1, w2};
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < g.nc;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int i, j, k;
+        decode(g, idx, i, j, k);
+        double K, nd[3];
+        if (!cs.template eval<T>(g, i, j, k, idx, K, nd)) continue;
+        for (int a = 0; a < g.ndim; ++a)
+            for (int b = 0; b < g.ndim; ++b) {
+                const double M = scale * g.nu * K * (w[a] * nd[b] + w[b] * nd[a]);
+                if (M == 0.0) continue;
+                T *ua = ub.p[a];
+                if (a == b) {
+                    int P[3] = {i, j, k};
+                    P[a] += 1;
+                    add_to(vel_slot<T>(g, ua, ueb, a, P[0], P[1], P[2]), (T)M);
+                    add_to(vel_slot<T>(g, ua, ueb, a, i, j, k), (T)(-M));
+                } else {
+                    int q1[3] = {i, j, k}, q2[3] = {i, j, k}, q3[3] = {i, j, k}, q4[3] = {i, j, k};
+                    q1[b] += 1;
+                    q2[a] += 1; q2[b] += 1;
+                    q3[b] -= 1;
+                    q4[a] += 1; q4[b] -= 1;
+                    const T m = (T)(0.25 * M);
+                    add_to(vel_slot<T>(g, ua, ueb, a, q1[0], q1[1], q1[2]), m);
+                    add_to(vel_slot<T>(g, ua, ueb, a, q2[0], q2[1], q2[2]), m);
+                    add_to(vel_slot<T>(g, ua, ueb, a, q3[0], q3[1], q3[2]), -m);
+                    add_to(vel_slot<T>(g, ua, ueb, a, q4[0], q4[1], q4[2]), -m);
+                }
+            }
+    }
+}
+
 // ------------------------------------------------ body-parameter tangents
 // Tangent of the body state with respect to one motion parameter: the heave
 // amplitude moves the centre by sin(omega t + phase) along the heave axis and

@@ -47,6 +47,13 @@ __global__ void k_bc_lower(GridD g, Vec3P<T> u) {
 }
 
 // Fill a plane with a constant.
+// y += alpha x over n elements.
+template <typename T>
+__global__ void k_axpy(long long n, T alpha, const T *x, T *y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] += alpha * x[i];
+}
+
 template <typename T>
 __global__ void k_fill(long long n, T v, T *x) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)

@@ -280,11 +280,11 @@ int wl_step_vjp(wl_sim *s, double t, double dt, const void *u0, const void *ue0,
 }
 int wl_window_forward(wl_sim *s, int nsteps, int ckpt_every, const double *dts, const double *w, double *J,
                       double *dts_out) {
-    return guard(s, [&] { return s->impl->window_forward(nsteps, ckpt_every, dts, w, nullptr, J, dts_out); });
+    return guard(s, [&] { return s->impl->window_forward(nsteps, ckpt_every, dts, w, nullptr, 0, J, dts_out); });
 }
 int wl_window_forward_weighted(wl_sim *s, int nsteps, int ckpt_every, const double *dts, const double *w,
-                               const double *step_w, double *J, double *dts_out) {
-    return guard(s, [&] { return s->impl->window_forward(nsteps, ckpt_every, dts, w, step_w, J, dts_out); });
+                               const double *step_w, int viscous, double *J, double *dts_out) {
+    return guard(s, [&] { return s->impl->window_forward(nsteps, ckpt_every, dts, w, step_w, viscous, J, dts_out); });
 }
 int wl_window_backward(wl_sim *s, double gJ, const void *lu, const void *le, double tol, void *du0, void *due0,
                        double *dparams) {

@@ -164,6 +164,8 @@ struct Sim : SimBase {
         int n = 0, k = 0;
         double w[3] = {0, 0, 0};
         std::vector<double> dts, t0s, ws;   // steps, start times, per-step weights
+        bool visc = false;                  // J includes the viscous force
+        T *gv[3] = {}, *gve = nullptr;      // d(w . F_v)/d(u, ue) (constant for a fixed body)
         std::vector<Snap> ck, seg;
         Snap fin{};
         double fin_dt_next = 0.0;
@@ -1800,8 +1802,8 @@ struct Sim : SimBase {
         t = s.t;
     }
 
-    int window_forward(int nsteps, int ckpt, const double *dts, const double *w, const double *step_w, double *J,
-                       double *dts_out) override {
+    int window_forward(int nsteps, int ckpt, const double *dts, const double *w, const double *step_w, int viscous,
+                       double *J, double *dts_out) override {
         if (nsteps < 1 || ckpt < 1) throw Err{WL_ERR_ARG, "window: nsteps and ckpt_every must be >= 1"};
         adj_alloc();
         const int nck = (nsteps + ckpt - 1) / ckpt;
@@ -1820,6 +1822,7 @@ struct Sim : SimBase {
         for (int a = 0; a < 3; ++a) win.w[a] = w ? w[a] : 0.0;
         win.dts.assign(nsteps, 0.0);
         win.ws.assign(nsteps, 1.0);
+        win.visc = viscous != 0;
         if (step_w) for (int n = 0; n < nsteps; ++n) win.ws[n] = step_w[n];
         double Jv = 0.0;
         for (int n = 0; n < nsteps; ++n) {
@@ -1831,6 +1834,11 @@ struct Sim : SimBase {
             if (w && has_body && win.ws[n] != 0.0) {
                 double F[3];
                 forces(F);
+                if (win.visc) {
+                    double Fv[3];
+                    forces_viscous(Fv);
+                    for (int a = 0; a < 3; ++a) F[a] += Fv[a];
+                }
                 Jv += win.ws[n] * (w[0] * F[0] + w[1] * F[1] + w[2] * F[2]);
             }
         }
@@ -1867,6 +1875,19 @@ struct Sim : SimBase {
         ad.qwarm = true;
         ad.qvalid[0] = ad.qvalid[1] = false;
         struct QOff { bool &q; ~QOff() { q = false; } } qoff{ad.qwarm};
+        // the viscous force is linear in the velocity: its gradient is one
+        // field for the window (the body is fixed or moves the same in every
+        // recomputation), added to the velocity cotangent after each step
+        const bool visc = force && win.visc;
+        if (visc) {
+            for (int a = 0; a < g.ndim; ++a) {
+                if (!win.gv[a]) win.gv[a] = alloc_n<T>(g.nc);
+                WL_CK(cudaMemsetAsync(win.gv[a], 0, vb, st));
+            }
+            if (!win.gve) win.gve = alloc_n<T>(np);
+            WL_CK(cudaMemsetAsync(win.gve, 0, pb, st));
+        }
+        double visc_t = -1.0;
         int rc = WL_OK;
         const int nseg = (win.n + win.k - 1) / win.k;
         for (int sgi = nseg - 1; sgi >= 0 && rc == WL_OK; --sgi) {
@@ -1892,6 +1913,25 @@ struct Sim : SimBase {
                 const bool fn = force && gn != 0.0;
                 const double wF[3] = {gn * win.w[0], gn * win.w[1], gn * win.w[2]};
                 if (fn) force_dp_w(s.t + dt, win.w, gn);
+                if (fn && visc) {
+                    if (visc_t != body_t || moving) {
+                        // (re)form d(w . F_v)/du for the body as measured now
+                        for (int a = 0; a < g.ndim; ++a) WL_CK(cudaMemsetAsync(win.gv[a], 0, vb, st));
+                        WL_CK(cudaMemsetAsync(win.gve, 0, pb, st));
+                        with_centre(body_t, [&](auto cs) {
+                            k_force_visc_du<T, decltype(cs)><<<blocks(g.nc), 256, 0, st>>>(
+                                g, cs, win.w[0], win.w[1], win.w[2], 1.0, vvp(win.gv), g.exit_x ? win.gve : nullptr);
+                        });
+                        WL_LAUNCH_CK();
+                        ++launches;
+                        visc_t = body_t;
+                    }
+                    for (int a = 0; a < g.ndim; ++a)
+                        k_axpy<T><<<blocks(g.nc), 256, 0, st>>>((long long)g.nc, (T)gn, win.gv[a], ad.lu[a]);
+                    if (g.exit_x) k_axpy<T><<<blocks(np), 256, 0, st>>>((long long)np, (T)gn, win.gve, ad.le);
+                    WL_LAUNCH_CK();
+                    launches += g.ndim + (g.exit_x ? 1 : 0);
+                }
                 const int r = vjp_core(s.t, dt, fn, tol, params, fn ? wF : nullptr, nullptr);
                 if (r == WL_ERR_NONFINITE) rc = r;
                 for (int a = 0; a < 3; ++a) std::swap(ad.lu[a], ad.ub[a]);

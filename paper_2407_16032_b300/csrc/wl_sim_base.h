@@ -60,7 +60,7 @@ struct SimBase {
                          const void *le, const double *lP, double tol, void *ub, void *ueb, wl_solve_stats *st) = 0;
     virtual void force_dp(int axis, double scale, double *g) = 0;
     virtual int window_forward(int nsteps, int ckpt, const double *dts, const double *w, const double *step_w,
-                               double *J, double *dts_out) = 0;
+                               int viscous, double *J, double *dts_out) = 0;
     virtual int window_backward(double gJ, const void *lu, const void *le, double tol, void *du0, void *due0,
                                 double *dparams) = 0;
     virtual void set_body(const wl_body *bd) = 0;

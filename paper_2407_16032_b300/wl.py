@@ -111,7 +111,7 @@ def lib() -> C.CDLL:
             "wl_set_body": ([vp, C.POINTER(Body)], ip),
             "wl_set_body_fields": ([vp, vp, vp, vp, vp, vp], ip),
             "wl_set_body_velocity_tangent": ([vp, vp], ip),
-            "wl_window_forward_weighted": ([vp, ip, ip, vp, vp, vp, dp, vp], ip),
+            "wl_window_forward_weighted": ([vp, ip, ip, vp, vp, vp, ip, dp, vp], ip),
             "wl_tguess_mode": ([vp, ip, ip], ip),
             "wl_tguess_fit": ([vp, vp, vp], ip),
             "wl_tguess_weights": ([vp, vp, vp], ip),
@@ -388,22 +388,22 @@ class Sim:
         self._check(lib().wl_force_dp(self._h, int(axis), float(scale), _ptr(out)), "wl_force_dp")
         return out
 
-    def window_forward(self, nsteps, ckpt_every=20, dts=None, w=(0.0, 0.0, 0.0), step_w=None):
+    def window_forward(self, nsteps, ckpt_every=20, dts=None, w=(0.0, 0.0, 0.0), step_w=None, viscous=False):
         """wl_window_forward (wl_window_forward_weighted with per-step weights
-        step_w): returns (J, dts taken)."""
+        step_w or the viscous force in the objective): returns (J, dts taken)."""
         J = C.c_double()
         out = np.zeros(int(nsteps))
         d = None if dts is None else np.ascontiguousarray(dts, dtype=np.float64)
         ww = np.ascontiguousarray((list(w) + [0.0, 0.0, 0.0])[:3], dtype=np.float64)
-        if step_w is None:
+        if step_w is None and not viscous:
             self._check(lib().wl_window_forward(self._h, int(nsteps), int(ckpt_every), _ptr(d), _ptr(ww),
                                                 C.byref(J), _ptr(out)), "wl_window_forward")
         else:
-            sw = np.ascontiguousarray(step_w, dtype=np.float64)
-            if sw.shape != (int(nsteps),):
+            sw = None if step_w is None else np.ascontiguousarray(step_w, dtype=np.float64)
+            if sw is not None and sw.shape != (int(nsteps),):
                 raise ValueError("step_w needs one weight per step")
             self._check(lib().wl_window_forward_weighted(self._h, int(nsteps), int(ckpt_every), _ptr(d), _ptr(ww),
-                                                         _ptr(sw), C.byref(J), _ptr(out)),
+                                                         _ptr(sw), int(bool(viscous)), C.byref(J), _ptr(out)),
                         "wl_window_forward_weighted")
         return J.value, out
 

@@ -180,10 +180,11 @@ def test_set_body_fields_rejects_an_analytic_body():
     assert e.value.code == WL_ERR_ARG
 
 
+@pytest.mark.parametrize("viscous", [False, True])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_spin_rate_window_gradient_matches_the_oracle(prec):
-    # Sec. 5's controlled cylinder (coarse): J = thrust weighted towards the
-    # window's last steps; its gradient along the spin rate's velocity tangent
+def test_spin_rate_window_gradient_matches_the_oracle(prec, viscous):
+    # Sec. 5's controlled cylinder (coarse): J = thrust (pressure, or pressure
+    # plus viscous force) weighted towards the window's last steps; its gradient along the spin rate's velocity tangent
     # (wl_set_body_velocity_tangent) and along the start velocity, against the
     # FP64 oracle's discrete adjoint on the same samples (the bars of the
     # analytic bodies' window test)
@@ -202,12 +203,12 @@ def test_spin_rate_window_gradient_matches_the_oracle(prec):
     sim.set_velocity(torch.tensor(u0, dtype=tdt).cuda(), torch.tensor(ue0, dtype=tdt).cuda())
     dts = [0.2, 0.22, 0.2, 0.21, 0.2, 0.2]
     w, sw = (-1.0, 0.0), [0.0, 0.0, 0.0, 0.25, 0.5, 1.0]
-    J, taken = sim.window_forward(len(dts), 2, dts, w, step_w=sw)
+    J, taken = sim.window_forward(len(dts), 2, dts, w, step_w=sw, viscous=viscous)
     du, due, dp = sim.window_backward(1.0, tol=1e-12 if prec == "f64" else 1e-7)
     fields = oracle.measure_sampled(g, *samples[:3])
     J_o, du_o, due_o, dth_o = oadj.window_gradient_sampled(case, fields, (samples[3], samples[4]),
                                                            dV.astype(np.float64), u0, ue0, np.zeros(u0.shape[1:]),
-                                                           dts, w, sw)
+                                                           dts, w, sw, viscous=viscous)
     du = du.double().cpu().numpy()
     assert abs(dth_o) > 1e-3 and dp[1] == 0.0
     if prec == "f64":

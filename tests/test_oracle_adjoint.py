@@ -231,7 +231,8 @@ def test_window_parameter_gradient_matches_central_differences():
     assert _close_to_one(_dot(du0, v), fds, 1e-5, 1e-9), (_dot(du0, v), fds)
 
 
-def test_sampled_body_velocity_gradient_matches_central_differences():
+@pytest.mark.parametrize("viscous", [False, True])
+def test_sampled_body_velocity_gradient_matches_central_differences(viscous):
     # a spinning control cylinder beside a fixed one (Sec. 5's controlled
     # flow, coarse): the window gradient of the final step's thrust along the
     # spin rate's velocity tangent against central differences of complete
@@ -249,12 +250,12 @@ def test_sampled_body_velocity_gradient_matches_central_differences():
     P0 = np.zeros(u0.shape[1:])
     dts = [0.2, 0.22, 0.2, 0.21]
     w, sw = (-1.0, 0.0), [0.0, 0.0, 0.5, 1.0]
-    J, du, due, dth = oadj.window_gradient_sampled(case, fields, (dc, nc), dV, u0, ue0, P0, dts, w, sw)
+    J, du, due, dth = oadj.window_gradient_sampled(case, fields, (dc, nc), dV, u0, ue0, P0, dts, w, sw, viscous)
     assert abs(dth) > 1e-3
     for h in (1e-4, 1e-5):
         Jp = oadj.window_forward_sampled(case, (fields[0], fields[1], fields[2] + h * dV), (dc, nc), u0, ue0, P0,
-                                         dts, w, sw)[0]
+                                         dts, w, sw, viscous=viscous)[0]
         Jm = oadj.window_forward_sampled(case, (fields[0], fields[1], fields[2] - h * dV), (dc, nc), u0, ue0, P0,
-                                         dts, w, sw)[0]
+                                         dts, w, sw, viscous=viscous)[0]
         fd = (Jp - Jm) / (2 * h)
         assert abs(fd - dth) <= 1e-5 * abs(dth), (fd, dth, h)

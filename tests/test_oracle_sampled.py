@@ -135,3 +135,23 @@ def test_sampled_fields_step_equals_the_analytic_step():
     fields = oracle.measure_sampled(g, d, nf, V)
     us, ues, Ps = oracle.step_fields_fn(g, fields, 0.2, u, ue, P)
     assert np.array_equal(us, ua) and np.array_equal(Ps, Pa)
+
+
+def test_viscous_force_transpose_is_its_linear_part():
+    # the viscous force is affine in (u, ue) (boundary constants aside), so its
+    # transpose contracted with (v, ve) is w . (F(u + v, ue + ve) - F(u, ue))
+    case, shape, _ = synth.spinning_cylinders(D=16, Re=50.0, xi=2.0)
+    g = oracle.grid_from_case(case)
+    _, _, _, dc, nc = synth.sample_body(shape, 2, case.n)
+    u = synth.random_field(7, 2, case.n, amp=0.3, offset=(1.0, 0.0))
+    v = synth.random_field(8, 2, case.n, amp=1.0)
+    ue = 1.0 + 0.1 * synth.random_scalar(9, 1, (case.n[1], 1, 1)).ravel()
+    ve = synth.random_scalar(10, 1, (case.n[1], 1, 1)).ravel()
+    w = (0.7, -1.3)
+    ub, ueb = oracle.forces_viscous_sampled_vjp(g, dc, nc, w)
+    F1 = oracle.forces_viscous_sampled(g, dc, nc, u + v, ue + ve)
+    F0 = oracle.forces_viscous_sampled(g, dc, nc, u, ue)
+    lhs = float(np.sum(ub * v) + np.dot(ueb[: ve.size], ve))
+    rhs = float(np.dot(w, (F1 - F0)[:2]))
+    assert abs(rhs) > 1e-3
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(rhs))
