@@ -277,6 +277,17 @@ void orc_body_eval(const orc_body *B, int ndim, const double *x, double t, doubl
     V[1] += thd * rx;
 }
 
+/* Smallest zeroth moment kept on a face (reading; Sec. 2 is silent on it):
+ * below it mu0 is taken as 0, i.e. the face is solid. A cell whose faces sum
+ * to a tiny but nonzero coefficient has its pressure fixed only by the
+ * rounding of its right-hand side divided by that sum (unbounded as the sum
+ * goes to zero, in any precision), and such a cell still counts in the mean
+ * over active rows that the pressure is reported against. The cut removes the
+ * outermost few percent of the kernel's reach (mu0 ~ pi^2 (1 + r)^3 / 12
+ * near r = -1), so no cell sums to less than it without being solid. */
+#define OR_MU0_MIN 1e-5
+static double mu0_kept(double m) { return m < OR_MU0_MIN ? 0.0 : m; }
+
 /* Measure the body onto every stored face of every component at time t:
  * mu0 (3 x nc), mu1n (9 x nc, index (a*3+b)*nc: mu1 * n_b on face a),
  * V (3 x nc).  Face a of cell I sits at (I + 1/2) - e_a/2. */
@@ -293,7 +304,7 @@ void orc_measure(const orc_grid *g, const orc_body *B, double t, double *mu0, do
                     double d, nrm[3], v[3];
                     orc_body_eval(B, g->ndim, x, t, &d, nrm, v);
                     size_t L = lin(g, i, j, k);
-                    mu0[(size_t)a * nc + L] = orc_mu0(d, g->eps);
+                    mu0[(size_t)a * nc + L] = mu0_kept(orc_mu0(d, g->eps));
                     double m1 = orc_mu1(d, g->eps);
                     for (int b = 0; b < 3; ++b) mu1n[(size_t)(a * 3 + b) * nc + L] = (b < g->ndim) ? m1 * nrm[b] : 0.0;
                     V[(size_t)a * nc + L] = v[a];
@@ -305,7 +316,8 @@ void orc_measure(const orc_grid *g, const orc_body *B, double t, double *mu0, do
  * a of every cell the signed distance d[a] (> 0 in the fluid), the unit normal
  * n[a*ndim + b] (component b, into the fluid) and the body velocity V[a]
  * (component a). The kernel moments are those of the analytic bodies:
- * mu0 = mu0(d), mu1n = mu1(d) n, V = V (layouts of orc_measure). */
+ * mu0 = mu0(d) (cut below OR_MU0_MIN), mu1n = mu1(d) n, V = V (layouts of
+ * orc_measure). */
 void orc_measure_sampled(const orc_grid *g, const double *d, const double *n, const double *Vin, double *mu0,
                          double *mu1n, double *V)
 {
@@ -315,7 +327,7 @@ void orc_measure_sampled(const orc_grid *g, const double *d, const double *n, co
         for (size_t L = 0; L < nc; ++L) {
             double da = d[(size_t)a * nc + L];
             double m1 = orc_mu1(da, g->eps);
-            mu0[(size_t)a * nc + L] = orc_mu0(da, g->eps);
+            mu0[(size_t)a * nc + L] = mu0_kept(orc_mu0(da, g->eps));
             for (int b = 0; b < 3; ++b)
                 mu1n[(size_t)(a * 3 + b) * nc + L] = b < nd ? m1 * n[(size_t)(a * nd + b) * nc + L] : 0.0;
             V[(size_t)a * nc + L] = Vin[(size_t)a * nc + L];

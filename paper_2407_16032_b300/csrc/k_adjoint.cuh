@@ -451,6 +451,7 @@ __device__ __forceinline__ FaceTan face_tangent(const BodyState &B, const BodyTa
     const double m1 = kmu1<double>(d, B.eps);
     f.mu0 = kmu0<double>(d, B.eps);
     f.dmu0 = K * dd;
+    if (f.mu0 < WL_MU0_MIN) { f.mu0 = 0.0; f.dmu0 = 0.0; }   // the measure's cut
     const double dm1 = -d * K * dd;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {

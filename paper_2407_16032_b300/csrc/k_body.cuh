@@ -47,6 +47,14 @@ __device__ __forceinline__ T kmu1(T d, T eps) {
     const T ip = T(0.31830988618379067154);
     return eps * (T(0.25) - T(0.25) * r * r - (r * sinpi_t(r) + (T(1) + cospi_t(r)) * ip) * (T(0.5) * ip));
 }
+// Smallest zeroth moment kept on a face: below it the face counts as solid
+// (mu0 = 0). A cell whose faces sum to a tiny nonzero coefficient has a
+// pressure fixed only by its right-hand side's rounding divided by that sum,
+// yet counts in the mean over active rows; the cut trims the outermost few
+// percent of the kernel's reach (mu0 ~ pi^2 (1 + r)^3 / 12 near r = -1).
+#define WL_MU0_MIN 1e-5
+__device__ __forceinline__ double mu0_kept(double m) { return m < WL_MU0_MIN ? 0.0 : m; }
+
 template <typename T>
 __device__ __forceinline__ T kkernel(T d, T eps) {
     const T r = d / eps;
@@ -116,14 +124,14 @@ __global__ void __launch_bounds__(256) k_measure(LevelD<T> L, BodyState B, Vec3P
             px[a] -= T(0.5);
             T d, nrm[3], v[3];
             body_eval<T>(B, NDIM, px, d, nrm, v);
-            T m0 = kmu0<T>(d, eps), m1 = kmu1<T>(d, eps);
+            T m0 = (T)mu0_kept((double)kmu0<T>(d, eps)), m1 = kmu1<T>(d, eps);
             if (sizeof(T) < sizeof(double) && d > -eps - T(0.5) && d < eps + T(0.5)) {
                 // inside the kernel band: distance, normal and moments in double
                 // (a thin shell of faces), rounded once to T
                 double pd[3] = {i + 0.5, j + 0.5, k + 0.5}, dd, nd[3], vd[3];
                 pd[a] -= 0.5;
                 body_eval<double>(B, NDIM, pd, dd, nd, vd);
-                m0 = (T)kmu0<double>(dd, B.eps);
+                m0 = (T)mu0_kept(kmu0<double>(dd, B.eps));
                 m1 = (T)kmu1<double>(dd, B.eps);
 #pragma unroll
                 for (int b = 0; b < 3; ++b) { nrm[b] = (T)nd[b]; v[b] = (T)vd[b]; }
@@ -141,7 +149,8 @@ __global__ void __launch_bounds__(256) k_measure(LevelD<T> L, BodyState B, Vec3P
 // Moments of a body given by samples (Sec. 3 states a body as a distance
 // function and a map; here the caller evaluates them): on entry c.p[a] holds
 // the signed distance at face a and mu1n slot a*NDIM+b the normal component b
-// there; on return c.p[a] = mu0(d) (0 on lower faces of non-periodic axes) and
+// there; on return c.p[a] = mu0(d) (cut below WL_MU0_MIN; 0 on lower faces of
+// non-periodic axes) and
 // slot a*3+b = mu1(d) n_b (0 for b >= NDIM), both formed in double from the
 // stored samples and rounded once to T. Every cell is read before it is
 // written, by the thread that owns it.
@@ -162,7 +171,7 @@ __global__ void __launch_bounds__(256) k_measure_sampled(GridD g, Vec3P<T> c, T 
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {
             const double m1 = kmu1<double>(d[a], eps);
-            c.p[a][idx] = (!g.per[a] && I[a] == 0) ? T(0) : (T)kmu0<double>(d[a], eps);
+            c.p[a][idx] = (!g.per[a] && I[a] == 0) ? T(0) : (T)mu0_kept(kmu0<double>(d[a], eps));
 #pragma unroll
             for (int b = 0; b < 3; ++b) mu1n0[(a * 3 + b) * mstride + idx] = b < NDIM ? (T)(m1 * n[a][b]) : T(0);
         }

@@ -483,6 +483,45 @@ __global__ void __launch_bounds__(256) k_pcg_u(LevelD<T> L, const T *dcur, T *ph
     pcg_u_run<T, LAST, FINE>(L, dcur, ph, pl, S, part, lev);
 }
 
+// Weakly coupled rows after a solve. A row whose face coefficients sum to
+// less than `cut` has its pressure fixed by the solve only to r / sum c, and r
+// is bounded by the global residual norm, not by the row's own size; where the
+// BDIM kernel weight is not zero such a row still enters the pressure force.
+// A Gauss-Seidel update in double, p += r / A_II (A_II = -sum c) with
+// r = (b - mean) - A p
+// formed from the pairs, sets the row's residual to rounding and changes a
+// neighbour's residual by c_f dp, at most |r|. Cells of one colour ((i + j + k)
+// parity) read only the other colour, so an update is race-free and the
+// result does not depend on the thread order. Level 0, non-uniform tiles only
+// (a uniform tile has no weak rows).
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_weak_rows(LevelD<T> L, const T *__restrict__ b, const T *__restrict__ bl,
+                                                   T *ph, T *pl, const DevScalars *S, double cut, int colour) {
+    const double bm = S->bmean;
+    for_cells<NDIM>(L.g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
+        if (uni || ((i + j + k) & 1) != colour || L.invD[idx] == T(0)) return;
+        long long ip[3], im[3];
+        T cp[3], cm[3];
+        nb_setup<T, NDIM>(L, false, i, j, k, idx, ip, im, cp, cm);
+        double csum = 0.0;
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) csum += (double)cp[a] + (double)cm[a];
+        if (!(csum > 0.0 && csum < cut)) return;
+        const double p0 = (double)ph[idx] + (double)pl[idx];
+        double Ap = 0.0;
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) {
+            Ap += (double)cp[a] * (((double)ph[ip[a]] + (double)pl[ip[a]]) - p0);
+            Ap += (double)cm[a] * (((double)ph[im[a]] + (double)pl[im[a]]) - p0);
+        }
+        const double r = (((double)b[idx] + (double)bl[idx]) - bm) - Ap;
+        const double pn = p0 - r / csum;   // p += r / A_II, A_II = -csum
+        const T h = (T)pn;
+        ph[idx] = h;
+        pl[idx] = (T)(pn - (double)h);
+    });
+}
+
 // Single-level case: the coarse solve itself is the fine correction.
 template <typename T>
 __global__ void k_padd(GridD g, const T *x, T *ph, T *pl) {

@@ -791,11 +791,26 @@ struct Sim : SimBase {
             read_scalars();
             ++it;
         }
+        if (!(hS->status & 1)) weak_rows();
         if (sts) { sts->vcycles = it; sts->rel_resid = hS->rel; sts->bnorm = hS->bnorm; sts->rel_initial = rel0; }
         if (collecting && !(hS->status & 1) && hS->rel <= cfg.tol) guess_end();
         if (hS->status & 1) return WL_ERR_NONFINITE;
         if (hS->rel > cfg.tol) return WL_ERR_NOT_CONVERGED;
         return WL_OK;
+    }
+
+    // Gauss-Seidel sweeps over the weakly coupled rows of level 0 (faces
+    // summing to less than half a face) after a solve (k_weak_rows): three
+    // red-black sweeps; only a body makes such rows.
+    void weak_rows() {
+        if (!has_body) return;
+        P0("weak_rows", 0, g.nc);
+        for (int sweep = 0; sweep < 3; ++sweep)
+            for (int colour = 0; colour < 2; ++colour)
+                k_weak_rows<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], b, bl, ph, pl, S, 0.5 * (double)lv[0].cu, colour);
+        P1();
+        WL_LAUNCH_CK();
+        launches += 6;
     }
 
     // status flags are per solve: clear them before its right-hand side is formed

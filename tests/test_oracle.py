@@ -334,6 +334,8 @@ def test_measure_places_bodies_on_face_centres():
         X = face_coords(2, n, a)
         d = np.sqrt((X[0] - 7.3) ** 2 + (X[1] - 5.9) ** 2) - 3.1
         exp0 = np.vectorize(oracle.mu0)(d)
+        # reading: a face whose mu0 is below 1e-5 is solid (mu0 = 0)
+        exp0 = np.where(exp0 < 1e-5, 0.0, exp0)
         np.testing.assert_allclose(mu0[a], exp0, atol=1e-15)
         m1 = np.vectorize(oracle.mu1)(d)
         nb = [(X[0] - 7.3) / (d + 3.1), (X[1] - 5.9) / (d + 3.1)]
@@ -743,3 +745,26 @@ def test_results_do_not_depend_on_the_thread_count():
     (u1, e1, p1, st1, dt1), (u2, e2, p2, st2, dt2) = runs
     assert np.array_equal(u1, u2) and np.array_equal(e1, e2) and np.array_equal(p1, p2)
     assert st1 == st2 and dt1 == dt2
+
+
+def test_measure_cuts_the_kernel_tail_so_no_cell_is_nearly_solid():
+    # reading: faces with mu0 below 1e-5 count as solid, so every cell's face
+    # coefficients sum to 0 or to at least 1e-5 (a cell with a tiny nonzero sum
+    # has a pressure fixed only by rounding / that sum); faces in the cut band
+    # exist for this body and are zeroed, the others keep mu0(d)
+    n = (48, 40, 1)
+    g = oracle.make_grid(2, n, (False,) * 3, True, (1, 0, 0), nu=0.01)
+    b = synth.Body("sphere", (21.37, 19.61, 0.0), 9.3)
+    mu0, _, _ = oracle.measure(g, oracle.make_body(b), 0.0)
+    raw = []
+    for a in range(2):
+        X = face_coords(2, n, a)
+        d = np.sqrt((X[0] - 21.37) ** 2 + (X[1] - 19.61) ** 2) - 9.3
+        raw.append(np.vectorize(oracle.mu0)(d))
+    raw = np.stack(raw)
+    tiny = (raw > 0) & (raw < 1e-5)
+    assert tiny.any()
+    assert (mu0[tiny] == 0).all() and np.array_equal(mu0[~tiny], raw[~tiny])
+    c = oracle.coeffs(g, mu0)
+    csum = c[0] + np.roll(c[0], -1, axis=1) + c[1] + np.roll(c[1], -1, axis=0)
+    assert not ((csum > 0) & (csum < 1e-5)).any()
