@@ -400,6 +400,14 @@ WL_API int wl_window_forward_weighted(wl_sim *sim, int nsteps, int ckpt_every, c
 WL_API int wl_window_backward(wl_sim *sim, double gJ, const void *lu, const void *le, double tol, void *du0,
                               void *due0, double *dparams);
 
+/* Adjoint Poisson solves of the last wl_window_backward (two per step):
+ * counts[0] solves, counts[1] solves that stopped above tol (the sweep goes on
+ * with them: their steps' share of the gradient is then less accurate),
+ * counts[2] the largest V-cycle count, counts[3] the window step (0-based) of
+ * the largest final relative residual, *max_rel that residual. Either
+ * pointer may be NULL. */
+WL_API int wl_window_stats(wl_sim *sim, int *counts, double *max_rel);
+
 /* Replace the body's parameters (same kind; e.g. new heave / pitch amplitudes)
  * and re-measure it at the time it was last measured. Drops a held window. */
 WL_API int wl_set_body(wl_sim *sim, const wl_body *body);

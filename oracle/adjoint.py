@@ -38,11 +38,25 @@ def _with(body, name, value):
 
 def dfields_dparam(g, body, t, name, h=1e-6):
     """Central difference of the measured face fields (mu0, mu1n, V) at time t
-    with respect to the body parameter `name` (e.g. heave_amp, pitch_amp)."""
+    with respect to the body parameter `name` (e.g. heave_amp, pitch_amp).
+    The measure cuts mu0 below 1e-5 to 0 (a solid face), so mu0 is a step
+    function there: its derivative is 0 on a face cut at the parameter value
+    itself and mu0'(d) elsewhere. A face within h of the cut on one side only
+    takes the one-sided difference from the side that is not cut, so that no
+    step of the cut enters the derivative."""
     v = getattr(body, name)
     fp = _fields(g, _with(body, name, v + h), t)
     fm = _fields(g, _with(body, name, v - h), t)
-    return [(a - b) / (2 * h) for a, b in zip(fp, fm)]
+    out = [(a - b) / (2 * h) for a, b in zip(fp, fm)]
+    f0 = _fields(g, body, t)
+    m0, mp, mm = f0[0], fp[0], fm[0]
+    d = out[0]
+    d[m0 == 0.0] = 0.0
+    up = (m0 > 0.0) & (mm == 0.0) & (mp > 0.0)
+    dn = (m0 > 0.0) & (mp == 0.0) & (mm > 0.0)
+    d[up] = (mp[up] - m0[up]) / h
+    d[dn] = (m0[dn] - mm[dn]) / h
+    return out
 
 
 def dforce_dparam(g, body, t, P, name, h=1e-6):

@@ -492,21 +492,32 @@ __global__ void __launch_bounds__(256) k_pcg_u(LevelD<T> L, const T *dcur, T *ph
 // formed from the pairs, sets the row's residual to rounding and changes a
 // neighbour's residual by c_f dp, at most |r|. Cells of one colour ((i + j + k)
 // parity) read only the other colour, so an update is race-free and the
-// result does not depend on the thread order. Level 0, non-uniform tiles only
-// (a uniform tile has no weak rows).
+// result does not depend on the thread order. Level 0, over the listed
+// non-uniform tiles only (a uniform tile has no weak rows).
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(256) k_weak_rows(LevelD<T> L, const T *__restrict__ b, const T *__restrict__ bl,
-                                                   T *ph, T *pl, const DevScalars *S, double cut, int colour) {
+                                                   T *ph, T *pl, const DevScalars *S, double cut, int colour,
+                                                   const int *tlist, const unsigned *tcount) {
     const double bm = S->bmean;
-    for_cells<NDIM>(L.g, L.tl, L.tflag, [&](int i, int j, int k, long long idx, bool uni) {
-        if (uni || ((i + j + k) & 1) != colour || L.invD[idx] == T(0)) return;
+    const GridD &g = L.g;
+    // work items: (listed non-uniform tile, plane of the tile), a 32 x 8 block each
+    const int nb = (int)*tcount * MT<NDIM>::TZ;
+    for (int q = blockIdx.x; q < nb; q += gridDim.x) {
+        const int t = tlist[q / MT<NDIM>::TZ];
+        const int bx = t % L.tl.ntx, rr = t / L.tl.ntx;
+        const int by = rr % L.tl.nty, bz = rr / L.tl.nty;
+        const int i = bx * 32 + threadIdx.x, j = by * 8 + threadIdx.y;
+        const int k = bz * MT<NDIM>::TZ + q % MT<NDIM>::TZ;
+        if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) continue;
+        const long long idx = (long long)i + (long long)g.n[0] * ((long long)j + (long long)g.n[1] * k);
+        if (((i + j + k) & 1) != colour || L.invD[idx] == T(0)) continue;
         long long ip[3], im[3];
         T cp[3], cm[3];
         nb_setup<T, NDIM>(L, false, i, j, k, idx, ip, im, cp, cm);
         double csum = 0.0;
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) csum += (double)cp[a] + (double)cm[a];
-        if (!(csum > 0.0 && csum < cut)) return;
+        if (!(csum > 0.0 && csum < cut)) continue;
         const double p0 = (double)ph[idx] + (double)pl[idx];
         double Ap = 0.0;
 #pragma unroll
@@ -519,7 +530,7 @@ __global__ void __launch_bounds__(256) k_weak_rows(LevelD<T> L, const T *__restr
         const T h = (T)pn;
         ph[idx] = h;
         pl[idx] = (T)(pn - (double)h);
-    });
+    }
 }
 
 // Single-level case: the coarse solve itself is the fine correction.

@@ -300,6 +300,9 @@ int wl_tguess_fit(wl_sim *s, double *w, double *ratio) {
 int wl_tguess_weights(wl_sim *s, const double *in, double *out) {
     return guard(s, [&] { s->impl->tguess_weights(in, out); return (int)WL_OK; });
 }
+int wl_window_stats(wl_sim *s, int *counts, double *max_rel) {
+    return guard(s, [&] { s->impl->window_stats(counts, max_rel); return (int)WL_OK; });
+}
 int wl_set_body(wl_sim *s, const wl_body *body) {
     return guard(s, [&] { s->impl->set_body(body); return (int)WL_OK; });
 }

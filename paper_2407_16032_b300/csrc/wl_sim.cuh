@@ -161,6 +161,10 @@ struct Sim : SimBase {
     struct Snap { T *u[3]; T *ue; T *ph; T *pl; double t; };
     struct Window {
         bool active = false;
+        // adjoint solves of the last backward sweep: count, not converged,
+        // largest V-cycle count, largest final relative residual, its step
+        int solves = 0, unconverged = 0, max_vc = 0, worst_step = -1;
+        double max_rel = 0.0;
         int n = 0, k = 0;
         double w[3] = {0, 0, 0};
         std::vector<double> dts, t0s, ws;   // steps, start times, per-step weights
@@ -534,7 +538,8 @@ struct Sim : SimBase {
             launches += 3;
         }
         if (cdense && (moving || user)) coarse_dense_device();
-        if (band_blend()) {
+        // the level-0 tiles of the body (the band blend, the weak-row sweeps)
+        if (has_body) {
             if (!tlist) {
                 tlist = alloc_n<int>(lv[0].tl.nt);
                 tcount = alloc_n<unsigned>(1);
@@ -807,7 +812,8 @@ struct Sim : SimBase {
         P0("weak_rows", 0, g.nc);
         for (int sweep = 0; sweep < 3; ++sweep)
             for (int colour = 0; colour < 2; ++colour)
-                k_weak_rows<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], b, bl, ph, pl, S, 0.5 * (double)lv[0].cu, colour);
+                k_weak_rows<T, ND><<<nsm * 4, tblk(), 0, st>>>(lv[0], b, bl, ph, pl, S, 0.5 * (double)lv[0].cu, colour,
+                                                                tlist, tcount);
         P1();
         WL_LAUNCH_CK();
         launches += 6;
@@ -1884,6 +1890,9 @@ struct Sim : SimBase {
             else WL_CK(cudaMemsetAsync(ad.le, 0, pb, st));
         }
         WL_CK(cudaMemsetAsync(ad.dpar, 0, 2 * sizeof(double), st));
+        win.solves = win.unconverged = win.max_vc = 0;
+        win.worst_step = -1;
+        win.max_rel = 0.0;
         const bool tgu = tg.use, gqu = gq.use;
         tg.use = gq.use = false;
         struct Restore { bool &a, &b; bool va, vb; ~Restore() { a = va; b = vb; } } rs{tg.use, gq.use, tgu, gqu};
@@ -1947,7 +1956,14 @@ struct Sim : SimBase {
                     WL_LAUNCH_CK();
                     launches += g.ndim + (g.exit_x ? 1 : 0);
                 }
-                const int r = vjp_core(s.t, dt, fn, tol, params, fn ? wF : nullptr, nullptr);
+                wl_solve_stats ss[2] = {};
+                const int r = vjp_core(s.t, dt, fn, tol, params, fn ? wF : nullptr, ss);
+                for (const wl_solve_stats &q : ss) {
+                    ++win.solves;
+                    if (q.rel_resid > tol) ++win.unconverged;
+                    win.max_vc = std::max(win.max_vc, q.vcycles);
+                    if (q.rel_resid > win.max_rel) { win.max_rel = q.rel_resid; win.worst_step = n; }
+                }
                 if (r == WL_ERR_NONFINITE) rc = r;
                 for (int a = 0; a < 3; ++a) std::swap(ad.lu[a], ad.ub[a]);
                 std::swap(ad.le, ad.ueb);
@@ -1966,6 +1982,11 @@ struct Sim : SimBase {
         WL_CK(cudaStreamSynchronize(st));
         prof.flush();
         return rc;
+    }
+
+    void window_stats(int *out4, double *max_rel) override {
+        if (out4) { out4[0] = win.solves; out4[1] = win.unconverged; out4[2] = win.max_vc; out4[3] = win.worst_step; }
+        if (max_rel) *max_rel = win.max_rel;
     }
 
     void set_body(const wl_body *bd) override {

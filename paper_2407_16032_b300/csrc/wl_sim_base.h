@@ -64,6 +64,7 @@ struct SimBase {
     virtual int window_backward(double gJ, const void *lu, const void *le, double tol, void *du0, void *due0,
                                 double *dparams) = 0;
     virtual void set_body(const wl_body *bd) = 0;
+    virtual void window_stats(int *out4, double *max_rel) = 0;
     virtual void set_body_fields(const void *d, const void *n, const void *V, const void *dc, const void *ncen) = 0;
     virtual void set_body_velocity_tangent(const void *dV) = 0;
     virtual void tguess_mode(int collect, int use) = 0;

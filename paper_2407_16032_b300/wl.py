@@ -29,7 +29,7 @@ EXPORTS = (
     "wl_guess_mode", "wl_guess_train", "wl_guess_weights", "wl_guess_info", "wl_net_eval", "wl_step_vjp",
     "wl_force_dp", "wl_window_forward", "wl_window_backward", "wl_set_body", "wl_tguess_mode", "wl_tguess_fit",
     "wl_tguess_weights", "wl_last_error", "wl_status_string", "wl_set_body_fields", "wl_set_body_velocity_tangent",
-    "wl_window_forward_weighted",
+    "wl_window_forward_weighted", "wl_window_stats",
 )
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t)
@@ -112,6 +112,7 @@ def lib() -> C.CDLL:
             "wl_set_body_fields": ([vp, vp, vp, vp, vp, vp], ip),
             "wl_set_body_velocity_tangent": ([vp, vp], ip),
             "wl_window_forward_weighted": ([vp, ip, ip, vp, vp, vp, ip, dp, vp], ip),
+            "wl_window_stats": ([vp, vp, dp], ip),
             "wl_tguess_mode": ([vp, ip, ip], ip),
             "wl_tguess_fit": ([vp, vp, vp], ip),
             "wl_tguess_weights": ([vp, vp, vp], ip),
@@ -440,6 +441,14 @@ class Sim:
         """wl_set_body_velocity_tangent (None clears it)."""
         x = None if dV_face is None else self._field(dV_face, self.ndim, "dV_face")
         self._check(lib().wl_set_body_velocity_tangent(self._h, _ptr(x)), "wl_set_body_velocity_tangent")
+
+    def window_stats(self):
+        """wl_window_stats: adjoint solves of the last backward sweep as a dict."""
+        c = np.zeros(4, dtype=np.int32)
+        r = C.c_double()
+        self._check(lib().wl_window_stats(self._h, _ptr(c), C.byref(r)), "wl_window_stats")
+        return {"solves": int(c[0]), "unconverged": int(c[1]), "max_vcycles": int(c[2]), "worst_step": int(c[3]),
+                "max_rel_resid": r.value}
 
     def set_body(self, body):
         """wl_set_body with a body description (kind unchanged)."""
