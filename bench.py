@@ -43,6 +43,8 @@ def workload(name):
         "tgv64": lambda: synth.config2_tgv(64),
         "sphere": lambda: synth.config3_sphere(),
         "msphere": lambda: synth.config5_moving_sphere(),
+        # the same flow at 3/4 scale (384 x 192 x 192): the size ncu captures use
+        "msphere384": lambda: synth.scaled(synth.config5_moving_sphere(), 0.75),
         "circle": lambda: synth.config1_circle(),
         "ellipse": lambda: synth.config4_ellipse(),
         "cylinder64": lambda: synth.cylinder_benchmark(64),
