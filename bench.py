@@ -322,6 +322,11 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.gpus != world:
+        # --gpus N is run as N processes (torchrun); a single process is one GPU
+        print(f"bench.py: --gpus {args.gpus} but {world} process(es) (WORLD_SIZE); launch one process per GPU "
+              f"with torch.distributed.run --nproc-per-node {args.gpus}", file=sys.stderr)
+        return 2
     if args.impl == "reference":
         return run_reference(args, rank, world)
 

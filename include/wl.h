@@ -400,6 +400,22 @@ WL_API int wl_window_forward_weighted(wl_sim *sim, int nsteps, int ckpt_every, c
 WL_API int wl_window_backward(wl_sim *sim, double gJ, const void *lu, const void *le, double tol, void *du0,
                               void *due0, double *dparams);
 
+/* Checkpoint and resume. wl_state_size gives the bytes of the sim's state;
+ * wl_get_state writes it to buf (host or device, at least that many bytes):
+ * a header (format version, ndim, n, precision, body kind), the time, the
+ * next CFL time step and the time the body was last measured, then the
+ * velocity (ndim arrays), the exit plane and the pressure pair (high and low
+ * parts, the warm start of the next solve), in cfg.precision. wl_set_state
+ * loads it into a sim created with the same configuration and body: a body
+ * is measured again at its saved time, so the steps that follow equal, bit
+ * for bit, those of the sim the state was taken from. Not included: a held
+ * window, the learned guesses' fitted state (resume with them off, or fit
+ * them again). Errors: WL_ERR_ARG (NULL buffer, too small, a state of another
+ * grid, precision or body kind), WL_ERR_CUDA. */
+WL_API int wl_state_size(wl_sim *sim, size_t *bytes);
+WL_API int wl_get_state(wl_sim *sim, void *buf, size_t bytes);
+WL_API int wl_set_state(wl_sim *sim, const void *buf, size_t bytes);
+
 /* Adjoint Poisson solves of the last wl_window_backward (two per step):
  * counts[0] solves, counts[1] solves that stopped above tol (the sweep goes on
  * with them: their steps' share of the gradient is then less accurate),

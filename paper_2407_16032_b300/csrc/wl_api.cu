@@ -300,6 +300,18 @@ int wl_tguess_fit(wl_sim *s, double *w, double *ratio) {
 int wl_tguess_weights(wl_sim *s, const double *in, double *out) {
     return guard(s, [&] { s->impl->tguess_weights(in, out); return (int)WL_OK; });
 }
+int wl_state_size(wl_sim *s, size_t *bytes) {
+    if (!bytes) return WL_ERR_ARG;
+    return guard(s, [&] { s->impl->state_size(bytes); return (int)WL_OK; });
+}
+int wl_get_state(wl_sim *s, void *buf, size_t bytes) {
+    if (!buf) return WL_ERR_ARG;
+    return guard(s, [&] { s->impl->get_state(buf, bytes); return (int)WL_OK; });
+}
+int wl_set_state(wl_sim *s, const void *buf, size_t bytes) {
+    if (!buf) return WL_ERR_ARG;
+    return guard(s, [&] { s->impl->set_state(buf, bytes); return (int)WL_OK; });
+}
 int wl_window_stats(wl_sim *s, int *counts, double *max_rel) {
     return guard(s, [&] { s->impl->window_stats(counts, max_rel); return (int)WL_OK; });
 }

@@ -1984,6 +1984,68 @@ struct Sim : SimBase {
         return rc;
     }
 
+    // ------------------------------------------------- checkpoint / resume
+    struct StateHeader {
+        char magic[8];
+        int version, ndim, n[3], precision, body_kind, pad;
+        double t, dt_next, body_t;
+    };
+    size_t state_bytes() const {
+        return sizeof(StateHeader) + ((size_t)ND * g.nc + (size_t)np + 2 * (size_t)g.nc) * sizeof(T);
+    }
+    void state_size(size_t *bytes) override { *bytes = state_bytes(); }
+
+    void get_state(void *buf, size_t bytes) override {
+        if (bytes < state_bytes()) throw Err{WL_ERR_ARG, "get_state: buffer smaller than wl_state_size"};
+        StateHeader h{};
+        std::memcpy(h.magic, "WLSTATE", 8);
+        h.version = 1;
+        h.ndim = ND;
+        for (int a = 0; a < 3; ++a) h.n[a] = g.n[a];
+        h.precision = cfg.precision;
+        h.body_kind = body.kind;
+        h.t = t;
+        h.dt_next = dt_next;
+        h.body_t = body_t;
+        char *o = (char *)buf;
+        WL_CK(cudaMemcpyAsync(o, &h, sizeof(h), cudaMemcpyDefault, st));
+        size_t off = sizeof(h);
+        const size_t vb = g.nc * sizeof(T);
+        for (int a = 0; a < ND; ++a, off += vb) WL_CK(cudaMemcpyAsync(o + off, vel[cur][a], vb, cudaMemcpyDefault, st));
+        WL_CK(cudaMemcpyAsync(o + off, ueA, (size_t)np * sizeof(T), cudaMemcpyDefault, st));
+        off += (size_t)np * sizeof(T);
+        WL_CK(cudaMemcpyAsync(o + off, ph, vb, cudaMemcpyDefault, st));
+        WL_CK(cudaMemcpyAsync(o + off + vb, pl, vb, cudaMemcpyDefault, st));
+        WL_CK(cudaStreamSynchronize(st));
+    }
+
+    void set_state(const void *buf, size_t bytes) override {
+        if (bytes < state_bytes()) throw Err{WL_ERR_ARG, "set_state: buffer smaller than wl_state_size"};
+        StateHeader h{};
+        WL_CK(cudaMemcpy(&h, buf, sizeof(h), cudaMemcpyDefault));
+        bool same = std::memcmp(h.magic, "WLSTATE", 8) == 0 && h.version == 1 && h.ndim == ND &&
+                    h.precision == cfg.precision && h.body_kind == body.kind;
+        for (int a = 0; a < 3; ++a) same = same && h.n[a] == g.n[a];
+        if (!same) throw Err{WL_ERR_ARG, "set_state: the state was taken from a sim of another grid, precision or body kind"};
+        const char *o = (const char *)buf;
+        size_t off = sizeof(h);
+        const size_t vb = g.nc * sizeof(T);
+        for (int a = 0; a < ND; ++a, off += vb) WL_CK(cudaMemcpyAsync(vel[cur][a], o + off, vb, cudaMemcpyDefault, st));
+        WL_CK(cudaMemcpyAsync(ueA, o + off, (size_t)np * sizeof(T), cudaMemcpyDefault, st));
+        off += (size_t)np * sizeof(T);
+        WL_CK(cudaMemcpyAsync(ph, o + off, vb, cudaMemcpyDefault, st));
+        WL_CK(cudaMemcpyAsync(pl, o + off + vb, vb, cudaMemcpyDefault, st));
+        t = h.t;
+        dt_next = h.dt_next;
+        win.active = false;
+        // a measured body at the time it stood for: the coefficients of a full
+        // measure equal those a run of box measures left (outside a box only
+        // the body velocity, which no kernel reads there, may differ)
+        if (has_body && !user && h.body_t >= 0) measure_body(h.body_t, false);
+        else body_t = h.body_t;
+        WL_CK(cudaStreamSynchronize(st));
+    }
+
     void window_stats(int *out4, double *max_rel) override {
         if (out4) { out4[0] = win.solves; out4[1] = win.unconverged; out4[2] = win.max_vc; out4[3] = win.worst_step; }
         if (max_rel) *max_rel = win.max_rel;

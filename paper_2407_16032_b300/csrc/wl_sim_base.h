@@ -65,6 +65,9 @@ struct SimBase {
                                 double *dparams) = 0;
     virtual void set_body(const wl_body *bd) = 0;
     virtual void window_stats(int *out4, double *max_rel) = 0;
+    virtual void state_size(size_t *bytes) = 0;
+    virtual void get_state(void *buf, size_t bytes) = 0;
+    virtual void set_state(const void *buf, size_t bytes) = 0;
     virtual void set_body_fields(const void *d, const void *n, const void *V, const void *dc, const void *ncen) = 0;
     virtual void set_body_velocity_tangent(const void *dV) = 0;
     virtual void tguess_mode(int collect, int use) = 0;

@@ -29,7 +29,7 @@ EXPORTS = (
     "wl_guess_mode", "wl_guess_train", "wl_guess_weights", "wl_guess_info", "wl_net_eval", "wl_step_vjp",
     "wl_force_dp", "wl_window_forward", "wl_window_backward", "wl_set_body", "wl_tguess_mode", "wl_tguess_fit",
     "wl_tguess_weights", "wl_last_error", "wl_status_string", "wl_set_body_fields", "wl_set_body_velocity_tangent",
-    "wl_window_forward_weighted", "wl_window_stats",
+    "wl_window_forward_weighted", "wl_window_stats", "wl_state_size", "wl_get_state", "wl_set_state",
 )
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t)
@@ -113,6 +113,9 @@ def lib() -> C.CDLL:
             "wl_set_body_velocity_tangent": ([vp, vp], ip),
             "wl_window_forward_weighted": ([vp, ip, ip, vp, vp, vp, ip, dp, vp], ip),
             "wl_window_stats": ([vp, vp, dp], ip),
+            "wl_state_size": ([vp, C.POINTER(C.c_size_t)], ip),
+            "wl_get_state": ([vp, vp, C.c_size_t], ip),
+            "wl_set_state": ([vp, vp, C.c_size_t], ip),
             "wl_tguess_mode": ([vp, ip, ip], ip),
             "wl_tguess_fit": ([vp, vp, vp], ip),
             "wl_tguess_weights": ([vp, vp, vp], ip),
@@ -441,6 +444,23 @@ class Sim:
         """wl_set_body_velocity_tangent (None clears it)."""
         x = None if dV_face is None else self._field(dV_face, self.ndim, "dV_face")
         self._check(lib().wl_set_body_velocity_tangent(self._h, _ptr(x)), "wl_set_body_velocity_tangent")
+
+    def get_state(self):
+        """wl_get_state into a host byte array (numpy uint8)."""
+        n = C.c_size_t()
+        self._check(lib().wl_state_size(self._h, C.byref(n)), "wl_state_size")
+        buf = np.zeros(n.value, dtype=np.uint8)
+        self._check(lib().wl_get_state(self._h, _ptr(buf), n.value), "wl_get_state")
+        return buf
+
+    def set_state(self, buf):
+        """wl_set_state from a byte array (numpy uint8 or a torch uint8 tensor)."""
+        if isinstance(buf, np.ndarray):
+            buf = np.ascontiguousarray(buf, dtype=np.uint8)
+            size = buf.nbytes
+        else:
+            size = buf.numel() * buf.element_size()
+        self._check(lib().wl_set_state(self._h, _ptr(buf), size), "wl_set_state")
 
     def window_stats(self):
         """wl_window_stats: adjoint solves of the last backward sweep as a dict."""

@@ -64,3 +64,15 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
     args = argparse.Namespace(gpus=2, steps=1, warmup=0, workload="tgv256", precision=None)
     assert bench.run_reference(args, rank=1, world=2) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_gpus_must_match_the_process_count():
+    # --gpus N is N processes under torchrun; one process asked for two GPUs
+    # refuses (exit 2) before it touches a GPU or the oracle
+    import subprocess
+    import sys
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--gpus", "2", "--impl", "reference"], cwd=root, env=env,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 2 and "WORLD_SIZE" in r.stderr, (r.returncode, r.stderr[-300:])

@@ -5,8 +5,9 @@ whose device memory is all held by its own pool or budget, or a time-critical
 loop that must not call cudaMalloc because it can synchronise the device) use
 this entry point; its working memory is a fixed device array inside the
 library. This test calls it through the C ABI and checks its
-output against the library's regular solve (wl_poisson_solve) on the same
-problem, twice in a row (the shared array keeps the previous call's contents).
+output against the FP64 oracle's solve and against the library's regular
+solve (wl_poisson_solve) on the same problem, twice in a row (the shared array
+keeps the previous call's contents).
 It lives in its own file so that it runs after every other test.
 """
 import ctypes as C
@@ -48,9 +49,11 @@ def test_static_solve_matches_regular_solve_on_two_calls(prec, body):
     dt = torch.float32 if prec == "f32" else torch.float64
     cs = [c[a].contiguous() for a in range(2)]
     cnp = c.double().cpu().numpy()
+    g = oracle.grid_from_case(case)
+    c_or = oracle.coeffs(g, oracle.measure(g, oracle.make_body(body), 0.0)[0] if body.kind != "none" else None)
     for seed in (3, 4):  # two calls in a row on the shared array
         # divergence only where the cell is mostly fluid, as in a projection
-        b = synth.random_scalar(seed, 2, case.n) * well_determined(cnp, 2)
+        b = synth.random_scalar(seed, 2, case.n) * well_determined(c_or, 2)
         p_ref = np.zeros(b.shape)
         sim.poisson_solve(torch.tensor(b, dtype=dt).cuda(), p_ref)
         x = torch.full(b.shape, float("nan"), dtype=dt, device="cuda")
@@ -59,6 +62,8 @@ def test_static_solve_matches_regular_solve_on_two_calls(prec, body):
         xs = x.double().cpu().numpy()
         tol = 2e-6 if prec == "f32" else 1e-10
         assert p_err(xs, p_ref, cnp, 2) < tol
+        p_or, rc_or, _ = oracle.poisson_solve(g, c_or, b, tol=1e-12, itmax=100)
+        assert rc_or == 0 and p_err(xs, p_or, c_or, 2) < tol
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
@@ -74,6 +79,8 @@ def test_static_solve_on_the_1024_thread_path_matches_regular_solve(prec):
     dt = torch.float32 if prec == "f32" else torch.float64
     cs = [c[a].contiguous() for a in range(2)]
     cnp = c.double().cpu().numpy()
+    g = oracle.grid_from_case(case)
+    c_or = oracle.coeffs(g, None)
     for seed in (5, 6):
         b = synth.random_scalar(seed, 2, case.n)
         p_ref = np.zeros(b.shape)
@@ -83,7 +90,10 @@ def test_static_solve_on_the_1024_thread_path_matches_regular_solve(prec):
                                          maxit=20000)
         assert rc == wl.WL_OK and rel <= 1e-12, (rc, rel)
         tol = 2e-6 if prec == "f32" else 1e-10
-        assert p_err(x.double().cpu().numpy(), p_ref, cnp, 2) < tol
+        xs = x.double().cpu().numpy()
+        assert p_err(xs, p_ref, cnp, 2) < tol
+        p_or, rc_or, _ = oracle.poisson_solve(g, c_or, b, tol=1e-12, itmax=100)
+        assert rc_or == 0 and p_err(xs, p_or, c_or, 2) < tol
 
 
 def test_static_solve_rejects_oversized_grids():
