@@ -23,6 +23,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <nvtx3/nvToolsExt.h>
 #include <algorithm>
 #include <map>
 #include <random>
@@ -76,6 +77,15 @@ struct Prof {
         for (auto &r : pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
         for (auto e : pool) cudaEventDestroy(e);
     }
+};
+
+// A named NVTX range for the current scope (the step's phases on a profiler's
+// timeline; without a tool attached the calls cost a few nanoseconds).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
 };
 
 template <typename T, int ND>
@@ -482,6 +492,7 @@ struct Sim : SimBase {
     // per-step update of a moving body; the body velocity outside that box is
     // then left at its previous value (the step reads it only inside).
     void measure_body(double tt, bool partial) {
+        Range rng("wl.measure");
         CellBox b0{};
         const bool box = partial && has_body && body_t >= 0 && body_box(body_t, tt, b0);
         if (!box)
@@ -773,6 +784,7 @@ struct Sim : SimBase {
 
     // b is in place; solve A (ph+pl) = b - mean with warm start; fills stats.
     int solve(wl_solve_stats *sts) {
+        Range rng("wl.solve");
         P0("resid", 0, g.nc);
         resid_launch(st);
         P1();
@@ -790,6 +802,7 @@ struct Sim : SimBase {
                 WL_LAUNCH_CK();
                 launches += nodes;
             } else {
+                Range vr("wl.vcycle");
                 WL_CK(cudaGraphLaunch(vexec, st));
                 launches += vnodes;
             }
@@ -823,6 +836,7 @@ struct Sim : SimBase {
     void clear_status() { WL_CK(cudaMemsetAsync(&S->status, 0, sizeof(int), st)); }
 
     int project_buf(int q, const T *ue, double w, double dt, wl_solve_stats *sts, int stage = -1) {
+        Range rng("wl.project");
         clear_status();
         P0("div", 0, g.nc);
         k_div<T, ND><<<tgrid(0), tblk(), 0, st>>>(lv[0], cv(q), ue, (T)(1.0 / (w * dt)), b, bl, S, part);
@@ -1051,6 +1065,7 @@ struct Sim : SimBase {
     }
 
     int mom_step(double dt_fixed, wl_step_stats *sts) override {
+        Range rng("wl.step");
         const double dt = dt_fixed > 0 ? dt_fixed : dt_next;
         if (!(dt > cfg.dt_min)) throw Err{WL_ERR_UNSTABLE, "time step below dt_min"};
         if (moving) measure_body(t + dt, true);
@@ -1060,6 +1075,7 @@ struct Sim : SimBase {
         int rc0, rc1;
         int ustar, unew;
         const bool band = band_blend();
+        nvtxRangePushA("wl.predictor");
         if (!has_body) {
             flux<FM_PRED_U>(fargs(A0, ueB, -1, B1, dt));
             ustar = B1;
@@ -1074,7 +1090,9 @@ struct Sim : SimBase {
         }
         exit_stage(false, A0, dt);
         rc0 = project_buf(ustar, ueA, 1.0, dt, &s0, 0);
+        nvtxRangePop();
         if (rc0 == WL_ERR_NONFINITE) return fail_restore(rc0, "non-finite values in the predictor projection");
+        nvtxRangePushA("wl.corrector");
         if (!has_body) {
             flux<FM_CORR_U>(fargs(ustar, ueA, A0, C2, dt));
             unew = C2;
@@ -1089,6 +1107,7 @@ struct Sim : SimBase {
         }
         exit_stage(true, ustar, dt);
         rc1 = project_buf(unew, ueA, 0.5, dt, &s1, 1);
+        nvtxRangePop();
         if (rc1 == WL_ERR_NONFINITE) return fail_restore(rc1, "non-finite values in the corrector projection");
         // CFL for the next step
         P0("cfl", 0, g.nc);
@@ -1624,6 +1643,7 @@ struct Sim : SimBase {
     // the step (and of wF . F of its pressure, wF may be null) is added into
     // ad.dpar. Leaves the velocity slots, exit planes and ph / pl changed.
     int vjp_core(double t0, double dt, bool haveP, double tol, bool params, const double *wF, wl_solve_stats *sts) {
+        Range rng("wl.step_vjp");
         const size_t pb = (size_t)np * sizeof(T);
         const double t1 = t0 + dt;
         const double tol0 = cfg.tol;
