@@ -110,13 +110,13 @@ __device__ __forceinline__ void body_eval(const BodyState &B, int ndim, const T 
 
 // Measure every stored face: c_a = mu0 (0 on lower faces of non-periodic axes),
 // mu1n[a*3+b] = mu1 n_b, V[a] = body velocity component a.
-// On the cells of box b only.
+// On the cells of box b only, one (tile, plane) item per block.
 template <typename T, int NDIM>
 __global__ void __launch_bounds__(256) k_measure(LevelD<T> L, BodyState B, Vec3P<T> c, T *mu1n0, long long mstride,
                                                  Vec3P<T> V, bool full, CellBox box) {
     const T eps = (T)B.eps;
     const GridD &g = L.g;
-    for_box_cells<NDIM>(g, box, [&](int i, int j, int k, long long idx) {
+    for_box_planes<NDIM>(g, box, [&](int i, int j, int k, long long idx) {
         const int I[3] = {i, j, k};
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) {

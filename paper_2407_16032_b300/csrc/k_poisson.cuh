@@ -99,6 +99,25 @@ __device__ __forceinline__ void for_box_cells(const GridD &g, const CellBox &b, 
     }
 }
 
+// The cells of box b as (tile, plane) work items, one 32 x 8 block each (a
+// block per plane rather than per column: 8 times the blocks of
+// for_box_cells, for work that is heavy per cell and a box that holds few
+// tiles).
+template <int NDIM, typename F>
+__device__ __forceinline__ void for_box_planes(const GridD &g, const CellBox &b, F &&f) {
+    constexpr int TZ = MT<NDIM>::TZ;
+    const int t0x = b.lo[0] / 32, t0y = b.lo[1] / 8, t0z = b.lo[2] / TZ;
+    const int nx = (b.hi[0] + 31) / 32 - t0x, ny = (b.hi[1] + 7) / 8 - t0y, nz = (b.hi[2] + TZ - 1) / TZ - t0z;
+    for (int q = blockIdx.x; q < nx * ny * nz * TZ; q += gridDim.x) {
+        const int tq = q / TZ, kk = q % TZ;
+        const int bx = t0x + tq % nx, rr = tq / nx;
+        const int by = t0y + rr % ny, bz = t0z + rr / ny;
+        const int i = bx * 32 + threadIdx.x, j = by * 8 + threadIdx.y, k = bz * TZ + kk;
+        if (i < b.lo[0] || i >= b.hi[0] || j < b.lo[1] || j >= b.hi[1] || k < b.lo[2] || k >= b.hi[2]) continue;
+        f(i, j, k, (long long)i + (long long)g.n[0] * ((long long)j + (long long)g.n[1] * k));
+    }
+}
+
 // Walk the tiles of a level: body(x0, y0, z0, uniform) for each tile.
 template <int NDIM, typename F>
 __device__ __forceinline__ void for_tiles(const Tiles &tl, const unsigned char *tflag, F &&body) {
@@ -483,22 +502,12 @@ __global__ void __launch_bounds__(256) k_pcg_u(LevelD<T> L, const T *dcur, T *ph
     pcg_u_run<T, LAST, FINE>(L, dcur, ph, pl, S, part, lev);
 }
 
-// Weakly coupled rows after a solve. A row whose face coefficients sum to
-// less than `cut` has its pressure fixed by the solve only to r / sum c, and r
-// is bounded by the global residual norm, not by the row's own size; where the
-// BDIM kernel weight is not zero such a row still enters the pressure force.
-// A Gauss-Seidel update in double, p += r / A_II (A_II = -sum c) with
-// r = (b - mean) - A p
-// formed from the pairs, sets the row's residual to rounding and changes a
-// neighbour's residual by c_f dp, at most |r|. Cells of one colour ((i + j + k)
-// parity) read only the other colour, so an update is race-free and the
-// result does not depend on the thread order. Level 0, over the listed
-// non-uniform tiles only (a uniform tile has no weak rows).
+// The weak rows themselves: the active level-0 cells of the listed tiles whose
+// face coefficients sum to less than cut, appended to wlist (in no
+// particular order; each row's update below is independent of the order).
 template <typename T, int NDIM>
-__global__ void __launch_bounds__(256) k_weak_rows(LevelD<T> L, const T *__restrict__ b, const T *__restrict__ bl,
-                                                   T *ph, T *pl, const DevScalars *S, double cut, int colour,
-                                                   const int *tlist, const unsigned *tcount) {
-    const double bm = S->bmean;
+__global__ void __launch_bounds__(256) k_weak_list(LevelD<T> L, double cut, const int *tlist, const unsigned *tcount,
+                                                   int *wlist, unsigned *wcount) {
     const GridD &g = L.g;
     // work items: (listed non-uniform tile, plane of the tile), a 32 x 8 block each
     const int nb = (int)*tcount * MT<NDIM>::TZ;
@@ -510,14 +519,45 @@ __global__ void __launch_bounds__(256) k_weak_rows(LevelD<T> L, const T *__restr
         const int k = bz * MT<NDIM>::TZ + q % MT<NDIM>::TZ;
         if (i >= g.n[0] || j >= g.n[1] || k >= g.n[2]) continue;
         const long long idx = (long long)i + (long long)g.n[0] * ((long long)j + (long long)g.n[1] * k);
-        if (((i + j + k) & 1) != colour || L.invD[idx] == T(0)) continue;
+        if (L.invD[idx] == T(0)) continue;
         long long ip[3], im[3];
         T cp[3], cm[3];
         nb_setup<T, NDIM>(L, false, i, j, k, idx, ip, im, cp, cm);
         double csum = 0.0;
 #pragma unroll
         for (int a = 0; a < NDIM; ++a) csum += (double)cp[a] + (double)cm[a];
-        if (!(csum > 0.0 && csum < cut)) continue;
+        if (csum > 0.0 && csum < cut) wlist[atomicAdd(wcount, 1u)] = (int)idx;
+    }
+}
+
+// Weakly coupled rows after a solve. A row whose face coefficients sum to
+// less than `cut` has its pressure fixed by the solve only to r / sum c, and r
+// is bounded by the global residual norm, not by the row's own size; where the
+// BDIM kernel weight is not zero such a row still enters the pressure force.
+// A Gauss-Seidel update in double, p += r / A_II (A_II = -sum c) with
+// r = (b - mean) - A p formed from the pairs, sets the row's residual to
+// rounding and changes a neighbour's residual by c_f dp, at most |r|. Cells of
+// one colour ((i + j + k) parity) read only the other colour, so an update is
+// race-free and the result does not depend on the thread order. Level 0, over
+// the rows k_weak_list collected.
+template <typename T, int NDIM>
+__global__ void __launch_bounds__(256) k_weak_rows(LevelD<T> L, const T *__restrict__ b, const T *__restrict__ bl,
+                                                   T *ph, T *pl, const DevScalars *S, int colour, const int *wlist,
+                                                   const unsigned *wcount) {
+    const double bm = S->bmean;
+    const GridD &g = L.g;
+    const int nw = (int)*wcount;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nw; e += gridDim.x * blockDim.x) {
+        const long long idx = wlist[e];
+        int i, j, k;
+        decode(g, idx, i, j, k);
+        if (((i + j + k) & 1) != colour) continue;
+        long long ip[3], im[3];
+        T cp[3], cm[3];
+        nb_setup<T, NDIM>(L, false, i, j, k, idx, ip, im, cp, cm);
+        double csum = 0.0;
+#pragma unroll
+        for (int a = 0; a < NDIM; ++a) csum += (double)cp[a] + (double)cm[a];
         const double p0 = (double)ph[idx] + (double)pl[idx];
         double Ap = 0.0;
 #pragma unroll

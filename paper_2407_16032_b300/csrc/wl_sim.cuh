@@ -114,6 +114,8 @@ struct Sim : SimBase {
     double *cMw = nullptr;  // scratch of its device build (moving bodies)
     int *tlist = nullptr;   // level-0 tiles flagged non-uniform (band blend)
     unsigned *tcount = nullptr;
+    int *wlist = nullptr;   // weakly coupled level-0 rows (k_weak_list)
+    unsigned *wcount = nullptr;
     double *pout = nullptr; // reported pressure scratch
     DevScalars *S = nullptr, *hS = nullptr;
     double *part = nullptr;
@@ -508,7 +510,8 @@ struct Sim : SimBase {
         Vec3P<T> c{}, V{};
         for (int a = 0; a < 3; ++a) { c.p[a] = lc[0][a]; V.p[a] = Vb[a]; }
         P0("measure", 0, bcells);
-        k_measure<T, ND><<<bgrid(b0, 0), tblk(), 0, st>>>(lv[0], B, c, mu1n, (long long)g.nc, V, has_body, b0);
+        const int mgrid = (int)std::min<long long>((long long)bgrid(b0, 0) * MT<ND>::TZ, (long long)maxb);
+        k_measure<T, ND><<<mgrid, tblk(), 0, st>>>(lv[0], B, c, mu1n, (long long)g.nc, V, has_body, b0);
         P1();
         WL_LAUNCH_CK();
         ++launches;
@@ -558,7 +561,14 @@ struct Sim : SimBase {
             WL_CK(cudaMemsetAsync(tcount, 0, sizeof(unsigned), st));
             k_tile_list<<<blocks(lv[0].tl.nt), 256, 0, st>>>(tfl[0], lv[0].tl.nt, tlist, tcount);
             WL_LAUNCH_CK();
-            ++launches;
+            if (!wlist) {
+                wlist = alloc_n<int>(g.nc);
+                wcount = alloc_n<unsigned>(1);
+            }
+            WL_CK(cudaMemsetAsync(wcount, 0, sizeof(unsigned), st));
+            k_weak_list<T, ND><<<nsm * 4, tblk(), 0, st>>>(lv[0], weak_cut(), tlist, tcount, wlist, wcount);
+            WL_LAUNCH_CK();
+            launches += 2;
         }
     }
 
@@ -820,13 +830,13 @@ struct Sim : SimBase {
     // Gauss-Seidel sweeps over the weakly coupled rows of level 0 (faces
     // summing to less than half a face) after a solve (k_weak_rows): three
     // red-black sweeps; only a body makes such rows.
+    double weak_cut() const { return 0.5 * (double)lv[0].cu; }
     void weak_rows() {
         if (!has_body) return;
         P0("weak_rows", 0, g.nc);
         for (int sweep = 0; sweep < 3; ++sweep)
             for (int colour = 0; colour < 2; ++colour)
-                k_weak_rows<T, ND><<<nsm * 4, tblk(), 0, st>>>(lv[0], b, bl, ph, pl, S, 0.5 * (double)lv[0].cu, colour,
-                                                                tlist, tcount);
+                k_weak_rows<T, ND><<<nsm, 256, 0, st>>>(lv[0], b, bl, ph, pl, S, colour, wlist, wcount);
         P1();
         WL_LAUNCH_CK();
         launches += 6;
