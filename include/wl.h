@@ -429,6 +429,24 @@ WL_API int wl_window_stats(wl_sim *sim, int *counts, double *max_rel);
  * and re-measure it at the time it was last measured. Drops a held window. */
 WL_API int wl_set_body(wl_sim *sim, const wl_body *body);
 
+/* How the coarsest level of the multigrid V-cycle (Sec. 2, geometric
+ * multigrid; Sec. 4.2, the pressure solver) is solved. A coarsest level of at
+ * most max_cells cells is solved by a dense FP64 solution operator (the
+ * inverse of the level's operator bordered by the mean constraint, built on
+ * the device by one PCG solve per column, again after every measure of a
+ * moving or sampled body) and a matrix-vector product; a larger one by
+ * Jacobi-PCG in FP64 on one thread block, to 1e-12 relative. Both give the
+ * level's exact mean-free solution up to rounding. The hierarchy halves every
+ * axis while all are even and all halves are at least 4, so a grid such as
+ * 9L x 6L x 2L keeps a coarsest level of 864 cells, where the one-block PCG
+ * can take most of a step; max_cells = 1024 moves it onto the dense
+ * operator (n^2 doubles of device memory, 8 MiB at most; its build costs about
+ * n one-block solves, once per measure of a moving body).
+ *   max_cells: 0 .. 1024 (256 when a sim is created; 0 = always PCG).
+ * Drops a held window. Errors: WL_ERR_ARG (out of range, NULL sim),
+ * WL_ERR_CUDA. */
+WL_API int wl_set_coarse_dense_max(wl_sim *sim, int max_cells);
+
 /* Largest grid (cells) wl_coarse_solve_static accepts: its working memory is
  * a fixed device array of 5 * WL_STATIC_MAX_CELLS + 8 doubles (~640 KiB) that
  * every GPU loading this library holds until the process exits. */

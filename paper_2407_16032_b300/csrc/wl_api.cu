@@ -318,6 +318,9 @@ int wl_window_stats(wl_sim *s, int *counts, double *max_rel) {
 int wl_set_body(wl_sim *s, const wl_body *body) {
     return guard(s, [&] { s->impl->set_body(body); return (int)WL_OK; });
 }
+int wl_set_coarse_dense_max(wl_sim *s, int max_cells) {
+    return guard(s, [&] { s->impl->set_coarse_dense_max(max_cells); return (int)WL_OK; });
+}
 int wl_set_body_fields(wl_sim *s, const void *d_face, const void *n_face, const void *V_face, const void *d_cell,
                        const void *n_cell) {
     if (!d_face || !n_face || !V_face || !d_cell || !n_cell) return WL_ERR_ARG;

@@ -111,6 +111,7 @@ struct Sim : SimBase {
     double *cw = nullptr;   // coarsest scratch
     double *cM = nullptr;   // dense solution operator of the coarsest level
     bool cdense = false;
+    int dense_max = 256;    // largest coarsest level (cells) solved by cM
     double *cMw = nullptr;  // scratch of its device build (moving bodies)
     int *tlist = nullptr;   // level-0 tiles flagged non-uniform (band blend)
     unsigned *tcount = nullptr;
@@ -321,7 +322,7 @@ struct Sim : SimBase {
         // the coarsest level (at most 256 cells) is solved by a dense solution
         // operator: built on the host once for fixed coefficients, on the
         // device after every measure of a moving body
-        cdense = gl[nlev - 1].nc <= 256 && coarse_dense();
+        cdense = gl[nlev - 1].nc <= dense_max && coarse_dense();
         build_vcycle_graph();
         WL_CK(cudaStreamSynchronize(st));
     }
@@ -428,8 +429,11 @@ struct Sim : SimBase {
 
     // The coarsest level's dense solution operator for the current
     // coefficients: on the device where they change during a run (a moving or
-    // sampled body), else on the host.
-    bool coarse_dense() { return (moving || user) ? coarse_dense_device() : coarse_dense_build(); }
+    // sampled body) or where the level has more than 256 cells, else on the
+    // host.
+    bool coarse_dense() {
+        return (moving || user || gl[nlev - 1].nc > 256) ? coarse_dense_device() : coarse_dense_build();
+    }
 
     // A body given by samples (Sec. 3: distance function and map evaluated by
     // the caller): face distances d, face normals n (component b of face a at
@@ -600,8 +604,13 @@ struct Sim : SimBase {
         int maxit = (int)(2 * ncl + 200);
         if (maxit > 2000) maxit = 2000;
         B("coarsest", L);
-        if (cdense) k_coarsest_dense<T><<<1, 256, 0, s>>>(lv[L], cM);
-        else k_coarsest<T><<<1, ncl >= 512 ? 512 : 256, 0, s>>>(lv[L], cw, maxit);
+        if (cdense && ncl <= 256) k_coarsest_dense<T><<<1, 256, 0, s>>>(lv[L], cM);
+        else if (cdense) {
+            k_coarsest_dense_rows<T><<<(int)((ncl + 7) / 8), 256, 0, s>>>(lv[L], cM, cw);
+            E();
+            B("coarsest_fin", L);
+            k_coarsest_dense_fin<T><<<1, 256, 0, s>>>(lv[L], cw);
+        } else k_coarsest<T><<<1, ncl >= 512 ? 512 : 256, 0, s>>>(lv[L], cw, maxit);
         E();
         for (int l = nlev - 2; l >= 0; --l) {
             B("pcg_init", l);
@@ -764,8 +773,9 @@ struct Sim : SimBase {
     bool coarse_dense_device() {
         const int L = nlev - 1;
         const long long n = gl[L].nc;
-        if (n > 256) return false;
-        if (!cM) cM = alloc_n<double>((size_t)256 * 256);
+        if (n > dense_max || n > WL_DENSE_MAX) return false;
+        const size_t nm = (size_t)std::max(n, 256LL);
+        if (!cM) cM = alloc_n<double>(nm * nm);
         if (!cMw) cMw = alloc_n<double>((size_t)4 * n * n);
         int maxit = (int)(2 * n + 200);
         P0("coarse_operator", L, n);
@@ -2088,9 +2098,22 @@ struct Sim : SimBase {
         win.active = false;
         if (has_body) body_update(body_t >= 0 ? body_t : t);
         // the coarsest level's dense operator follows the new coefficients
-        const bool want = gl[nlev - 1].nc <= 256;
+        const bool want = gl[nlev - 1].nc <= dense_max;
         const bool was = cdense;
         cdense = want && coarse_dense();
+        if (cdense != was) build_vcycle_graph();
+        WL_CK(cudaStreamSynchronize(st));
+    }
+
+    // Largest coarsest level (cells) that the dense solution operator solves
+    // (0 to WL_DENSE_MAX; 256 at creation); a larger one is solved by the
+    // one-block PCG. Ends an open adjoint window (its solves would change).
+    void set_coarse_dense_max(int m) override {
+        if (m < 0 || m > WL_DENSE_MAX) throw Err{WL_ERR_ARG, "set_coarse_dense_max: max_cells must lie in [0, 1024]"};
+        dense_max = m;
+        win.active = false;
+        const bool was = cdense;
+        cdense = gl[nlev - 1].nc <= dense_max && coarse_dense();
         if (cdense != was) build_vcycle_graph();
         WL_CK(cudaStreamSynchronize(st));
     }

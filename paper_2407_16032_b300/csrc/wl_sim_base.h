@@ -64,6 +64,7 @@ struct SimBase {
     virtual int window_backward(double gJ, const void *lu, const void *le, double tol, void *du0, void *due0,
                                 double *dparams) = 0;
     virtual void set_body(const wl_body *bd) = 0;
+    virtual void set_coarse_dense_max(int max_cells) = 0;
     virtual void window_stats(int *out4, double *max_rel) = 0;
     virtual void state_size(size_t *bytes) = 0;
     virtual void get_state(void *buf, size_t bytes) = 0;

@@ -30,6 +30,7 @@ EXPORTS = (
     "wl_force_dp", "wl_window_forward", "wl_window_backward", "wl_set_body", "wl_tguess_mode", "wl_tguess_fit",
     "wl_tguess_weights", "wl_last_error", "wl_status_string", "wl_set_body_fields", "wl_set_body_velocity_tangent",
     "wl_window_forward_weighted", "wl_window_stats", "wl_state_size", "wl_get_state", "wl_set_state",
+    "wl_set_coarse_dense_max",
 )
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t)
@@ -109,6 +110,7 @@ def lib() -> C.CDLL:
             "wl_window_forward": ([vp, ip, ip, vp, vp, dp, vp], ip),
             "wl_window_backward": ([vp, C.c_double, vp, vp, C.c_double, vp, vp, vp], ip),
             "wl_set_body": ([vp, C.POINTER(Body)], ip),
+            "wl_set_coarse_dense_max": ([vp, ip], ip),
             "wl_set_body_fields": ([vp, vp, vp, vp, vp, vp], ip),
             "wl_set_body_velocity_tangent": ([vp, vp], ip),
             "wl_window_forward_weighted": ([vp, ip, ip, vp, vp, vp, ip, dp, vp], ip),
@@ -474,6 +476,11 @@ class Sim:
         """wl_set_body with a body description (kind unchanged)."""
         self._check(lib().wl_set_body(self._h, C.byref(_body_struct(body))), "wl_set_body")
         self.body = body
+
+    def set_coarse_dense_max(self, max_cells):
+        """wl_set_coarse_dense_max: coarsest levels of at most max_cells cells
+        (0..1024; 256 at creation) are solved by the dense FP64 operator."""
+        self._check(lib().wl_set_coarse_dense_max(self._h, int(max_cells)), "wl_set_coarse_dense_max")
 
     # ------------------------------------------------ learned temporal guess
     def tguess_mode(self, collect=False, use=False):

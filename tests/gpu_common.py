@@ -19,14 +19,18 @@ def start_fields(case, precision):
     return u, ue
 
 
-def run_pair(case, steps, precision="f32", dt=None, gpu_tol=5e-9, oracle_tol=1e-11, smooth_iters=4, on_step=None):
+def run_pair(case, steps, precision="f32", dt=None, gpu_tol=5e-9, oracle_tol=1e-11, smooth_iters=4, on_step=None,
+             setup=None):
     """Advance the oracle and the GPU path `steps` steps with the oracle's
     time steps; returns (oracle Sim, gpu Sim, per-step GPU stats). on_step(k,
-    orc, sim), if given, runs after step k (1-based) of both."""
+    orc, sim), if given, runs after step k (1-based) of both; setup(sim), if
+    given, runs on the new GPU sim before its first step."""
     import torch
     u, ue = start_fields(case, precision)
     orc = oracle.Sim(case, tol=oracle_tol, u=u, ue=ue)
     sim = gpu_sim(case, precision, tol=gpu_tol, itmax=60, smooth_iters=smooth_iters)
+    if setup:
+        setup(sim)
     tdt = torch.float32 if precision == "f32" else torch.float64
     sim.set_velocity(torch.tensor(orc.u, dtype=tdt).cuda(), torch.tensor(orc.ue, dtype=tdt).cuda())
     stats = []

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 # named launches that are not fine-grid streaming passes of the forward step:
 # latency-bound or plane-sized work, the learned guess and the adjoint
-NOT_STREAMING = {"coarsest", "weak_rows", "coarse_operator", "blend_band", "band_copy", "padd", "exit", "tguess_apply", "guess_net", "guess_apply", "force_dparam", "flux_raw"}
+NOT_STREAMING = {"coarsest", "coarsest_fin", "weak_rows", "coarse_operator", "blend_band", "band_copy", "padd", "exit", "tguess_apply", "guess_net", "guess_apply", "force_dparam", "flux_raw"}
 
 
 def _named_launches():

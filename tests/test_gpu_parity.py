@@ -91,6 +91,10 @@ def test_poisson_solve_matches_oracle(prec, nd, shape, per, body):
         # FP32-only layout case: its cut cells with coefficients near 1e-7 make
         # the FP64 face fluxes agree only to ~2e-9 of their maximum
         pytest.skip("the plane-marching kernels this case covers are FP32 only")
+    _poisson_case(prec, nd, shape, per, body)
+
+
+def _poisson_case(prec, nd, shape, per, body, dense_max=None):
     case = synth.Case("p", nd, shape, per, False, (0, 0, 0), 0.0, body or synth.Body())
     g = oracle.grid_from_case(case)
     mu0 = oracle.measure(g, oracle.make_body(case.body), 0.0)[0] if body else None
@@ -101,12 +105,32 @@ def test_poisson_solve_matches_oracle(prec, nd, shape, per, body):
     p_or, rc, st = oracle.poisson_solve(g, c, b, tol=1e-12, itmax=100)
     assert rc == 0
     sim = gpu_sim(case, prec, tol=5e-9 if prec == "f32" else 1e-12, itmax=60)
+    if dense_max is not None:
+        sim.set_coarse_dense_max(dense_max)
+        sim.profile(True)
     p = np.zeros(b.shape)
     res, rcg = sim.poisson_solve(_t(b, prec), p)
     assert res.rel_resid <= (5e-9 if prec == "f32" else 1e-12), res
     tol = 2e-6 if prec == "f32" else 1e-10
     assert p_err(p, p_or, c, nd) < tol, (p_err(p, p_or, c, nd), res)
     assert flux_err(p, p_or, c, nd) < tol
+    return sim
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("nd,shape,per,body", [
+    (3, (48, 32, 24), (False, False, False), synth.Body("sphere", (16.2, 15.1, 12.3), 5.5)),   # coarsest 12x8x6
+    (2, (70, 36, 1), (False, True, False), None),                                              # coarsest 35x18
+])
+def test_poisson_solve_with_the_dense_coarsest_above_256_cells(prec, nd, shape, per, body):
+    # coarsest levels of 576 and 630 cells moved from the one-block PCG onto
+    # the dense FP64 operator (built on the device, applied by many blocks):
+    # the same bars as the PCG path, and the dense kernels are the ones run
+    sim = _poisson_case(prec, nd, shape, per, body, dense_max=1024)
+    names = {r[0] for r in sim.profile_report()}
+    assert "coarsest_fin" in names, names
+    with pytest.raises(RuntimeError):
+        sim.set_coarse_dense_max(1025)
 
 
 # ----------------------------------------------------------- whole steps ---
@@ -225,6 +249,22 @@ def test_moving_cylinder_benchmark_reduced_fp32_1_and_10_steps():
     orc, sim, st = run_pair(case, 10, "f32")
     tu, tp = calibrated_bars(case, orc)
     _compare(orc, sim, tu, tp, name=case.name + " reduced")
+    F_or = oracle.forces(orc.g, orc.b, orc.t, orc.P)
+    F = sim.forces()
+    assert np.abs(F - F_or).max() < tp * max(np.abs(F_or).max(), 1.0)
+
+
+def test_moving_cylinder_with_the_dense_coarsest_fp32_1_and_10_steps():
+    # the same flow with its 864-cell coarsest level (18 x 12 x 4, kept by the
+    # 9L x 6L x 2L shape) on the dense operator, rebuilt on the device after
+    # every measure of the moving body; the bars of the PCG path
+    case = synth.cylinder_benchmark(8)
+    dense = lambda s: s.set_coarse_dense_max(1024)
+    orc, sim, st = run_pair(case, 1, "f32", setup=dense)
+    _compare(orc, sim, 1e-6, 1e-6)
+    orc, sim, st = run_pair(case, 10, "f32", setup=dense)
+    tu, tp = calibrated_bars(case, orc)
+    _compare(orc, sim, tu, tp, name=case.name + " reduced, dense coarsest")
     F_or = oracle.forces(orc.g, orc.b, orc.t, orc.P)
     F = sim.forces()
     assert np.abs(F - F_or).max() < tp * max(np.abs(F_or).max(), 1.0)
