@@ -13,6 +13,7 @@
 #include "k_flux.cuh"
 #include "k_body.cuh"
 #include "k_poisson.cuh"
+#include "k_coarse_dense.cuh"
 #include "k_mg_march.cuh"
 #include "k_resid.cuh"
 #include "k_march4.cuh"
