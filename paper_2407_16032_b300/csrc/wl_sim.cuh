@@ -894,12 +894,7 @@ struct Sim : SimBase {
         P1();
         WL_LAUNCH_CK();
         ++launches;
-        // the first residual is of the guess
-        P0("resid", 0, g.nc);
-        resid_launch(st);
-        P1();
-        WL_LAUNCH_CK();
-        ++launches;
+        // the solve that follows forms the guess's residual first
     }
     // after a converged projection of stage sg: gather the fit's normal
     // equations (collecting) and push the solution into the stage's history
