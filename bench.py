@@ -467,7 +467,7 @@ def main():
                    "temporal": {"net": "1x1x1 conv over (H1, H1 - H2, Ho - H1) per projection stage",
                                 "weights": {"predictor": tw[0].tolist(), "corrector": tw[1].tolist()},
                                 "fit_residual_ratio": tratio.tolist(), "projections_fitted": 30},
-                   "cnn": {"net": "bias-free ReLU 3D CNN 1-16-16-1, 3^3 kernels, BF16 mma.sync, on MG level 2",
+                   "cnn": {"net": "bias-free ReLU 3D CNN 1-16-16-1, 3^3 kernels, BF16 tcgen05 convolutions (weight gradient on mma.sync), on MG level 2",
                            "train": {"samples": 32, "adam_steps": 300, "batch": 4, "loss_first": loss0,
                                      "loss_last": loss1, "seconds": t_train}}}
 

@@ -282,8 +282,10 @@ WL_API int wl_profile_report(wl_sim *sim, char *buf, size_t len, size_t *needed)
  * the pressure by injection before the V-cycles; the V-cycles then converge to
  * the same tolerance (the guess only changes where they start, never when
  * they stop).
- * Convolutions run on BF16 tensor cores (mma.sync) with FP32 accumulation;
- * weights are kept in FP32 (Adam) and copied to BF16.
+ * Convolutions run on BF16 tensor cores with FP32 accumulation (tcgen05 MMAs
+ * into tensor memory for the forward and data-gradient convolutions, mma.sync
+ * for the weight gradient); weights are kept in FP32 (Adam) and copied to BF16.
+ * A tensor-core wait that times out ends the call with WL_ERR_CUDA.
  *   wl_guess_setup: allocate the network and room for `capacity` samples.
  *   wl_guess_mode: collect != 0 records (restricted residual, coarse mean of
  *     the converged-minus-initial pressure) of every converged projection;

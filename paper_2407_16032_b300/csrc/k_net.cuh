@@ -1,6 +1,8 @@
 // k_net.cuh -- the learned Poisson initial guess: a small 3D convolutional
-// network on a coarse multigrid level, with BF16 tensor-core convolutions
-// (mma.sync m16n8k16, FP32 accumulation), its backward pass and Adam.
+// network on a coarse multigrid level, with BF16 tensor-core convolutions and
+// FP32 accumulation (the forward and data-gradient convolutions on tcgen05,
+// k_net_tc.cuh; the weight gradient here, mma.sync m16n8k16), its backward
+// pass and Adam.
 //
 // No counterpart in the paper (the paper cites data-driven multigrid, Sec. 3,
 // as the precedent of learned solver components). Network:
@@ -44,59 +46,6 @@ __device__ __forceinline__ int tap_nb(const NetGrid &g, int x, int y, int z, int
     const int X = x + dx, Y = y + dy, Z = z + dz;
     if (X < 0 || X >= g.nx || Y < 0 || Y >= g.ny || Z < 0 || Z >= g.nz) return -1;
     return X + g.nx * (Y + g.ny * Z);
-}
-
-// Y = conv(X, W) (FP32 pre-activation) and optionally A = relu(Y) in BF16.
-// Wt: [27][16 out][16 in] BF16. Each warp computes 16 voxels x 16 channels as
-// two m16n8 tiles, K = 16 input channels per tap, 27 taps.
-static __global__ void __launch_bounds__(128) k_conv_fwd(NetGrid g, const __nv_bfloat16 *__restrict__ X,
-                                                  const __nv_bfloat16 *__restrict__ Wt, float *__restrict__ Y,
-                                                  __nv_bfloat16 *__restrict__ A) {
-    __shared__ uint32_t sW[NET_TAPS * NET_C * NET_C / 2];
-    const uint32_t *W32 = reinterpret_cast<const uint32_t *>(Wt);
-    for (int e = threadIdx.x; e < NET_TAPS * NET_C * NET_C / 2; e += blockDim.x) sW[e] = W32[e];
-    __syncthreads();
-    const uint32_t *X32 = reinterpret_cast<const uint32_t *>(X);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gid = lane >> 2, tig = lane & 3;
-    const int nchunk = (g.V + 15) / 16;
-    for (int ch = blockIdx.x * 4 + warp; ch < nchunk; ch += gridDim.x * 4) {
-        const int r0 = ch * 16 + gid, r1 = r0 + 8;
-        const bool v0ok = r0 < g.V, v1ok = r1 < g.V;
-        const int q0 = v0ok ? r0 : 0, q1 = v1ok ? r1 : 0;
-        const int x0 = q0 % g.nx, y0 = (q0 / g.nx) % g.ny, z0 = q0 / (g.nx * g.ny);
-        const int x1 = q1 % g.nx, y1 = (q1 / g.nx) % g.ny, z1 = q1 / (g.nx * g.ny);
-        float d[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-        for (int t = 0; t < NET_TAPS; ++t) {
-            const int nb0 = v0ok ? tap_nb(g, x0, y0, z0, t) : -1;
-            const int nb1 = v1ok ? tap_nb(g, x1, y1, z1, t) : -1;
-            uint32_t a[4];
-            a[0] = nb0 >= 0 ? X32[nb0 * 8 + tig] : 0u;
-            a[1] = nb1 >= 0 ? X32[nb1 * 8 + tig] : 0u;
-            a[2] = nb0 >= 0 ? X32[nb0 * 8 + tig + 4] : 0u;
-            a[3] = nb1 >= 0 ? X32[nb1 * 8 + tig + 4] : 0u;
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-                const int row = (t * NET_C + nt * 8 + gid) * 8;
-                const uint32_t b[2] = {sW[row + tig], sW[row + tig + 4]};
-                mma_bf16(d[nt], a, b);
-            }
-        }
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-            const int c = nt * 8 + tig * 2;
-            if (v0ok) {
-                Y[r0 * NET_C + c] = d[nt][0];
-                Y[r0 * NET_C + c + 1] = d[nt][1];
-                if (A) reinterpret_cast<uint32_t *>(A)[r0 * 8 + (c >> 1)] = pack_bf16(fmaxf(d[nt][0], 0.f), fmaxf(d[nt][1], 0.f));
-            }
-            if (v1ok) {
-                Y[r1 * NET_C + c] = d[nt][2];
-                Y[r1 * NET_C + c + 1] = d[nt][3];
-                if (A) reinterpret_cast<uint32_t *>(A)[r1 * 8 + (c >> 1)] = pack_bf16(fmaxf(d[nt][2], 0.f), fmaxf(d[nt][3], 0.f));
-            }
-        }
-    }
 }
 
 // dW[t][i][o] += sum_v X[v + tap t][i] dZ[v][o] (FP32 atomics). One tap per

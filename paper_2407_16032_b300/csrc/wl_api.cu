@@ -5,6 +5,7 @@
 #include "wl_sim_base.h"
 #include "wl_common.cuh"
 #include "k_net.cuh"
+#include "k_net_tc.cuh"
 
 #include <cstdio>
 #include <cstring>
@@ -234,6 +235,7 @@ int wl_net_eval(int ndim, const int *n, const float *w, const float *x, const fl
     __nv_bfloat16 *A0 = (__nv_bfloat16 *)dal(V * NET_C * 2), *A1 = (__nv_bfloat16 *)dal(V * NET_C * 2);
     __nv_bfloat16 *A2 = (__nv_bfloat16 *)dal(V * NET_C * 2), *dY = (__nv_bfloat16 *)dal(V * NET_C * 2);
     double *dl = (double *)dal(2 * sizeof(double));
+    int *es = (int *)dal(sizeof(int));   // bit 2: a tensor-core wait timed out
     int rc = ok ? WL_OK : WL_ERR_ALLOC;
     if (rc == WL_OK) {
         cudaMemcpy(W, w, 3 * NET_WL * 4, cudaMemcpyDefault);
@@ -241,28 +243,30 @@ int wl_net_eval(int ndim, const int *n, const float *w, const float *x, const fl
         if (t) cudaMemcpy(ft, t, V * 4, cudaMemcpyDefault);
         cudaMemset(G, 0, 3 * NET_WL * 4);
         cudaMemset(dl, 0, 2 * sizeof(double));
+        cudaMemset(es, 0, sizeof(int));
         const int eb = (int)((V + 255) / 256), vb = (int)((V * NET_C + 255) / 256);
-        const int nb = (int)((V + 63) / 64), cb = nb < 2048 ? nb : 2048;
         const int wb = (int)((V + 1023) / 1024);
         const dim3 dwg(wb < 1 ? 1 : (wb > 512 ? 512 : wb), NET_TAPS);
         k_net_weights<<<(3 * NET_WL + 255) / 256, 256>>>(W, Wf, Wb);
         k_net_input<<<eb, 256>>>(ng.V, fx, A0);
-        k_conv_fwd<<<cb, 128>>>(ng, A0, Wf, Z1, A1);
-        k_conv_fwd<<<cb, 128>>>(ng, A1, Wf + NET_WL, Z2, A2);
-        k_conv_fwd<<<cb, 128>>>(ng, A2, Wf + 2 * NET_WL, Y, nullptr);
+        conv_fwd_tc(0, ng, A0, Wf, Z1, A1, es);
+        conv_fwd_tc(0, ng, A1, Wf + NET_WL, Z2, A2, es);
+        conv_fwd_tc(0, ng, A2, Wf + 2 * NET_WL, Y, nullptr, es);
         k_channel0<<<eb, 256>>>(ng.V, Y, yo);
         if (t) {
             k_sumsq<<<eb, 256>>>(ng.V, ft, dl + 1);
             k_net_loss<<<eb, 256>>>(ng.V, Y, ft, dl + 1, dY, dl);
             k_conv_dw<<<dwg, 128>>>(ng, A2, dY, G + 2 * NET_WL);
-            k_conv_fwd<<<cb, 128>>>(ng, dY, Wb + 2 * NET_WL, Y, nullptr);
+            conv_fwd_tc(0, ng, dY, Wb + 2 * NET_WL, Y, nullptr, es);
             k_relu_bwd<<<vb, 256>>>(ng.V * NET_C, Y, Z2, A2);
             k_conv_dw<<<dwg, 128>>>(ng, A1, A2, G + NET_WL);
-            k_conv_fwd<<<cb, 128>>>(ng, A2, Wb + NET_WL, Y, nullptr);
+            conv_fwd_tc(0, ng, A2, Wb + NET_WL, Y, nullptr, es);
             k_relu_bwd<<<vb, 256>>>(ng.V * NET_C, Y, Z1, A1);
             k_conv_dw<<<dwg, 128>>>(ng, A0, A1, G);
         }
         if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) rc = WL_ERR_CUDA;
+        int hes = 0;
+        if (rc == WL_OK && (cudaMemcpy(&hes, es, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || hes)) rc = WL_ERR_CUDA;
         if (rc == WL_OK) {
             if (y) cudaMemcpy(y, yo, V * 4, cudaMemcpyDefault);
             if (dw && t) cudaMemcpy(dw, G, 3 * NET_WL * 4, cudaMemcpyDefault);

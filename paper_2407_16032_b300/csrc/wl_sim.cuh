@@ -20,6 +20,7 @@
 #include "k_flux4.cuh"
 #include "k_misc.cuh"
 #include "k_net.cuh"
+#include "k_net_tc.cuh"
 #include "k_adjoint.cuh"
 #include <cmath>
 #include <cstdio>
@@ -144,6 +145,7 @@ struct Sim : SimBase {
         float *fx = nullptr, *tt = nullptr;   // network input and scaled target (one sample)
         __nv_bfloat16 *Wf = nullptr, *Wb = nullptr, *A0 = nullptr, *A1 = nullptr, *A2 = nullptr, *dY = nullptr;
         double *loss = nullptr;
+        int *tcst = nullptr;                  // bit 2: a tensor-core wait timed out during training
         T *ph0 = nullptr, *pl0 = nullptr;
     } gq;
     // adjoint of one step: forward copies, cotangents, and a backup of the state
@@ -830,6 +832,8 @@ struct Sim : SimBase {
             read_scalars();
             ++it;
         }
+        // status bit 2: the learned guess's tensor-core convolution gave up on a wait
+        if (hS->status & 4) throw Err{WL_ERR_CUDA, "learned guess: a tensor-core convolution's wait timed out"};
         if (!(hS->status & 1)) weak_rows();
         if (sts) { sts->vcycles = it; sts->rel_resid = hS->rel; sts->bnorm = hS->bnorm; sts->rel_initial = rel0; }
         if (collecting && !(hS->status & 1) && hS->rel <= cfg.tol) guess_end();
@@ -1327,6 +1331,7 @@ struct Sim : SimBase {
         gq.A2 = alloc_n<__nv_bfloat16>(V * NET_C);
         gq.dY = alloc_n<__nv_bfloat16>(V * NET_C);
         gq.loss = alloc_n<double>(1);
+        gq.tcst = alloc_n<int>(1);
         WL_CK(cudaStreamSynchronize(st));
     }
 
@@ -1365,13 +1370,12 @@ struct Sim : SimBase {
     }
 
     // network forward on fx (FP32 input) -> Y (channel 0 = output)
-    void net_forward(const float *x) {
+    void net_forward(const float *x, int *status) {
         const NetGrid &ng = gq.ng;
-        const int nb = (ng.V + 63) / 64, cb = nb < 2048 ? nb : 2048;
         k_net_input<<<blocks(ng.V), 256, 0, st>>>(ng.V, x, gq.A0);
-        k_conv_fwd<<<cb, 128, 0, st>>>(ng, gq.A0, gq.Wf, gq.Z1, gq.A1);
-        k_conv_fwd<<<cb, 128, 0, st>>>(ng, gq.A1, gq.Wf + NET_WL, gq.Z2, gq.A2);
-        k_conv_fwd<<<cb, 128, 0, st>>>(ng, gq.A2, gq.Wf + 2 * NET_WL, gq.Y, nullptr);
+        conv_fwd_tc(st, ng, gq.A0, gq.Wf, gq.Z1, gq.A1, status);
+        conv_fwd_tc(st, ng, gq.A1, gq.Wf + NET_WL, gq.Z2, gq.A2, status);
+        conv_fwd_tc(st, ng, gq.A2, gq.Wf + 2 * NET_WL, gq.Y, nullptr, status);
         WL_LAUNCH_CK();
         launches += 4;
     }
@@ -1392,7 +1396,7 @@ struct Sim : SimBase {
             if (sizeof(T) == sizeof(float)) WL_CK(cudaMemcpyAsync(gq.fx, lv[gq.lev].r, V * sizeof(float), cudaMemcpyDeviceToDevice, st));
             else k_to_float<T><<<blocks(V), 256, 0, st>>>((long long)V, lv[gq.lev].r, gq.fx);
             P0("guess_net", gq.lev, (long long)V);
-            net_forward(gq.fx);
+            net_forward(gq.fx, &S->status);
             P1();
             P0("guess_apply", 0, g.nc);
             k_guess_apply<T><<<blocks(g.nc), 256, 0, st>>>(g, gq.shift, gq.ng, (float)gq.gain, gq.Y, ph, pl);
@@ -1467,8 +1471,8 @@ struct Sim : SimBase {
         double *tnorm = nullptr;
         tnorm = alloc_n<double>(1);
         const NetGrid &ng = gq.ng;
-        const int nbk = (ng.V + 63) / 64, cb = nbk < 2048 ? nbk : 2048;
         const int wb = (ng.V + 16 * 4 * 16 - 1) / (16 * 4 * 16);
+        WL_CK(cudaMemsetAsync(gq.tcst, 0, sizeof(int), st));
         const dim3 dwg(wb < 1 ? 1 : (wb > 512 ? 512 : wb), NET_TAPS);
         for (int itn = 0; itn < iters; ++itn) {
             WL_CK(cudaMemsetAsync(gq.G, 0, 3 * NET_WL * sizeof(float), st));
@@ -1481,15 +1485,15 @@ struct Sim : SimBase {
                 k_scale_copy<<<blocks(V), 256, 0, st>>>(ng.V, (float)(sxi / gain), gq.dt + (size_t)sm * V, tt);
                 WL_CK(cudaMemsetAsync(tnorm, 0, sizeof(double), st));
                 k_sumsq<<<blocks(V), 256, 0, st>>>(ng.V, tt, tnorm);
-                net_forward(gq.fx);
+                net_forward(gq.fx, gq.tcst);
                 k_net_loss<<<blocks(V), 256, 0, st>>>(ng.V, gq.Y, tt, tnorm, gq.dY, dtn);
                 // layer 3
                 k_conv_dw<<<dwg, 128, 0, st>>>(ng, gq.A2, gq.dY, gq.G + 2 * NET_WL);
-                k_conv_fwd<<<cb, 128, 0, st>>>(ng, gq.dY, gq.Wb + 2 * NET_WL, gq.Y, nullptr);
+                conv_fwd_tc(st, ng, gq.dY, gq.Wb + 2 * NET_WL, gq.Y, nullptr, gq.tcst);
                 k_relu_bwd<<<blocks(V * NET_C), 256, 0, st>>>((int)(V * NET_C), gq.Y, gq.Z2, gq.A2);
                 // layer 2 (A2 now holds dZ2)
                 k_conv_dw<<<dwg, 128, 0, st>>>(ng, gq.A1, gq.A2, gq.G + NET_WL);
-                k_conv_fwd<<<cb, 128, 0, st>>>(ng, gq.A2, gq.Wb + NET_WL, gq.Y, nullptr);
+                conv_fwd_tc(st, ng, gq.A2, gq.Wb + NET_WL, gq.Y, nullptr, gq.tcst);
                 k_relu_bwd<<<blocks(V * NET_C), 256, 0, st>>>((int)(V * NET_C), gq.Y, gq.Z1, gq.A1);
                 // layer 1 (A1 now holds dZ1)
                 k_conv_dw<<<dwg, 128, 0, st>>>(ng, gq.A0, gq.A1, gq.G);
@@ -1508,9 +1512,12 @@ struct Sim : SimBase {
                 if (itn == iters - 1 && l1) *l1 = hl[0] / batch;
             }
         }
+        int tcst = 0;
+        WL_CK(cudaMemcpyAsync(&tcst, gq.tcst, sizeof(int), cudaMemcpyDeviceToHost, st));
+        WL_CK(cudaStreamSynchronize(st));
+        if (tcst) throw Err{WL_ERR_CUDA, "guess_train: a tensor-core convolution's wait timed out"};
         gq.gain = gain;
         gq.ready = true;
-        WL_CK(cudaStreamSynchronize(st));
     }
 
     // ------------------------------------------------------------ adjoint
