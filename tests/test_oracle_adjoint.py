@@ -32,11 +32,16 @@ def _case(kind):
         u0 = synth.random_field(14, 3, (12, 10, 8), amp=0.4)
     elif kind == "sphere3d_exit":
         # a 3D body with an exit plane: the sphere's kernel band crosses the
-        # periodic z boundary and reaches the lower y wall, and the free stream
-        # is 1.6 so that terms scaled by the exit plane's mean velocity count
-        g = oracle.make_grid(3, (14, 10, 8), (False, False, True), True, (1.6, 0.0, 0.0), 0.02)
-        u0 = synth.random_field(15, 3, (14, 10, 8), amp=0.2, offset=(1.6, 0.0, 0.0))
-        B = synth.Body(kind="sphere", centre=(6.1, 3.3, 1.2), radius=2.4)
+        # periodic z boundary and reaches both y walls, and the free stream is
+        # 1.6 so that terms scaled by the exit plane's mean velocity count
+        g = oracle.make_grid(3, (14, 10, 12), (False, False, True), True, (1.6, 0.0, 0.0), 0.02)
+        u0 = synth.random_field(15, 3, (14, 10, 12), amp=0.2, offset=(1.6, 0.0, 0.0))
+        B = synth.Body(kind="sphere", centre=(7.0, 4.9, 1.2), radius=4.3)
+    elif kind == "walled3d_body":
+        # walls on every face and a sphere whose band reaches the lower z wall
+        g = oracle.make_grid(3, (12, 10, 8), (False, False, False), False, (0.0, 0.0, 0.0), 0.02)
+        u0 = synth.random_field(18, 3, (12, 10, 8), amp=0.3)
+        B = synth.Body(kind="sphere", centre=(6.2, 5.1, 2.3), radius=2.5)
     elif kind == "square_wave2d":
         # a square wave in x with small noise: the limiter clips many faces
         g = oracle.make_grid(2, (24, 16), (True, True), False, (0.0, 0.0), 0.01)
@@ -97,7 +102,7 @@ def test_conv_diff_vjp_matches_central_differences(kind):
 
 
 @pytest.mark.parametrize("kind", ["periodic2d", "channel_exit", "circle", "walled3d", "sphere3d_exit",
-                                  "square_wave2d"])
+                                  "walled3d_body", "square_wave2d"])
 def test_step_vjp_matches_central_differences(kind):
     g, B, u0, ue0 = _case(kind)
     dt, t = 0.3, 0.0
@@ -169,6 +174,13 @@ def _fields_case(kind):
     if kind == "circle":
         g, B, u0, ue0 = _case("circle")
         body = synth.Body(kind="sphere", centre=(10.0, 10.3, 0.0), radius=4.2)
+    elif kind == "periodic_circle":
+        # periodic in y with the circle's kernel band across the periodic seam
+        g = oracle.make_grid(2, (28, 20), (False, True), True, (1.0, 0.0), 0.01)
+        u0 = synth.random_field(19, 2, (28, 20), amp=0.2, offset=(1.0, 0.0))
+        ue0 = 1.0 + 0.1 * (2 * synth.uniform01(24, 0, 20) - 1)
+        body = synth.Body(kind="sphere", centre=(10.0, 1.1, 0.0), radius=4.2)
+        B = oracle.make_body(body)
     else:
         g = oracle.make_grid(2, (40, 28), (False, False), True, (1.0, 0.0), 0.02)
         u0 = synth.random_field(17, 2, (40, 28), amp=0.1, offset=(1.0, 0.0))
@@ -178,7 +190,7 @@ def _fields_case(kind):
     return g, B, body, u0, ue0
 
 
-@pytest.mark.parametrize("kind", ["circle", "ellipse"])
+@pytest.mark.parametrize("kind", ["circle", "ellipse", "periodic_circle"])
 def test_field_cotangents_match_central_differences(kind):
     # the step's dependence on the measured face fields (mu0 in the blend and
     # in the Poisson coefficients, mu1 n and V in the blend), checked against

@@ -137,6 +137,25 @@ def test_sampled_fields_step_equals_the_analytic_step():
     assert np.array_equal(us, ua) and np.array_equal(Ps, Pa)
 
 
+def test_viscous_force_transpose_is_its_linear_part_3d():
+    # the same identity on a sampled sphere in a 3D channel with an exit plane
+    case = synth.Case("v3", 3, (20, 14, 12), (False, False, True), True, (1.0, 0.0, 0.0), 0.02)
+    g = oracle.grid_from_case(case)
+    _, _, _, dc, nc = synth.sample_body(synth.Circle((8.3, 7.1, 5.6), 3.7), 3, case.n)
+    u = synth.random_field(7, 3, case.n, amp=0.3, offset=(1.0, 0.0, 0.0))
+    v = synth.random_field(8, 3, case.n, amp=1.0)
+    ue = 1.0 + 0.1 * synth.random_scalar(9, 2, (case.n[1], case.n[2], 1)).ravel()
+    ve = synth.random_scalar(10, 2, (case.n[1], case.n[2], 1)).ravel()
+    w = (0.7, -1.3, 0.4)
+    ub, ueb = oracle.forces_viscous_sampled_vjp(g, dc, nc, w)
+    F1 = oracle.forces_viscous_sampled(g, dc, nc, u + v, ue + ve)
+    F0 = oracle.forces_viscous_sampled(g, dc, nc, u, ue)
+    lhs = float(np.sum(ub * v) + np.dot(ueb[: ve.size], ve))
+    rhs = float(np.dot(w, (F1 - F0)[:3]))
+    assert abs(rhs) > 1e-3
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(rhs))
+
+
 def test_viscous_force_transpose_is_its_linear_part():
     # the viscous force is affine in (u, ue) (boundary constants aside), so its
     # transpose contracted with (v, ve) is w . (F(u + v, ue + ve) - F(u, ue))
