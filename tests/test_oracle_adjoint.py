@@ -181,6 +181,13 @@ def _fields_case(kind):
         ue0 = 1.0 + 0.1 * (2 * synth.uniform01(24, 0, 20) - 1)
         body = synth.Body(kind="sphere", centre=(10.0, 1.1, 0.0), radius=4.2)
         B = oracle.make_body(body)
+    elif kind == "wall_circle":
+        # the circle's kernel band reaches the upper y wall
+        g = oracle.make_grid(2, (28, 20), (False, False), True, (1.0, 0.0), 0.01)
+        u0 = synth.random_field(20, 2, (28, 20), amp=0.2, offset=(1.0, 0.0))
+        ue0 = 1.0 + 0.1 * (2 * synth.uniform01(25, 0, 20) - 1)
+        body = synth.Body(kind="sphere", centre=(10.0, 17.2, 0.0), radius=3.5)
+        B = oracle.make_body(body)
     else:
         g = oracle.make_grid(2, (40, 28), (False, False), True, (1.0, 0.0), 0.02)
         u0 = synth.random_field(17, 2, (40, 28), amp=0.1, offset=(1.0, 0.0))
@@ -190,7 +197,7 @@ def _fields_case(kind):
     return g, B, body, u0, ue0
 
 
-@pytest.mark.parametrize("kind", ["circle", "ellipse", "periodic_circle"])
+@pytest.mark.parametrize("kind", ["circle", "ellipse", "periodic_circle", "wall_circle"])
 def test_field_cotangents_match_central_differences(kind):
     # the step's dependence on the measured face fields (mu0 in the blend and
     # in the Poisson coefficients, mu1 n and V in the blend), checked against
