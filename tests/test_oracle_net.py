@@ -72,3 +72,19 @@ def test_network_is_positively_homogeneous():
     y1 = net.forward(x, Ws)[0]
     y2 = net.forward(3.7 * x, Ws)[0]
     np.testing.assert_allclose(y2, 3.7 * y1, rtol=1e-12, atol=1e-14)
+
+
+def test_backward_loss_of_an_identity_network_is_its_closed_form():
+    # centre-tap identity weights pass a positive input through both ReLUs
+    # unchanged, so y = x and the relative loss is |x - t|^2 / |t|^2 exactly:
+    # 1/4 for t = 2x, 4 for t = -x
+    x = np.abs(RNG.normal(size=(4, 5, 6))) + 0.1
+    W1, W2, W3 = np.zeros((27, 1, 3)), np.zeros((27, 3, 3)), np.zeros((27, 3, 1))
+    W1[13, 0, 0] = W2[13, 0, 0] = W3[13, 0, 0] = 1.0
+    Ws = (W1, W2, W3)
+    y, _ = net.forward(x, Ws)
+    np.testing.assert_array_equal(y, x)
+    for t, want in ((2.0 * x, 0.25), (-x, 4.0)):
+        L, _, _ = net.backward(x, Ws, t)
+        assert L == pytest.approx(want, rel=1e-14)
+        assert net.loss(y, t) == pytest.approx(want, rel=1e-14)
