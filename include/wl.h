@@ -442,8 +442,9 @@ WL_API int wl_set_body(wl_sim *sim, const wl_body *body);
  * axis while all are even and all halves are at least 4, so a grid such as
  * 9L x 6L x 2L keeps a coarsest level of 864 cells, where the one-block PCG
  * can take most of a step; max_cells = 1024 moves it onto the dense
- * operator (n^2 doubles of device memory, 8 MiB at most; its build costs about
- * n one-block solves, once per measure of a moving body).
+ * operator. It holds 5 n^2 doubles of device memory, 40 MiB at most: the
+ * operator and its build's scratch. The build costs about n one-block solves,
+ * once per measure of a moving body.
  *   max_cells: 0 .. 1024 (256 when a sim is created; 0 = always PCG).
  * Drops a held window. Errors: WL_ERR_ARG (out of range, NULL sim),
  * WL_ERR_CUDA. */
