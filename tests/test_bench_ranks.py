@@ -76,3 +76,27 @@ def test_gpus_must_match_the_process_count():
     r = subprocess.run([sys.executable, "bench.py", "--gpus", "2", "--impl", "reference"], cwd=root, env=env,
                        capture_output=True, text=True, timeout=300)
     assert r.returncode == 2 and "WORLD_SIZE" in r.stderr, (r.returncode, r.stderr[-300:])
+
+
+def test_reference_arm_prints_one_contract_line():
+    # the oracle arm on the host cores prints one JSON line with the keys the
+    # bench contract asks for, on the default workload's bounded sample
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
+                       cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 3
+    assert d["higher_is_better"] is True and d["scaling"] == "weak" and d["vs_baseline"] is None
+    assert d["dtype"] == "f64" and d["config"]["workload"].startswith("msphere3d 512x256x256")
+    # value is the sample's cell-steps over the timed seconds
+    assert d["value"] * d["ms_per_step"] / 1000.0 == pytest.approx(128 * 64 * 64, rel=1e-9)
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and "128x64x64" in cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
