@@ -412,8 +412,10 @@ WL_API int wl_window_backward(wl_sim *sim, double gJ, const void *lu, const void
  * is measured again at its saved time, so the steps that follow equal, bit
  * for bit, those of the sim the state was taken from. Not included: a held
  * window, the learned guesses' fitted state (resume with them off, or fit
- * them again), and a WL_BODY_USER_FACE_FIELDS body's samples (set the same
- * fields on the resumed sim, before or after wl_set_state). Errors: WL_ERR_ARG (NULL buffer, too small, a state of another
+ * them again), a WL_BODY_USER_FACE_FIELDS body's samples (set the same
+ * fields on the resumed sim, before or after wl_set_state), and the
+ * coarsest-level setting of wl_set_coarse_dense_max (set it on the resumed
+ * sim as on the original). Errors: WL_ERR_ARG (NULL buffer, too small, a state of another
  * grid, precision or body kind), WL_ERR_CUDA. */
 WL_API int wl_state_size(wl_sim *sim, size_t *bytes);
 WL_API int wl_get_state(wl_sim *sim, void *buf, size_t bytes);
