@@ -768,3 +768,39 @@ def test_measure_cuts_the_kernel_tail_so_no_cell_is_nearly_solid():
     c = oracle.coeffs(g, mu0)
     csum = c[0] + np.roll(c[0], -1, axis=1) + c[1] + np.roll(c[1], -1, axis=0)
     assert not ((csum > 0) & (csum < 1e-5)).any()
+
+
+def test_sim_takes_the_first_then_the_cfl_time_step():
+    # reading 10: the first step is dt0, the next min(dt_max, cfl / (max
+    # outflux + 5 nu)); a uniform stream U = 1 along x has outflux 1 per cell
+    case = synth.Case("u", 2, (32, 16), (False, False), True, (1.0, 0.0), 0.05, init="uniform+noise",
+                      noise_amp=0.0)
+    s = oracle.Sim(case, tol=1e-12)
+    assert s.dt == case.dt0 == 0.25
+    s.step()
+    assert s.dt == pytest.approx(min(case.dt_max, case.cfl / (1.0 + 5.0 * case.nu)), rel=1e-12)
+
+
+def test_sim_moves_a_body_on_its_own_clock():
+    # two steps of a heaving circle through Sim equal two explicit steps with
+    # the body measured at t = 0.2 and t = 0.5, and its clock reads 0.5
+    body = synth.Body("sphere", (12.0, 12.0, 0.0), 4.0, heave_amp=2.0, omega=0.3, heave_axis=1)
+    case = synth.Case("m", 2, (40, 24), (False, False), True, (1.0, 0.0), 0.02, body, init="noise", seed=2)
+    s = oracle.Sim(case, tol=1e-12)
+    u0, ue0, P0 = s.u.copy(), s.ue.copy(), s.P.copy()
+    s.step(0.2)
+    s.step(0.3)
+    assert s.t == pytest.approx(0.5, abs=1e-15)
+    u1, ue1, P1 = oracle.step_fn(s.g, s.b, 0.0, 0.2, u0, ue0, P0, tol=1e-12)
+    u2, _, _ = oracle.step_fn(s.g, s.b, 0.2, 0.3, u1, ue1, P1, tol=1e-12)
+    assert np.abs(s.u - u2).max() < 1e-9
+
+
+def test_sim_starts_with_the_free_stream_on_inflow_and_wall_faces():
+    # config 1: noise everywhere, then the lower normal faces of the
+    # non-periodic axes carry U (inflow u_x = 1 at x = 0, wall u_y = 0 at y = 0)
+    case = synth.config1_circle()
+    s = oracle.Sim(case)
+    u, v = s.u[0], s.u[1]                       # [y, x]
+    assert np.all(u[:, 0] == 1.0) and np.all(v[0, :] == 0.0)
+    assert np.abs(u[:, 1:] - 0.0).max() <= case.noise_amp and np.abs(u[:, 1:]).max() > 0
