@@ -40,6 +40,14 @@ CASES = [
     ("viscous_transpose_z_index", C, "su_loc(g, a, i + A[0], j + A[1], k + A[2], &kind, &at);",
      "su_loc(g, a, i + A[0], j + A[1], k - A[2], &kind, &at);",
      ["tests/test_oracle_sampled.py::test_viscous_force_transpose_is_its_linear_part_3d"]),
+    ("adjoint_blend_periodic_wrap", C, "P[ax] = ((P[ax] % N) + N) % N; M[ax]", "P[ax] = ((P[ax] % N) - N) % N; M[ax]",
+     ["tests/test_oracle_adjoint.py::test_step_vjp_matches_central_differences[sphere3d_exit]"]),
+    ("adjoint_exit_scaling", C, "ueGb[p] += -w * dt * Ubar * e;", "ueGb[p] += -w * dt / Ubar * e;",
+     ["tests/test_oracle_adjoint.py::test_step_vjp_matches_central_differences[sphere3d_exit]"]),
+    ("field_cotangent_upper_clamp", C, "else if (P[ax] > N - 1) P[ax] = N - 1;", "else if (P[ax] > N + 1) P[ax] = N - 1;",
+     ["tests/test_oracle_adjoint.py::test_field_cotangents_match_central_differences[wall_circle]"]),
+    ("stepping_clock", "oracle/__init__.py", "self.t += dt", "self.t -= dt",
+     [T + "test_sim_moves_a_body_on_its_own_clock"]),
     ("network_loss_sign", "oracle/net.py", "L = float(np.sum((y - t) ** 2) / den)",
      "L = float(np.sum((y + t) ** 2) / den)",
      ["tests/test_oracle_net.py::test_backward_loss_of_an_identity_network_is_its_closed_form"]),
