@@ -336,7 +336,7 @@ WL_API int wl_net_eval(int ndim, const int *n, const float *w, const float *x, c
                        double *loss);
 
 /* Adjoint of one time step (no counterpart in the paper, which differentiates
- * the solver in forward mode with dual numbers, Sec. 3 / Sec. 5.3): the
+ * the solver in forward mode with dual numbers, Sec. 3 / Sec. 6.1): the
  * vector-Jacobian product of wl_mom_step with the fixed step dt from the start
  * state (u0, ue0) at time t, the body measured at t + dt as the step does.
  * Given the cotangents lu (velocity), le (exit plane, may be NULL) and lP
@@ -364,7 +364,7 @@ WL_API int wl_step_vjp(wl_sim *sim, double t, double dt, const void *u0, const v
 WL_API int wl_force_dp(wl_sim *sim, int axis, double scale, double *g);
 
 /* Gradient over a window of time steps, with checkpointed recomputation (no
- * counterpart in the paper; its forward-mode dual numbers, Sec. 3 / Sec. 5.3,
+ * counterpart in the paper; its forward-mode dual numbers, Sec. 3 / Sec. 6.1,
  * are replaced by the step's hand-written adjoint, wl_step_vjp). Objective:
  *   J = sum_{n=1..nsteps} w . F_n  (+ <lu, u_N> + <le, ue_N> in the backward call)
  * with F_n the pressure force of wl_forces after step n (mean thrust of a

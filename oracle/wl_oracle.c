@@ -848,7 +848,7 @@ double orc_cfl(const orc_grid *g, const double *u, const double *ue, double cfl,
     return dt < dt_max ? dt : dt_max;
 }
 
-/* Pressure force on the body (Sec. 5 uses drag / power coefficients).
+/* Pressure force on the body (Sec. 5 reports drag, Sec. 6.1 power coefficients).
  * Reading: F = -sum_I p_I n(x_I) K_eps(d(x_I)) over cell centres (h^n = 1). */
 void orc_forces(const orc_grid *g, const orc_body *B, double t, const double *p, double *F)
 {

@@ -1,5 +1,5 @@
 """Davidon's cubic-interpolation search on an interval (the optimiser of the
-spin-rate study, Sec. 5): from the values and derivatives of a smooth function
+spin-rate study, Sec. 6.1): from the values and derivatives of a smooth function
 at the two ends of an interval that brackets an extremum, the extremum of the
 cubic that matches all four numbers is evaluated next, and the end whose
 derivative has the same sign is moved there.

@@ -1,4 +1,4 @@
-"""Spin-rate control of the flow past a circle (Sec. 5, the optimised control
+"""Spin-rate control of the flow past a circle (Sec. 6.1, the optimised control
 cylinders): a fixed circle of diameter D and a small control circle that
 spins with surface speed xi U, joined by the union of their distance
 functions and handed to the library as samples (WL_BODY_USER_FACE_FIELDS).

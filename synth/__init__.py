@@ -254,7 +254,7 @@ def scaled(case: Case, factor: float) -> Case:
 # wl_set_body_fields. The shapes below play that user: each evaluates its
 # distance d (> 0 in the fluid), unit normal grad d and body velocity at given
 # points; union and difference combine them the way the paper's body
-# arithmetic does (Sec. 5: `big + small`, a sphere minus a plane).
+# arithmetic does (Sec. 6: `big + small`, a sphere minus a plane).
 
 class SDF:
     def eval(self, x):
@@ -360,7 +360,7 @@ def sample_body(shape: SDF, ndim: int, n: tuple, dtype=np.float64):
 
 
 def spinning_cylinders(D=96, Re=500.0, d_D=0.15, g_D=0.05, xi=1.0, U=1.0):
-    """The controlled-cylinder flow of Sec. 5: a fixed circle of diameter D at
+    """The controlled-cylinder flow of Sec. 6.1: a fixed circle of diameter D at
     (2D, 0) on the symmetry plane y = 0 (a slip wall) of a 6D x 2D domain (the
     upper half of the full flow; uniform inflow U, convective exit), and a small circle of radius r = d_D D / 2 centred at
     distance D/2 + r + g_D D from it, 60 degrees above the downstream axis,

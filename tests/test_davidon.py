@@ -1,5 +1,5 @@
 """CPU checks of Davidon's cubic-interpolation search (the spin-rate study's
-optimiser, Sec. 5) on functions with known maxima."""
+optimiser, Sec. 6.1) on functions with known maxima."""
 import math
 
 import pytest

@@ -183,7 +183,7 @@ def test_set_body_fields_rejects_an_analytic_body():
 @pytest.mark.parametrize("viscous", [False, True])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_spin_rate_window_gradient_matches_the_oracle(prec, viscous):
-    # Sec. 5's controlled cylinder (coarse): J = thrust (pressure, or pressure
+    # Sec. 6.1's controlled cylinder (coarse): J = thrust (pressure, or pressure
     # plus viscous force) weighted towards the window's last steps; its gradient along the spin rate's velocity tangent
     # (wl_set_body_velocity_tangent) and along the start velocity, against the
     # FP64 oracle's discrete adjoint on the same samples (the bars of the

@@ -1,4 +1,4 @@
-"""GPU check of the spin-rate study (Sec. 5, the optimised control
+"""GPU check of the spin-rate study (Sec. 6.1, the optimised control
 cylinders): dC_P/dxi from the window adjoint along the control circle's
 velocity tangent against central differences of C_P itself, both at the same
 (fixed) time steps, on a coarse version of the flow."""

@@ -272,7 +272,7 @@ def test_window_parameter_gradient_matches_central_differences():
 
 @pytest.mark.parametrize("viscous", [False, True])
 def test_sampled_body_velocity_gradient_matches_central_differences(viscous):
-    # a spinning control cylinder beside a fixed one (Sec. 5's controlled
+    # a spinning control cylinder beside a fixed one (Sec. 6.1's controlled
     # flow, coarse): the window gradient of the final step's thrust along the
     # spin rate's velocity tangent against central differences of complete
     # forward windows with the face velocity moved by +-h dV

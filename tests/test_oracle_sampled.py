@@ -2,7 +2,7 @@
 distance function and motion, Sec. 3): they must reproduce the analytic
 bodies exactly where the samples come from the same shape, and the solid they
 describe must have the area of the shape, composite shapes included (the body
-arithmetic of Sec. 5)."""
+arithmetic of Sec. 6)."""
 import math
 
 import numpy as np
